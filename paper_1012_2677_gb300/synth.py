@@ -1,0 +1,49 @@
+"""Seeded synthetic input generators shared by the tests, the bench and the oracle runs.
+
+This module holds none of the method's arithmetic (no potential, no forces, no
+integration, no cell grid): only seeded random draws and the shapes of the
+workloads (random directions, displacements, subsets, replica parameters).
+Random numbers that the method itself needs are passed in from here as inputs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.PCG64(seed))
+
+
+def unit_vectors(n: int, seed: int) -> np.ndarray:
+    """n random directions, uniform on the sphere, float64 (n, 3)."""
+    u = rng(seed).normal(size=(n, 3))
+    return u / np.linalg.norm(u, axis=1, keepdims=True)
+
+
+def displacements(n: int, amplitude: float, seed: int) -> np.ndarray:
+    """Uniform random displacements in [-amplitude, amplitude]^3, float64 (n, 3)."""
+    return rng(seed).uniform(-amplitude, amplitude, size=(n, 3))
+
+
+def uniform_positions(n: int, L: float, seed: int) -> np.ndarray:
+    """n positions uniform in the periodic box [0, L)^3."""
+    x = rng(seed).uniform(0.0, L, size=(n, 3))
+    return np.where(x >= L, 0.0, x)
+
+
+def gaussian(shape, seed: int) -> np.ndarray:
+    return rng(seed).normal(size=shape)
+
+
+def subset(n_total: int, n_keep: int, seed: int) -> np.ndarray:
+    """Sorted random subset of range(n_total) of size n_keep (thinning a filled lattice)."""
+    return np.sort(rng(seed).choice(n_total, size=n_keep, replace=False))
+
+
+def replica_table(R: int, seed: int, n_range=(500, 50000), rho_range=(0.3, 0.9), T_range=(0.7, 1.5)):
+    """Per-replica (N, rho, T) drawn uniformly: the batched-replica workload shape."""
+    g = rng(seed)
+    N = g.integers(n_range[0], n_range[1] + 1, size=R)
+    rho = g.uniform(*rho_range, size=R)
+    T = g.uniform(*T_range, size=R)
+    return N.astype(np.int64), rho, T
