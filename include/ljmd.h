@@ -1,0 +1,202 @@
+/*
+ * ljmd.h -- C ABI of the GB300 Lennard-Jones molecular-dynamics library.
+ *
+ * The method is the one of Watanabe, Suzuki and Ito, "Efficient
+ * Implementations of Molecular Dynamics Simulations for Lennard-Jones
+ * Systems": the truncated LJ pair force (Sec. 2.1, Eq. 2) summed over a
+ * bookkeeping (Verlet) pair list with a search length r_s = r_c + margin
+ * (Sec. 2.3), built from a cell grid whose counting sort also reorders the
+ * particles for locality (Sec. 2.2, Sec. 3.3), stored as a sorted list
+ * (Sec. 2.4, KeyPointer/SortedList), and driven by a second-order symplectic
+ * (velocity-Verlet) integrator (Sec. 4.4).
+ *
+ * Conventions for every call:
+ *   - Reduced units (sigma, eps of the potential; m = 1, kB = 1).
+ *   - A periodic cubic box of side L in [0, L)^3.
+ *   - Host arrays are caller-owned, float64, particle-major: x[3*i + k].
+ *     Device arrays (on_device = 1) have the same layout and must live on the
+ *     device the handle was created on.  The library never frees caller memory.
+ *   - Particle order in and out of the library is the caller's id order; the
+ *     library keeps particles sorted by cell internally.
+ *   - Every call is asynchronous on the stream given to ljmd_create except
+ *     where it says it synchronises.
+ *   - Return value: LJ_OK (0) or a negative LJ_E* code; ljmd_strerror()
+ *     names it.  After LJ_EDEVICE the handle should be destroyed.
+ *   - The handle owns all device memory it allocates and is not thread-safe.
+ */
+#ifndef LJMD_H
+#define LJMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LJ_OK 0
+#define LJ_EINVAL (-1)   /* bad argument (N <= 0, cutoff <= 0, margin < 0, L < 2 (r_s + margin), NULL) */
+#define LJ_ENOMEM (-2)   /* device or host allocation failed */
+#define LJ_EDEVICE (-3)  /* CUDA error, or the device status word was raised (see LJ_ST_*) */
+#define LJ_ESTATE (-4)   /* call out of order (no particles yet) */
+#define LJ_ERANGE (-5)   /* size beyond a library limit (e.g. more than 2^32 - 1 list entries) */
+
+/* ---- device status word bits (ljmd_stats.status_word) ---- */
+#define LJ_ST_NONFINITE 1   /* a position, velocity or force became NaN/Inf */
+#define LJ_ST_LIST_OVERFLOW 2 /* a list fill exceeded its counted size (internal consistency check) */
+#define LJ_ST_TIMEOUT 4     /* a bounded device-side wait gave up */
+#define LJ_ST_CELL_RANGE 8  /* a particle's cell index was out of range */
+
+/* ---- precision forms ---- */
+#define LJ_FP64 0   /* FP64 pair arithmetic, FP64 state and sums */
+#define LJ_MIXED 1  /* FP32 pair arithmetic; FP64 positions, velocities and global energy/virial sums */
+
+/* ---- pair-list forms ---- */
+#define LJ_LIST_FULL 0  /* every particle lists all partners; force kernel writes without atomics */
+#define LJ_LIST_HALF 1  /* each pair once, key = lower index (Sec. 2.4); Newton-3 scatter with atomics */
+
+/* ---- truncation of the potential (Sec. 2.1) ---- */
+#define LJ_TRUNC_QUADRATIC 0  /* Eq. 2: 4 eps [c2 (r/sigma)^2 + c0] added, V(r_c) = V'(r_c) = 0 */
+#define LJ_TRUNC_SHIFT 1      /* c2 = 0, c0 from V(r_c) = 0 (force identical to Eq. 1) */
+#define LJ_TRUNC_CUT 2        /* Eq. 1 cut at r_c (c2 = c0 = 0) */
+
+typedef struct ljmd_params {
+  double eps;          /* well depth of Eq. 1 */
+  double sigma;        /* diameter of Eq. 1 */
+  double cutoff;       /* r_c (absolute length), > 0 */
+  double margin;       /* r_s - r_c (Sec. 2.3), >= 0 */
+  int32_t truncation;  /* LJ_TRUNC_* */
+  int32_t list_form;   /* LJ_LIST_FULL or LJ_LIST_HALF */
+  int32_t energy_every; /* inside ljmd_step: evaluate PE and virial every k-th step (0 = only on request) */
+  int32_t lanes;       /* threads per key particle in the force kernel: 1,2,4,8,16,32; 0 = tuned default */
+} ljmd_params;
+
+typedef struct ljmd_stats {
+  int64_t n;               /* particles */
+  int64_t steps;           /* velocity-Verlet steps taken since the state was set */
+  int64_t rebuilds;        /* pair-list constructions since the state was set */
+  int64_t list_entries;    /* entries in the current list (2x the pairs for LJ_LIST_FULL) */
+  int64_t cells_per_side;  /* n_g per axis of the cell grid (cell side >= r_s, Sec. 2.2) */
+  double box;              /* L */
+  double mean_lifetime;    /* steps / rebuilds (list lifetime, Sec. 5.2) */
+  double max_displacement; /* largest displacement since the last rebuild, at the last check */
+  int32_t status_word;     /* LJ_ST_* bits raised on the device (synchronises) */
+  int32_t precision;       /* LJ_FP64 / LJ_MIXED */
+} ljmd_stats;
+
+typedef struct ljmd_sys ljmd_sys;
+
+/*
+ * Create a system handle with potential/list parameters p and precision form
+ * (LJ_FP64 or LJ_MIXED).  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream) on the current device; all work of this handle is ordered on it.
+ * No particles exist until ljmd_init_lattice or ljmd_set_state.
+ * Errors: LJ_EINVAL (NULL out/p, cutoff <= 0, margin < 0, bad enum), LJ_EDEVICE.
+ */
+int ljmd_create(ljmd_sys** out, const ljmd_params* p, int32_t precision, void* cuda_stream);
+
+/* Free every device and host resource of the handle (NULL is ignored). */
+void ljmd_destroy(ljmd_sys* sys);
+
+/*
+ * FCC start of the benchmark (Sec. 4.4): M^3 cubic cells of side
+ * a = (4/density)^(1/3), four sites per cell, N = 4 M^3, L = M a; particle id
+ * order ix, iy, iz, basis site.  Velocities: Gaussian components from the
+ * counter-based SplitMix64 stream `seed` (draws 4i..4i+3 of particle i, Box-
+ * Muller), mean removed, scaled to sum v^2 = 3 (N - 1) T.  Forces are zero
+ * until the next ljmd_compute_forces / ljmd_step.
+ * Errors: LJ_EINVAL (M <= 0, density <= 0, T < 0, box too small for the list),
+ * LJ_ENOMEM.
+ */
+int ljmd_init_lattice(ljmd_sys* sys, int64_t cells_per_side, double density, double T, uint64_t seed);
+
+/*
+ * Set N particles in a periodic box of side `box`: x[3N] positions (any real
+ * values; folded into [0, box) at the next list construction), v[3N]
+ * velocities (NULL = zero).  on_device = 0: host arrays; 1: device arrays.
+ * Resets step and rebuild counters; the list is rebuilt before the next force.
+ * Errors: LJ_EINVAL (n <= 0, box < 2 (r_c + 2 margin), NULL x), LJ_ENOMEM.
+ */
+int ljmd_set_state(ljmd_sys* sys, int64_t n, double box, const double* x, const double* v, int32_t on_device);
+
+/*
+ * Copy the state out in id order: x[3N] (positions as stored: folded into the
+ * box at the last list construction, possibly up to margin/2 outside it
+ * since), v[3N], f[3N] (forces of the last evaluation).  Any pointer may be
+ * NULL.  img (int32 [3N], may be NULL) receives the periodic image counts so
+ * that x + img * L is the unwrapped trajectory.  Synchronises the stream.
+ */
+int ljmd_get_state(ljmd_sys* sys, double* x, double* v, double* f, int32_t* img, int32_t on_device);
+
+/*
+ * Construct the pair list (Sec. 2.2-2.4, Alg. 1): fold positions into the
+ * box, label particles by cell (cells per side = floor(L / r_s), so the cell
+ * side is at least r_s), counting-sort the particles by cell and reorder
+ * every particle array in that order (Sec. 3.3), then list every pair with
+ * r < r_s = cutoff + margin as a sorted list (KeyPointer / SortedList).  The
+ * list is exact: its pair set equals brute force over all pairs with
+ * r^2 = dx*dx + dy*dy + dz*dz evaluated in FP64 without FMA.  The cutoff and
+ * margin replace those given at creation.  Synchronises once (list size).
+ * Errors: LJ_EINVAL (cutoff <= 0, margin < 0, box too small), LJ_ESTATE,
+ * LJ_ENOMEM, LJ_ERANGE (more than 2^32 - 1 entries).
+ */
+int ljmd_build_pairlist(ljmd_sys* sys, double cutoff, double margin);
+
+/*
+ * Forces for the current positions over the current list (Alg. 4-6:
+ * f = [(24 r^6 - 48)/r^14 + 8 c2] eps/sigma^2 with r in units of sigma, zero
+ * for r >= r_c without branching, force on i = f (q_j - q_i)), plus the
+ * potential energy (Eq. 2) and virial W = sum_{i<j} r_ij . F_ij.  If no list
+ * exists or a particle moved more than margin/2 since it was built, the list
+ * is rebuilt first.
+ */
+int ljmd_compute_forces(ljmd_sys* sys);
+
+/*
+ * Advance nsteps of velocity-Verlet (m = 1): v += dt/2 F; x += dt v;
+ * F = F(x); v += dt/2 F.  After each drift the largest displacement since
+ * the last list construction is reduced on the device; the list is rebuilt
+ * whenever it exceeds margin/2 (the two particles of a pair can then have
+ * closed in by at most the margin, so every pair with r < r_c is still
+ * listed).  Forces must be current on entry (they are computed first if not).
+ * Energies are evaluated every params.energy_every steps.
+ */
+int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps);
+
+/*
+ * Energies of the current state: pe = sum_{i<j} V(r_ij) (Eq. 2), ke = 1/2 sum v^2,
+ * virial = sum_{i<j} r_ij . F_ij (FP64 totals).  Evaluates PE/virial first if
+ * the stored values are not for the current positions.  Any pointer may be
+ * NULL.  Synchronises the stream.
+ */
+int ljmd_energies(ljmd_sys* sys, double* pe, double* ke, double* virial);
+
+/*
+ * Register a device buffer (float64, 4 values per record: step, pe, ke,
+ * virial) that ljmd_step fills at every energy evaluation; capacity in
+ * records.  NULL disables.  The buffer is caller-owned.  Records past the
+ * capacity are dropped.  ljmd_stats().steps tells how far it was filled.
+ */
+int ljmd_set_energy_log(ljmd_sys* sys, double* device_log, int64_t capacity);
+
+/*
+ * The current pair list as unique pairs (i, j), i < j in id order, sorted
+ * lexicographically: ij[2k], ij[2k+1] for k < min(cap, npairs).  *npairs
+ * receives the number of unique pairs.  Synchronises the stream.
+ */
+int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
+
+/* Counters and state of the handle (synchronises the stream). */
+int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out);
+
+/* Human-readable name of a status code. */
+const char* ljmd_strerror(int code);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int ljmd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LJMD_H */

@@ -1,0 +1,335 @@
+// Cell grid (Sec. 2.2, Fig. 3): fold into the box, label by cell, count, scan, scatter;
+// then reorder the particle arrays in cell order (Sec. 3.3).  Also the id-order copies.
+#include "common.cuh"
+
+namespace ljmd {
+
+static int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b < 1048576 ? b : 1048576);
+}
+
+// Fold x_state into [offset, offset + L) (one correction per component, counted in img),
+// label c = (cx n + cy) n + cz with cx = floor((x_state - offset) * n / L) clamped to [0, n-1],
+// and count particles per cell.
+__global__ void k_wrap_label(double* __restrict__ x, int32_t* __restrict__ img, int64_t N, Geom g,
+                             uint32_t* __restrict__ cell_of, uint32_t* __restrict__ count,
+                             int32_t* __restrict__ status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    int c[3];
+    bool bad = false;
+    for (int k = 0; k < 3; ++k) {
+      double xs = x[k * N + i];
+      if (!finite_d(xs)) bad = true;
+      if (xs >= g.offset + g.L) {
+        xs -= g.L;
+        img[k * N + i] += 1;
+      } else if (xs < g.offset) {
+        xs += g.L;
+        img[k * N + i] -= 1;
+      }
+      x[k * N + i] = xs;
+      const double rel = xs - g.offset;  // exact: both in [offset/2, 2 offset)
+      int ck = (int)floor(rel * g.inv_h);
+      ck = ck < 0 ? 0 : (ck >= g.n ? g.n - 1 : ck);
+      c[k] = ck;
+    }
+    if (bad) {
+      atomicOr(status, LJ_ST_NONFINITE);
+      c[0] = c[1] = c[2] = 0;
+    }
+    const uint32_t cell = ((uint32_t)c[0] * (uint32_t)g.n + (uint32_t)c[1]) * (uint32_t)g.n + (uint32_t)c[2];
+    cell_of[i] = cell;
+    atomicAdd(&count[cell], 1u);
+  }
+}
+
+void launch_wrap_label(double* x, int32_t* img, int64_t N, Geom g, uint32_t* cell_of, uint32_t* cell_count,
+                       int32_t* status, cudaStream_t s) {
+  k_wrap_label<<<grid_for(N, 256), 256, 0, s>>>(x, img, N, g, cell_of, cell_count, status);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Exclusive scan, three passes: per-tile sums, scan of the tile sums (recursively), tile scan.
+constexpr int kScanTile = 2048;  // 256 threads x 8 values
+
+__global__ void k_tile_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t sh[8];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t s = 0;
+  for (int k = 0; k < 8; ++k) {
+    const int64_t i = base + threadIdx.x + k * 256;
+    if (i < n) s += in[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// Scan of one tile: each thread owns 8 consecutive values; out[i] = base + exclusive prefix.
+__global__ void k_tile_scan(const uint32_t* __restrict__ in, int64_t n, const uint32_t* __restrict__ tile_base,
+                            uint32_t* __restrict__ out) {
+  __shared__ uint32_t sh[8];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * 8;
+  uint32_t v[8], t = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    t += v[k];
+  }
+  // inclusive warp scan of the per-thread totals
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  uint32_t wbase = 0;
+  for (int q = 0; q < w; ++q) wbase += sh[q];
+  uint32_t run = (tile_base ? tile_base[blockIdx.x] : 0u) + wbase + inc - t;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 255) out[n] = run;  // total
+}
+
+size_t scan_tmp_words(int64_t n) {
+  size_t words = 0;
+  int64_t m = n;
+  while (m > kScanTile) {
+    const int64_t tiles = (m + kScanTile - 1) / kScanTile;
+    words += 2 * (size_t)tiles + 1;
+    m = tiles;
+  }
+  return words + 1;
+}
+
+void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles <= 1) {
+    k_tile_scan<<<1, 256, 0, s>>>(in, n, nullptr, out);
+    return;
+  }
+  uint32_t* sums = tmp;                // [tiles]
+  uint32_t* base = tmp + tiles;        // [tiles + 1]
+  k_tile_sums<<<(int)tiles, 256, 0, s>>>(in, n, sums);
+  launch_scan_u32(sums, base, tiles, tmp + 2 * tiles + 1, s);
+  k_tile_scan<<<(int)tiles, 256, 0, s>>>(in, n, base, out);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Scatter (Fig. 3 (ii)-(iii)): place each particle at its cell's pointer and advance it.
+// The arrival order inside a cell is made deterministic afterwards by k_cell_order.
+__global__ void k_scatter(const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ start,
+                          uint32_t* __restrict__ fill, uint32_t* __restrict__ perm, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = cell_of[i];
+    const uint32_t slot = atomicAdd(&fill[c], 1u);
+    perm[start[c] + slot] = (uint32_t)i;
+  }
+}
+
+void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_t* cell_fill, uint32_t* perm,
+                    int64_t N, cudaStream_t s) {
+  k_scatter<<<grid_for(N, 256), 256, 0, s>>>(cell_of, cell_start, cell_fill, perm, N);
+}
+
+// Inside each cell order the particles by id (insertion sort of the cell's slice of perm):
+// the sorted order then depends only on the positions, not on atomic arrival order.
+__global__ void k_cell_order(const uint32_t* __restrict__ start, int64_t ncells, uint32_t* __restrict__ perm,
+                             const int32_t* __restrict__ id) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = start[c], e = start[c + 1];
+    for (uint32_t a = b + 1; a < e; ++a) {
+      const uint32_t p = perm[a];
+      const int32_t key = id[p];
+      uint32_t q = a;
+      while (q > b && id[perm[q - 1]] > key) {
+        perm[q] = perm[q - 1];
+        --q;
+      }
+      perm[q] = p;
+    }
+  }
+}
+
+void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* perm, const int32_t* id,
+                       cudaStream_t s) {
+  k_cell_order<<<grid_for(ncells, 128), 128, 0, s>>>(cell_start, ncells, perm, id);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gathers: out[k] = in[perm[k]].
+__global__ void k_gather_f64x3(const double* __restrict__ in, double* __restrict__ out,
+                               const uint32_t* __restrict__ perm, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = perm[k];
+    out[k] = in[p];
+    out[N + k] = in[N + p];
+    out[2 * N + k] = in[2 * N + p];
+  }
+}
+void launch_gather_f64x3(const double* in, double* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
+  k_gather_f64x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N);
+}
+
+__global__ void k_gather_i32x3(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                               const uint32_t* __restrict__ perm, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = perm[k];
+    out[k] = in[p];
+    out[N + k] = in[N + p];
+    out[2 * N + k] = in[2 * N + p];
+  }
+}
+void launch_gather_i32x3(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
+  k_gather_i32x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N);
+}
+
+__global__ void k_gather_i32(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                             const uint32_t* __restrict__ perm, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = in[perm[k]];
+}
+void launch_gather_i32(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
+  k_gather_i32<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N);
+}
+
+__global__ void k_gather_u32(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                             const uint32_t* __restrict__ perm, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = in[perm[k]];
+}
+void launch_gather_u32(const uint32_t* in, uint32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
+  k_gather_u32<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N);
+}
+
+__global__ void k_gather_16B(const uint4* __restrict__ in, uint4* __restrict__ out, const uint32_t* __restrict__ perm,
+                             int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = in[perm[k]];
+}
+void launch_gather_16B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
+  k_gather_16B<<<grid_for(N, 256), 256, 0, s>>>((const uint4*)in, (uint4*)out, perm, N);
+}
+
+__global__ void k_gather_32B(const uint4* __restrict__ in, uint4* __restrict__ out, const uint32_t* __restrict__ perm,
+                             int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = perm[k];
+    out[2 * k] = in[2 * (size_t)p];
+    out[2 * k + 1] = in[2 * (size_t)p + 1];
+  }
+}
+void launch_gather_32B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
+  k_gather_32B<<<grid_for(N, 256), 256, 0, s>>>((const uint4*)in, (uint4*)out, perm, N);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Copies between the sorted SoA state and caller-order AoS (x[3 id + k]).
+__global__ void k_scatter_back_f64x3(const double* __restrict__ in, double* __restrict__ out,
+                                     const int32_t* __restrict__ id, int64_t N, double sub) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = id[k];
+    out[3 * p + 0] = in[k] - sub;
+    out[3 * p + 1] = in[N + k] - sub;
+    out[3 * p + 2] = in[2 * N + k] - sub;
+  }
+}
+void launch_scatter_back_f64x3(const double* in, double* out_idorder, const int32_t* id, int64_t N, double sub,
+                               cudaStream_t s) {
+  k_scatter_back_f64x3<<<grid_for(N, 256), 256, 0, s>>>(in, out_idorder, id, N, sub);
+}
+
+__global__ void k_scatter_back_f32x4(const float4* __restrict__ in, double* __restrict__ out,
+                                     const int32_t* __restrict__ id, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = id[k];
+    const float4 f = in[k];
+    out[3 * p + 0] = f.x;
+    out[3 * p + 1] = f.y;
+    out[3 * p + 2] = f.z;
+  }
+}
+void launch_scatter_back_f32x4_to_f64x3(const float4* in, double* out, const int32_t* id, int64_t N,
+                                        cudaStream_t s) {
+  k_scatter_back_f32x4<<<grid_for(N, 256), 256, 0, s>>>(in, out, id, N);
+}
+
+__global__ void k_scatter_back_f64x4(const dvec4* __restrict__ in, double* __restrict__ out,
+                                     const int32_t* __restrict__ id, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = id[k];
+    const dvec4 f = in[k];
+    out[3 * p + 0] = f.x;
+    out[3 * p + 1] = f.y;
+    out[3 * p + 2] = f.z;
+  }
+}
+void launch_scatter_back_f64x4_to_f64x3(const dvec4* in, double* out, const int32_t* id, int64_t N,
+                                        cudaStream_t s) {
+  k_scatter_back_f64x4<<<grid_for(N, 256), 256, 0, s>>>(in, out, id, N);
+}
+
+__global__ void k_scatter_back_i32x3(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                     const int32_t* __restrict__ id, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = id[k];
+    out[3 * p + 0] = in[k];
+    out[3 * p + 1] = in[N + k];
+    out[3 * p + 2] = in[2 * N + k];
+  }
+}
+void launch_scatter_back_i32x3(const int32_t* in, int32_t* out, const int32_t* id, int64_t N, cudaStream_t s) {
+  k_scatter_back_i32x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, id, N);
+}
+
+// Caller-order AoS (x[3 p + k], v or NULL) into the SoA state; id = p.  Positions are folded
+// into [0, L) (img counts the folds, so x_in = x + img L) and stored as offset + x.
+__global__ void k_load_state(const double* __restrict__ xin, const double* __restrict__ vin, double* __restrict__ x,
+                             double* __restrict__ v, int32_t* __restrict__ id, int32_t* __restrict__ img, int64_t N,
+                             double offset, double L) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < 3; ++k) {
+      const double xi = xin[3 * p + k];
+      double m = floor(xi / L);
+      double xr = xi - m * L;
+      if (xr >= L) {
+        xr -= L;
+        m += 1.0;
+      } else if (xr < 0.0) {
+        xr += L;
+        m -= 1.0;
+      }
+      x[k * N + p] = offset + xr;
+      v[k * N + p] = vin ? vin[3 * p + k] : 0.0;
+      img[k * N + p] = (int32_t)m;
+    }
+    id[p] = (int32_t)p;
+  }
+}
+void launch_load_state(const double* x_in, const double* v_in, double* x, double* v, int32_t* id, int32_t* img,
+                       int64_t N, double offset, double L, cudaStream_t s) {
+  k_load_state<<<grid_for(N, 256), 256, 0, s>>>(x_in, v_in, x, v, id, img, N, offset, L);
+}
+
+__global__ void k_iota(int32_t* __restrict__ id, int64_t N) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+    id[p] = (int32_t)p;
+}
+void launch_iota_i32(int32_t* id, int64_t N, cudaStream_t s) { k_iota<<<grid_for(N, 256), 256, 0, s>>>(id, N); }
+
+}  // namespace ljmd

@@ -1,0 +1,137 @@
+// Velocity-Verlet (the benchmark's second-order symplectic integrator, Sec. 4.4), fused:
+//
+//   v_full = v + kpre F          (completes the previous step; its kinetic energy is taken)
+//   v     <- v + (kpre + kpost) F (the first half-kick of the next step folded in)
+//   x     <- x + dt v             (drift)
+//
+// then the force kernel's copy of the positions is rewritten and the displacement since the
+// last list construction is reduced (device-wide max) for the margin/2 validity rule.
+// State x, v is FP64 (positions stored as offset + x).  Per component the FP64 pipe does two
+// FMAs; the kinetic energy of the mixed form is taken in FP32 per particle and summed in FP64.
+#include "common.cuh"
+
+namespace ljmd {
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, double* __restrict__ v,
+                                                   const void* __restrict__ fptr, void* __restrict__ pos,
+                                                   float4* __restrict__ lo, const void* __restrict__ refp,
+                                                   int64_t N, IntegrateArgs a, double* __restrict__ ke_part,
+                                                   uint32_t* __restrict__ dmax_bits, int32_t* __restrict__ status) {
+  const double kk = a.kpre + a.kpost;
+  const float kpre_f = (float)a.kpre;
+  double ke_acc = 0.0;
+  float d2max = 0.0f;
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double F[3];
+    if (MIXED) {
+      const float4 f = ((const float4*)fptr)[i];
+      F[0] = f.x;
+      F[1] = f.y;
+      F[2] = f.z;
+    } else {
+      const dvec4 f = ((const dvec4*)fptr)[i];
+      F[0] = f.x;
+      F[1] = f.y;
+      F[2] = f.z;
+    }
+    double xs[3];
+    float ke_i = 0.0f;
+    double ke_d = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double vk = v[k * N + i];
+      if (a.ke) {
+        if (MIXED) {
+          const float vf = fmaf(kpre_f, (float)F[k], (float)vk);
+          ke_i = fmaf(vf, vf, ke_i);
+        } else {
+          const double vf = fma(a.kpre, F[k], vk);
+          ke_d = fma(vf, vf, ke_d);
+        }
+      }
+      if (kk != 0.0) vk = fma(kk, F[k], vk);
+      double xk = x[k * N + i];
+      if (a.dt != 0.0) xk = fma(a.dt, vk, xk);
+      v[k * N + i] = vk;
+      x[k * N + i] = xk;
+      xs[k] = xk;
+      bad |= !finite_d(xk) || !finite_d(vk);
+    }
+    ke_acc += MIXED ? 0.5 * (double)ke_i : 0.5 * ke_d;
+    if (a.shadow) {
+      if (MIXED) {
+        float4 h, l;
+        split_hi_lo(xs[0], h.x, l.x);
+        split_hi_lo(xs[1], h.y, l.y);
+        split_hi_lo(xs[2], h.z, l.z);
+        h.w = 0.0f;
+        l.w = 0.0f;
+        ((float4*)pos)[i] = h;
+        lo[i] = l;
+        // displacement since the list was built: (hi - hi_ref) is exact, plus lo
+        const float4 r = ((const float4*)refp)[i];
+        const float dx = (h.x - r.x) + l.x, dy = (h.y - r.y) + l.y, dz = (h.z - r.z) + l.z;
+        d2max = fmaxf(d2max, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      } else {
+        ((dvec4*)pos)[i] = make_dvec4(xs[0], xs[1], xs[2], 0.0);
+        const dvec4 r = ((const dvec4*)refp)[i];
+        const double dx = xs[0] - r.x, dy = xs[1] - r.y, dz = xs[2] - r.z;
+        d2max = fmaxf(d2max, (float)fma(dx, dx, fma(dy, dy, dz * dz)));
+      }
+    }
+  }
+  if (bad) atomicOr(status, LJ_ST_NONFINITE);
+  __shared__ double sh[32];
+  __shared__ float shf[32];
+  const double tk = block_sum(ke_acc, sh);
+  if (threadIdx.x == 0 && a.ke) ke_part[blockIdx.x] = tk;
+  if (a.shadow) {
+    const float m = block_max(d2max, shf);
+    if (threadIdx.x == 0) atomicMax(dmax_bits, __float_as_uint(m));
+  }
+}
+
+int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, float4* lo, const void* ref,
+                     int64_t N, IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status,
+                     cudaStream_t s) {
+  const int blocks = red_blocks(N);
+  if (precision == LJ_MIXED)
+    k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, lo, ref, N, a, ke_part, dmax_bits, status);
+  else
+    k_integrate<false><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, lo, ref, N, a, ke_part, dmax_bits, status);
+  return blocks;
+}
+
+// Position copies for the force and list kernels from the FP64 state (no integration):
+// the hi/lo split always (the list build uses it in both forms); for FP64 also the dvec4
+// copy; and the displacement reference (hi for mixed, the dvec4 for FP64) if ref != NULL.
+__global__ void k_shadow(const double* __restrict__ x, int64_t N, int mixed, float4* __restrict__ hi,
+                         float4* __restrict__ lo, dvec4* __restrict__ pos64, void* __restrict__ ref) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = x[i], b = x[N + i], c = x[2 * N + i];
+    float4 h, l;
+    split_hi_lo(a, h.x, l.x);
+    split_hi_lo(b, h.y, l.y);
+    split_hi_lo(c, h.z, l.z);
+    h.w = 0.0f;
+    l.w = 0.0f;
+    hi[i] = h;
+    lo[i] = l;
+    if (!mixed) pos64[i] = make_dvec4(a, b, c, 0.0);
+    if (ref) {
+      if (mixed) ((float4*)ref)[i] = h;
+      else ((dvec4*)ref)[i] = make_dvec4(a, b, c, 0.0);
+    }
+  }
+}
+
+void launch_shadow_all(const double* x, int64_t N, int mixed, float4* hi, float4* lo, dvec4* pos64, void* ref,
+                       cudaStream_t s) {
+  int64_t b = (N + 255) / 256;
+  if (b < 1) b = 1;
+  k_shadow<<<(int)(b < 1048576 ? b : 1048576), 256, 0, s>>>(x, N, mixed, hi, lo, pos64, ref);
+}
+
+}  // namespace ljmd

@@ -1,0 +1,706 @@
+// C ABI of libljmd (declared in include/ljmd.h): handle management and the host-side
+// orchestration of the hot path.  Every step of the computation runs in the kernels of the
+// other translation units; this file only sizes buffers, launches and reads back scalars.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ljmd_internal.h"
+
+using namespace ljmd;
+
+struct ljmd_sys {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  ljmd_params prm{};
+  int precision = LJ_MIXED;
+  bool broken = false;
+
+  // particles and geometry
+  int64_t n = 0;
+  double L = 0.0;
+  Geom g{};
+  LJConst c{};
+  ListBand band{};
+  double rs = 0.0;
+  int64_t ncells = 0;
+  double disp_limit = 0.0;  // rebuild when the measured displacement exceeds this
+
+  // bookkeeping
+  bool have_list = false;
+  bool forces_current = false;
+  int64_t pe_step = -1;      // state index whose PE/virial partials are in part_force
+  int64_t energy_step = -1;  // state index of the energies in d_energies
+  int64_t steps = 0, rebuilds = 0;
+  uint64_t list_entries = 0;
+  double last_dmax = 0.0;
+  int nb_force = 0;
+  double* log_ptr = nullptr;
+  int64_t log_cap = 0;
+
+  // device buffers (sorted order)
+  double *x = nullptr, *v = nullptr, *x_alt = nullptr, *v_alt = nullptr;
+  void *f = nullptr, *f_alt = nullptr;
+  float4 *hi = nullptr, *lo = nullptr;
+  dvec4* pos64 = nullptr;
+  void* ref = nullptr;
+  int32_t *id = nullptr, *id_alt = nullptr, *img = nullptr, *img_alt = nullptr;
+  uint32_t *cell_of = nullptr, *cell_alt = nullptr, *perm = nullptr;
+  uint32_t *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
+  uint32_t *row_cnt = nullptr, *row_ptr = nullptr, *col = nullptr;
+  size_t col_cap = 0;
+  uint32_t* scan_tmp = nullptr;
+  size_t scan_tmp_cap = 0;
+  int64_t cap_n = 0;       // particle capacity of the per-particle buffers
+  int64_t cap_cells = 0;   // capacity of the per-cell buffers
+  double *part_force = nullptr, *part_ke = nullptr, *part_misc = nullptr, *d_scalars = nullptr;
+  double* d_energies = nullptr;
+  int64_t* d_log_count = nullptr;
+  int32_t* d_status = nullptr;
+  uint32_t* d_dmax = nullptr;
+  unsigned long long* d_total64 = nullptr;
+  // pinned host mirrors
+  uint32_t* h_u32 = nullptr;
+  double* h_f64 = nullptr;
+  int32_t* h_i32 = nullptr;
+};
+
+// ----------------------------------------------------------------------------------------------
+#define CK(call)                         \
+  do {                                   \
+    cudaError_t e_ = (call);             \
+    if (e_ != cudaSuccess) {             \
+      sys->broken = true;                \
+      return LJ_EDEVICE;                 \
+    }                                    \
+  } while (0)
+#define CKL() CK(cudaGetLastError())
+#define TRY(expr)            \
+  do {                       \
+    int r_ = (expr);         \
+    if (r_ != LJ_OK) return r_; \
+  } while (0)
+
+static int dalloc(ljmd_sys* sys, void** p, size_t bytes) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return LJ_ENOMEM;
+  }
+  (void)sys;
+  return LJ_OK;
+}
+template <class T>
+static int dalloc_t(ljmd_sys* sys, T** p, size_t count) {
+  return dalloc(sys, (void**)p, count * sizeof(T));
+}
+
+static void free_all(ljmd_sys* s) {
+  void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->lo, s->pos64, s->ref, s->id,
+                  s->id_alt, s->img, s->img_alt, s->cell_of, s->cell_alt, s->perm, s->cell_count, s->cell_start,
+                  s->cell_fill, s->row_cnt, s->row_ptr, s->col, s->scan_tmp, s->part_force, s->part_ke,
+                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (s->h_u32) cudaFreeHost(s->h_u32);
+  if (s->h_f64) cudaFreeHost(s->h_f64);
+  if (s->h_i32) cudaFreeHost(s->h_i32);
+}
+
+// Coefficients of the additive truncation terms of Eq. 2 (Sec. 2.1), from V(r_c) = V'(r_c) = 0
+// with x = r_c / sigma: c2 = 6 x^-14 - 3 x^-8, c0 = 4 x^-6 - 7 x^-12.  Shift-only: c2 = 0,
+// c0 = x^-6 - x^-12.  Plain cut: both zero.
+static void truncation_terms(double x, int mode, double* c2, double* c0) {
+  const double ix2 = 1.0 / (x * x), ix6 = ix2 * ix2 * ix2, ix8 = ix6 * ix2, ix12 = ix6 * ix6, ix14 = ix12 * ix2;
+  if (mode == LJ_TRUNC_QUADRATIC) {
+    *c2 = 6.0 * ix14 - 3.0 * ix8;
+    *c0 = 4.0 * ix6 - 7.0 * ix12;
+  } else if (mode == LJ_TRUNC_SHIFT) {
+    *c2 = 0.0;
+    *c0 = ix6 - ix12;
+  } else {
+    *c2 = 0.0;
+    *c0 = 0.0;
+  }
+}
+
+static int check_params(const ljmd_params* p) {
+  if (!(p->cutoff > 0.0) || !(p->margin >= 0.0) || !(p->eps > 0.0) || !(p->sigma > 0.0)) return LJ_EINVAL;
+  if (p->truncation < 0 || p->truncation > 2) return LJ_EINVAL;
+  if (p->list_form != LJ_LIST_FULL && p->list_form != LJ_LIST_HALF) return LJ_EINVAL;
+  if (p->energy_every < 0) return LJ_EINVAL;
+  const int l = p->lanes;
+  if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32)) return LJ_EINVAL;
+  return LJ_OK;
+}
+
+// Box, cutoff and margin -> grid, offsets, constants.  Requires L >= 2 (r_s + margin) so that a
+// listed pair, which can close in by at most the margin, keeps a unique minimum image.
+static int setup_geometry(ljmd_sys* s, double L) {
+  const ljmd_params& p = s->prm;
+  const double rs = p.cutoff + p.margin;
+  if (!(L >= 2.0 * (rs + p.margin)) || !isfinite(L)) return LJ_EINVAL;
+  s->L = L;
+  s->rs = rs;
+  int64_t n = (int64_t)floor(L / rs);
+  if (n < 1) n = 1;
+  if (n > 1024) n = 1024;
+  s->ncells = n * n * n;
+  int pw = 2;
+  while (ldexp(1.0, pw) < L + p.margin + 1.0 || ldexp(1.0, pw - 1) < p.margin + 1.0) ++pw;
+  Geom& g = s->g;
+  g.L = L;
+  g.half_L = 0.5 * L;
+  g.offset = ldexp(1.0, pw);
+  g.inv_h = (double)n / L;
+  g.n = (int32_t)n;
+  g.p = pw;
+  const double q = ldexp(1.0, pw - 23);
+  const double Lhi = floor(L / q) * q;
+  g.L_hi = (float)Lhi;
+  g.L_lo = (float)(L - Lhi);
+  g.inv_L = (float)(1.0 / L);
+  g.inv_L64 = 1.0 / L;
+
+  double c2, c0;
+  truncation_terms(p.cutoff / p.sigma, p.truncation, &c2, &c0);
+  LJConst& c = s->c;
+  c.eps = p.eps;
+  c.sigma = p.sigma;
+  c.sig2 = p.sigma * p.sigma;
+  c.rc2 = p.cutoff * p.cutoff;
+  c.c2 = c2;
+  c.c0 = c0;
+  c.f24 = (float)(24.0 * p.eps);
+  c.f48 = (float)(48.0 * p.eps);
+  c.f8c2 = (float)(8.0 * p.eps * c2 / c.sig2);
+  c.sig2f = (float)c.sig2;
+  c.rc2f = (float)c.rc2;
+  c.e4 = (float)(4.0 * p.eps);
+  c.c2f = (float)(c2 / c.sig2);
+  c.c0f = (float)c0;
+
+  // FP32 list band: r2f within 1e-5 relative of r_s^2 goes to the exact FP64 test.  The FP32
+  // r2 is within ~5 ulp (3e-7 relative) of the exact value, so outside the band it decides.
+  s->band.rs2 = rs * rs;
+  s->band.lo = (float)(rs * rs * (1.0 - 1e-5));
+  s->band.hi = (float)(rs * rs * (1.0 + 1e-5));
+  // Displacement rule: rebuild when max |x - x_ref| > margin / 2.  The measured value can
+  // undershoot by the FP32 hi/lo reference error (mixed: dropped lo of the reference,
+  // <= 2^(p-23) per component), so the limit is lowered by twice that bound.
+  const double slack = (s->precision == LJ_MIXED) ? 2.0 * sqrt(3.0) * ldexp(1.0, pw - 23) + 1e-6 : 1e-12;
+  s->disp_limit = 0.5 * p.margin - slack;
+  return LJ_OK;
+}
+
+static int ensure_particles(ljmd_sys* s, int64_t n) {
+  if (n <= s->cap_n) return LJ_OK;
+  const bool mixed = s->precision == LJ_MIXED;
+  const size_t fsz = mixed ? sizeof(float4) : sizeof(dvec4);
+  TRY(dalloc_t(s, &s->x, 3 * n));
+  TRY(dalloc_t(s, &s->v, 3 * n));
+  TRY(dalloc_t(s, &s->x_alt, 3 * n));
+  TRY(dalloc_t(s, &s->v_alt, 3 * n));
+  TRY(dalloc(s, &s->f, fsz * n));
+  TRY(dalloc(s, &s->f_alt, fsz * n));
+  TRY(dalloc_t(s, &s->hi, n));
+  TRY(dalloc_t(s, &s->lo, n));
+  if (!mixed) TRY(dalloc_t(s, &s->pos64, n));
+  TRY(dalloc(s, &s->ref, fsz * n));
+  TRY(dalloc_t(s, &s->id, n));
+  TRY(dalloc_t(s, &s->id_alt, n));
+  TRY(dalloc_t(s, &s->img, 3 * n));
+  TRY(dalloc_t(s, &s->img_alt, 3 * n));
+  TRY(dalloc_t(s, &s->cell_of, n));
+  TRY(dalloc_t(s, &s->cell_alt, n));
+  TRY(dalloc_t(s, &s->perm, n));
+  TRY(dalloc_t(s, &s->row_cnt, n + 1));
+  TRY(dalloc_t(s, &s->row_ptr, n + 1));
+  s->cap_n = n;
+  return LJ_OK;
+}
+
+static int ensure_scan_tmp(ljmd_sys* s, int64_t n) {
+  const size_t w = scan_tmp_words(n);
+  if (w <= s->scan_tmp_cap) return LJ_OK;
+  TRY(dalloc_t(s, &s->scan_tmp, w));
+  s->scan_tmp_cap = w;
+  return LJ_OK;
+}
+
+static int ensure_cells(ljmd_sys* s) {
+  if (s->ncells > s->cap_cells) {
+    TRY(dalloc_t(s, &s->cell_count, s->ncells));
+    TRY(dalloc_t(s, &s->cell_start, s->ncells + 1));
+    TRY(dalloc_t(s, &s->cell_fill, s->ncells));
+    s->cap_cells = s->ncells;
+  }
+  TRY(ensure_scan_tmp(s, s->ncells));
+  TRY(ensure_scan_tmp(s, s->n));
+  return LJ_OK;
+}
+
+static void reset_counters(ljmd_sys* s) {
+  s->have_list = false;
+  s->forces_current = false;
+  s->pe_step = -1;
+  s->energy_step = -1;
+  s->steps = 0;
+  s->rebuilds = 0;
+  s->list_entries = 0;
+  s->last_dmax = 0.0;
+}
+
+static int device_status(ljmd_sys* s, int32_t* out) {
+  ljmd_sys* sys = s;
+  CK(cudaMemcpyAsync(s->h_i32, s->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  *out = *s->h_i32;
+  return LJ_OK;
+}
+
+static int check_status(ljmd_sys* s) {
+  int32_t w = 0;
+  TRY(device_status(s, &w));
+  return w ? LJ_EDEVICE : LJ_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Pair-list construction: fold, label, counting sort (Fig. 3), reorder (Sec. 3.3), sorted list.
+static int rebuild(ljmd_sys* s) {
+  ljmd_sys* sys = s;
+  const int64_t N = s->n;
+  cudaStream_t st = s->st;
+  TRY(ensure_cells(s));
+  CK(cudaMemsetAsync(s->cell_count, 0, sizeof(uint32_t) * s->ncells, st));
+  launch_wrap_label(s->x, s->img, N, s->g, s->cell_of, s->cell_count, s->d_status, st);
+  CKL();
+  launch_scan_u32(s->cell_count, s->cell_start, s->ncells, s->scan_tmp, st);
+  CKL();
+  CK(cudaMemsetAsync(s->cell_fill, 0, sizeof(uint32_t) * s->ncells, st));
+  launch_scatter(s->cell_of, s->cell_start, s->cell_fill, s->perm, N, st);
+  launch_cell_order(s->cell_start, s->ncells, s->perm, s->id, st);
+  launch_gather_f64x3(s->x, s->x_alt, s->perm, N, st);
+  launch_gather_f64x3(s->v, s->v_alt, s->perm, N, st);
+  launch_gather_i32(s->id, s->id_alt, s->perm, N, st);
+  launch_gather_i32x3(s->img, s->img_alt, s->perm, N, st);
+  launch_gather_u32(s->cell_of, s->cell_alt, s->perm, N, st);
+  if (s->precision == LJ_MIXED) launch_gather_16B(s->f, s->f_alt, s->perm, N, st);
+  else launch_gather_32B(s->f, s->f_alt, s->perm, N, st);
+  CKL();
+  std::swap(s->x, s->x_alt);
+  std::swap(s->v, s->v_alt);
+  std::swap(s->id, s->id_alt);
+  std::swap(s->img, s->img_alt);
+  std::swap(s->cell_of, s->cell_alt);
+  std::swap(s->f, s->f_alt);
+  launch_shadow_all(s->x, N, s->precision == LJ_MIXED, s->hi, s->lo, s->pos64, s->ref, st);
+  CKL();
+  const int half = s->prm.list_form == LJ_LIST_HALF;
+  CK(cudaMemsetAsync(s->d_total64, 0, sizeof(unsigned long long), st));
+  launch_list_count(s->hi, s->lo, s->x, s->cell_of, s->cell_start, N, s->g, s->band, half, s->precision, s->row_cnt,
+                    s->d_total64, st);
+  CKL();
+  launch_scan_u32(s->row_cnt, s->row_ptr, N, s->scan_tmp, st);
+  CKL();
+  CK(cudaMemcpyAsync(s->h_u32, s->row_ptr + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(s->h_u32 + 2, s->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  unsigned long long total64;
+  memcpy(&total64, s->h_u32 + 2, sizeof(total64));
+  if (total64 > 4294967294ULL) return LJ_ERANGE;  // offsets are 32-bit
+  const uint64_t total = *s->h_u32;
+  if (total != total64) return LJ_EDEVICE;
+  if (total + 1 > s->col_cap) {
+    const size_t want = (size_t)(total * 1.15) + 1024;
+    TRY(dalloc_t(s, &s->col, want));
+    s->col_cap = want;
+  }
+  launch_list_fill(s->hi, s->lo, s->x, s->cell_of, s->cell_start, N, s->g, s->band, half, s->precision, s->row_ptr,
+                   s->col, s->d_status, st);
+  CKL();
+  s->list_entries = total;
+  s->have_list = true;
+  s->rebuilds += 1;
+  s->pe_step = -1;
+  return LJ_OK;
+}
+
+static void* force_pos(ljmd_sys* s) { return s->precision == LJ_MIXED ? (void*)s->hi : (void*)s->pos64; }
+
+static int run_force(ljmd_sys* s, bool energy) {
+  ljmd_sys* sys = s;
+  const int half = s->prm.list_form == LJ_LIST_HALF;
+  if (half) CK(cudaMemsetAsync(s->f, 0, (s->precision == LJ_MIXED ? 16 : 32) * (size_t)s->n, s->st));
+  int lanes = s->prm.lanes;
+  if (lanes == 0) lanes = (s->precision == LJ_MIXED) ? 8 : 8;
+  s->nb_force = launch_force(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->lo, s->row_ptr, s->col,
+                             s->n, s->g, s->c, s->f, s->part_force, s->st);
+  CKL();
+  s->forces_current = true;
+  s->pe_step = energy ? s->steps : -1;
+  return LJ_OK;
+}
+
+// Largest displacement since the list was built, as measured by the last integrate launch.
+static int read_dmax(ljmd_sys* s, double* out) {
+  ljmd_sys* sys = s;
+  CK(cudaMemcpyAsync(s->h_u32, s->d_dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  float d2;
+  memcpy(&d2, s->h_u32, sizeof(float));
+  *out = sqrt((double)d2);
+  return LJ_OK;
+}
+
+static int ensure_forces(ljmd_sys* s, bool energy) {
+  if (!s->have_list) TRY(rebuild(s));
+  if (!s->forces_current || (energy && s->pe_step != s->steps)) TRY(run_force(s, energy));
+  return LJ_OK;
+}
+
+// KE of the current (full-step) velocities and the energy record of the current state.
+static int finalize_energies_now(ljmd_sys* s) {
+  ljmd_sys* sys = s;
+  TRY(ensure_forces(s, true));
+  IntegrateArgs a{0.0, 0.0, 0.0, 1, 0};
+  const int nb = launch_integrate(s->precision, s->x, s->v, s->f, force_pos(s), s->lo, s->ref, s->n, a, s->part_ke,
+                                  s->d_dmax, s->d_status, s->st);
+  CKL();
+  const double scale = s->prm.list_form == LJ_LIST_FULL ? 0.5 : 1.0;
+  launch_energy_finalize(s->part_force, s->nb_force, s->part_ke, nb, scale, s->d_energies, nullptr, 0, nullptr,
+                         (double)s->steps, s->st);
+  CKL();
+  s->energy_step = s->steps;
+  return LJ_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
+extern "C" {
+
+int ljmd_version(void) { return 100; }
+
+const char* ljmd_strerror(int code) {
+  switch (code) {
+    case LJ_OK: return "ok";
+    case LJ_EINVAL: return "invalid argument";
+    case LJ_ENOMEM: return "out of memory";
+    case LJ_EDEVICE: return "CUDA error or device status raised";
+    case LJ_ESTATE: return "call out of order (no particles)";
+    case LJ_ERANGE: return "size beyond a library limit";
+    default: return "unknown status";
+  }
+}
+
+int ljmd_create(ljmd_sys** out, const ljmd_params* p, int32_t precision, void* cuda_stream) {
+  if (!out || !p) return LJ_EINVAL;
+  *out = nullptr;
+  if (precision != LJ_FP64 && precision != LJ_MIXED) return LJ_EINVAL;
+  if (check_params(p) != LJ_OK) return LJ_EINVAL;
+  ljmd_sys* sys = new (std::nothrow) ljmd_sys();
+  if (!sys) return LJ_ENOMEM;
+  sys->prm = *p;
+  sys->precision = precision;
+  sys->st = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&sys->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete sys;
+    return LJ_EDEVICE;
+  }
+  int r = LJ_OK;
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->part_force, 2 * kMaxRedBlocks);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->part_ke, kMaxRedBlocks);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->part_misc, 4 * kMaxRedBlocks);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_scalars, 8);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_energies, 4);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_log_count, 1);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_status, 1);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_dmax, 1);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_total64, 1);
+  if (r == LJ_OK && cudaMallocHost(&sys->h_u32, 64) != cudaSuccess) r = LJ_ENOMEM;
+  if (r == LJ_OK && cudaMallocHost(&sys->h_f64, 64) != cudaSuccess) r = LJ_ENOMEM;
+  if (r == LJ_OK && cudaMallocHost(&sys->h_i32, 64) != cudaSuccess) r = LJ_ENOMEM;
+  if (r == LJ_OK && cudaMemsetAsync(sys->d_status, 0, 4, sys->st) != cudaSuccess) r = LJ_EDEVICE;
+  if (r == LJ_OK && cudaMemsetAsync(sys->d_log_count, 0, 8, sys->st) != cudaSuccess) r = LJ_EDEVICE;
+  if (r != LJ_OK) {
+    cudaGetLastError();
+    free_all(sys);
+    delete sys;
+    return r;
+  }
+  *out = sys;
+  return LJ_OK;
+}
+
+void ljmd_destroy(ljmd_sys* sys) {
+  if (!sys) return;
+  if (sys->st) cudaStreamSynchronize(sys->st);
+  else cudaDeviceSynchronize();
+  free_all(sys);
+  cudaGetLastError();
+  delete sys;
+}
+
+int ljmd_init_lattice(ljmd_sys* sys, int64_t M, double density, double T, uint64_t seed) {
+  if (!sys || M <= 0 || !(density > 0.0) || !(T >= 0.0)) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (M > 2000) return LJ_ERANGE;
+  const int64_t N = 4 * M * M * M;
+  if (N > 1000000000LL) return LJ_ERANGE;
+  const double a = cbrt(4.0 / density);
+  TRY(setup_geometry(sys, a * (double)M));
+  TRY(ensure_particles(sys, N));
+  sys->n = N;
+  TRY(ensure_cells(sys));
+  reset_counters(sys);
+  launch_fcc(sys->x, M, a, sys->g.offset, sys->st);
+  CKL();
+  launch_gaussian(sys->v, N, seed, sys->st);
+  CKL();
+  const int nb = red_blocks(N);
+  launch_sums3(sys->v, N, sys->part_misc, nb, sys->st);
+  launch_final_reduce(sys->part_misc, nb, 3, sys->d_scalars, sys->st);
+  launch_sumsq_centered(sys->v, N, sys->d_scalars, sys->part_misc, nb, sys->st);
+  launch_final_reduce(sys->part_misc, nb, 1, sys->d_scalars + 4, sys->st);
+  launch_center_scale(sys->v, N, sys->d_scalars, sys->d_scalars + 4, T, sys->st);
+  CKL();
+  CK(cudaMemsetAsync(sys->img, 0, sizeof(int32_t) * 3 * N, sys->st));
+  CK(cudaMemsetAsync(sys->f, 0, (sys->precision == LJ_MIXED ? 16 : 32) * (size_t)N, sys->st));
+  launch_iota_i32(sys->id, N, sys->st);  // id = lattice order
+  CKL();
+  return LJ_OK;
+}
+
+int ljmd_set_state(ljmd_sys* sys, int64_t n, double box, const double* x, const double* v, int32_t on_device) {
+  if (!sys || n <= 0 || !x) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (n > 1000000000LL) return LJ_ERANGE;
+  TRY(setup_geometry(sys, box));
+  TRY(ensure_particles(sys, n));
+  sys->n = n;
+  TRY(ensure_cells(sys));
+  reset_counters(sys);
+  const double* xs = x;
+  const double* vs = v;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(sys->x_alt, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, sys->st));
+    xs = sys->x_alt;
+    if (v) {
+      CK(cudaMemcpyAsync(sys->v_alt, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, sys->st));
+      vs = sys->v_alt;
+    }
+  }
+  launch_load_state(xs, vs, sys->x, sys->v, sys->id, sys->img, n, sys->g.offset, sys->L, sys->st);
+  CKL();
+  CK(cudaMemsetAsync(sys->f, 0, (sys->precision == LJ_MIXED ? 16 : 32) * (size_t)n, sys->st));
+  if (!on_device) CK(cudaStreamSynchronize(sys->st));  // host buffers may be reused by the caller
+  return LJ_OK;
+}
+
+int ljmd_get_state(ljmd_sys* sys, double* x, double* v, double* f, int32_t* img, int32_t on_device) {
+  if (!sys) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0) return LJ_ESTATE;
+  const int64_t N = sys->n;
+  cudaStream_t st = sys->st;
+  // x_alt / v_alt / img_alt are free between list constructions and serve as staging
+  if (x) {
+    double* dst = on_device ? x : sys->x_alt;
+    launch_scatter_back_f64x3(sys->x, dst, sys->id, N, sys->g.offset, st);
+    CKL();
+    if (!on_device) CK(cudaMemcpyAsync(x, dst, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+  }
+  if (v) {
+    double* dst = on_device ? v : sys->v_alt;
+    launch_scatter_back_f64x3(sys->v, dst, sys->id, N, 0.0, st);
+    CKL();
+    if (!on_device) CK(cudaMemcpyAsync(v, dst, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+  }
+  if (f) {
+    CK(cudaStreamSynchronize(st));  // x_alt may be in use by the x copy above
+    double* dst = on_device ? f : sys->x_alt;
+    if (sys->precision == LJ_MIXED) launch_scatter_back_f32x4_to_f64x3((const float4*)sys->f, dst, sys->id, N, st);
+    else launch_scatter_back_f64x4_to_f64x3((const dvec4*)sys->f, dst, sys->id, N, st);
+    CKL();
+    if (!on_device) CK(cudaMemcpyAsync(f, dst, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+  }
+  if (img) {
+    int32_t* dst = on_device ? img : sys->img_alt;
+    launch_scatter_back_i32x3(sys->img, dst, sys->id, N, st);
+    CKL();
+    if (!on_device) CK(cudaMemcpyAsync(img, dst, sizeof(int32_t) * 3 * N, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return check_status(sys);
+}
+
+int ljmd_build_pairlist(ljmd_sys* sys, double cutoff, double margin) {
+  if (!sys) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0) return LJ_ESTATE;
+  if (!(cutoff > 0.0) || !(margin >= 0.0)) return LJ_EINVAL;
+  const ljmd_params old = sys->prm;
+  sys->prm.cutoff = cutoff;
+  sys->prm.margin = margin;
+  int r = setup_geometry(sys, sys->L);
+  if (r != LJ_OK) {
+    sys->prm = old;
+    setup_geometry(sys, sys->L);
+    return r;
+  }
+  sys->forces_current = false;
+  TRY(rebuild(sys));
+  return LJ_OK;
+}
+
+int ljmd_compute_forces(ljmd_sys* sys) {
+  if (!sys) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0) return LJ_ESTATE;
+  if (!sys->have_list) {
+    TRY(rebuild(sys));
+  } else {
+    // displacement since the list was built (shadow copies are current): rebuild if invalid
+    IntegrateArgs a{0.0, 0.0, 0.0, 0, 1};
+    CK(cudaMemsetAsync(sys->d_dmax, 0, 4, sys->st));
+    launch_integrate(sys->precision, sys->x, sys->v, sys->f, force_pos(sys), sys->lo, sys->ref, sys->n, a,
+                     sys->part_ke, sys->d_dmax, sys->d_status, sys->st);
+    CKL();
+    TRY(read_dmax(sys, &sys->last_dmax));
+    if (sys->last_dmax > sys->disp_limit) TRY(rebuild(sys));
+  }
+  return run_force(sys, true);
+}
+
+int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
+  if (!sys || nsteps < 0 || !isfinite(dt)) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0) return LJ_ESTATE;
+  if (nsteps == 0) return LJ_OK;
+  const int ee = sys->prm.energy_every;
+  auto want_energy = [&](int64_t t) { return ee > 0 && (t % ee) == 0; };
+  TRY(ensure_forces(sys, want_energy(sys->steps)));
+  const double h = 0.5 * dt;
+  const double scale = sys->prm.list_form == LJ_LIST_FULL ? 0.5 : 1.0;
+  cudaStream_t st = sys->st;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const bool rec = sys->pe_step == sys->steps && want_energy(sys->steps);
+    IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, rec ? 1 : 0, 1};
+    CK(cudaMemsetAsync(sys->d_dmax, 0, 4, st));
+    const int nb = launch_integrate(sys->precision, sys->x, sys->v, sys->f, force_pos(sys), sys->lo, sys->ref,
+                                    sys->n, a, sys->part_ke, sys->d_dmax, sys->d_status, st);
+    CKL();
+    if (rec) {
+      launch_energy_finalize(sys->part_force, sys->nb_force, sys->part_ke, nb, scale, sys->d_energies,
+                             sys->log_ptr, sys->log_cap, sys->d_log_count, (double)sys->steps, st);
+      CKL();
+      sys->energy_step = sys->steps;
+    }
+    sys->steps += 1;
+    sys->forces_current = false;
+    TRY(read_dmax(sys, &sys->last_dmax));
+    if (sys->last_dmax > sys->disp_limit) TRY(rebuild(sys));
+    TRY(run_force(sys, want_energy(sys->steps)));
+  }
+  // final half-kick: v at the full step of the last state
+  const bool rec = sys->pe_step == sys->steps && want_energy(sys->steps);
+  IntegrateArgs a{h, 0.0, 0.0, rec ? 1 : 0, 0};
+  const int nb = launch_integrate(sys->precision, sys->x, sys->v, sys->f, force_pos(sys), sys->lo, sys->ref, sys->n,
+                                  a, sys->part_ke, sys->d_dmax, sys->d_status, st);
+  CKL();
+  if (rec) {
+    launch_energy_finalize(sys->part_force, sys->nb_force, sys->part_ke, nb, scale, sys->d_energies, sys->log_ptr,
+                           sys->log_cap, sys->d_log_count, (double)sys->steps, st);
+    CKL();
+    sys->energy_step = sys->steps;
+  }
+  return check_status(sys);
+}
+
+int ljmd_energies(ljmd_sys* sys, double* pe, double* ke, double* virial) {
+  if (!sys) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0) return LJ_ESTATE;
+  if (sys->energy_step != sys->steps) TRY(finalize_energies_now(sys));
+  CK(cudaMemcpyAsync(sys->h_f64, sys->d_energies, 4 * sizeof(double), cudaMemcpyDeviceToHost, sys->st));
+  CK(cudaStreamSynchronize(sys->st));
+  if (pe) *pe = sys->h_f64[0];
+  if (ke) *ke = sys->h_f64[1];
+  if (virial) *virial = sys->h_f64[2];
+  return check_status(sys);
+}
+
+int ljmd_set_energy_log(ljmd_sys* sys, double* device_log, int64_t capacity) {
+  if (!sys || capacity < 0) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  sys->log_ptr = device_log;
+  sys->log_cap = device_log ? capacity : 0;
+  if (cudaMemsetAsync(sys->d_log_count, 0, 8, sys->st) != cudaSuccess) return LJ_EDEVICE;
+  return LJ_OK;
+}
+
+int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
+  if (!sys || !npairs || cap < 0 || (cap > 0 && !ij)) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0) return LJ_ESTATE;
+  if (!sys->have_list) TRY(rebuild(sys));
+  const int64_t N = sys->n;
+  std::vector<uint32_t> rp(N + 1), cl(sys->list_entries);
+  std::vector<int32_t> id(N);
+  CK(cudaMemcpyAsync(rp.data(), sys->row_ptr, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, sys->st));
+  if (sys->list_entries)
+    CK(cudaMemcpyAsync(cl.data(), sys->col, sizeof(uint32_t) * sys->list_entries, cudaMemcpyDeviceToHost, sys->st));
+  CK(cudaMemcpyAsync(id.data(), sys->id, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, sys->st));
+  CK(cudaStreamSynchronize(sys->st));
+  std::vector<std::pair<int64_t, int64_t>> pairs;
+  pairs.reserve(sys->prm.list_form == LJ_LIST_FULL ? sys->list_entries / 2 : sys->list_entries);
+  for (int64_t i = 0; i < N; ++i)
+    for (uint32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const int64_t a = id[i], b = id[cl[k]];
+      if (sys->prm.list_form == LJ_LIST_FULL) {
+        if (a < b) pairs.emplace_back(a, b);
+      } else {
+        pairs.emplace_back(std::min(a, b), std::max(a, b));
+      }
+    }
+  std::sort(pairs.begin(), pairs.end());
+  *npairs = (int64_t)pairs.size();
+  const int64_t m = std::min<int64_t>(cap, (int64_t)pairs.size());
+  for (int64_t k = 0; k < m; ++k) {
+    ij[2 * k] = pairs[k].first;
+    ij[2 * k + 1] = pairs[k].second;
+  }
+  return check_status(sys);
+}
+
+int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
+  if (!sys || !out) return LJ_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->n = sys->n;
+  out->steps = sys->steps;
+  out->rebuilds = sys->rebuilds;
+  out->list_entries = (int64_t)sys->list_entries;
+  out->cells_per_side = sys->g.n;
+  out->box = sys->L;
+  out->mean_lifetime = sys->rebuilds > 0 ? (double)sys->steps / (double)sys->rebuilds : 0.0;
+  out->max_displacement = sys->last_dmax;
+  out->precision = sys->precision;
+  if (sys->broken) {
+    out->status_word = -1;
+    return LJ_EDEVICE;
+  }
+  int32_t w = 0;
+  TRY(device_status(sys, &w));
+  out->status_word = w;
+  return LJ_OK;
+}
+
+}  // extern "C"

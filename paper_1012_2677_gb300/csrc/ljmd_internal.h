@@ -1,0 +1,127 @@
+// Internal declarations shared by the CUDA translation units of libljmd.
+// Nothing here is part of the C ABI (include/ljmd.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ljmd.h"
+
+namespace ljmd {
+
+// 32-byte aligned four-double vector (one 32-byte access per particle).
+typedef double4_32a dvec4;
+
+// Kernels that produce per-block partial sums run on at most this many blocks
+// (grid-stride loops), so partial buffers have a fixed size and the final
+// reduction has a fixed order (results do not depend on timing).
+constexpr int kMaxRedBlocks = 1216;  // 152 SMs x 8
+constexpr int kRedThreads = 256;
+
+// Box geometry.  Positions are stored as x_state = offset + x with
+// offset = 2^p >= L + margin (and >= 4), so every stored coordinate lies in
+// [offset/2, 2 offset) and shares one binade-pair: differences of stored
+// coordinates are exact in FP64, and their FP32 "hi" parts (the top 24
+// significand bits) are all multiples of 2^(p-24), which makes the FP32
+// difference of two hi parts exact as well.
+struct Geom {
+  double L;        // box side
+  double half_L;   // L / 2 (exact)
+  double offset;   // 2^p
+  double inv_h;    // cells per side / L
+  int32_t n;       // cells per side
+  int32_t p;       // log2(offset)
+  float L_hi;      // L truncated to a multiple of 2^(p-23) (exact FP32)
+  float L_lo;      // L - L_hi rounded to FP32
+  float inv_L;     // 1 / L in FP32 (picks the periodic image)
+  double inv_L64;  // 1 / L in FP64
+};
+
+// Potential constants (Eq. 2) in the forms the kernels use.
+struct LJConst {
+  double eps, sigma, rc2, c2, c0, sig2;  // FP64 form
+  float f24, f48, f8c2;                  // force: f = ri2 s3i (f24 - f48 s3i) + f8c2
+  float sig2f, rc2f, e4, c2f, c0f;       // energy: 4 eps (s3i (s3i - 1) + c2 s + c0)
+};
+
+struct ListBand {
+  double rs2;      // r_s^2 in FP64 (exact test)
+  float lo, hi;    // FP32 band: r2f < lo accept, r2f >= hi reject, else exact FP64 test
+};
+
+// ---- reductions / status -------------------------------------------------------
+void launch_final_reduce(const double* partials, int nblocks, int nq, double* out, cudaStream_t s);
+void launch_energy_finalize(const double* pe_vir_part, int nb_force, const double* ke_part, int nb_int,
+                            double pe_scale, double* energies, double* log, int64_t log_cap, int64_t* log_count,
+                            double step, cudaStream_t s);
+
+// ---- init ---------------------------------------------------------------------------
+void launch_fcc(double* x, int64_t M, double a, double offset, cudaStream_t s);
+void launch_gaussian(double* v, int64_t N, uint64_t seed, cudaStream_t s);
+void launch_sums3(const double* v, int64_t N, double* partials, int nb, cudaStream_t s);
+void launch_sumsq_centered(const double* v, int64_t N, const double* sums, double* partials, int nb, cudaStream_t s);
+void launch_center_scale(double* v, int64_t N, const double* sums, const double* sumsq, double T, cudaStream_t s);
+int red_blocks(int64_t n);
+
+// ---- grid ---------------------------------------------------------------------------
+void launch_wrap_label(double* x, int32_t* img, int64_t N, Geom g, uint32_t* cell_of, uint32_t* cell_count,
+                       int32_t* status, cudaStream_t s);
+// exclusive scan of n uint32 values into out[0..n] (out[n] = total); tmp >= scan_tmp_words(n)
+size_t scan_tmp_words(int64_t n);
+void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
+void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_t* cell_fill, uint32_t* perm,
+                    int64_t N, cudaStream_t s);
+void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* perm, const int32_t* id,
+                       cudaStream_t s);
+void launch_gather_f64x3(const double* in, double* out, const uint32_t* perm, int64_t N, cudaStream_t s);
+void launch_gather_i32x3(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s);
+void launch_gather_i32(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s);
+void launch_gather_u32(const uint32_t* in, uint32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s);
+void launch_gather_16B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s);
+void launch_gather_32B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s);
+void launch_scatter_back_f64x3(const double* in, double* out_idorder, const int32_t* id, int64_t N,
+                               double sub, cudaStream_t s);
+void launch_scatter_back_f32x4_to_f64x3(const float4* in, double* out, const int32_t* id, int64_t N,
+                                        cudaStream_t s);
+void launch_scatter_back_f64x4_to_f64x3(const dvec4* in, double* out, const int32_t* id, int64_t N,
+                                        cudaStream_t s);
+void launch_scatter_back_i32x3(const int32_t* in, int32_t* out, const int32_t* id, int64_t N, cudaStream_t s);
+void launch_iota_i32(int32_t* id, int64_t N, cudaStream_t s);
+void launch_load_state(const double* x_in, const double* v_in, double* x, double* v, int32_t* id, int32_t* img,
+                       int64_t N, double offset, double L, cudaStream_t s);
+
+// ---- shadow positions ---------------------------------------------------------------
+// mixed: hi/lo FP32 split of x_state; fp64: dvec4 copy.  ref (optional) receives hi
+// (mixed) or the dvec4 (fp64) as the displacement reference.
+void launch_shadow_all(const double* x, int64_t N, int mixed, float4* hi, float4* lo, dvec4* pos64, void* ref,
+                       cudaStream_t s);
+
+// ---- list ---------------------------------------------------------------------------
+void launch_list_count(const void* hi_or_pos, const float4* lo, const double* x, const uint32_t* cell_of,
+                       const uint32_t* cell_start, int64_t N, Geom g, ListBand band, int half, int precision,
+                       uint32_t* row_count, unsigned long long* total64, cudaStream_t s);
+void launch_list_fill(const void* hi_or_pos, const float4* lo, const double* x, const uint32_t* cell_of,
+                      const uint32_t* cell_start, int64_t N, Geom g, ListBand band, int half, int precision,
+                      const uint32_t* row_ptr, uint32_t* col, int32_t* status, cudaStream_t s);
+
+// ---- forces ---------------------------------------------------------------------------
+// Writes F (float4 mixed / dvec4 fp64) and, if energy, per-block partials (pe, vir) into
+// partials[2 * block]; returns the number of blocks used.
+int launch_force(int precision, int half, int lanes, int energy, const void* hi_or_pos, const float4* lo,
+                 const uint32_t* row_ptr, const uint32_t* col, int64_t N, Geom g, LJConst c, void* f,
+                 double* partials, cudaStream_t s);
+
+// ---- integrator ---------------------------------------------------------------------
+struct IntegrateArgs {
+  double kpre;     // kick that brings v to the full step before the kinetic energy is taken
+  double kpost;    // kick after it (the first half-kick of the next step)
+  double dt;       // drift length (0 = no drift)
+  int ke;          // accumulate the kinetic energy of the full-step velocity
+  int shadow;      // rewrite the force kernel's position copy after the drift
+};
+// Returns the number of blocks used for KE partials.
+int launch_integrate(int precision, double* x, double* v, const void* f, void* hi_or_pos, float4* lo,
+                     const void* ref, int64_t N, IntegrateArgs a, double* ke_part, uint32_t* dmax_bits,
+                     int32_t* status, cudaStream_t s);
+
+}  // namespace ljmd

@@ -1,0 +1,280 @@
+"""Thin Python binding of libljmd (declared in include/ljmd.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libljmd.so.  Functions carry the C names (ljmd_create, ...);
+``System`` wraps a handle.  Arrays may be numpy (host) or torch CUDA tensors
+(device, passed by pointer); torch streams are passed as cudaStream_t.
+There is no CPU fallback: if the library cannot be loaded, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libljmd.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ljmd.h")
+
+LJ_OK, LJ_EINVAL, LJ_ENOMEM, LJ_EDEVICE, LJ_ESTATE, LJ_ERANGE = 0, -1, -2, -3, -4, -5
+LJ_FP64, LJ_MIXED = 0, 1
+LJ_LIST_FULL, LJ_LIST_HALF = 0, 1
+LJ_TRUNC_QUADRATIC, LJ_TRUNC_SHIFT, LJ_TRUNC_CUT = 0, 1, 2
+LJ_ST_NONFINITE, LJ_ST_LIST_OVERFLOW, LJ_ST_TIMEOUT, LJ_ST_CELL_RANGE = 1, 2, 4, 8
+
+
+class LjmdError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, ljmd_strerror(code) if _LIB else "?", code))
+
+
+class ljmd_params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("sigma", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("margin", ctypes.c_double), ("truncation", ctypes.c_int32), ("list_form", ctypes.c_int32),
+                ("energy_every", ctypes.c_int32), ("lanes", ctypes.c_int32)]
+
+
+class ljmd_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("steps", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
+                ("list_entries", ctypes.c_int64), ("cells_per_side", ctypes.c_int64), ("box", ctypes.c_double),
+                ("mean_lifetime", ctypes.c_double), ("max_displacement", ctypes.c_double),
+                ("status_word", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_I32, _I64, _U64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+_SIGS = {
+    "ljmd_version": (ctypes.c_int, []),
+    "ljmd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "ljmd_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ljmd_params), _I32, _P]),
+    "ljmd_destroy": (None, [_P]),
+    "ljmd_init_lattice": (ctypes.c_int, [_P, _I64, _D, _D, _U64]),
+    "ljmd_set_state": (ctypes.c_int, [_P, _I64, _D, _P, _P, _I32]),
+    "ljmd_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _I32]),
+    "ljmd_build_pairlist": (ctypes.c_int, [_P, _D, _D]),
+    "ljmd_compute_forces": (ctypes.c_int, [_P]),
+    "ljmd_step": (ctypes.c_int, [_P, _D, _I64]),
+    "ljmd_energies": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ljmd_set_energy_log": (ctypes.c_int, [_P, _P, _I64]),
+    "ljmd_get_pairs": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ljmd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_stats)]),
+}
+
+
+def load(build_if_missing: bool = True):
+    """Load libljmd.so (building it with nvcc first if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH) and build_if_missing:
+        from .build import build
+        build()
+    if not os.path.exists(LIB_PATH):
+        raise OSError("libljmd.so is not built (%s); run paper_1012_2677_gb300/build.py" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions declared in an include/*.h header."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ljmd_\w+)\s*\(", txt)))
+
+
+def _chk(code: int, what: str):
+    if code != LJ_OK:
+        raise LjmdError(code, what)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _arr_ptr(a, dtype, n_expected=None):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor of the given dtype."""
+    if a is None:
+        return None, 0, None
+    if _is_torch(a):
+        import torch
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError("tensor must be contiguous %s" % tdt)
+        if n_expected is not None and a.numel() != n_expected:
+            raise ValueError("tensor has %d elements, expected %d" % (a.numel(), n_expected))
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if n_expected is not None and arr.size != n_expected:
+        raise ValueError("array has %d elements, expected %d" % (arr.size, n_expected))
+    return arr.ctypes.data_as(ctypes.c_void_p), 0, arr
+
+
+# ---- C names -------------------------------------------------------------------------------------
+
+def ljmd_version() -> int:
+    return load().ljmd_version()
+
+
+def ljmd_strerror(code: int) -> str:
+    return load().ljmd_strerror(int(code)).decode()
+
+
+def ljmd_create(params: ljmd_params, precision: int, stream=None):
+    h = _P()
+    s = _stream_handle(stream)
+    _chk(load().ljmd_create(ctypes.byref(h), ctypes.byref(params), int(precision), s), "ljmd_create")
+    return h
+
+
+def ljmd_destroy(h) -> None:
+    if h:
+        load().ljmd_destroy(h)
+
+
+def ljmd_init_lattice(h, cells_per_side: int, density: float, T: float, seed: int) -> None:
+    _chk(load().ljmd_init_lattice(h, int(cells_per_side), float(density), float(T), int(seed) & (2 ** 64 - 1)),
+         "ljmd_init_lattice")
+
+
+def ljmd_set_state(h, n: int, box: float, x, v=None) -> None:
+    px, dx, kx = _arr_ptr(x, np.float64, 3 * n)
+    pv, dv, kv = _arr_ptr(v, np.float64, 3 * n)
+    if v is not None and dv != dx:
+        raise ValueError("x and v must both be host or both be device arrays")
+    _chk(load().ljmd_set_state(h, int(n), float(box), px, pv, dx), "ljmd_set_state")
+
+
+def ljmd_get_state(h, x=None, v=None, f=None, img=None, on_device: int = 0) -> None:
+    ptrs = [_arr_ptr(a, dt)[0] for a, dt in ((x, np.float64), (v, np.float64), (f, np.float64), (img, np.int32))]
+    _chk(load().ljmd_get_state(h, *ptrs, int(on_device)), "ljmd_get_state")
+
+
+def ljmd_build_pairlist(h, cutoff: float, margin: float) -> None:
+    _chk(load().ljmd_build_pairlist(h, float(cutoff), float(margin)), "ljmd_build_pairlist")
+
+
+def ljmd_compute_forces(h) -> None:
+    _chk(load().ljmd_compute_forces(h), "ljmd_compute_forces")
+
+
+def ljmd_step(h, dt: float, nsteps: int) -> None:
+    _chk(load().ljmd_step(h, float(dt), int(nsteps)), "ljmd_step")
+
+
+def ljmd_energies(h):
+    pe, ke, vir = _D(), _D(), _D()
+    _chk(load().ljmd_energies(h, ctypes.byref(pe), ctypes.byref(ke), ctypes.byref(vir)), "ljmd_energies")
+    return pe.value, ke.value, vir.value
+
+
+def ljmd_set_energy_log(h, device_log_ptr, capacity: int) -> None:
+    _chk(load().ljmd_set_energy_log(h, device_log_ptr, int(capacity)), "ljmd_set_energy_log")
+
+
+def ljmd_get_pairs(h):
+    n = _I64()
+    _chk(load().ljmd_get_pairs(h, None, 0, ctypes.byref(n)), "ljmd_get_pairs")
+    out = np.empty((max(n.value, 1), 2), dtype=np.int64)
+    _chk(load().ljmd_get_pairs(h, out.ctypes.data_as(_P), n.value, ctypes.byref(n)), "ljmd_get_pairs")
+    return out[:n.value]
+
+
+def ljmd_get_stats(h) -> dict:
+    st = ljmd_stats()
+    _chk(load().ljmd_get_stats(h, ctypes.byref(st)), "ljmd_get_stats")
+    return {name: getattr(st, name) for name, _ in ljmd_stats._fields_}
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(int(stream.cuda_stream))  # torch.cuda.Stream
+
+
+# ---- object wrapper ------------------------------------------------------------------------------
+
+class System:
+    """One LJ system on the current CUDA device (a handle of libljmd)."""
+
+    def __init__(self, eps=1.0, sigma=1.0, cutoff=2.5, margin=0.5, truncation=LJ_TRUNC_QUADRATIC,
+                 list_form=LJ_LIST_FULL, energy_every=1, lanes=0, precision=LJ_MIXED, stream=None):
+        self.params = ljmd_params(eps, sigma, cutoff, margin, truncation, list_form, energy_every, lanes)
+        self.precision = precision
+        self._keep = []
+        self.h = ljmd_create(self.params, precision, stream)
+        self.n = 0
+        self.box = 0.0
+
+    def close(self):
+        if getattr(self, "h", None):
+            ljmd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init_lattice(self, cells_per_side, density, T, seed):
+        ljmd_init_lattice(self.h, cells_per_side, density, T, seed)
+        st = self.stats()
+        self.n, self.box = st["n"], st["box"]
+
+    def set_state(self, x, v=None, box=None):
+        n = (x.numel() if _is_torch(x) else np.asarray(x).size) // 3
+        ljmd_set_state(self.h, n, float(box), x, v)
+        self.n, self.box = n, float(box)
+
+    def get_state(self):
+        """(x, v, f, img) as numpy arrays in id order."""
+        x = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        f = np.empty((self.n, 3))
+        img = np.empty((self.n, 3), dtype=np.int32)
+        ljmd_get_state(self.h, x, v, f, img, 0)
+        return x, v, f, img
+
+    def build_pairlist(self, cutoff=None, margin=None):
+        ljmd_build_pairlist(self.h, self.params.cutoff if cutoff is None else cutoff,
+                            self.params.margin if margin is None else margin)
+
+    def compute_forces(self):
+        ljmd_compute_forces(self.h)
+
+    def step(self, dt, nsteps=1):
+        ljmd_step(self.h, dt, nsteps)
+
+    def energies(self):
+        return ljmd_energies(self.h)
+
+    def pairs(self):
+        return ljmd_get_pairs(self.h)
+
+    def stats(self):
+        return ljmd_get_stats(self.h)
+
+    def set_energy_log(self, tensor):
+        """Register a float64 CUDA tensor of shape (cap, 4) for (step, pe, ke, virial) records."""
+        if tensor is None:
+            ljmd_set_energy_log(self.h, None, 0)
+            return
+        self._keep = [tensor]
+        ljmd_set_energy_log(self.h, ctypes.c_void_p(tensor.data_ptr()), tensor.shape[0])

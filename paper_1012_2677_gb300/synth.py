@@ -47,3 +47,10 @@ def replica_table(R: int, seed: int, n_range=(500, 50000), rho_range=(0.3, 0.9),
     rho = g.uniform(*rho_range, size=R)
     T = g.uniform(*T_range, size=R)
     return N.astype(np.int64), rho, T
+
+
+def dyadic(x, bits: int = 40) -> np.ndarray:
+    """Round values to multiples of 2^-bits, so that adding a power-of-two offset up to
+    2^(52 - bits) is exact (inputs then survive any offset storage bit for bit)."""
+    s = float(2 ** bits)
+    return np.round(np.asarray(x, dtype=np.float64) * s) / s
