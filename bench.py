@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the LJ Verlet-list MD hot path: particle-steps/s at 16.4M atoms, mixed vs FP64.
+
+One "step" is one velocity-Verlet step of the whole path (kick/drift, displacement check,
+list rebuild when due, force over the list, energy and virial reductions).  Timed with CUDA
+events on the library's stream, inputs resident in HBM (and far larger than L2).  Prints one
+JSON line.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+For N > 1 launch under torch.distributed.run: every rank advances an independent replica
+(the method has no data-path exchange on one box), and the job value is the sum.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LJ particle-steps/s at 16.4M atoms, mixed vs FP64 form; roofline fraction"
+UNIT = "particle-steps/s"
+
+# FCC workloads: M^3 cells x 4 at density rho (L = M (4/rho)^(1/3)), Eq. 2 truncation.
+WORKLOADS = {
+    "fcc16m_rho0.5": dict(M=160, rho=0.5, T=1.0, seed=3, cutoff=2.5, margin=0.5, dt=0.005),
+    "fcc16m_rho0.8": dict(M=160, rho=0.8, T=0.9, seed=4, cutoff=2.5, margin=0.5, dt=0.005),
+    "fcc1m_rho0.5": dict(M=64, rho=0.5, T=1.0, seed=2, cutoff=2.5, margin=0.5, dt=0.005),
+    "fcc4k_rho0.5": dict(M=10, rho=0.5, T=1.0, seed=1, cutoff=2.5, margin=0.5, dt=0.005),
+}
+
+# Nominal FP32 peak of the GPU from its unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_name):
+    """DRAM bytes per launch of the force kernel from the committed ncu summary, if the kernel
+    source is unchanged since it was taken (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "force_kernel_traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1012_2677_gb300", "csrc", "kernels_force.cu")
+    if rec.get("source_sha") != source_sha(src) or rec.get("kernel") != kernel_name:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def force_kernel_work(N, entries, precision, energy=True):
+    """Algorithmic bytes and flops of one force launch over the full list (mixed form):
+    the list entries (4 B), row offsets (4 B), the key particle's hi/lo copy (32 B) and the
+    force written (16 B); partner positions come from L1/L2 thanks to the cell order and
+    count zero.  Flops: 22 per listed pair (Alg. 6), 8 more with the energy and virial."""
+    pos = 32 if precision == "mixed" else 32
+    fout = 16 if precision == "mixed" else 32
+    bytes_ = 4 * entries + N * (4 + pos + fout)
+    flops = entries * (22 + (8 if energy else 0))
+    return bytes_, flops
+
+
+def run_ours(args, wl, world, rank, local):
+    import torch
+    from paper_1012_2677_gb300 import ljmd
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    seed = wl["seed"] + 1000 * rank  # independent replica per rank
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    s = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=ljmd.LJ_MIXED, list_form=ljmd.LJ_LIST_FULL,
+                    energy_every=1, stream=stream)
+    s.init_lattice(wl["M"], wl["rho"], wl["T"], seed)
+    N = s.n
+    s.step(wl["dt"], args.warmup)
+    torch.cuda.synchronize()
+    st0 = s.stats()
+    s.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(wl["dt"], args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    st1 = s.stats()
+    pe, ke, vir = s.energies()
+    s.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * args.steps * world / (ms * 1e-3)
+
+    # dominant kernel: the force kernel (CUDA events around each launch on the library's stream)
+    f_ms = prof["force_ms"] / max(prof["force_launches"], 1)
+    entries = st1["list_entries"]
+    b, fl = force_kernel_work(N, entries, "mixed")
+    peaks, peak_kind = measured_peaks()
+    ach_gbs = b / (f_ms * 1e-3) / 1e9
+    ach_tf = fl / (f_ms * 1e-3) / 1e12
+    hbm_frac = ach_gbs / peaks["hbm_gbs"]
+    alu_frac = ach_tf / FP32_PEAK_TFLOPS
+    kernel_name = "k_force_mixed"
+    traffic = recorded_traffic(kernel_name)
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": round(ach_tf, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                "frac": round(alu_frac, 4), "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "hbm": {"achieved": round(ach_gbs, 1), "peak": peaks["hbm_gbs"], "frac": round(hbm_frac, 4),
+                        "peak_source": peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "traffic": traffic, "peak_source": peak_kind,
+                "alu": {"achieved": round(ach_tf, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "frac": round(alu_frac, 4)}}
+    roof["kernel"] = kernel_name
+    roof["kernel_ms"] = round(f_ms, 4)
+    roof["algorithmic_bytes_per_launch"] = b
+    roof["algorithmic_flops_per_launch"] = fl
+
+    breakdown = {k: round(prof[k], 3) for k in ("force_ms", "integrate_ms", "rebuild_ms", "energy_ms")}
+    breakdown.update({k: prof[k] for k in ("force_launches", "integrate_launches", "rebuilds", "energy_launches")})
+    s.close()
+
+    # FP64 form, same workload (shorter run: it is FP64-pipe bound)
+    fp64 = None
+    if not args.no_fp64:
+        k64 = max(3, args.steps // 20)
+        s64 = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=ljmd.LJ_FP64,
+                          list_form=ljmd.LJ_LIST_HALF, energy_every=1, stream=stream)
+        s64.init_lattice(wl["M"], wl["rho"], wl["T"], seed)
+        s64.step(wl["dt"], 3)
+        torch.cuda.synchronize()
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        s64.step(wl["dt"], k64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms64 = a0.elapsed_time(a1)
+        fp64 = {"value": N * k64 * world / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
+                "list": "half", "speedup_mixed_over_fp64": (ms64 / k64) / (ms / args.steps)}
+        s64.close()
+
+    # end to end through the public API with host buffers: H2D of the initial state from pinned
+    # memory, K steps, D2H of the final state and energies, all inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        s2 = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=ljmd.LJ_MIXED,
+                         list_form=ljmd.LJ_LIST_FULL, energy_every=1, stream=stream)
+        s2.init_lattice(wl["M"], wl["rho"], wl["T"], seed)
+        x0 = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+        v0 = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+        ljmd.ljmd_get_state(s2.h, x0, v0, None, None, 0)
+        xo = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+        vo = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ljmd.ljmd_set_state(s2.h, N, s2.box, x0, v0)
+        s2.step(wl["dt"], args.steps)
+        ljmd.ljmd_get_state(s2.h, xo, vo, None, None, 0)
+        s2.energies()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        barrier()
+        if dist is not None:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": N * args.steps * world / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 24 * N / args.steps, "d2h_bytes_per_step": (2 * 24 * N + 24) / args.steps,
+               "note": "set_state from pinned host + K steps + get_state/energies to host, per K-step job"}
+        s2.close()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 pair arithmetic, f64 state and sums", "data": "synthetic FCC start, Gaussian velocities",
+        "config": {"workload": args.workload, "N": N, "density": wl["rho"], "T": wl["T"], "cutoff": wl["cutoff"],
+                   "margin": wl["margin"], "dt": wl["dt"], "list": "full", "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2 (state and list ~%.1f GB)" % ((N * 250 + 4 * entries) / 1e9)},
+        "roofline": roof,
+        "fp64": fp64,
+        "e2e": e2e,
+        "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+        "clocks": clk,
+        "phases": breakdown,
+        "list": {"entries_per_particle": entries / N, "rebuilds": st1["rebuilds"] - st0["rebuilds"],
+                 "mean_lifetime_steps": args.steps / max(st1["rebuilds"] - st0["rebuilds"], 1)},
+        "energies_final": {"pe_per_particle": pe / N, "ke_per_particle": ke / N, "virial": vir},
+        "pair_interactions_per_s": entries * args.steps * world / (ms * 1e-3),
+    }
+    if rank == 0 and not args.no_cpu_baseline and not args.skip_cpu:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def _oracle_sample_rate(wl, target_s, sample_seed=7):
+    """Oracle (all-pairs FP64) on a sample of the workload: forces on S particles against all N.
+    Returns (particle-steps/s, cores, sample description)."""
+    import numpy as np
+    import oracle as O
+    from paper_1012_2677_gb300 import synth
+    x, L = O.fcc_lattice(wl["M"], wl["rho"])
+    N = len(x)
+    x = O.wrap(x + synth.displacements(N, 0.05, sample_seed), L)
+    p = O.LJParams(rc_over_sigma=wl["cutoff"])
+    idx = synth.subset(N, 64, sample_seed)
+    t0 = time.perf_counter()
+    O.forces_sample(x, L, idx, p)
+    t_small = time.perf_counter() - t0
+    S = int(max(64, min(N, 64 * target_s / max(t_small, 1e-6))))
+    idx = synth.subset(N, S, sample_seed + 1)
+    t0 = time.perf_counter()
+    O.forces_sample(x, L, idx, p)
+    t = time.perf_counter() - t0
+    return S / t, O.num_threads(), "all-pairs FP64 forces on %d of %d particles (%.1f s)" % (S, N, t), t, S
+
+
+def cpu_baseline(wl, seconds):
+    rate, cores, desc, _, _ = _oracle_sample_rate(wl, seconds)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+
+def run_reference(args, wl, world, rank):
+    """The oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle as O
+    from paper_1012_2677_gb300 import synth
+    x, L = O.fcc_lattice(wl["M"], wl["rho"])
+    N = len(x)
+    x = O.wrap(x + synth.displacements(N, 0.05, 7), L)
+    p = O.LJParams(rc_over_sigma=wl["cutoff"])
+    budget = max(30.0, min(150.0, 1.0 * (args.steps + args.warmup)))
+    t0 = time.perf_counter()
+    O.forces_sample(x, L, synth.subset(N, 16, 1), p)
+    per_particle = (time.perf_counter() - t0) / 16
+    S = int(max(4, min(N, budget / (args.steps + args.warmup) / max(per_particle, 1e-9))))
+    for w in range(args.warmup):
+        O.forces_sample(x, L, synth.subset(N, S, 100 + w), p)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.forces_sample(x, L, synth.subset(N, S, 1000 + k), p)
+    t = time.perf_counter() - t0
+    value = S * args.steps / t
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic FCC start",
+        "config": {"workload": args.workload, "N": N, "density": wl["rho"], "cutoff": wl["cutoff"],
+                   "margin": wl["margin"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": "each step: all-pairs FP64 forces on %d of %d particles" % (S, N)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="fcc16m_rho0.5", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        out = run_reference(args, wl, world, rank)
+    else:
+        out = run_ours(args, wl, world, rank, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

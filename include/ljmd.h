@@ -82,7 +82,20 @@ typedef struct ljmd_stats {
   double max_displacement; /* largest displacement since the last rebuild, at the last check */
   int32_t status_word;     /* LJ_ST_* bits raised on the device (synchronises) */
   int32_t precision;       /* LJ_FP64 / LJ_MIXED */
+  int64_t kernel_launches; /* CUDA kernels this handle has launched */
 } ljmd_stats;
+
+/* Per-phase device time (CUDA events on the handle's stream), accumulated while profiling is on. */
+typedef struct ljmd_profile {
+  double force_ms;         /* force kernel (Alg. 4-6) */
+  int64_t force_launches;
+  double integrate_ms;     /* velocity-Verlet kernel (kick, drift, displacement max, KE) */
+  int64_t integrate_launches;
+  double rebuild_ms;       /* fold + cell sort + reorder + two-pass list build */
+  int64_t rebuilds;
+  double energy_ms;        /* final energy reductions */
+  int64_t energy_launches;
+} ljmd_profile;
 
 typedef struct ljmd_sys ljmd_sys;
 
@@ -188,6 +201,16 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
 
 /* Counters and state of the handle (synchronises the stream). */
 int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out);
+
+/*
+ * Turn per-phase timing on (enable = 1, resets the accumulators) or off (0).  While on, CUDA
+ * events are recorded on the handle's stream around every force, integrate, rebuild and
+ * energy launch; the kernels themselves are unchanged.
+ */
+int ljmd_set_profiling(ljmd_sys* sys, int32_t enable);
+
+/* Accumulated per-phase device times since profiling was enabled (synchronises the stream). */
+int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out);
 
 /* Human-readable name of a status code. */
 const char* ljmd_strerror(int code);

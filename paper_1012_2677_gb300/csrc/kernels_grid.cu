@@ -116,17 +116,18 @@ size_t scan_tmp_words(int64_t n) {
   return words + 1;
 }
 
-void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s) {
+int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s) {
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles <= 1) {
     k_tile_scan<<<1, 256, 0, s>>>(in, n, nullptr, out);
-    return;
+    return 1;
   }
   uint32_t* sums = tmp;                // [tiles]
   uint32_t* base = tmp + tiles;        // [tiles + 1]
   k_tile_sums<<<(int)tiles, 256, 0, s>>>(in, n, sums);
-  launch_scan_u32(sums, base, tiles, tmp + 2 * tiles + 1, s);
+  const int inner = launch_scan_u32(sums, base, tiles, tmp + 2 * tiles + 1, s);
   k_tile_scan<<<(int)tiles, 256, 0, s>>>(in, n, base, out);
+  return inner + 2;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -63,6 +63,13 @@ struct ljmd_sys {
   int32_t* d_status = nullptr;
   uint32_t* d_dmax = nullptr;
   unsigned long long* d_total64 = nullptr;
+  // profiling: event pairs per phase, resolved when the profile is read
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;  // (phase, (start, stop))
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_n[4] = {0, 0, 0, 0};
+  int64_t launches = 0;
   // pinned host mirrors
   uint32_t* h_u32 = nullptr;
   double* h_f64 = nullptr;
@@ -110,9 +117,62 @@ static void free_all(ljmd_sys* s) {
                   s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& p : s->ev_pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   if (s->h_u32) cudaFreeHost(s->h_u32);
   if (s->h_f64) cudaFreeHost(s->h_f64);
   if (s->h_i32) cudaFreeHost(s->h_i32);
+}
+
+enum { PH_FORCE = 0, PH_INTEGRATE = 1, PH_REBUILD = 2, PH_ENERGY = 3 };
+
+static cudaEvent_t ev_get(ljmd_sys* s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Scoped phase timer: records a start event now and a stop event at scope exit (profiling only).
+struct PhaseTimer {
+  ljmd_sys* s;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(ljmd_sys* s_, int ph) : s(s_), phase(ph) {
+    if (s->profiling && (a = ev_get(s))) cudaEventRecord(a, s->st);
+  }
+  ~PhaseTimer() {
+    if (!a) return;
+    cudaEvent_t b = ev_get(s);
+    if (!b) return;
+    cudaEventRecord(b, s->st);
+    s->ev_pending.push_back({phase, {a, b}});
+  }
+};
+
+static void resolve_events(ljmd_sys* s) {
+  for (auto& p : s->ev_pending) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(p.second.second) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+      s->prof_ms[p.first] += ms;
+      s->prof_n[p.first] += 1;
+    }
+    cudaGetLastError();
+    s->ev_pool.push_back(p.second.first);
+    s->ev_pool.push_back(p.second.second);
+  }
+  s->ev_pending.clear();
 }
 
 // Coefficients of the additive truncation terms of Eq. 2 (Sec. 2.1), from V(r_c) = V'(r_c) = 0
@@ -280,10 +340,13 @@ static int rebuild(ljmd_sys* s) {
   const int64_t N = s->n;
   cudaStream_t st = s->st;
   TRY(ensure_cells(s));
+  PhaseTimer timer(s, PH_REBUILD);
+  // wrap_label, scatter, cell_order, 6 gathers, shadow, list count, list fill (+ the scans below)
+  s->launches += 12;
   CK(cudaMemsetAsync(s->cell_count, 0, sizeof(uint32_t) * s->ncells, st));
   launch_wrap_label(s->x, s->img, N, s->g, s->cell_of, s->cell_count, s->d_status, st);
   CKL();
-  launch_scan_u32(s->cell_count, s->cell_start, s->ncells, s->scan_tmp, st);
+  s->launches += launch_scan_u32(s->cell_count, s->cell_start, s->ncells, s->scan_tmp, st);
   CKL();
   CK(cudaMemsetAsync(s->cell_fill, 0, sizeof(uint32_t) * s->ncells, st));
   launch_scatter(s->cell_of, s->cell_start, s->cell_fill, s->perm, N, st);
@@ -309,7 +372,7 @@ static int rebuild(ljmd_sys* s) {
   launch_list_count(s->hi, s->lo, s->x, s->cell_of, s->cell_start, N, s->g, s->band, half, s->precision, s->row_cnt,
                     s->d_total64, st);
   CKL();
-  launch_scan_u32(s->row_cnt, s->row_ptr, N, s->scan_tmp, st);
+  s->launches += launch_scan_u32(s->row_cnt, s->row_ptr, N, s->scan_tmp, st);
   CKL();
   CK(cudaMemcpyAsync(s->h_u32, s->row_ptr + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->h_u32 + 2, s->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -336,14 +399,35 @@ static int rebuild(ljmd_sys* s) {
 
 static void* force_pos(ljmd_sys* s) { return s->precision == LJ_MIXED ? (void*)s->hi : (void*)s->pos64; }
 
+static int integrate(ljmd_sys* s, IntegrateArgs a) {
+  PhaseTimer timer(s, PH_INTEGRATE);
+  s->launches += 1;
+  return launch_integrate(s->precision, s->x, s->v, s->f, force_pos(s), s->lo, s->ref, s->n, a, s->part_ke, s->d_dmax,
+                          s->d_status, s->st);
+}
+
+static void energy_record(ljmd_sys* s, int nb_ke, bool to_log) {
+  PhaseTimer timer(s, PH_ENERGY);
+  s->launches += 1;
+  const double scale = s->prm.list_form == LJ_LIST_FULL ? 0.5 : 1.0;
+  launch_energy_finalize(s->part_force, s->nb_force, s->part_ke, nb_ke, scale, s->d_energies,
+                         to_log ? s->log_ptr : nullptr, to_log ? s->log_cap : 0, s->d_log_count, (double)s->steps,
+                         s->st);
+  s->energy_step = s->steps;
+}
+
 static int run_force(ljmd_sys* s, bool energy) {
   ljmd_sys* sys = s;
   const int half = s->prm.list_form == LJ_LIST_HALF;
   if (half) CK(cudaMemsetAsync(s->f, 0, (s->precision == LJ_MIXED ? 16 : 32) * (size_t)s->n, s->st));
   int lanes = s->prm.lanes;
   if (lanes == 0) lanes = (s->precision == LJ_MIXED) ? 8 : 8;
-  s->nb_force = launch_force(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->lo, s->row_ptr, s->col,
-                             s->n, s->g, s->c, s->f, s->part_force, s->st);
+  {
+    PhaseTimer timer(s, PH_FORCE);
+    s->nb_force = launch_force(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->lo, s->row_ptr, s->col,
+                               s->n, s->g, s->c, s->f, s->part_force, s->st);
+  }
+  s->launches += 1;
   CKL();
   s->forces_current = true;
   s->pe_step = energy ? s->steps : -1;
@@ -372,14 +456,10 @@ static int finalize_energies_now(ljmd_sys* s) {
   ljmd_sys* sys = s;
   TRY(ensure_forces(s, true));
   IntegrateArgs a{0.0, 0.0, 0.0, 1, 0};
-  const int nb = launch_integrate(s->precision, s->x, s->v, s->f, force_pos(s), s->lo, s->ref, s->n, a, s->part_ke,
-                                  s->d_dmax, s->d_status, s->st);
+  const int nb = integrate(s, a);
   CKL();
-  const double scale = s->prm.list_form == LJ_LIST_FULL ? 0.5 : 1.0;
-  launch_energy_finalize(s->part_force, s->nb_force, s->part_ke, nb, scale, s->d_energies, nullptr, 0, nullptr,
-                         (double)s->steps, s->st);
+  energy_record(s, nb, false);
   CKL();
-  s->energy_step = s->steps;
   return LJ_OK;
 }
 
@@ -571,8 +651,7 @@ int ljmd_compute_forces(ljmd_sys* sys) {
     // displacement since the list was built (shadow copies are current): rebuild if invalid
     IntegrateArgs a{0.0, 0.0, 0.0, 0, 1};
     CK(cudaMemsetAsync(sys->d_dmax, 0, 4, sys->st));
-    launch_integrate(sys->precision, sys->x, sys->v, sys->f, force_pos(sys), sys->lo, sys->ref, sys->n, a,
-                     sys->part_ke, sys->d_dmax, sys->d_status, sys->st);
+    integrate(sys, a);
     CKL();
     TRY(read_dmax(sys, &sys->last_dmax));
     if (sys->last_dmax > sys->disp_limit) TRY(rebuild(sys));
@@ -589,20 +668,16 @@ int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
   auto want_energy = [&](int64_t t) { return ee > 0 && (t % ee) == 0; };
   TRY(ensure_forces(sys, want_energy(sys->steps)));
   const double h = 0.5 * dt;
-  const double scale = sys->prm.list_form == LJ_LIST_FULL ? 0.5 : 1.0;
   cudaStream_t st = sys->st;
   for (int64_t s = 0; s < nsteps; ++s) {
     const bool rec = sys->pe_step == sys->steps && want_energy(sys->steps);
     IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, rec ? 1 : 0, 1};
     CK(cudaMemsetAsync(sys->d_dmax, 0, 4, st));
-    const int nb = launch_integrate(sys->precision, sys->x, sys->v, sys->f, force_pos(sys), sys->lo, sys->ref,
-                                    sys->n, a, sys->part_ke, sys->d_dmax, sys->d_status, st);
+    const int nb = integrate(sys, a);
     CKL();
     if (rec) {
-      launch_energy_finalize(sys->part_force, sys->nb_force, sys->part_ke, nb, scale, sys->d_energies,
-                             sys->log_ptr, sys->log_cap, sys->d_log_count, (double)sys->steps, st);
+      energy_record(sys, nb, true);
       CKL();
-      sys->energy_step = sys->steps;
     }
     sys->steps += 1;
     sys->forces_current = false;
@@ -613,14 +688,11 @@ int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
   // final half-kick: v at the full step of the last state
   const bool rec = sys->pe_step == sys->steps && want_energy(sys->steps);
   IntegrateArgs a{h, 0.0, 0.0, rec ? 1 : 0, 0};
-  const int nb = launch_integrate(sys->precision, sys->x, sys->v, sys->f, force_pos(sys), sys->lo, sys->ref, sys->n,
-                                  a, sys->part_ke, sys->d_dmax, sys->d_status, st);
+  const int nb = integrate(sys, a);
   CKL();
   if (rec) {
-    launch_energy_finalize(sys->part_force, sys->nb_force, sys->part_ke, nb, scale, sys->d_energies, sys->log_ptr,
-                           sys->log_cap, sys->d_log_count, (double)sys->steps, st);
+    energy_record(sys, nb, true);
     CKL();
-    sys->energy_step = sys->steps;
   }
   return check_status(sys);
 }
@@ -693,6 +765,7 @@ int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
   out->mean_lifetime = sys->rebuilds > 0 ? (double)sys->steps / (double)sys->rebuilds : 0.0;
   out->max_displacement = sys->last_dmax;
   out->precision = sys->precision;
+  out->kernel_launches = sys->launches;
   if (sys->broken) {
     out->status_word = -1;
     return LJ_EDEVICE;
@@ -700,6 +773,33 @@ int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
   int32_t w = 0;
   TRY(device_status(sys, &w));
   out->status_word = w;
+  return LJ_OK;
+}
+
+int ljmd_set_profiling(ljmd_sys* sys, int32_t enable) {
+  if (!sys) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  resolve_events(sys);
+  sys->profiling = enable != 0;
+  for (int k = 0; k < 4; ++k) {
+    sys->prof_ms[k] = 0.0;
+    sys->prof_n[k] = 0;
+  }
+  return LJ_OK;
+}
+
+int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out) {
+  if (!sys || !out) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  resolve_events(sys);
+  out->force_ms = sys->prof_ms[PH_FORCE];
+  out->force_launches = sys->prof_n[PH_FORCE];
+  out->integrate_ms = sys->prof_ms[PH_INTEGRATE];
+  out->integrate_launches = sys->prof_n[PH_INTEGRATE];
+  out->rebuild_ms = sys->prof_ms[PH_REBUILD];
+  out->rebuilds = sys->prof_n[PH_REBUILD];
+  out->energy_ms = sys->prof_ms[PH_ENERGY];
+  out->energy_launches = sys->prof_n[PH_ENERGY];
   return LJ_OK;
 }
 

@@ -68,7 +68,8 @@ void launch_wrap_label(double* x, int32_t* img, int64_t N, Geom g, uint32_t* cel
                        int32_t* status, cudaStream_t s);
 // exclusive scan of n uint32 values into out[0..n] (out[n] = total); tmp >= scan_tmp_words(n)
 size_t scan_tmp_words(int64_t n);
-void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
+// returns the number of kernels launched
+int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
 void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_t* cell_fill, uint32_t* perm,
                     int64_t N, cudaStream_t s);
 void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* perm, const int32_t* id,

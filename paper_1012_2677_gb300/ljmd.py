@@ -41,7 +41,15 @@ class ljmd_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("steps", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
                 ("list_entries", ctypes.c_int64), ("cells_per_side", ctypes.c_int64), ("box", ctypes.c_double),
                 ("mean_lifetime", ctypes.c_double), ("max_displacement", ctypes.c_double),
-                ("status_word", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("status_word", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+class ljmd_profile(ctypes.Structure):
+    _fields_ = [("force_ms", ctypes.c_double), ("force_launches", ctypes.c_int64),
+                ("integrate_ms", ctypes.c_double), ("integrate_launches", ctypes.c_int64),
+                ("rebuild_ms", ctypes.c_double), ("rebuilds", ctypes.c_int64),
+                ("energy_ms", ctypes.c_double), ("energy_launches", ctypes.c_int64)]
 
 
 _LIB = None
@@ -62,6 +70,8 @@ _SIGS = {
     "ljmd_set_energy_log": (ctypes.c_int, [_P, _P, _I64]),
     "ljmd_get_pairs": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_stats)]),
+    "ljmd_set_profiling": (ctypes.c_int, [_P, _I32]),
+    "ljmd_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_profile)]),
 }
 
 
@@ -194,6 +204,16 @@ def ljmd_get_stats(h) -> dict:
     return {name: getattr(st, name) for name, _ in ljmd_stats._fields_}
 
 
+def ljmd_set_profiling(h, enable: bool) -> None:
+    _chk(load().ljmd_set_profiling(h, 1 if enable else 0), "ljmd_set_profiling")
+
+
+def ljmd_get_profile(h) -> dict:
+    pr = ljmd_profile()
+    _chk(load().ljmd_get_profile(h, ctypes.byref(pr)), "ljmd_get_profile")
+    return {name: getattr(pr, name) for name, _ in ljmd_profile._fields_}
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -270,6 +290,12 @@ class System:
 
     def stats(self):
         return ljmd_get_stats(self.h)
+
+    def set_profiling(self, enable=True):
+        ljmd_set_profiling(self.h, enable)
+
+    def profile(self):
+        return ljmd_get_profile(self.h)
 
     def set_energy_log(self, tensor):
         """Register a float64 CUDA tensor of shape (cap, 4) for (step, pe, ke, virial) records."""
