@@ -1,0 +1,841 @@
+// Cell-column tiles staged in shared memory: pair-list construction (Alg. 1 over the grid of
+// Sec. 2.2, stored as the sorted list of Sec. 2.4) and the force over that list (Alg. 4-6).
+//
+// A tile is T consecutive cells along z of one (cx, cy) column.  Its CTA stages the particles
+// of the 9 neighbouring columns over the cells z0-1 .. z0+T (9 (T+2) cells, wrapped
+// periodically) into shared memory, adding each cell's periodic image shift (-L, 0, +L per
+// axis).  Mixed form: the copies are the hi/lo FP32 split of the stored FP64 coordinates and
+// the shift is split the same way, so hi + shift_hi is exact and a partner difference
+// d = (hi_j - hi_i) + (lo_j - lo_i) carries one rounding.  FP64 form: the FP64 coordinates,
+// with the shift kept aside and added to the exact difference.
+//
+// The list holds 16-bit indices into the key particle's staged tile; rows are (start, length)
+// per particle, and the rows of one tile form one contiguous segment (recorded per tile), so
+// the force kernel loads the tile's rows and its whole list segment into shared memory with
+// the positions, in two dependent rounds of fully parallel loads.  If the box has fewer than
+// 3 cells per side, the whole box is one tile (all particles, no shifts, image per pair).
+//
+// List construction: a warp per key particle tests its 27 neighbour cells from shared memory
+// in chunks of 32 (FP32 hi differences, which are exact, so r^2 is within a bounded error of
+// the FP64 value; inside that band the FP64 no-FMA test of the oracle decides, and the pair
+// set equals brute force bit for bit).  Ballots are kept in shared memory; one atomic per tile
+// reserves the tile's segment; the entries are written with ballot compaction.
+#include "common.cuh"
+
+namespace ljmd {
+
+constexpr int kTileThreads = 256;
+constexpr int kWarps = kTileThreads / 32;
+constexpr int kMaxCells = 9 * (kMaxTileT + 2);
+
+struct TileInfo {
+  int cx, cy, z0, Tp;
+};
+
+__device__ __forceinline__ TileInfo tile_info(int64_t t64, const TileArgs& ta) {
+  TileInfo ti;
+  const unsigned t = (unsigned)t64;  // tiles < 2^31 (n <= 1024)
+  const unsigned tz = t % (unsigned)ta.ntz;
+  const unsigned r = t / (unsigned)ta.ntz;
+  ti.cy = (int)(r % (unsigned)ta.n);
+  ti.cx = (int)(r / (unsigned)ta.n);
+  ti.z0 = (int)tz * ta.T;
+  ti.Tp = min(ta.T, ta.n - ti.z0);
+  return ti;
+}
+
+// Shared bookkeeping of one staged tile.
+struct TileShared {
+  int offq[kMaxCells + 1];  // staged index of the first particle of cell q = k (Tp+2) + m
+  int g0[kMaxCells];        // sorted (global) index of the first particle of cell q
+  int ncol, ncell, total;   // cells per column, staged cells, staged particles
+  int own0, own1;           // staged range of the tile's own particles
+  int gown0;                // sorted index of the first own particle
+  unsigned list_base, list_len;
+};
+
+// Wrapped coordinate and image shift (-1, 0, +1) of a neighbour cell index.
+__device__ __forceinline__ int wrap_cell(int c, int n, int& shift) {
+  shift = 0;
+  if (c < 0) {
+    c += n;
+    shift = -1;
+  } else if (c >= n) {
+    c -= n;
+    shift = 1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t cell_of_q(const TileInfo& ti, int n, int ncol, int q, int& sx, int& sy, int& sz) {
+  const int k = q / ncol, m = q - (q / ncol) * ncol;
+  const int X = wrap_cell(ti.cx + k / 3 - 1, n, sx);
+  const int Y = wrap_cell(ti.cy + k % 3 - 1, n, sy);
+  const int Z = wrap_cell(ti.z0 - 1 + m, n, sz);
+  return ((uint32_t)X * (uint32_t)n + (uint32_t)Y) * (uint32_t)n + (uint32_t)Z;
+}
+
+// Round 1: cell bounds of the tile's 9 (Tp + 2) staged cells, then their prefix (one warp).
+// Returns false (all threads) if the tile exceeds the staged capacity.
+__device__ __forceinline__ bool stage_offsets(const TileInfo& ti, const TileArgs& ta, const uint32_t* __restrict__ cs,
+                                              TileShared& S) {
+  const int ncol = ti.Tp + 2;
+  const int ncell = 9 * ncol;
+  for (int q = threadIdx.x; q < ncell; q += blockDim.x) {
+    int sx, sy, sz;
+    const uint32_t c = cell_of_q(ti, ta.n, ncol, q, sx, sy, sz);
+    const uint32_t a = cs[c], b = cs[c + 1];
+    S.g0[q] = (int)a;
+    S.offq[q + 1] = (int)(b - a);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int run = 0;
+    for (int base = 0; base < ncell; base += 32) {
+      const int q = base + lane;
+      const int v = q < ncell ? S.offq[q + 1] : 0;
+      int inc = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (q < ncell) S.offq[q + 1] = run + inc;
+      run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      S.offq[0] = 0;
+      S.ncol = ncol;
+      S.ncell = ncell;
+      S.total = run;
+      S.own0 = S.offq[4 * ncol + 1];
+      S.own1 = S.offq[4 * ncol + ti.Tp + 1];
+      S.gown0 = S.g0[4 * ncol + 1];
+    }
+  }
+  __syncthreads();
+  return S.total <= ta.max_staged;
+}
+
+// Staged cell of staged slot s: the largest q with offq[q] <= s.
+__device__ __forceinline__ int slot_cell(const TileShared& S, int s) {
+  int lo = 0, hi = S.ncell - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (S.offq[mid] <= s) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Round 2: copy every staged particle with its image shift (one independent load per slot).
+// MIXED: hi (and lo if WANT_LO) as float4; FP64: dvec4 with w = shift code
+// (sx + 1) + 3 (sy + 1) + 9 (sz + 1).
+template <bool MIXED, bool WANT_LO>
+__device__ __forceinline__ void stage_copy(const TileInfo& ti, const TileArgs& ta, const Geom& g,
+                                           const void* __restrict__ pos, const float4* __restrict__ lo,
+                                           const TileShared& S, void* sh_pos, float4* sh_lo, int* sh_gid) {
+  for (int s = threadIdx.x; s < S.total; s += blockDim.x) {
+    const int q = slot_cell(S, s);
+    int sx, sy, sz;
+    cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
+    const int gi = S.g0[q] + (s - S.offq[q]);
+    if (MIXED) {
+      float4 h = ((const float4*)pos)[gi];
+      h.x = fmaf((float)sx, g.L_hi, h.x);  // exact
+      h.y = fmaf((float)sy, g.L_hi, h.y);
+      h.z = fmaf((float)sz, g.L_hi, h.z);
+      ((float4*)sh_pos)[s] = h;
+      if (WANT_LO) {
+        float4 l = lo[gi];
+        l.x = fmaf((float)sx, g.L_lo, l.x);
+        l.y = fmaf((float)sy, g.L_lo, l.y);
+        l.z = fmaf((float)sz, g.L_lo, l.z);
+        sh_lo[s] = l;
+      }
+    } else {
+      dvec4 p = ((const dvec4*)pos)[gi];
+      p.w = (double)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
+      ((dvec4*)sh_pos)[s] = p;
+    }
+    sh_gid[s] = gi;
+  }
+}
+
+// Whole box as one tile (fewer than 3 cells per side): everything staged, no shifts.
+template <bool MIXED, bool WANT_LO>
+__device__ __forceinline__ void stage_whole(int64_t N, const void* __restrict__ pos, const float4* __restrict__ lo,
+                                            TileShared& S, void* sh_pos, float4* sh_lo, int* sh_gid) {
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    if (MIXED) {
+      ((float4*)sh_pos)[e] = ((const float4*)pos)[e];
+      if (WANT_LO) sh_lo[e] = lo[e];
+    } else {
+      dvec4 p = ((const dvec4*)pos)[e];
+      p.w = 13.0;  // no shift
+      ((dvec4*)sh_pos)[e] = p;
+    }
+    sh_gid[e] = e;
+  }
+  if (threadIdx.x == 0) {
+    S.ncol = 1;
+    S.ncell = 1;
+    S.total = (int)N;
+    S.own0 = 0;
+    S.own1 = (int)N;
+    S.gown0 = 0;
+    S.offq[0] = 0;
+    S.offq[1] = (int)N;
+  }
+}
+
+// Image shift of an FP64 staged copy (decoded from w), times L.
+__device__ __forceinline__ void shift_of(double w, const Geom& g, double& sx, double& sy, double& sz) {
+  const int code = (int)w;
+  sx = (double)(code % 3 - 1) * g.L;
+  sy = (double)((code / 3) % 3 - 1) * g.L;
+  sz = (double)(code / 9 - 1) * g.L;
+}
+
+// Exact list test of the oracle (FP64, fixed min-image formula, no FMA) on stored coordinates.
+__device__ __forceinline__ bool pair_in_exact(const double* __restrict__ x, int64_t N, int i, int j, const Geom& g,
+                                              double rs2) {
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = __dsub_rn(x[k * N + j], x[k * N + i]);
+    if (t > g.half_L) t = __dsub_rn(t, g.L);
+    else if (t < -g.half_L) t = __dadd_rn(t, g.L);
+    d[k] = t;
+  }
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+  return r2 < rs2;
+}
+
+// Candidate test in FP32 on staged copies (exact hi differences for the mixed form; the FP64
+// form rounds its exact difference), then the exact FP64 test inside the band.
+template <bool MIXED, bool WHOLE>
+__device__ __forceinline__ bool candidate_in(const void* sh_pos, int li, int lj, const int* sh_gid,
+                                             const double* __restrict__ x, int64_t N, const Geom& g,
+                                             const ListBand& band) {
+  float r2;
+  if (MIXED) {
+    const float4 a = ((const float4*)sh_pos)[li], b = ((const float4*)sh_pos)[lj];
+    float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;  // exact
+    if (WHOLE) {
+      dx = fmaf(-rintf(dx * g.inv_L), g.L_hi, dx);
+      dy = fmaf(-rintf(dy * g.inv_L), g.L_hi, dy);
+      dz = fmaf(-rintf(dz * g.inv_L), g.L_hi, dz);
+    }
+    r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  } else {
+    const dvec4 a = ((const dvec4*)sh_pos)[li], b = ((const dvec4*)sh_pos)[lj];
+    double dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;  // exact
+    if (!WHOLE) {
+      double sx, sy, sz;
+      shift_of(b.w, g, sx, sy, sz);
+      dx += sx;
+      dy += sy;
+      dz += sz;
+    } else {
+      dx = fma(-rint(dx * g.inv_L64), g.L, dx);
+      dy = fma(-rint(dy * g.inv_L64), g.L, dy);
+      dz = fma(-rint(dz * g.inv_L64), g.L, dz);
+    }
+    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+    r2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+  }
+  if (r2 < band.lo) return true;
+  if (r2 >= band.hi) return false;
+  return pair_in_exact(x, N, sh_gid[li], sh_gid[lj], g, band.rs2);
+}
+
+__device__ __forceinline__ int own_cell(const TileShared& S, int l, int Tp) {
+  const int base = 4 * S.ncol;
+  int m = 1;
+  while (m < Tp && l >= S.offq[base + m + 1]) ++m;
+  return m;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Shared-memory layout of the list kernel: staged copies, sorted indices, per-own counts,
+// prefixes and chunk ballots.
+size_t list_smem_bytes(const TileArgs& ta, int precision) {
+  const size_t ps = precision == LJ_MIXED ? 16 : 32;
+  size_t b = (ps + 4) * (size_t)ta.max_staged + 8 * (size_t)ta.max_own + 4 * (size_t)ta.max_own * ta.max_chunks;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <bool MIXED, bool HALF, bool WHOLE>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_list_tile(const void* __restrict__ pos, const double* __restrict__ x, const uint32_t* __restrict__ cs, int64_t N,
+                Geom g, TileArgs ta, ListBand band, uint2* __restrict__ rows, uint2* __restrict__ tile_list,
+                uint16_t* __restrict__ ent, uint64_t cap, unsigned long long* __restrict__ counter,
+                unsigned int* __restrict__ max_list, int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileShared S;
+  __shared__ int s_ok;
+  __shared__ unsigned int s_base;
+  const int ms = ta.max_staged;
+  void* sh_pos = smem;
+  int* sh_gid = (int*)(smem + (MIXED ? 16 : 32) * (size_t)ms);
+  int* s_cnt = sh_gid + ms;                           // [max_own]
+  int* s_pre = s_cnt + ta.max_own;                    // [max_own]
+  uint32_t* masks = (uint32_t*)(s_pre + ta.max_own);  // [max_own * max_chunks]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+
+  for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
+    TileInfo ti{0, 0, 0, 1};
+    if (WHOLE) {
+      stage_whole<MIXED, false>(N, pos, nullptr, S, sh_pos, nullptr, sh_gid);
+    } else {
+      ti = tile_info(t, ta);
+      if (!stage_offsets(ti, ta, cs, S)) {
+        if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
+        __syncthreads();
+        continue;
+      }
+      stage_copy<MIXED, false>(ti, ta, g, pos, nullptr, S, sh_pos, nullptr, sh_gid);
+    }
+    __syncthreads();
+    const int n_own = S.own1 - S.own0;
+    const int nk = WHOLE ? 1 : 9;
+    if (n_own > ta.max_own) {  // sizing inconsistency: record and skip the tile
+      if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
+      __syncthreads();
+      continue;
+    }
+    // phase 1: test, keep ballots, count
+    for (int o = warp; o < n_own; o += kWarps) {
+      const int l = S.own0 + o;
+      const int gi = sh_gid[l];
+      const int m = WHOLE ? 0 : own_cell(S, l, ti.Tp);
+      int cnt = 0, c = 0;
+      for (int k = 0; k < nk; ++k) {
+        const int a = WHOLE ? 0 : S.offq[k * S.ncol + m - 1], b = WHOLE ? S.total : S.offq[k * S.ncol + m + 2];
+        for (int base = a; base < b; base += 32) {
+          const int j = base + lane;
+          bool in = false;
+          if (j < b && j != l && (!HALF || sh_gid[j] > gi))
+            in = candidate_in<MIXED, WHOLE>(sh_pos, l, j, sh_gid, x, N, g, band);
+          const unsigned msk = __ballot_sync(0xffffffffu, in);
+          if (lane == 0 && c < ta.max_chunks) masks[o * ta.max_chunks + c] = msk;
+          ++c;
+          cnt += __popc(msk);
+        }
+      }
+      if (lane == 0) s_cnt[o] = (c <= ta.max_chunks) ? cnt : -1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // exclusive prefix of the row sizes; one atomic reserves the tile's segment
+      unsigned run = 0;
+      bool ok = true;
+      for (int base = 0; base < n_own; base += 32) {
+        const int o = base + lane;
+        const int v0 = o < n_own ? s_cnt[o] : 0;
+        ok = ok && __all_sync(0xffffffffu, v0 >= 0);
+        const unsigned v = v0 > 0 ? (unsigned)v0 : 0u;
+        unsigned inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, inc, d);
+          if (lane >= d) inc += y;
+        }
+        if (o < n_own) s_pre[o] = (int)(run + inc - v);
+        run += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) {
+        const unsigned long long b = atomicAdd(counter, (unsigned long long)run);
+        const bool fits = ok && (b + run <= cap);
+        s_base = (unsigned)b;
+        s_ok = fits;
+        tile_list[t] = fits ? make_uint2((unsigned)b, run) : make_uint2(0u, 0u);
+        atomicMax(max_list, run);
+        if (!ok) atomicOr(status, LJ_ST_CELL_RANGE);
+      }
+    }
+    __syncthreads();
+    // phase 2: rows and entries
+    for (int o = warp; o < n_own; o += kWarps) {
+      const int l = S.own0 + o;
+      const int gi = sh_gid[l];
+      const int m = WHOLE ? 0 : own_cell(S, l, ti.Tp);
+      const unsigned start = s_base + (unsigned)s_pre[o];
+      if (lane == 0) rows[gi] = s_ok ? make_uint2(start, (unsigned)s_cnt[o]) : make_uint2(0u, 0u);
+      if (!s_ok) continue;
+      unsigned p = start;
+      int c = 0;
+      for (int k = 0; k < nk; ++k) {
+        const int a = WHOLE ? 0 : S.offq[k * S.ncol + m - 1], b = WHOLE ? S.total : S.offq[k * S.ncol + m + 2];
+        for (int base = a; base < b; base += 32) {
+          const unsigned msk = masks[o * ta.max_chunks + c];
+          ++c;
+          if ((msk >> lane) & 1u) ent[p + __popc(msk & lt)] = (uint16_t)(base + lane);
+          p += __popc(msk);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+template <int LANES>
+__device__ __forceinline__ float gsum(float v) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int LANES>
+__device__ __forceinline__ double gsum(double v) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Shared-memory layout of the force kernel: staged copies (32 B each), sorted indices, the
+// tile's rows (relative starts) and its list segment.
+static __host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+size_t force_smem_bytes(const TileArgs& ta) {
+  size_t b = align16(36 * (size_t)ta.max_staged) + 8 * (size_t)ta.max_own;
+  if (!ta.whole) b += 2 * (size_t)ta.max_list;
+  return align16(b);
+}
+
+// Force over the staged tile.  Pair math (Alg. 6 in eps/sigma form):
+//   f = ri2 s3i (24 eps - 48 eps s3i) + 8 eps c2 / sigma^2, zero for r^2 >= r_c^2 (select)
+//   V = 4 eps [s3i (s3i - 1) + c2 r^2 / sigma^2 + c0],  W += -f r^2
+template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_force_tile(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
+                 int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows,
+                 const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent, void* __restrict__ fout,
+                 double* __restrict__ part, int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileShared S;
+  const int ms = ta.max_staged;
+  void* sh_pos = smem;
+  float4* sh_lo = (float4*)(smem + 16 * (size_t)ms);
+  int* sh_gid = (int*)(smem + 32 * (size_t)ms);
+  uint2* s_rows = (uint2*)(smem + align16(36 * (size_t)ms));  // [max_own], starts relative to the segment
+  uint16_t* s_ent = (uint16_t*)(s_rows + ta.max_own);  // [max_list]
+  const int lane = threadIdx.x & (LANES - 1);
+  const int grp = threadIdx.x / LANES;
+  constexpr int kGroups = kTileThreads / LANES;
+  const double f24d = 24.0 * c.eps, f48d = 48.0 * c.eps, f8c2d = 8.0 * c.eps * c.c2 / c.sig2;
+  const double e4d = 4.0 * c.eps, c2sd = c.c2 / c.sig2;
+  double pe_acc = 0.0, vir_acc = 0.0;
+
+  for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
+    if (WHOLE) {
+      stage_whole<MIXED, true>(N, pos, lo, S, sh_pos, sh_lo, sh_gid);
+    } else {
+      const TileInfo ti = tile_info(t, ta);
+      if (threadIdx.x == blockDim.x - 1) {
+        const uint2 tl = tile_list[t];
+        S.list_base = tl.x;
+        S.list_len = tl.y;
+      }
+      if (!stage_offsets(ti, ta, cs, S)) {
+        if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
+        __syncthreads();
+        continue;
+      }
+      stage_copy<MIXED, true>(ti, ta, g, pos, lo, S, sh_pos, sh_lo, sh_gid);
+      const int n_own = S.own1 - S.own0;
+      const bool fits = n_own <= ta.max_own && S.list_len <= (unsigned)ta.max_list;
+      for (int o = threadIdx.x; o < n_own; o += blockDim.x) {
+        const uint2 r = rows[S.gown0 + o];
+        const bool ok = fits && r.x >= S.list_base && r.x - S.list_base + r.y <= S.list_len;
+        s_rows[o] = ok ? make_uint2(r.x - S.list_base, r.y) : make_uint2(0u, 0u);
+        if (!ok) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+      }
+      if (fits)
+        for (unsigned e = threadIdx.x; e < S.list_len; e += blockDim.x) s_ent[e] = ent[S.list_base + e];
+    }
+    __syncthreads();
+    const int n_own = S.own1 - S.own0;
+    for (int o = grp; __any_sync(0xffffffffu, o < n_own); o += kGroups) {
+      const bool valid = o < n_own;
+      float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, vir = 0.f;
+      double dfx = 0.0, dfy = 0.0, dfz = 0.0, dpe = 0.0, dvir = 0.0;
+      int gi = 0;
+      if (valid) {
+        const int l = S.own0 + o;
+        gi = sh_gid[l];
+        uint2 row;
+        const uint16_t* el;
+        if (WHOLE) {
+          row = rows[gi];
+          el = ent;
+        } else {
+          row = s_rows[o];
+          el = s_ent;
+        }
+        if (MIXED) {
+          const float4 hi_i = ((const float4*)sh_pos)[l], lo_i = sh_lo[l];
+          for (unsigned e = lane; e < row.y; e += LANES) {
+            const int j = el[row.x + e];
+            if (j >= S.total) {  // inconsistent list: record and skip
+              atomicOr(status, LJ_ST_LIST_OVERFLOW);
+              continue;
+            }
+            const float4 hj = ((const float4*)sh_pos)[j], lj = sh_lo[j];
+            float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;  // exact
+            if (WHOLE) {
+              const float mx = rintf(dx * g.inv_L), my = rintf(dy * g.inv_L), mz = rintf(dz * g.inv_L);
+              dx = fmaf(-mx, g.L_hi, dx) + fmaf(-mx, g.L_lo, lj.x - lo_i.x);
+              dy = fmaf(-my, g.L_hi, dy) + fmaf(-my, g.L_lo, lj.y - lo_i.y);
+              dz = fmaf(-mz, g.L_hi, dz) + fmaf(-mz, g.L_lo, lj.z - lo_i.z);
+            } else {
+              dx += lj.x - lo_i.x;
+              dy += lj.y - lo_i.y;
+              dz += lj.z - lo_i.z;
+            }
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri2 = __frcp_rn(r2);
+            const float si = c.sig2f * ri2;
+            const float s3i = si * si * si;
+            const bool in = r2 < c.rc2f;
+            float ff = fmaf(ri2 * s3i, fmaf(-c.f48, s3i, c.f24), c.f8c2);
+            ff = in ? ff : 0.0f;
+            fx = fmaf(ff, dx, fx);
+            fy = fmaf(ff, dy, fy);
+            fz = fmaf(ff, dz, fz);
+            if (HALF) atomicAdd(&((float4*)fout)[sh_gid[j]], make_float4(-ff * dx, -ff * dy, -ff * dz, 0.0f));
+            if (ENERGY) {
+              const float v = c.e4 * fmaf(s3i, s3i - 1.0f, fmaf(c.c2f, r2, c.c0f));
+              pe += in ? v : 0.0f;
+              vir = fmaf(-ff, r2, vir);
+            }
+          }
+        } else {
+          const dvec4 qi = ((const dvec4*)sh_pos)[l];
+          for (unsigned e = lane; e < row.y; e += LANES) {
+            const int j = el[row.x + e];
+            if (j >= S.total) {  // inconsistent list: record and skip
+              atomicOr(status, LJ_ST_LIST_OVERFLOW);
+              continue;
+            }
+            const dvec4 qj = ((const dvec4*)sh_pos)[j];
+            double dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;  // exact
+            if (!WHOLE) {
+              double sx, sy, sz;
+              shift_of(qj.w, g, sx, sy, sz);
+              dx += sx;
+              dy += sy;
+              dz += sz;
+            } else {
+              dx = fma(-rint(dx * g.inv_L64), g.L, dx);
+              dy = fma(-rint(dy * g.inv_L64), g.L, dy);
+              dz = fma(-rint(dz * g.inv_L64), g.L, dz);
+            }
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            const double ri2 = __drcp_rn(r2);
+            const double si = c.sig2 * ri2;
+            const double s3i = si * si * si;
+            const bool in = r2 < c.rc2;
+            double ff = fma(ri2 * s3i, fma(-f48d, s3i, f24d), f8c2d);
+            ff = in ? ff : 0.0;
+            dfx = fma(ff, dx, dfx);
+            dfy = fma(ff, dy, dfy);
+            dfz = fma(ff, dz, dfz);
+            if (HALF) {
+              dvec4* F = (dvec4*)fout;
+              const int gj = sh_gid[j];
+              atomicAdd(&F[gj].x, -ff * dx);
+              atomicAdd(&F[gj].y, -ff * dy);
+              atomicAdd(&F[gj].z, -ff * dz);
+            }
+            if (ENERGY) {
+              const double v = e4d * fma(s3i, s3i - 1.0, fma(c2sd, r2, c.c0));
+              dpe += in ? v : 0.0;
+              dvir = fma(-ff, r2, dvir);
+            }
+          }
+        }
+      }
+      if (MIXED) {
+        fx = gsum<LANES>(fx);
+        fy = gsum<LANES>(fy);
+        fz = gsum<LANES>(fz);
+        if (valid && lane == 0) {
+          if (HALF) atomicAdd(&((float4*)fout)[gi], make_float4(fx, fy, fz, 0.0f));
+          else ((float4*)fout)[gi] = make_float4(fx, fy, fz, 0.0f);
+        }
+        if (ENERGY) {
+          pe_acc += (double)pe;
+          vir_acc += (double)vir;
+        }
+      } else {
+        dfx = gsum<LANES>(dfx);
+        dfy = gsum<LANES>(dfy);
+        dfz = gsum<LANES>(dfz);
+        if (valid && lane == 0) {
+          dvec4* F = (dvec4*)fout;
+          if (HALF) {
+            atomicAdd(&F[gi].x, dfx);
+            atomicAdd(&F[gi].y, dfy);
+            atomicAdd(&F[gi].z, dfz);
+          } else {
+            F[gi] = make_dvec4(dfx, dfy, dfz, 0.0);
+          }
+        }
+        if (ENERGY) {
+          pe_acc += dpe;
+          vir_acc += dvir;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (ENERGY) {
+    __shared__ double sh[32];
+    const double tp = block_sum(pe_acc, sh);
+    __syncthreads();
+    const double tv = block_sum(vir_acc, sh);
+    if (threadIdx.x == 0) {
+      part[2 * (size_t)blockIdx.x] = tp;
+      part[2 * (size_t)blockIdx.x + 1] = tv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Expand the list into (key, partner) sorted-index pairs (for inspection).  The whole-box
+// case is a template parameter: no barrier sits under a runtime branch.
+template <bool WHOLE>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_list_decode(const uint32_t* __restrict__ cs, int64_t N, TileArgs ta, const uint2* __restrict__ rows,
+                  const uint16_t* __restrict__ ent, uint64_t E, uint32_t* __restrict__ out,
+                  int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileShared S;
+  int* sh_gid = (int*)smem;
+  for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
+    if (WHOLE) {
+      for (int e = threadIdx.x; e < N; e += blockDim.x) sh_gid[e] = e;
+      if (threadIdx.x == 0) {
+        S.own0 = 0;
+        S.own1 = (int)N;
+        S.total = (int)N;
+      }
+    } else {
+      const TileInfo ti = tile_info(t, ta);
+      if (!stage_offsets(ti, ta, cs, S)) {
+        if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
+        __syncthreads();
+        continue;
+      }
+      for (int s = threadIdx.x; s < S.total; s += blockDim.x) {
+        const int q = slot_cell(S, s);
+        sh_gid[s] = S.g0[q] + (s - S.offq[q]);
+      }
+    }
+    __syncthreads();
+    for (int l = S.own0 + (int)threadIdx.x / 32; l < S.own1; l += kWarps) {
+      const int gi = sh_gid[l];
+      const uint2 row = rows[gi];
+      if ((uint64_t)row.x + row.y > E) {  // inconsistent row: record and skip
+        if ((threadIdx.x & 31) == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+        continue;
+      }
+      for (unsigned e = threadIdx.x & 31; e < row.y; e += 32) {
+        const int j = ent[row.x + e];
+        const bool ok = j < S.total;
+        if (!ok) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+        out[2 * (size_t)(row.x + e)] = (uint32_t)gi;
+        out[2 * (size_t)(row.x + e) + 1] = ok ? (uint32_t)sh_gid[j] : 0xffffffffu;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+static int sm_count() {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+static int tile_grid(const TileArgs& ta, int per_sm) {
+  int64_t b = (int64_t)sm_count() * per_sm;
+  if (b > ta.ntiles) b = ta.ntiles;
+  if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <class K>
+static void set_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static int per_sm_for(size_t smem_bytes) {
+  int dev = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int k = (int)(smem_sm / (int)(smem_bytes + sizeof(TileShared) + 1024));
+  return k < 1 ? 1 : (k > 4 ? 4 : k);
+}
+
+void launch_list_tile(int precision, int half, const void* pos, const double* x, const uint32_t* cs, int64_t N,
+                      Geom g, TileArgs ta, ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
+                      unsigned long long* counter, unsigned int* max_list, int32_t* status, cudaStream_t s) {
+  const size_t sm = list_smem_bytes(ta, precision);
+  const int grid = tile_grid(ta, per_sm_for(sm));
+#define LJ_LIST_LAUNCH(M, H, W)                                                                                 \
+  do {                                                                                                          \
+    set_smem(k_list_tile<M, H, W>, sm);                                                                         \
+    k_list_tile<M, H, W><<<grid, kTileThreads, sm, s>>>(pos, x, cs, N, g, ta, band, rows, tile_list, ent, cap, \
+                                                        counter, max_list, status);                             \
+  } while (0)
+  const bool mixed = precision == LJ_MIXED;
+  if (ta.whole) {
+    if (mixed) {
+      if (half) LJ_LIST_LAUNCH(true, true, true);
+      else LJ_LIST_LAUNCH(true, false, true);
+    } else {
+      if (half) LJ_LIST_LAUNCH(false, true, true);
+      else LJ_LIST_LAUNCH(false, false, true);
+    }
+  } else {
+    if (mixed) {
+      if (half) LJ_LIST_LAUNCH(true, true, false);
+      else LJ_LIST_LAUNCH(true, false, false);
+    } else {
+      if (half) LJ_LIST_LAUNCH(false, true, false);
+      else LJ_LIST_LAUNCH(false, false, false);
+    }
+  }
+#undef LJ_LIST_LAUNCH
+}
+
+template <bool MIXED, int LANES, bool HALF, bool ENERGY>
+static void force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
+                    const uint2* rows, const uint2* tl, const uint16_t* ent, void* f, double* part, int32_t* status,
+                    int grid, size_t sm, cudaStream_t s) {
+  if (ta.whole) {
+    set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, true>, sm);
+    k_force_tile<MIXED, LANES, HALF, ENERGY, true><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c, rows, tl,
+                                                                                  ent, f, part, status);
+  } else {
+    set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, false>, sm);
+    k_force_tile<MIXED, LANES, HALF, ENERGY, false><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c, rows, tl,
+                                                                                   ent, f, part, status);
+  }
+}
+
+template <bool MIXED, int LANES>
+static void force_l(int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
+                    TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
+                    double* part, int32_t* status, int grid, size_t sm, cudaStream_t s) {
+  if (half) {
+    if (energy) force_w<MIXED, LANES, true, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s);
+    else force_w<MIXED, LANES, true, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s);
+  } else {
+    if (energy) force_w<MIXED, LANES, false, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s);
+    else force_w<MIXED, LANES, false, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s);
+  }
+}
+
+template <bool MIXED>
+static void force_p(int lanes, int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N,
+                    Geom g, TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
+                    double* part, int32_t* status, int grid, size_t sm, cudaStream_t s) {
+  switch (lanes) {
+    case 1: force_l<MIXED, 1>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
+    case 2: force_l<MIXED, 2>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
+    case 4: force_l<MIXED, 4>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
+    case 8: force_l<MIXED, 8>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
+    case 16: force_l<MIXED, 16>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
+    default: force_l<MIXED, 32>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
+  }
+}
+
+int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const float4* lo,
+                      const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
+                      const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
+                      cudaStream_t s) {
+  const size_t sm = force_smem_bytes(ta);
+  if (per_sm <= 0) per_sm = per_sm_for(sm);
+  const int grid = tile_grid(ta, per_sm);
+  if (precision == LJ_MIXED)
+    force_p<true>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, grid, sm, s);
+  else
+    force_p<false>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, grid, sm, s);
+  return grid;
+}
+
+void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,
+                        uint64_t E, uint32_t* out, int32_t* status, cudaStream_t s) {
+  const size_t sm = ((4 * (size_t)ta.max_staged) + 15) & ~(size_t)15;
+  const int grid = tile_grid(ta, 4);
+  if (ta.whole) {
+    set_smem(k_list_decode<true>, sm);
+    k_list_decode<true><<<grid, kTileThreads, sm, s>>>(cs, N, ta, rows, ent, E, out, status);
+  } else {
+    set_smem(k_list_decode<false>, sm);
+    k_list_decode<false><<<grid, kTileThreads, sm, s>>>(cs, N, ta, rows, ent, E, out, status);
+  }
+}
+
+// Largest staged count and own count over all tiles (sizes the shared-memory tiles).
+__global__ void k_tile_sizes(const uint32_t* __restrict__ cs, TileArgs ta, unsigned int* __restrict__ out) {
+  unsigned int mst = 0, mown = 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ta.ntiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const TileInfo ti = tile_info(t, ta);
+    const int ncol = ti.Tp + 2;
+    unsigned int tot = 0;
+    for (int q = 0; q < 9 * ncol; ++q) {
+      int sx, sy, sz;
+      const uint32_t cq = cell_of_q(ti, ta.n, ncol, q, sx, sy, sz);
+      tot += cs[cq + 1] - cs[cq];
+    }
+    const uint32_t c0 = ((uint32_t)ti.cx * (uint32_t)ta.n + (uint32_t)ti.cy) * (uint32_t)ta.n + (uint32_t)ti.z0;
+    mst = max(mst, tot);
+    mown = max(mown, cs[c0 + ti.Tp] - cs[c0]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mst = max(mst, __shfl_xor_sync(0xffffffffu, mst, o));
+    mown = max(mown, __shfl_xor_sync(0xffffffffu, mown, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], mst);
+    atomicMax(&out[1], mown);
+  }
+}
+
+void launch_tile_sizes(const uint32_t* cs, TileArgs ta, unsigned int* out, cudaStream_t s) {
+  int64_t b = (ta.ntiles + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 4096) b = 4096;
+  k_tile_sizes<<<(int)b, 256, 0, s>>>(cs, ta, out);
+}
+
+// Largest cell occupancy.
+__global__ void k_max_count(const uint32_t* __restrict__ cnt, int64_t n, unsigned int* __restrict__ out) {
+  unsigned int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, cnt[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStream_t s) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 4096) b = 4096;
+  k_max_count<<<(int)b, 256, 0, s>>>(cnt, n, out);
+}
+
+}  // namespace ljmd

@@ -51,8 +51,14 @@ struct ljmd_sys {
   int32_t *id = nullptr, *id_alt = nullptr, *img = nullptr, *img_alt = nullptr;
   uint32_t *cell_of = nullptr, *cell_alt = nullptr, *perm = nullptr;
   uint32_t *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
-  uint32_t *row_cnt = nullptr, *row_ptr = nullptr, *col = nullptr;
-  size_t col_cap = 0;
+  uint2* rows = nullptr;        // per particle: (start, length) of its row in ent
+  uint2* tile_list = nullptr;   // per tile: (start, length) of its segment of ent
+  int64_t tile_list_cap = 0;
+  uint16_t* ent = nullptr;       // SortedList: partner indices into the key's staged tile
+  size_t ent_cap = 0;
+  TileArgs ta{};
+  int tile_T = 0;                // preferred cells per tile along z (0 = default)
+  int force_per_sm = 0;          // force CTAs per SM (0 = as many as fit)
   uint32_t* scan_tmp = nullptr;
   size_t scan_tmp_cap = 0;
   int64_t cap_n = 0;       // particle capacity of the per-particle buffers
@@ -63,6 +69,7 @@ struct ljmd_sys {
   int32_t* d_status = nullptr;
   uint32_t* d_dmax = nullptr;
   unsigned long long* d_total64 = nullptr;
+  unsigned int* d_sizes = nullptr;
   // profiling: event pairs per phase, resolved when the profile is read
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -113,8 +120,8 @@ static int dalloc_t(ljmd_sys* sys, T** p, size_t count) {
 static void free_all(ljmd_sys* s) {
   void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->lo, s->pos64, s->ref, s->id,
                   s->id_alt, s->img, s->img_alt, s->cell_of, s->cell_alt, s->perm, s->cell_count, s->cell_start,
-                  s->cell_fill, s->row_cnt, s->row_ptr, s->col, s->scan_tmp, s->part_force, s->part_ke,
-                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64};
+                  s->cell_fill, s->rows, s->tile_list, s->ent, s->scan_tmp, s->part_force, s->part_ke,
+                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64, s->d_sizes};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& p : s->ev_pending) {
@@ -248,11 +255,18 @@ static int setup_geometry(ljmd_sys* s, double L) {
   c.c2f = (float)(c2 / c.sig2);
   c.c0f = (float)c0;
 
-  // FP32 list band: r2f within 1e-5 relative of r_s^2 goes to the exact FP64 test.  The FP32
-  // r2 is within ~5 ulp (3e-7 relative) of the exact value, so outside the band it decides.
-  s->band.rs2 = rs * rs;
-  s->band.lo = (float)(rs * rs * (1.0 - 1e-5));
-  s->band.hi = (float)(rs * rs * (1.0 + 1e-5));
+  // FP32 list filter on hi parts: each hi difference is exact and differs from the exact
+  // difference by at most eps = 2^(p-22) (two dropped lo parts and the split of L), so
+  // |r2f - r^2| <= eps (2 sqrt(3) r_s + 3 eps) + 4 ulp(r_s^2).  Twice that bound plus 1e-6
+  // relative is the band around r_s^2 inside which the exact FP64 test decides.
+  {
+    const double eps = ldexp(1.0, pw - 22);
+    const double bound = eps * (2.0 * sqrt(3.0) * rs + 3.0 * eps) + 4.0 * 1.2e-7 * rs * rs;
+    const double band = 2.0 * bound + 1e-6 * rs * rs;
+    s->band.rs2 = rs * rs;
+    s->band.lo = (float)(rs * rs - band);
+    s->band.hi = (float)(rs * rs + band);
+  }
   // Displacement rule: rebuild when max |x - x_ref| > margin / 2.  The measured value can
   // undershoot by the FP32 hi/lo reference error (mixed: dropped lo of the reference,
   // <= 2^(p-23) per component), so the limit is lowered by twice that bound.
@@ -282,8 +296,7 @@ static int ensure_particles(ljmd_sys* s, int64_t n) {
   TRY(dalloc_t(s, &s->cell_of, n));
   TRY(dalloc_t(s, &s->cell_alt, n));
   TRY(dalloc_t(s, &s->perm, n));
-  TRY(dalloc_t(s, &s->row_cnt, n + 1));
-  TRY(dalloc_t(s, &s->row_ptr, n + 1));
+  TRY(dalloc_t(s, &s->rows, n));
   s->cap_n = n;
   return LJ_OK;
 }
@@ -333,6 +346,62 @@ static int check_status(ljmd_sys* s) {
   return w ? LJ_EDEVICE : LJ_OK;
 }
 
+static void* force_pos(ljmd_sys* s);
+
+static int ensure_tile_list(ljmd_sys* s) {
+  if (s->ta.ntiles > s->tile_list_cap) {
+    TRY(dalloc_t(s, &s->tile_list, s->ta.ntiles));
+    s->tile_list_cap = s->ta.ntiles;
+  }
+  return LJ_OK;
+}
+
+// Tile geometry for the staged list/force kernels: T cells along z per tile, shared-memory
+// capacities from the actual largest tile of the current cell occupancy.
+static int choose_tiles(ljmd_sys* s) {
+  ljmd_sys* sys = s;
+  TileArgs& ta = s->ta;
+  const int n = s->g.n;
+  ta.n = n;
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (n < 3) {
+    ta.whole = 1;
+    ta.T = 1;
+    ta.ntz = 1;
+    ta.ntiles = 1;
+    ta.max_staged = (int32_t)s->n;
+    ta.max_own = (int32_t)s->n;
+    ta.max_chunks = (int32_t)((s->n + 31) / 32);
+    if (s->n > 65535 || list_smem_bytes(ta, s->precision) > (size_t)smem_max) return LJ_ERANGE;
+    return ensure_tile_list(s);
+  }
+  ta.whole = 0;
+  int T = s->tile_T > 0 ? s->tile_T : 4;
+  if (T > n - 2) T = n - 2;
+  if (T > kMaxTileT) T = kMaxTileT;
+  if (T < 1) T = 1;
+  for (;; --T) {
+    ta.T = T;
+    ta.ntz = (n + T - 1) / T;
+    ta.ntiles = (int64_t)n * n * ta.ntz;
+    CK(cudaMemsetAsync(s->d_sizes, 0, 3 * sizeof(unsigned int), s->st));
+    launch_tile_sizes(s->cell_start, ta, s->d_sizes, s->st);
+    launch_max_count(s->cell_count, s->ncells, s->d_sizes + 2, s->st);
+    s->launches += 2;
+    CKL();
+    CK(cudaMemcpyAsync(s->h_u32 + 8, s->d_sizes, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    const unsigned staged = s->h_u32[8], own = s->h_u32[9], maxcell = s->h_u32[10];
+    ta.max_staged = (int32_t)staged;
+    ta.max_own = (int32_t)(own > 0 ? own : 1);
+    ta.max_chunks = (int32_t)(9 * ((3 * maxcell + 31) / 32) + 1);
+    if (staged <= 65535 && list_smem_bytes(ta, s->precision) <= (size_t)smem_max) return ensure_tile_list(s);
+    if (T == 1) return LJ_ERANGE;  // cell occupancy beyond what a tile can stage
+  }
+}
+
 // ----------------------------------------------------------------------------------------------
 // Pair-list construction: fold, label, counting sort (Fig. 3), reorder (Sec. 3.3), sorted list.
 static int rebuild(ljmd_sys* s) {
@@ -341,8 +410,8 @@ static int rebuild(ljmd_sys* s) {
   cudaStream_t st = s->st;
   TRY(ensure_cells(s));
   PhaseTimer timer(s, PH_REBUILD);
-  // wrap_label, scatter, cell_order, 6 gathers, shadow, list count, list fill (+ the scans below)
-  s->launches += 12;
+  // wrap_label, scatter, cell_order, 6 gathers, shadow (+ the scan, tile sizing and list below)
+  s->launches += 10;
   CK(cudaMemsetAsync(s->cell_count, 0, sizeof(uint32_t) * s->ncells, st));
   launch_wrap_label(s->x, s->img, N, s->g, s->cell_of, s->cell_count, s->d_status, st);
   CKL();
@@ -367,29 +436,51 @@ static int rebuild(ljmd_sys* s) {
   std::swap(s->f, s->f_alt);
   launch_shadow_all(s->x, N, s->precision == LJ_MIXED, s->hi, s->lo, s->pos64, s->ref, st);
   CKL();
+  TRY(choose_tiles(s));
   const int half = s->prm.list_form == LJ_LIST_HALF;
-  CK(cudaMemsetAsync(s->d_total64, 0, sizeof(unsigned long long), st));
-  launch_list_count(s->hi, s->lo, s->x, s->cell_of, s->cell_start, N, s->g, s->band, half, s->precision, s->row_cnt,
-                    s->d_total64, st);
-  CKL();
-  s->launches += launch_scan_u32(s->row_cnt, s->row_ptr, N, s->scan_tmp, st);
-  CKL();
-  CK(cudaMemcpyAsync(s->h_u32, s->row_ptr + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(s->h_u32 + 2, s->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  unsigned long long total64;
-  memcpy(&total64, s->h_u32 + 2, sizeof(total64));
-  if (total64 > 4294967294ULL) return LJ_ERANGE;  // offsets are 32-bit
-  const uint64_t total = *s->h_u32;
-  if (total != total64) return LJ_EDEVICE;
-  if (total + 1 > s->col_cap) {
-    const size_t want = (size_t)(total * 1.15) + 1024;
-    TRY(dalloc_t(s, &s->col, want));
-    s->col_cap = want;
+  uint64_t total = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (s->ent_cap == 0) {
+      // first construction: the continuum estimate of partners within r_s, with headroom
+      const double est = 4.18879 * s->rs * s->rs * s->rs * (double)N / (s->L * s->L * s->L);
+      const size_t want = (size_t)((double)N * (est * (half ? 0.5 : 1.0) * 1.3 + 8.0)) + 4096;
+      TRY(dalloc_t(s, &s->ent, want));
+      s->ent_cap = want;
+    }
+    CK(cudaMemsetAsync(s->d_total64, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(s->d_sizes + 3, 0, sizeof(unsigned int), st));
+    launch_list_tile(s->precision, half, force_pos(s), s->x, s->cell_start, N, s->g, s->ta, s->band, s->rows,
+                     s->tile_list, s->ent, (uint64_t)s->ent_cap, s->d_total64, s->d_sizes + 3, s->d_status, st);
+    s->launches += 1;
+    CKL();
+    CK(cudaMemcpyAsync(s->h_u32 + 2, s->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->h_u32 + 12, s->d_sizes + 3, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    unsigned long long total64;
+    memcpy(&total64, s->h_u32 + 2, sizeof(total64));
+    s->ta.max_list = (int32_t)s->h_u32[12];
+    if (total64 > 4294967295ULL) return LJ_ERANGE;  // row starts are 32-bit
+    total = total64;
+    if (total <= s->ent_cap) {
+      int32_t w = 0;
+      TRY(device_status(s, &w));
+      if (w) {
+        fprintf(stderr, "ljmd: list construction raised status %d (n=%d T=%d tiles=%lld staged<=%d own<=%d)\n", w,
+                s->ta.n, s->ta.T, (long long)s->ta.ntiles, s->ta.max_staged, s->ta.max_own);
+        return LJ_EDEVICE;
+      }
+      int dev = 0, smem_max = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (force_smem_bytes(s->ta) > (size_t)smem_max) return LJ_ERANGE;
+      break;
+    }
+    // the rows did not fit: grow to the exact size plus headroom and construct again
+    const size_t want = (size_t)(total * 1.2) + 4096;
+    TRY(dalloc_t(s, &s->ent, want));
+    s->ent_cap = want;
+    if (attempt == 1) return LJ_EDEVICE;
   }
-  launch_list_fill(s->hi, s->lo, s->x, s->cell_of, s->cell_start, N, s->g, s->band, half, s->precision, s->row_ptr,
-                   s->col, s->d_status, st);
-  CKL();
   s->list_entries = total;
   s->have_list = true;
   s->rebuilds += 1;
@@ -421,11 +512,13 @@ static int run_force(ljmd_sys* s, bool energy) {
   const int half = s->prm.list_form == LJ_LIST_HALF;
   if (half) CK(cudaMemsetAsync(s->f, 0, (s->precision == LJ_MIXED ? 16 : 32) * (size_t)s->n, s->st));
   int lanes = s->prm.lanes;
-  if (lanes == 0) lanes = (s->precision == LJ_MIXED) ? 8 : 8;
+  if (lanes == 0) lanes = 4;
+  const int per_sm = s->force_per_sm;  // 0: as many CTAs per SM as shared memory allows
   {
     PhaseTimer timer(s, PH_FORCE);
-    s->nb_force = launch_force(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->lo, s->row_ptr, s->col,
-                               s->n, s->g, s->c, s->f, s->part_force, s->st);
+    s->nb_force = launch_force_tile(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->lo, s->cell_start, s->n,
+                                    s->g, s->ta, s->c, s->rows, s->tile_list, s->ent, s->f, s->part_force, s->d_status,
+                                    per_sm, s->st);
   }
   s->launches += 1;
   CKL();
@@ -505,6 +598,7 @@ int ljmd_create(ljmd_sys** out, const ljmd_params* p, int32_t precision, void* c
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_status, 1);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_dmax, 1);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_total64, 1);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_sizes, 4);
   if (r == LJ_OK && cudaMallocHost(&sys->h_u32, 64) != cudaSuccess) r = LJ_ENOMEM;
   if (r == LJ_OK && cudaMallocHost(&sys->h_f64, 64) != cudaSuccess) r = LJ_ENOMEM;
   if (r == LJ_OK && cudaMallocHost(&sys->h_i32, 64) != cudaSuccess) r = LJ_ENOMEM;
@@ -725,24 +819,38 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
   if (sys->n <= 0) return LJ_ESTATE;
   if (!sys->have_list) TRY(rebuild(sys));
   const int64_t N = sys->n;
-  std::vector<uint32_t> rp(N + 1), cl(sys->list_entries);
+  const uint64_t E = sys->list_entries;
+  uint32_t* d_pairs = nullptr;
+  TRY(dalloc_t(sys, &d_pairs, 2 * E + 2));
+  launch_list_decode(sys->cell_start, N, sys->ta, sys->rows, sys->ent, E, d_pairs, sys->d_status, sys->st);
+  sys->launches += 1;
+  std::vector<uint32_t> pr(2 * E);
   std::vector<int32_t> id(N);
-  CK(cudaMemcpyAsync(rp.data(), sys->row_ptr, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, sys->st));
-  if (sys->list_entries)
-    CK(cudaMemcpyAsync(cl.data(), sys->col, sizeof(uint32_t) * sys->list_entries, cudaMemcpyDeviceToHost, sys->st));
-  CK(cudaMemcpyAsync(id.data(), sys->id, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, sys->st));
-  CK(cudaStreamSynchronize(sys->st));
+  cudaError_t e1 = cudaGetLastError();
+  if (e1 == cudaSuccess && E) e1 = cudaMemcpyAsync(pr.data(), d_pairs, sizeof(uint32_t) * 2 * E, cudaMemcpyDeviceToHost,
+                                                   sys->st);
+  if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(id.data(), sys->id, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, sys->st);
+  if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(sys->st);
+  cudaFree(d_pairs);
+  if (e1 != cudaSuccess) {
+    sys->broken = true;
+    return LJ_EDEVICE;
+  }
   std::vector<std::pair<int64_t, int64_t>> pairs;
-  pairs.reserve(sys->prm.list_form == LJ_LIST_FULL ? sys->list_entries / 2 : sys->list_entries);
-  for (int64_t i = 0; i < N; ++i)
-    for (uint32_t k = rp[i]; k < rp[i + 1]; ++k) {
-      const int64_t a = id[i], b = id[cl[k]];
-      if (sys->prm.list_form == LJ_LIST_FULL) {
-        if (a < b) pairs.emplace_back(a, b);
-      } else {
-        pairs.emplace_back(std::min(a, b), std::max(a, b));
-      }
+  pairs.reserve(sys->prm.list_form == LJ_LIST_FULL ? E / 2 : E);
+  for (uint64_t k = 0; k < E; ++k) {
+    if (pr[2 * k] >= (uint64_t)N || pr[2 * k + 1] >= (uint64_t)N) {
+      fprintf(stderr, "ljmd_get_pairs: list entry %llu decodes to (%u, %u), N = %lld\n", (unsigned long long)k,
+              pr[2 * k], pr[2 * k + 1], (long long)N);
+      return LJ_EDEVICE;
     }
+    const int64_t a = id[pr[2 * k]], b = id[pr[2 * k + 1]];
+    if (sys->prm.list_form == LJ_LIST_FULL) {
+      if (a < b) pairs.emplace_back(a, b);
+    } else {
+      pairs.emplace_back(std::min(a, b), std::max(a, b));
+    }
+  }
   std::sort(pairs.begin(), pairs.end());
   *npairs = (int64_t)pairs.size();
   const int64_t m = std::min<int64_t>(cap, (int64_t)pairs.size());
@@ -776,6 +884,22 @@ int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
   return LJ_OK;
 }
 
+int ljmd_set_tuning(ljmd_sys* sys, int32_t tile_cells, int32_t lanes, int32_t force_ctas_per_sm) {
+  if (!sys) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (tile_cells < 0 || tile_cells > kMaxTileT || force_ctas_per_sm < 0 || force_ctas_per_sm > 4) return LJ_EINVAL;
+  if (!(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
+    return LJ_EINVAL;
+  if (tile_cells != sys->tile_T) {
+    sys->tile_T = tile_cells;
+    sys->have_list = false;  // list indices depend on the tile shape
+    sys->forces_current = false;
+  }
+  if (lanes) sys->prm.lanes = lanes;
+  sys->force_per_sm = force_ctas_per_sm;
+  return LJ_OK;
+}
+
 int ljmd_set_profiling(ljmd_sys* sys, int32_t enable) {
   if (!sys) return LJ_EINVAL;
   if (sys->broken) return LJ_EDEVICE;
@@ -802,5 +926,6 @@ int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out) {
   out->energy_launches = sys->prof_n[PH_ENERGY];
   return LJ_OK;
 }
+
 
 }  // extern "C"

@@ -97,20 +97,33 @@ void launch_load_state(const double* x_in, const double* v_in, double* x, double
 void launch_shadow_all(const double* x, int64_t N, int mixed, float4* hi, float4* lo, dvec4* pos64, void* ref,
                        cudaStream_t s);
 
-// ---- list ---------------------------------------------------------------------------
-void launch_list_count(const void* hi_or_pos, const float4* lo, const double* x, const uint32_t* cell_of,
-                       const uint32_t* cell_start, int64_t N, Geom g, ListBand band, int half, int precision,
-                       uint32_t* row_count, unsigned long long* total64, cudaStream_t s);
-void launch_list_fill(const void* hi_or_pos, const float4* lo, const double* x, const uint32_t* cell_of,
-                      const uint32_t* cell_start, int64_t N, Geom g, ListBand band, int half, int precision,
-                      const uint32_t* row_ptr, uint32_t* col, int32_t* status, cudaStream_t s);
-
-// ---- forces ---------------------------------------------------------------------------
-// Writes F (float4 mixed / dvec4 fp64) and, if energy, per-block partials (pe, vir) into
-// partials[2 * block]; returns the number of blocks used.
-int launch_force(int precision, int half, int lanes, int energy, const void* hi_or_pos, const float4* lo,
-                 const uint32_t* row_ptr, const uint32_t* col, int64_t N, Geom g, LJConst c, void* f,
-                 double* partials, cudaStream_t s);
+// ---- staged cell-column tiles: list and force ---------------------------------------------
+constexpr int kMaxTileT = 14;  // cells per tile along z, at most
+struct TileArgs {
+  int32_t n;           // cells per side
+  int32_t T;           // cells per tile along z (1 <= T <= n - 2); tile path needs n >= 3
+  int32_t ntz;         // tiles per column, ceil(n / T)
+  int32_t whole;       // 1: the whole box is one tile (n < 3), periodic image chosen per pair
+  int64_t ntiles;
+  int32_t max_staged;  // staged particles per tile, at most (<= 65535: entries are 16-bit)
+  int32_t max_own;     // own particles per tile, at most
+  int32_t max_chunks;  // 32-candidate chunks per own particle, at most
+  int32_t max_list;    // list entries per tile, at most (known after construction)
+};
+size_t list_smem_bytes(const TileArgs& ta, int precision);
+size_t force_smem_bytes(const TileArgs& ta);
+void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStream_t s);
+void launch_tile_sizes(const uint32_t* cs, TileArgs ta, unsigned int* out, cudaStream_t s);
+void launch_list_tile(int precision, int half, const void* pos, const double* x, const uint32_t* cs, int64_t N,
+                      Geom g, TileArgs ta, ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
+                      unsigned long long* counter, unsigned int* max_list, int32_t* status, cudaStream_t s);
+// Returns the number of blocks (energy partials written to part[2 b], part[2 b + 1]).
+int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const float4* lo,
+                      const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
+                      const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
+                      cudaStream_t s);
+void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,
+                        uint64_t E, uint32_t* out, int32_t* status, cudaStream_t s);
 
 // ---- integrator ---------------------------------------------------------------------
 struct IntegrateArgs {
