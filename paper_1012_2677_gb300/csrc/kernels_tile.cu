@@ -3,17 +3,21 @@
 //
 // A tile is T consecutive cells along z of one (cx, cy) column.  Its CTA stages the particles
 // of the 9 neighbouring columns over the cells z0-1 .. z0+T (9 (T+2) cells, wrapped
-// periodically) into shared memory, adding each cell's periodic image shift (-L, 0, +L per
-// axis).  Mixed form: the copies are the hi/lo FP32 split of the stored FP64 coordinates and
-// the shift is split the same way, so hi + shift_hi is exact and a partner difference
+// periodically) into shared memory.  The cells of one column are contiguous in the cell-sorted
+// particle arrays (except where z wraps), so each column is one to three contiguous ranges:
+// one lane per column issues asynchronous bulk copies (cp.async.bulk) of those ranges, plus
+// the tile's rows and its list segment, all completing on one mbarrier that the CTA waits on
+// (bounded).  The periodic image shifts (-L, 0, +L per axis) are then added in shared memory.
+//
+// Mixed form: the copies are the hi/lo FP32 split of the stored FP64 coordinates and the shift
+// is split the same way, so hi + shift_hi is exact and a partner difference
 // d = (hi_j - hi_i) + (lo_j - lo_i) carries one rounding.  FP64 form: the FP64 coordinates,
-// with the shift kept aside and added to the exact difference.
+// with the shift code kept in w and added to the exact difference.
 //
 // The list holds 16-bit indices into the key particle's staged tile; rows are (start, length)
-// per particle, and the rows of one tile form one contiguous segment (recorded per tile), so
-// the force kernel loads the tile's rows and its whole list segment into shared memory with
-// the positions, in two dependent rounds of fully parallel loads.  If the box has fewer than
-// 3 cells per side, the whole box is one tile (all particles, no shifts, image per pair).
+// per particle; the rows of one tile form one contiguous segment, padded to 8 entries so that
+// it can be bulk-copied.  If the box has fewer than 3 cells per side the whole box is one tile
+// (all particles staged directly, no shifts, image chosen per pair).
 //
 // List construction: a warp per key particle tests its 27 neighbour cells from shared memory
 // in chunks of 32 (FP32 hi differences, which are exact, so r^2 is within a bounded error of
@@ -51,7 +55,8 @@ struct TileShared {
   int ncol, ncell, total;   // cells per column, staged cells, staged particles
   int own0, own1;           // staged range of the tile's own particles
   int gown0;                // sorted index of the first own particle
-  unsigned list_base, list_len;
+  unsigned list_base, list_len;  // the tile's (padded) list segment
+  int row_off;              // index of the first own row in the staged row copy
 };
 
 // Wrapped coordinate and image shift (-1, 0, +1) of a neighbour cell index.
@@ -75,8 +80,8 @@ __device__ __forceinline__ uint32_t cell_of_q(const TileInfo& ti, int n, int nco
   return ((uint32_t)X * (uint32_t)n + (uint32_t)Y) * (uint32_t)n + (uint32_t)Z;
 }
 
-// Round 1: cell bounds of the tile's 9 (Tp + 2) staged cells, then their prefix (one warp).
-// Returns false (all threads) if the tile exceeds the staged capacity.
+// Cell bounds of the tile's 9 (Tp + 2) staged cells and their prefix (one warp).  Returns false
+// (all threads) if the tile exceeds the staged capacity.
 __device__ __forceinline__ bool stage_offsets(const TileInfo& ti, const TileArgs& ta, const uint32_t* __restrict__ cs,
                                               TileShared& S) {
   const int ncol = ti.Tp + 2;
@@ -130,54 +135,159 @@ __device__ __forceinline__ int slot_cell(const TileShared& S, int s) {
   return lo;
 }
 
-// Round 2: copy every staged particle with its image shift (one independent load per slot).
-// MIXED: hi (and lo if WANT_LO) as float4; FP64: dvec4 with w = shift code
-// (sx + 1) + 3 (sy + 1) + 9 (sz + 1).
-template <bool MIXED, bool WANT_LO>
-__device__ __forceinline__ void stage_copy(const TileInfo& ti, const TileArgs& ta, const Geom& g,
-                                           const void* __restrict__ pos, const float4* __restrict__ lo,
-                                           const TileShared& S, void* sh_pos, float4* sh_lo, int* sh_gid) {
-  for (int s = threadIdx.x; s < S.total; s += blockDim.x) {
-    const int q = slot_cell(S, s);
-    int sx, sy, sz;
-    cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
-    const int gi = S.g0[q] + (s - S.offq[q]);
-    if (MIXED) {
-      float4 h = ((const float4*)pos)[gi];
-      h.x = fmaf((float)sx, g.L_hi, h.x);  // exact
-      h.y = fmaf((float)sy, g.L_hi, h.y);
-      h.z = fmaf((float)sz, g.L_hi, h.z);
-      ((float4*)sh_pos)[s] = h;
-      if (WANT_LO) {
-        float4 l = lo[gi];
-        l.x = fmaf((float)sx, g.L_lo, l.x);
-        l.y = fmaf((float)sy, g.L_lo, l.y);
-        l.z = fmaf((float)sz, g.L_lo, l.z);
-        sh_lo[s] = l;
-      }
-    } else {
-      dvec4 p = ((const dvec4*)pos)[gi];
-      p.w = (double)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
-      ((dvec4*)sh_pos)[s] = p;
-    }
-    sh_gid[s] = gi;
+// Shared-memory layout of a staged tile (byte offsets from the dynamic shared base).
+struct TileLayout {
+  size_t pos;    // MIXED: hi float4 [ms]; FP64: dvec4 [ms]
+  size_t lo;     // MIXED: lo float4 [ms] (force only)
+  size_t gid;    // int [ms]
+  size_t rows;   // uint2 [max_own + 2] (force only)
+  size_t ent;    // uint16 [max_list] (force only)
+  size_t cnt;    // int [max_own] (list only), then pre [max_own], then masks [max_own * max_chunks]
+  size_t total;
+};
+
+static __host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, bool mixed, bool force) {
+  TileLayout L;
+  const size_t ms = (size_t)ta.max_staged;
+  L.pos = 0;
+  size_t o = align16(ms * (mixed ? 16 : 32));
+  L.lo = o;
+  if (mixed && force) o += align16(ms * 16);
+  L.gid = o;
+  o += align16(ms * 4);
+  L.rows = o;
+  L.ent = o;
+  L.cnt = o;
+  if (force) {
+    o += align16(8 * ((size_t)ta.max_own + 2));
+    L.ent = o;
+    if (!ta.whole) o += align16(2 * (size_t)ta.max_list);
+  } else {
+    o += align16(8 * (size_t)ta.max_own + 4 * (size_t)ta.max_own * ta.max_chunks);
   }
+  L.total = o;
+  return L;
 }
 
-// Whole box as one tile (fewer than 3 cells per side): everything staged, no shifts.
+// Issue the bulk copies of one tile (warp 0; lane k < 9 handles column k, lane 9 the rows and
+// list segment) and wait for them (all threads, bounded).  Copies: positions (hi [+ lo] or
+// FP64), and for the force kernel the own rows and the list segment.  Then the image shifts
+// (and the sorted indices, if wanted) are filled in.  Returns false (all threads) on timeout.
+template <bool MIXED, bool FORCE>
+__device__ __forceinline__ bool stage_copy_async(const TileInfo& ti, const TileArgs& ta, const Geom& g,
+                                                 const void* __restrict__ pos, const float4* __restrict__ lo,
+                                                 const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
+                                                 TileShared& S, unsigned char* smem, const TileLayout& L,
+                                                 uint64_t* bar, uint32_t& phase, bool want_gid, int32_t* status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned bpp = MIXED ? 16u : 32u;
+  if (warp == 0) {
+    unsigned bytes = (unsigned)S.total * bpp * ((MIXED && FORCE) ? 2u : 1u);
+    int r0 = 0, r1 = 0;
+    const int n_own = S.own1 - S.own0;
+    if (FORCE) {
+      r0 = S.gown0 & ~1;
+      r1 = (S.gown0 + n_own + 1) & ~1;
+      if (n_own > 0) bytes += 8u * (unsigned)(r1 - r0);
+      bytes += 2u * S.list_len;
+    }
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect(bar, bytes);
+    }
+    __syncwarp();
+    if (lane < 9) {
+      // runs of consecutive z in column `lane`
+      const int k = lane, ncol = S.ncol;
+      int m = 0;
+      while (m < ncol) {
+        int sx, sy, sz;
+        const uint32_t c0 = cell_of_q(ti, ta.n, ncol, k * ncol + m, sx, sy, sz);
+        int m1 = m + 1;
+        uint32_t c1 = c0;
+        while (m1 < ncol) {
+          int tx, ty, tz;
+          const uint32_t c = cell_of_q(ti, ta.n, ncol, k * ncol + m1, tx, ty, tz);
+          if (c != c1 + 1) break;
+          c1 = c;
+          ++m1;
+        }
+        const int q0 = k * ncol + m;
+        const unsigned n = (unsigned)(S.offq[k * ncol + m1] - S.offq[q0]);
+        if (n > 0) {
+          const size_t gsrc = (size_t)S.g0[q0];
+          const size_t dst = (size_t)S.offq[q0];
+          if (MIXED) {
+            bulk_g2s(smem + L.pos + 16 * dst, (const float4*)pos + gsrc, 16u * n, bar);
+            if (FORCE) bulk_g2s(smem + L.lo + 16 * dst, lo + gsrc, 16u * n, bar);
+          } else {
+            bulk_g2s(smem + L.pos + 32 * dst, (const dvec4*)pos + gsrc, 32u * n, bar);
+          }
+        }
+        m = m1;
+      }
+    } else if (FORCE && lane == 9) {
+      if (n_own > 0) bulk_g2s(smem + L.rows, rows + r0, 8u * (unsigned)(r1 - r0), bar);
+      if (S.list_len > 0) bulk_g2s(smem + L.ent, ent + S.list_base, 2u * S.list_len, bar);
+      S.row_off = S.gown0 - r0;
+    }
+  }
+  bool ok = mbar_wait(bar, phase, kWaitBudget);
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(status, LJ_ST_TIMEOUT);
+    mbar_wait(bar, phase, kWaitBudget);  // let copies in flight land before the CTA leaves
+    return false;
+  }
+  phase ^= 1u;
+  // image shifts (mixed: add to hi/lo; FP64: code in w) and sorted indices, one warp per cell
+  for (int q = warp; q < S.ncell; q += kWarps) {
+    int sx, sy, sz;
+    cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
+    const int a = S.offq[q], b = S.offq[q + 1], gq = S.g0[q];
+    const bool shifted = (sx | sy | sz) != 0;
+    for (int s = a + lane; s < b; s += 32) {
+      if (MIXED) {
+        if (shifted) {
+          float4* h = (float4*)(smem + L.pos) + s;
+          h->x = fmaf((float)sx, g.L_hi, h->x);  // exact
+          h->y = fmaf((float)sy, g.L_hi, h->y);
+          h->z = fmaf((float)sz, g.L_hi, h->z);
+          if (FORCE) {
+            float4* l = (float4*)(smem + L.lo) + s;
+            l->x = fmaf((float)sx, g.L_lo, l->x);
+            l->y = fmaf((float)sy, g.L_lo, l->y);
+            l->z = fmaf((float)sz, g.L_lo, l->z);
+          }
+        }
+      } else {
+        ((dvec4*)(smem + L.pos))[s].w = (double)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
+      }
+      if (want_gid) ((int*)(smem + L.gid))[s] = gq + (s - a);
+    }
+  }
+  // these generic writes precede the next tile's bulk copies into the same bytes
+  fence_proxy_async_smem();
+  __syncthreads();
+  return true;
+}
+
+// Whole box as one tile (fewer than 3 cells per side): everything staged directly, no shifts.
 template <bool MIXED, bool WANT_LO>
 __device__ __forceinline__ void stage_whole(int64_t N, const void* __restrict__ pos, const float4* __restrict__ lo,
-                                            TileShared& S, void* sh_pos, float4* sh_lo, int* sh_gid) {
+                                            TileShared& S, unsigned char* smem, const TileLayout& L) {
   for (int e = threadIdx.x; e < N; e += blockDim.x) {
     if (MIXED) {
-      ((float4*)sh_pos)[e] = ((const float4*)pos)[e];
-      if (WANT_LO) sh_lo[e] = lo[e];
+      ((float4*)(smem + L.pos))[e] = ((const float4*)pos)[e];
+      if (WANT_LO) ((float4*)(smem + L.lo))[e] = lo[e];
     } else {
       dvec4 p = ((const dvec4*)pos)[e];
       p.w = 13.0;  // no shift
-      ((dvec4*)sh_pos)[e] = p;
+      ((dvec4*)(smem + L.pos))[e] = p;
     }
-    sh_gid[e] = e;
+    ((int*)(smem + L.gid))[e] = e;
   }
   if (threadIdx.x == 0) {
     S.ncol = 1;
@@ -217,12 +327,12 @@ __device__ __forceinline__ bool pair_in_exact(const double* __restrict__ x, int6
 // Candidate test in FP32 on staged copies (exact hi differences for the mixed form; the FP64
 // form rounds its exact difference), then the exact FP64 test inside the band.
 template <bool MIXED, bool WHOLE>
-__device__ __forceinline__ bool candidate_in(const void* sh_pos, int li, int lj, const int* sh_gid,
+__device__ __forceinline__ bool candidate_in(const unsigned char* smem, const TileLayout& L, int li, int lj,
                                              const double* __restrict__ x, int64_t N, const Geom& g,
                                              const ListBand& band) {
   float r2;
   if (MIXED) {
-    const float4 a = ((const float4*)sh_pos)[li], b = ((const float4*)sh_pos)[lj];
+    const float4 a = ((const float4*)(smem + L.pos))[li], b = ((const float4*)(smem + L.pos))[lj];
     float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;  // exact
     if (WHOLE) {
       dx = fmaf(-rintf(dx * g.inv_L), g.L_hi, dx);
@@ -231,7 +341,7 @@ __device__ __forceinline__ bool candidate_in(const void* sh_pos, int li, int lj,
     }
     r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   } else {
-    const dvec4 a = ((const dvec4*)sh_pos)[li], b = ((const dvec4*)sh_pos)[lj];
+    const dvec4 a = ((const dvec4*)(smem + L.pos))[li], b = ((const dvec4*)(smem + L.pos))[lj];
     double dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;  // exact
     if (!WHOLE) {
       double sx, sy, sz;
@@ -249,7 +359,8 @@ __device__ __forceinline__ bool candidate_in(const void* sh_pos, int li, int lj,
   }
   if (r2 < band.lo) return true;
   if (r2 >= band.hi) return false;
-  return pair_in_exact(x, N, sh_gid[li], sh_gid[lj], g, band.rs2);
+  const int* gid = (const int*)(smem + L.gid);
+  return pair_in_exact(x, N, gid[li], gid[lj], g, band.rs2);
 }
 
 __device__ __forceinline__ int own_cell(const TileShared& S, int l, int Tp) {
@@ -260,12 +371,8 @@ __device__ __forceinline__ int own_cell(const TileShared& S, int l, int Tp) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Shared-memory layout of the list kernel: staged copies, sorted indices, per-own counts,
-// prefixes and chunk ballots.
 size_t list_smem_bytes(const TileArgs& ta, int precision) {
-  const size_t ps = precision == LJ_MIXED ? 16 : 32;
-  size_t b = (ps + 4) * (size_t)ta.max_staged + 8 * (size_t)ta.max_own + 4 * (size_t)ta.max_own * ta.max_chunks;
-  return (b + 15) & ~(size_t)15;
+  return tile_layout(ta, precision == LJ_MIXED, false).total;
 }
 
 template <bool MIXED, bool HALF, bool WHOLE>
@@ -276,21 +383,29 @@ __global__ void __launch_bounds__(kTileThreads, 4)
                 unsigned int* __restrict__ max_list, int32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared S;
+  __shared__ __align__(8) uint64_t bar;
   __shared__ int s_ok;
   __shared__ unsigned int s_base;
-  const int ms = ta.max_staged;
-  void* sh_pos = smem;
-  int* sh_gid = (int*)(smem + (MIXED ? 16 : 32) * (size_t)ms);
-  int* s_cnt = sh_gid + ms;                           // [max_own]
+  const TileLayout L = tile_layout(ta, MIXED, false);
+  int* sh_gid = (int*)(smem + L.gid);
+  int* s_cnt = (int*)(smem + L.cnt);                  // [max_own]
   int* s_pre = s_cnt + ta.max_own;                    // [max_own]
   uint32_t* masks = (uint32_t*)(s_pre + ta.max_own);  // [max_own * max_chunks]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
+  uint32_t phase = 0;
+  if (!WHOLE) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      fence_proxy_async_smem();
+    }
+    __syncthreads();
+  }
 
   for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
     TileInfo ti{0, 0, 0, 1};
     if (WHOLE) {
-      stage_whole<MIXED, false>(N, pos, nullptr, S, sh_pos, nullptr, sh_gid);
+      stage_whole<MIXED, false>(N, pos, nullptr, S, smem, L);
     } else {
       ti = tile_info(t, ta);
       if (!stage_offsets(ti, ta, cs, S)) {
@@ -298,7 +413,9 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         __syncthreads();
         continue;
       }
-      stage_copy<MIXED, false>(ti, ta, g, pos, nullptr, S, sh_pos, nullptr, sh_gid);
+      if (!stage_copy_async<MIXED, false>(ti, ta, g, pos, nullptr, nullptr, nullptr, S, smem, L, &bar, phase, true,
+                                          status))
+        return;
     }
     __syncthreads();
     const int n_own = S.own1 - S.own0;
@@ -320,7 +437,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
           const int j = base + lane;
           bool in = false;
           if (j < b && j != l && (!HALF || sh_gid[j] > gi))
-            in = candidate_in<MIXED, WHOLE>(sh_pos, l, j, sh_gid, x, N, g, band);
+            in = candidate_in<MIXED, WHOLE>(smem, L, l, j, x, N, g, band);
           const unsigned msk = __ballot_sync(0xffffffffu, in);
           if (lane == 0 && c < ta.max_chunks) masks[o * ta.max_chunks + c] = msk;
           ++c;
@@ -331,7 +448,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     }
     __syncthreads();
     if (warp == 0) {
-      // exclusive prefix of the row sizes; one atomic reserves the tile's segment
+      // exclusive prefix of the row sizes; one atomic reserves the tile's segment, padded to a
+      // multiple of 8 entries (16 bytes) so that the force kernel can bulk-copy it
       unsigned run = 0;
       bool ok = true;
       for (int base = 0; base < n_own; base += 32) {
@@ -349,12 +467,14 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         run += __shfl_sync(0xffffffffu, inc, 31);
       }
       if (lane == 0) {
-        const unsigned long long b = atomicAdd(counter, (unsigned long long)run);
-        const bool fits = ok && (b + run <= cap);
+        const unsigned padded = (run + 7u) & ~7u;
+        const unsigned long long b = atomicAdd(counter, (unsigned long long)padded);
+        atomicAdd(counter + 1, (unsigned long long)run);
+        const bool fits = ok && (b + padded <= cap);
         s_base = (unsigned)b;
         s_ok = fits;
-        tile_list[t] = fits ? make_uint2((unsigned)b, run) : make_uint2(0u, 0u);
-        atomicMax(max_list, run);
+        tile_list[t] = fits ? make_uint2((unsigned)b, padded) : make_uint2(0u, 0u);
+        atomicMax(max_list, padded);
         if (!ok) atomicOr(status, LJ_ST_CELL_RANGE);
       }
     }
@@ -397,14 +517,8 @@ __device__ __forceinline__ double gsum(double v) {
   return v;
 }
 
-// Shared-memory layout of the force kernel: staged copies (32 B each), sorted indices, the
-// tile's rows (relative starts) and its list segment.
-static __host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
-
-size_t force_smem_bytes(const TileArgs& ta) {
-  size_t b = align16(36 * (size_t)ta.max_staged) + 8 * (size_t)ta.max_own;
-  if (!ta.whole) b += 2 * (size_t)ta.max_list;
-  return align16(b);
+size_t force_smem_bytes(const TileArgs& ta, int precision) {
+  return tile_layout(ta, precision == LJ_MIXED, true).total;
 }
 
 // Force over the staged tile.  Pair math (Alg. 6 in eps/sigma form):
@@ -418,22 +532,31 @@ __global__ void __launch_bounds__(kTileThreads, 4)
                  double* __restrict__ part, int32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared S;
-  const int ms = ta.max_staged;
-  void* sh_pos = smem;
-  float4* sh_lo = (float4*)(smem + 16 * (size_t)ms);
-  int* sh_gid = (int*)(smem + 32 * (size_t)ms);
-  uint2* s_rows = (uint2*)(smem + align16(36 * (size_t)ms));  // [max_own], starts relative to the segment
-  uint16_t* s_ent = (uint16_t*)(s_rows + ta.max_own);  // [max_list]
+  __shared__ __align__(8) uint64_t bar;
+  const TileLayout L = tile_layout(ta, MIXED, true);
+  const void* sh_pos = smem + L.pos;
+  const float4* sh_lo = (const float4*)(smem + L.lo);
+  const int* sh_gid = (const int*)(smem + L.gid);
+  const uint2* s_rows = (const uint2*)(smem + L.rows);
+  const uint16_t* s_ent = (const uint16_t*)(smem + L.ent);
   const int lane = threadIdx.x & (LANES - 1);
   const int grp = threadIdx.x / LANES;
   constexpr int kGroups = kTileThreads / LANES;
   const double f24d = 24.0 * c.eps, f48d = 48.0 * c.eps, f8c2d = 8.0 * c.eps * c.c2 / c.sig2;
   const double e4d = 4.0 * c.eps, c2sd = c.c2 / c.sig2;
   double pe_acc = 0.0, vir_acc = 0.0;
+  uint32_t phase = 0;
+  if (!WHOLE) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      fence_proxy_async_smem();
+    }
+    __syncthreads();
+  }
 
   for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
     if (WHOLE) {
-      stage_whole<MIXED, true>(N, pos, lo, S, sh_pos, sh_lo, sh_gid);
+      stage_whole<MIXED, true>(N, pos, lo, S, smem, L);
     } else {
       const TileInfo ti = tile_info(t, ta);
       if (threadIdx.x == blockDim.x - 1) {
@@ -446,17 +569,13 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         __syncthreads();
         continue;
       }
-      stage_copy<MIXED, true>(ti, ta, g, pos, lo, S, sh_pos, sh_lo, sh_gid);
-      const int n_own = S.own1 - S.own0;
-      const bool fits = n_own <= ta.max_own && S.list_len <= (unsigned)ta.max_list;
-      for (int o = threadIdx.x; o < n_own; o += blockDim.x) {
-        const uint2 r = rows[S.gown0 + o];
-        const bool ok = fits && r.x >= S.list_base && r.x - S.list_base + r.y <= S.list_len;
-        s_rows[o] = ok ? make_uint2(r.x - S.list_base, r.y) : make_uint2(0u, 0u);
-        if (!ok) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+      if (S.own1 - S.own0 > ta.max_own || S.list_len > (unsigned)ta.max_list) {
+        if (threadIdx.x == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+        __syncthreads();
+        continue;
       }
-      if (fits)
-        for (unsigned e = threadIdx.x; e < S.list_len; e += blockDim.x) s_ent[e] = ent[S.list_base + e];
+      if (!stage_copy_async<MIXED, true>(ti, ta, g, pos, lo, rows, ent, S, smem, L, &bar, phase, HALF, status))
+        return;
     }
     __syncthreads();
     const int n_own = S.own1 - S.own0;
@@ -467,24 +586,25 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       int gi = 0;
       if (valid) {
         const int l = S.own0 + o;
-        gi = sh_gid[l];
+        gi = S.gown0 + o;
         uint2 row;
         const uint16_t* el;
         if (WHOLE) {
           row = rows[gi];
           el = ent;
         } else {
-          row = s_rows[o];
+          row = s_rows[S.row_off + o];
+          row.x -= S.list_base;
           el = s_ent;
+          if (row.x + row.y > S.list_len) {  // inconsistent row: record and skip
+            if (lane == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+            row.y = 0;
+          }
         }
         if (MIXED) {
           const float4 hi_i = ((const float4*)sh_pos)[l], lo_i = sh_lo[l];
           for (unsigned e = lane; e < row.y; e += LANES) {
             const int j = el[row.x + e];
-            if (j >= S.total) {  // inconsistent list: record and skip
-              atomicOr(status, LJ_ST_LIST_OVERFLOW);
-              continue;
-            }
             const float4 hj = ((const float4*)sh_pos)[j], lj = sh_lo[j];
             float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;  // exact
             if (WHOLE) {
@@ -518,10 +638,6 @@ __global__ void __launch_bounds__(kTileThreads, 4)
           const dvec4 qi = ((const dvec4*)sh_pos)[l];
           for (unsigned e = lane; e < row.y; e += LANES) {
             const int j = el[row.x + e];
-            if (j >= S.total) {  // inconsistent list: record and skip
-              atomicOr(status, LJ_ST_LIST_OVERFLOW);
-              continue;
-            }
             const dvec4 qj = ((const dvec4*)sh_pos)[j];
             double dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;  // exact
             if (!WHOLE) {
@@ -607,8 +723,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Expand the list into (key, partner) sorted-index pairs (for inspection).  The whole-box
-// case is a template parameter: no barrier sits under a runtime branch.
+// Expand the list into (key, partner) sorted-index pairs (for inspection).  The whole-box case
+// is a template parameter: no barrier sits under a runtime branch.
 template <bool WHOLE>
 __global__ void __launch_bounds__(kTileThreads, 4)
     k_list_decode(const uint32_t* __restrict__ cs, int64_t N, TileArgs ta, const uint2* __restrict__ rows,
@@ -763,7 +879,7 @@ int launch_force_tile(int precision, int half, int lanes, int energy, const void
                       const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
                       const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
                       cudaStream_t s) {
-  const size_t sm = force_smem_bytes(ta);
+  const size_t sm = force_smem_bytes(ta, precision);
   if (per_sm <= 0) per_sm = per_sm_for(sm);
   const int grid = tile_grid(ta, per_sm);
   if (precision == LJ_MIXED)

@@ -36,7 +36,8 @@ struct ljmd_sys {
   int64_t pe_step = -1;      // state index whose PE/virial partials are in part_force
   int64_t energy_step = -1;  // state index of the energies in d_energies
   int64_t steps = 0, rebuilds = 0;
-  uint64_t list_entries = 0;
+  uint64_t list_entries = 0;     // reserved entries (tile segments padded to 8)
+  uint64_t list_actual = 0;      // entries actually listed
   double last_dmax = 0.0;
   int nb_force = 0;
   double* log_ptr = nullptr;
@@ -296,7 +297,7 @@ static int ensure_particles(ljmd_sys* s, int64_t n) {
   TRY(dalloc_t(s, &s->cell_of, n));
   TRY(dalloc_t(s, &s->cell_alt, n));
   TRY(dalloc_t(s, &s->perm, n));
-  TRY(dalloc_t(s, &s->rows, n));
+  TRY(dalloc_t(s, &s->rows, n + 2));  // +2: aligned bulk copies of a tile's rows may read past the end
   s->cap_n = n;
   return LJ_OK;
 }
@@ -447,17 +448,18 @@ static int rebuild(ljmd_sys* s) {
       TRY(dalloc_t(s, &s->ent, want));
       s->ent_cap = want;
     }
-    CK(cudaMemsetAsync(s->d_total64, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(s->d_total64, 0, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(s->d_sizes + 3, 0, sizeof(unsigned int), st));
     launch_list_tile(s->precision, half, force_pos(s), s->x, s->cell_start, N, s->g, s->ta, s->band, s->rows,
                      s->tile_list, s->ent, (uint64_t)s->ent_cap, s->d_total64, s->d_sizes + 3, s->d_status, st);
     s->launches += 1;
     CKL();
-    CK(cudaMemcpyAsync(s->h_u32 + 2, s->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->h_u32 + 4, s->d_total64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(s->h_u32 + 12, s->d_sizes + 3, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    unsigned long long total64;
-    memcpy(&total64, s->h_u32 + 2, sizeof(total64));
+    unsigned long long total64, actual64;
+    memcpy(&total64, s->h_u32 + 4, sizeof(total64));
+    memcpy(&actual64, s->h_u32 + 6, sizeof(actual64));
     s->ta.max_list = (int32_t)s->h_u32[12];
     if (total64 > 4294967295ULL) return LJ_ERANGE;  // row starts are 32-bit
     total = total64;
@@ -472,7 +474,8 @@ static int rebuild(ljmd_sys* s) {
       int dev = 0, smem_max = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if (force_smem_bytes(s->ta) > (size_t)smem_max) return LJ_ERANGE;
+      if (force_smem_bytes(s->ta, s->precision) > (size_t)smem_max) return LJ_ERANGE;
+      s->list_actual = actual64;
       break;
     }
     // the rows did not fit: grow to the exact size plus headroom and construct again
@@ -597,7 +600,7 @@ int ljmd_create(ljmd_sys** out, const ljmd_params* p, int32_t precision, void* c
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_log_count, 1);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_status, 1);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_dmax, 1);
-  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_total64, 1);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_total64, 2);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_sizes, 4);
   if (r == LJ_OK && cudaMallocHost(&sys->h_u32, 64) != cudaSuccess) r = LJ_ENOMEM;
   if (r == LJ_OK && cudaMallocHost(&sys->h_f64, 64) != cudaSuccess) r = LJ_ENOMEM;
@@ -822,6 +825,11 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
   const uint64_t E = sys->list_entries;
   uint32_t* d_pairs = nullptr;
   TRY(dalloc_t(sys, &d_pairs, 2 * E + 2));
+  if (cudaMemsetAsync(d_pairs, 0xff, sizeof(uint32_t) * (2 * E + 2), sys->st) != cudaSuccess) {
+    cudaFree(d_pairs);
+    sys->broken = true;
+    return LJ_EDEVICE;
+  }
   launch_list_decode(sys->cell_start, N, sys->ta, sys->rows, sys->ent, E, d_pairs, sys->d_status, sys->st);
   sys->launches += 1;
   std::vector<uint32_t> pr(2 * E);
@@ -837,8 +845,9 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
     return LJ_EDEVICE;
   }
   std::vector<std::pair<int64_t, int64_t>> pairs;
-  pairs.reserve(sys->prm.list_form == LJ_LIST_FULL ? E / 2 : E);
+  pairs.reserve(sys->prm.list_form == LJ_LIST_FULL ? sys->list_actual / 2 : sys->list_actual);
   for (uint64_t k = 0; k < E; ++k) {
+    if (pr[2 * k] == 0xffffffffu) continue;  // padding between tile segments
     if (pr[2 * k] >= (uint64_t)N || pr[2 * k + 1] >= (uint64_t)N) {
       fprintf(stderr, "ljmd_get_pairs: list entry %llu decodes to (%u, %u), N = %lld\n", (unsigned long long)k,
               pr[2 * k], pr[2 * k + 1], (long long)N);
@@ -867,7 +876,7 @@ int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
   out->n = sys->n;
   out->steps = sys->steps;
   out->rebuilds = sys->rebuilds;
-  out->list_entries = (int64_t)sys->list_entries;
+  out->list_entries = (int64_t)sys->list_actual;
   out->cells_per_side = sys->g.n;
   out->box = sys->L;
   out->mean_lifetime = sys->rebuilds > 0 ? (double)sys->steps / (double)sys->rebuilds : 0.0;

@@ -108,12 +108,13 @@ struct TileArgs {
   int32_t max_staged;  // staged particles per tile, at most (<= 65535: entries are 16-bit)
   int32_t max_own;     // own particles per tile, at most
   int32_t max_chunks;  // 32-candidate chunks per own particle, at most
-  int32_t max_list;    // list entries per tile, at most (known after construction)
+  int32_t max_list;    // list entries per tile (padded to 8), at most (known after construction)
 };
 size_t list_smem_bytes(const TileArgs& ta, int precision);
-size_t force_smem_bytes(const TileArgs& ta);
+size_t force_smem_bytes(const TileArgs& ta, int precision);
 void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStream_t s);
 void launch_tile_sizes(const uint32_t* cs, TileArgs ta, unsigned int* out, cudaStream_t s);
+// counter[0] += padded tile segments (reservations), counter[1] += actual entries
 void launch_list_tile(int precision, int half, const void* pos, const double* x, const uint32_t* cs, int64_t N,
                       Geom g, TileArgs ta, ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
                       unsigned long long* counter, unsigned int* max_list, int32_t* status, cudaStream_t s);
