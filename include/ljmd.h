@@ -199,6 +199,41 @@ int ljmd_set_energy_log(ljmd_sys* sys, double* device_log, int64_t capacity);
  */
 int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
 
+/*
+ * Capacity, in list entries (tile padding included), of the static device scratch that
+ * ljmd_get_pairs_static uses: 2^19 entries of 8 bytes (4 MiB) per device.
+ */
+#define LJ_PAIRS_STATIC_MAX_ENTRIES 524288
+
+/*
+ * Allocation-free variant of ljmd_get_pairs: the same output (unique pairs (i, j), i < j in id
+ * order, sorted lexicographically; the first min(cap, npairs) of them in ij[2k], ij[2k+1];
+ * *npairs = the number of unique pairs) for lists of at most LJ_PAIRS_STATIC_MAX_ENTRIES
+ * entries.  It has no counterpart in the paper; it exists so that the list can be exported
+ * repeatedly (e.g. checked inside a long run) without the per-call device buffer of
+ * ljmd_get_pairs.
+ *
+ * It allocates nothing: the list is decoded into a file-scope static device array of
+ * LJ_PAIRS_STATIC_MAX_ENTRIES 64-bit slots plus a 256-byte header, turned into 64-bit keys
+ * (i << 32 | j), sorted on the device and copied into ij.  Each call clears what must start
+ * cleared: the kept-pair counter (to zero) and the key slots it uses (to all ones).
+ *  - The first call on a device resolves the scratch's address (cudaGetSymbolAddress, which may
+ *    load the module); make that first call before any stream capture.  Later calls on the
+ *    device reuse the address.
+ *  - One scratch per device is shared by every handle and stream of the process: calls that
+ *    overlap on one device (from two threads, or on two streams before either completes) race
+ *    and give wrong pairs.  Serialise them.
+ *  - The list must exist (ljmd_build_pairlist, ljmd_compute_forces or ljmd_step made it):
+ *    constructing one may allocate, so this call never does.
+ *  - The handle's device must be the current device.
+ *  - Synchronises the stream.
+ * Errors: LJ_EINVAL (NULL sys/npairs, cap < 0, ij NULL with cap > 0, another device current),
+ * LJ_ESTATE (no particles or no list), LJ_ERANGE (the list has more than
+ * LJ_PAIRS_STATIC_MAX_ENTRIES entries; a line naming both sizes goes to stderr and nothing is
+ * written), LJ_EDEVICE.
+ */
+int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
+
 /* Counters and state of the handle (synchronises the stream). */
 int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out);
 

@@ -937,4 +937,56 @@ int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out) {
 }
 
 
+int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
+  if (!sys || !npairs || cap < 0 || (cap > 0 && !ij)) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0 || !sys->have_list) return LJ_ESTATE;
+  const uint64_t E = sys->list_entries;
+  if (E > (uint64_t)LJ_PAIRS_STATIC_MAX_ENTRIES) {
+    fprintf(stderr, "ljmd_get_pairs_static: the list has %llu entries; the static scratch holds %d\n",
+            (unsigned long long)E, LJ_PAIRS_STATIC_MAX_ENTRIES);
+    return LJ_ERANGE;
+  }
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != sys->device) return LJ_EINVAL;
+  unsigned long long *counter = nullptr, *keys = nullptr;
+  TRY(pairs_static_scratch(dev, &counter, &keys));
+  if (E == 0) {
+    *npairs = 0;
+    return check_status(sys);
+  }
+  uint32_t P = 2;
+  while (P < E) P <<= 1;
+  // The counter must start at zero; every key slot starts all-ones (tile padding is never written
+  // by the decode, and the slots from E to P pad the sort).
+  CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), sys->st));
+  CK(cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * P, sys->st));
+  launch_list_decode(sys->cell_start, sys->n, sys->ta, sys->rows, sys->ent, E, (uint32_t*)keys, sys->d_status,
+                     sys->st);
+  CKL();
+  launch_entries_to_keys(keys, E, sys->id, sys->n, sys->prm.list_form == LJ_LIST_FULL ? 1 : 0,
+                         (unsigned int*)counter, sys->d_status, sys->st);
+  CKL();
+  sys->launches += 2 + launch_bitonic_sort(keys, P, sys->st);
+  CKL();
+  CK(cudaMemcpyAsync(sys->h_u32, counter, sizeof(uint32_t), cudaMemcpyDeviceToHost, sys->st));
+  CK(cudaStreamSynchronize(sys->st));
+  const int64_t count = (int64_t)sys->h_u32[0];
+  const int64_t m = std::min<int64_t>(cap, count);
+  if (m > 0) {
+    CK(cudaMemcpyAsync(ij, keys, sizeof(unsigned long long) * m, cudaMemcpyDeviceToHost, sys->st));
+    CK(cudaStreamSynchronize(sys->st));
+    // keys occupy ij[0, m); widen in place from the back (slot k is read before 2k, 2k+1 are written)
+    for (int64_t k = m - 1; k >= 0; --k) {
+      const uint64_t key = (uint64_t)ij[k];
+      ij[2 * k] = (int64_t)(key >> 32);
+      ij[2 * k + 1] = (int64_t)(key & 0xffffffffu);
+    }
+  }
+  *npairs = count;
+  return check_status(sys);
+}
+
+
 }  // extern "C"

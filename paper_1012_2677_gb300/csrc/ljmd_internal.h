@@ -139,4 +139,13 @@ int launch_integrate(int precision, double* x, double* v, const void* f, void* h
                      const void* ref, int64_t N, IntegrateArgs a, double* ke_part, uint32_t* dmax_bits,
                      int32_t* status, cudaStream_t s);
 
+// ---- pair export through a static device scratch array (no allocation) ----------------
+// Address of this device's scratch (resolved once per device): the kept-pair counter word and
+// LJ_PAIRS_STATIC_MAX_ENTRIES 64-bit key slots.
+int pairs_static_scratch(int device, unsigned long long** counter_word, unsigned long long** keys);
+void launch_entries_to_keys(unsigned long long* keys, uint64_t E, const int32_t* id, int64_t N, int full,
+                            unsigned int* counter, int32_t* status, cudaStream_t s);
+// Ascending bitonic sort of P = 2^m keys in place; returns the number of kernel launches.
+int launch_bitonic_sort(unsigned long long* keys, uint32_t P, cudaStream_t s);
+
 }  // namespace ljmd

@@ -22,6 +22,7 @@ LJ_OK, LJ_EINVAL, LJ_ENOMEM, LJ_EDEVICE, LJ_ESTATE, LJ_ERANGE = 0, -1, -2, -3, -
 LJ_FP64, LJ_MIXED = 0, 1
 LJ_LIST_FULL, LJ_LIST_HALF = 0, 1
 LJ_TRUNC_QUADRATIC, LJ_TRUNC_SHIFT, LJ_TRUNC_CUT = 0, 1, 2
+LJ_PAIRS_STATIC_MAX_ENTRIES = 524288  # static scratch of ljmd_get_pairs_static, in list entries
 LJ_ST_NONFINITE, LJ_ST_LIST_OVERFLOW, LJ_ST_TIMEOUT, LJ_ST_CELL_RANGE = 1, 2, 4, 8
 
 
@@ -69,6 +70,7 @@ _SIGS = {
     "ljmd_energies": (ctypes.c_int, [_P, _P, _P, _P]),
     "ljmd_set_energy_log": (ctypes.c_int, [_P, _P, _I64]),
     "ljmd_get_pairs": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ljmd_get_pairs_static": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_stats)]),
     "ljmd_set_profiling": (ctypes.c_int, [_P, _I32]),
     "ljmd_set_tuning": (ctypes.c_int, [_P, _I32, _I32, _I32]),
@@ -199,6 +201,16 @@ def ljmd_get_pairs(h):
     return out[:n.value]
 
 
+def ljmd_get_pairs_static(h, cap=None):
+    """Unique pairs of the current list through the allocation-free export (one call)."""
+    if cap is None:
+        cap = max(ljmd_get_stats(h)["list_entries"], 1)
+    n = _I64()
+    out = np.empty((max(cap, 1), 2), dtype=np.int64)
+    _chk(load().ljmd_get_pairs_static(h, out.ctypes.data_as(_P), cap, ctypes.byref(n)), "ljmd_get_pairs_static")
+    return out[:min(n.value, cap)], n.value
+
+
 def ljmd_get_stats(h) -> dict:
     st = ljmd_stats()
     _chk(load().ljmd_get_stats(h, ctypes.byref(st)), "ljmd_get_stats")
@@ -292,6 +304,10 @@ class System:
 
     def pairs(self):
         return ljmd_get_pairs(self.h)
+
+    def pairs_static(self, cap=None):
+        """(pairs, npairs) from the allocation-free export; pairs holds the first min(cap, npairs)."""
+        return ljmd_get_pairs_static(self.h, cap)
 
     def stats(self):
         return ljmd_get_stats(self.h)
