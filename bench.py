@@ -108,28 +108,41 @@ def source_sha(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def recorded_traffic(kernel_name):
-    """DRAM bytes per launch of the force kernel from the committed ncu summary, if the kernel
-    source is unchanged since it was taken (else None)."""
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_force_tile_fcc1m_rho0.5.md")
+FORCE_SOURCE = os.path.join(ROOT, "paper_1012_2677_gb300", "csrc", "kernels_tile.cu")
+
+
+def recorded_traffic(kernel_name, N):
+    """DRAM bytes of one force launch at N particles, scaled by N from the per-particle traffic in
+    the committed ncu summary of a smaller case of the same kernel, if the kernel source is
+    unchanged since the counters were taken (else None).  The summary's lines 'key: value'
+    give kernel, source_sha and dram_bytes_per_particle."""
+    rec = {}
     try:
-        with open(os.path.join(ROOT, "profiles", "force_kernel_traffic.json")) as f:
-            rec = json.load(f)
-    except (OSError, ValueError):
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if line.startswith("- ") and ": " in line:
+                    k, v = line[2:].split(": ", 1)
+                    rec[k.strip().strip("`")] = v.strip().strip("`")
+    except OSError:
         return None
-    src = os.path.join(ROOT, "paper_1012_2677_gb300", "csrc", "kernels_force.cu")
-    if rec.get("source_sha") != source_sha(src) or rec.get("kernel") != kernel_name:
+    if rec.get("source_sha") != source_sha(FORCE_SOURCE) or rec.get("kernel") != kernel_name:
         return None
-    return rec.get("dram_bytes_per_launch")
+    try:
+        return round(float(rec["dram_bytes_per_particle"]) * N)
+    except (KeyError, ValueError):
+        return None
 
 
 def force_kernel_work(N, entries, precision, energy=True):
-    """Algorithmic bytes and flops of one force launch over the full list (mixed form):
-    the list entries (4 B), row offsets (4 B), the key particle's hi/lo copy (32 B) and the
-    force written (16 B); partner positions come from L1/L2 thanks to the cell order and
-    count zero.  Flops: 22 per listed pair (Alg. 6), 8 more with the energy and virial."""
-    pos = 32 if precision == "mixed" else 32
+    """Algorithmic bytes and flops of one force launch over the full list.  Bytes: each list
+    entry once (2 B: a 16-bit index into the key's staged tile), each particle's row (start,
+    length: 8 B), its position once (mixed: FP32 hi and lo parts, 32 B; FP64: 32 B) and its force
+    written once (mixed: float4, 16 B; FP64: 32 B).  Re-reads of neighbour cells for the halo of
+    a tile count zero.  Flops: 22 per listed pair (Alg. 6 with the r^2 < r_c^2 select), 8 more
+    with the energy and virial."""
     fout = 16 if precision == "mixed" else 32
-    bytes_ = 4 * entries + N * (4 + pos + fout)
+    bytes_ = 2 * entries + N * (8 + 32 + fout)
     flops = entries * (22 + (8 if energy else 0))
     return bytes_, flops
 
@@ -189,8 +202,8 @@ def run_ours(args, wl, world, rank, local):
     ach_tf = fl / (f_ms * 1e-3) / 1e12
     hbm_frac = ach_gbs / peaks["hbm_gbs"]
     alu_frac = ach_tf / FP32_PEAK_TFLOPS
-    kernel_name = "k_force_mixed"
-    traffic = recorded_traffic(kernel_name)
+    kernel_name = "k_force_tile"
+    traffic = recorded_traffic(kernel_name, N)
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": round(ach_tf, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
                 "frac": round(alu_frac, 4), "traffic": traffic,
