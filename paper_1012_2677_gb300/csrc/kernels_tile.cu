@@ -172,82 +172,93 @@ __host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, b
 }
 
 // Issue the bulk copies of one tile (warp 0; lane k < 9 handles column k, lane 9 the rows and
-// list segment) and wait for them (all threads, bounded).  Copies: positions (hi [+ lo] or
-// FP64), and for the force kernel the own rows and the list segment.  Then the image shifts
-// (and the sorted indices, if wanted) are filled in.  Returns false (all threads) on timeout.
+// list segment), all completing on `bar`.  Copies: positions (hi [+ lo] or FP64), and for the
+// force kernel the own rows and the list segment.  No barrier inside: the other warps go on.
 template <bool MIXED, bool FORCE>
-__device__ __forceinline__ bool stage_copy_async(const TileInfo& ti, const TileArgs& ta, const Geom& g,
-                                                 const void* __restrict__ pos, const float4* __restrict__ lo,
-                                                 const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
-                                                 TileShared& S, unsigned char* smem, const TileLayout& L,
-                                                 uint64_t* bar, uint32_t& phase, bool want_gid, int32_t* status) {
+__device__ __forceinline__ void stage_issue(const TileInfo& ti, const TileArgs& ta, const void* __restrict__ pos,
+                                            const float4* __restrict__ lo, const uint2* __restrict__ rows,
+                                            const uint16_t* __restrict__ ent, TileShared& S, unsigned char* smem,
+                                            const TileLayout& L, uint64_t* bar) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned bpp = MIXED ? 16u : 32u;
-  if (warp == 0) {
-    unsigned bytes = (unsigned)S.total * bpp * ((MIXED && FORCE) ? 2u : 1u);
-    int r0 = 0, r1 = 0;
-    const int n_own = S.own1 - S.own0;
-    if (FORCE) {
-      r0 = S.gown0 & ~1;
-      r1 = (S.gown0 + n_own + 1) & ~1;
-      if (n_own > 0) bytes += 8u * (unsigned)(r1 - r0);
-      bytes += 2u * S.list_len;
-    }
-    if (lane == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect(bar, bytes);
-    }
-    __syncwarp();
-    if (lane < 9) {
-      // runs of consecutive z in column `lane`
-      const int k = lane, ncol = S.ncol;
-      int m = 0;
-      while (m < ncol) {
-        int sx, sy, sz;
-        const uint32_t c0 = cell_of_q(ti, ta.n, ncol, k * ncol + m, sx, sy, sz);
-        int m1 = m + 1;
-        uint32_t c1 = c0;
-        while (m1 < ncol) {
-          int tx, ty, tz;
-          const uint32_t c = cell_of_q(ti, ta.n, ncol, k * ncol + m1, tx, ty, tz);
-          if (c != c1 + 1) break;
-          c1 = c;
-          ++m1;
-        }
-        const int q0 = k * ncol + m;
-        const unsigned n = (unsigned)(S.offq[k * ncol + m1] - S.offq[q0]);
-        if (n > 0) {
-          const size_t gsrc = (size_t)S.g0[q0];
-          const size_t dst = (size_t)S.offq[q0];
-          if (MIXED) {
-            bulk_g2s(smem + L.pos + 16 * dst, (const float4*)pos + gsrc, 16u * n, bar);
-            if (FORCE) bulk_g2s(smem + L.lo + 16 * dst, lo + gsrc, 16u * n, bar);
-          } else {
-            bulk_g2s(smem + L.pos + 32 * dst, (const dvec4*)pos + gsrc, 32u * n, bar);
-          }
-        }
-        m = m1;
-      }
-    } else if (FORCE && lane == 9) {
-      if (n_own > 0) bulk_g2s(smem + L.rows, rows + r0, 8u * (unsigned)(r1 - r0), bar);
-      if (S.list_len > 0) bulk_g2s(smem + L.ent, ent + S.list_base, 2u * S.list_len, bar);
-      S.row_off = S.gown0 - r0;
-    }
+  if (warp != 0) return;
+  unsigned bytes = (unsigned)S.total * bpp * ((MIXED && FORCE) ? 2u : 1u);
+  int r0 = 0, r1 = 0;
+  const int n_own = S.own1 - S.own0;
+  if (FORCE) {
+    r0 = S.gown0 & ~1;
+    r1 = (S.gown0 + n_own + 1) & ~1;
+    if (n_own > 0) bytes += 8u * (unsigned)(r1 - r0);
+    bytes += 2u * S.list_len;
   }
-  bool ok = mbar_wait(bar, phase, kWaitBudget);
+  if (lane == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect(bar, bytes);
+  }
+  __syncwarp();
+  if (lane < 9) {
+    // column `lane`: cells z0-1 .. z0+Tp wrapped in z; they are contiguous in the sorted arrays
+    // except where z wraps (first cell when z0 = 0, last cell when z0 + Tp = n), so one to two runs
+    const int k = lane, ncol = S.ncol;
+    int cut0 = 0, cut1 = ncol;  // middle run [cut0, cut1); wrapped single cells outside it
+    if (ti.z0 == 0) cut0 = 1;
+    if (ti.z0 + ti.Tp == ta.n) cut1 = ncol - 1;
+    const int bounds[4] = {0, cut0, cut1, ncol};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int m0 = bounds[r], m1 = bounds[r + 1];
+      if (m1 <= m0) continue;
+      const int q0 = k * ncol + m0;
+      const unsigned n = (unsigned)(S.offq[k * ncol + m1] - S.offq[q0]);
+      if (n > 0) {
+        const size_t gsrc = (size_t)S.g0[q0];
+        const size_t dst = (size_t)S.offq[q0];
+        if (MIXED) {
+          bulk_g2s(smem + L.pos + 16 * dst, (const float4*)pos + gsrc, 16u * n, bar);
+          if (FORCE) bulk_g2s(smem + L.lo + 16 * dst, lo + gsrc, 16u * n, bar);
+        } else {
+          bulk_g2s(smem + L.pos + 32 * dst, (const dvec4*)pos + gsrc, 32u * n, bar);
+        }
+      }
+    }
+  } else if (FORCE && lane == 9) {
+    if (n_own > 0) bulk_g2s(smem + L.rows, rows + r0, 8u * (unsigned)(r1 - r0), bar);
+    if (S.list_len > 0) bulk_g2s(smem + L.ent, ent + S.list_base, 2u * S.list_len, bar);
+    S.row_off = S.gown0 - r0;
+  }
+}
+
+// Wait (all threads, bounded) for the copies of a staged tile, then fill in the image shifts
+// (mixed: added to hi/lo; FP64: code in w) and, if wanted, the sorted indices.  Returns false
+// (all threads) on timeout, after recording it; the caller drains any other copies in flight.
+template <bool MIXED, bool FORCE>
+__device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs& ta, const Geom& g, TileShared& S,
+                                             unsigned char* smem, const TileLayout& L, uint64_t* bar,
+                                             uint32_t& phase, bool want_gid, int32_t* status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // one thread polls the barrier; the others wait at the CTA barrier without taking issue slots
+  bool ok = true;
+  if (threadIdx.x == 0) ok = mbar_wait(bar, phase, kWaitBudget);
   ok = __syncthreads_and(ok) != 0;
   if (!ok) {
-    if (threadIdx.x == 0) atomicOr(status, LJ_ST_TIMEOUT);
-    mbar_wait(bar, phase, kWaitBudget);  // let copies in flight land before the CTA leaves
+    if (threadIdx.x == 0) {
+      atomicOr(status, LJ_ST_TIMEOUT);
+      mbar_wait(bar, phase, kWaitBudget);  // let copies in flight land before the CTA leaves
+    }
+    __syncthreads();
     return false;
   }
   phase ^= 1u;
-  // image shifts (mixed: add to hi/lo; FP64: code in w) and sorted indices, one warp per cell
+  // interior tiles (no periodic image among the staged cells) need no shifts
+  const bool interior = ti.cx >= 1 && ti.cx <= ta.n - 2 && ti.cy >= 1 && ti.cy <= ta.n - 2 && ti.z0 >= 1 &&
+                        ti.z0 + ti.Tp <= ta.n - 1;
+  if (MIXED && interior && !want_gid) return true;
   for (int q = warp; q < S.ncell; q += kWarps) {
-    int sx, sy, sz;
-    cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
-    const int a = S.offq[q], b = S.offq[q + 1], gq = S.g0[q];
+    int sx = 0, sy = 0, sz = 0;
+    if (!interior) cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
     const bool shifted = (sx | sy | sz) != 0;
+    if (MIXED && !shifted && !want_gid) continue;  // FP64: every slot gets its shift code
+    const int a = S.offq[q], b = S.offq[q + 1], gq = S.g0[q];
     for (int s = a + lane; s < b; s += 32) {
       if (MIXED) {
         if (shifted) {
@@ -268,10 +279,21 @@ __device__ __forceinline__ bool stage_copy_async(const TileInfo& ti, const TileA
       if (want_gid) ((int*)(smem + L.gid))[s] = gq + (s - a);
     }
   }
-  // these generic writes precede the next tile's bulk copies into the same bytes
+  // these generic writes precede later bulk copies into the same bytes
   fence_proxy_async_smem();
   __syncthreads();
   return true;
+}
+
+// Issue, wait and fix up one tile (single-buffered use).
+template <bool MIXED, bool FORCE>
+__device__ __forceinline__ bool stage_copy_async(const TileInfo& ti, const TileArgs& ta, const Geom& g,
+                                                 const void* __restrict__ pos, const float4* __restrict__ lo,
+                                                 const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
+                                                 TileShared& S, unsigned char* smem, const TileLayout& L,
+                                                 uint64_t* bar, uint32_t& phase, bool want_gid, int32_t* status) {
+  stage_issue<MIXED, FORCE>(ti, ta, pos, lo, rows, ent, S, smem, L, bar);
+  return stage_finish<MIXED, FORCE>(ti, ta, g, S, smem, L, bar, phase, want_gid, status);
 }
 
 // Whole box as one tile (fewer than 3 cells per side): everything staged directly, no shifts.
@@ -517,198 +539,287 @@ __device__ __forceinline__ double gsum(double v) {
   return v;
 }
 
-size_t force_smem_bytes(const TileArgs& ta, int precision) {
-  return tile_layout(ta, precision == LJ_MIXED, true).total;
+// Shared memory of the force kernel: `nbuf` tile buffers (with two, the next tile's copies are in
+// flight while the current one is computed); one for the whole-box case.
+size_t force_buffer_bytes(const TileArgs& ta, int precision) {
+  return align16(tile_layout(ta, precision == LJ_MIXED, true).total);
+}
+size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf) {
+  return (ta.whole ? 1 : (nbuf == 2 ? 2 : 1)) * force_buffer_bytes(ta, precision);
 }
 
-// Force over the staged tile.  Pair math (Alg. 6 in eps/sigma form):
+// 1/x from the hardware approximation (rcp.approx) refined by one Newton-Raphson step
+// r' = r + r (1 - x r), which roughly squares its relative error.
+__device__ __forceinline__ float rcp_nr(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
+struct AccF {
+  float fx, fy, fz, pe, vir;
+};
+
+// One listed pair in the mixed form (Alg. 6 in eps/sigma form):
 //   f = ri2 s3i (24 eps - 48 eps s3i) + 8 eps c2 / sigma^2, zero for r^2 >= r_c^2 (select)
 //   V = 4 eps [s3i (s3i - 1) + c2 r^2 / sigma^2 + c0],  W += -f r^2
+template <bool HALF, bool ENERGY, bool WHOLE>
+__device__ __forceinline__ void pair_mixed(const float4& hi_i, const float4& lo_i, const float4& hj, const float4& lj,
+                                           const LJConst& c, const Geom& g, AccF& a, float4* fout, int gj) {
+  float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;  // exact
+  if (WHOLE) {
+    const float mx = rintf(dx * g.inv_L), my = rintf(dy * g.inv_L), mz = rintf(dz * g.inv_L);
+    dx = fmaf(-mx, g.L_hi, dx) + fmaf(-mx, g.L_lo, lj.x - lo_i.x);
+    dy = fmaf(-my, g.L_hi, dy) + fmaf(-my, g.L_lo, lj.y - lo_i.y);
+    dz = fmaf(-mz, g.L_hi, dz) + fmaf(-mz, g.L_lo, lj.z - lo_i.z);
+  } else {
+    dx += lj.x - lo_i.x;
+    dy += lj.y - lo_i.y;
+    dz += lj.z - lo_i.z;
+  }
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float ri2 = rcp_nr(r2);
+  const float si = c.sig2f * ri2;
+  const float s3i = si * si * si;
+  const bool in = r2 < c.rc2f;
+  float ff = fmaf(ri2 * s3i, fmaf(-c.f48, s3i, c.f24), c.f8c2);
+  ff = in ? ff : 0.0f;
+  a.fx = fmaf(ff, dx, a.fx);
+  a.fy = fmaf(ff, dy, a.fy);
+  a.fz = fmaf(ff, dz, a.fz);
+  if (HALF) atomicAdd(&fout[gj], make_float4(-ff * dx, -ff * dy, -ff * dz, 0.0f));
+  if (ENERGY) {
+    const float v = c.e4 * fmaf(s3i, s3i - 1.0f, fmaf(c.c2f, r2, c.c0f));
+    a.pe += in ? v : 0.0f;
+    a.vir = fmaf(-ff, r2, a.vir);
+  }
+}
+
+// Forces of the own particles of one staged tile (buffer `buf`); group `grp` of LANES threads per
+// key particle, lanes striding over its row.
 template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE>
-__global__ void __launch_bounds__(kTileThreads, 4)
-    k_force_tile(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
-                 int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows,
-                 const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent, void* __restrict__ fout,
-                 double* __restrict__ part, int32_t* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ TileShared S;
-  __shared__ __align__(8) uint64_t bar;
-  const TileLayout L = tile_layout(ta, MIXED, true);
-  const void* sh_pos = smem + L.pos;
-  const float4* sh_lo = (const float4*)(smem + L.lo);
-  const int* sh_gid = (const int*)(smem + L.gid);
-  const uint2* s_rows = (const uint2*)(smem + L.rows);
-  const uint16_t* s_ent = (const uint16_t*)(smem + L.ent);
+__device__ __forceinline__ void force_tile_compute(const TileShared& S, const unsigned char* buf, const TileLayout& L,
+                                                   const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
+                                                   const LJConst& c, const Geom& g, void* __restrict__ fout,
+                                                   int32_t* __restrict__ status, double& pe_acc, double& vir_acc) {
+  const void* sh_pos = buf + L.pos;
+  const float4* sh_lo = (const float4*)(buf + L.lo);
+  const int* sh_gid = (const int*)(buf + L.gid);
+  const uint2* s_rows = (const uint2*)(buf + L.rows);
+  const uint16_t* s_ent = (const uint16_t*)(buf + L.ent);
   const int lane = threadIdx.x & (LANES - 1);
   const int grp = threadIdx.x / LANES;
   constexpr int kGroups = kTileThreads / LANES;
   const double f24d = 24.0 * c.eps, f48d = 48.0 * c.eps, f8c2d = 8.0 * c.eps * c.c2 / c.sig2;
   const double e4d = 4.0 * c.eps, c2sd = c.c2 / c.sig2;
-  double pe_acc = 0.0, vir_acc = 0.0;
-  uint32_t phase = 0;
-  if (!WHOLE) {
-    if (threadIdx.x == 0) {
-      mbar_init(&bar, 1);
-      fence_proxy_async_smem();
-    }
-    __syncthreads();
-  }
-
-  for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
-    if (WHOLE) {
-      stage_whole<MIXED, true>(N, pos, lo, S, smem, L);
-    } else {
-      const TileInfo ti = tile_info(t, ta);
-      if (threadIdx.x == blockDim.x - 1) {
-        const uint2 tl = tile_list[t];
-        S.list_base = tl.x;
-        S.list_len = tl.y;
-      }
-      if (!stage_offsets(ti, ta, cs, S)) {
-        if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
-        __syncthreads();
-        continue;
-      }
-      if (S.own1 - S.own0 > ta.max_own || S.list_len > (unsigned)ta.max_list) {
-        if (threadIdx.x == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
-        __syncthreads();
-        continue;
-      }
-      if (!stage_copy_async<MIXED, true>(ti, ta, g, pos, lo, rows, ent, S, smem, L, &bar, phase, HALF, status))
-        return;
-    }
-    __syncthreads();
-    const int n_own = S.own1 - S.own0;
-    for (int o = grp; __any_sync(0xffffffffu, o < n_own); o += kGroups) {
-      const bool valid = o < n_own;
-      float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f, vir = 0.f;
-      double dfx = 0.0, dfy = 0.0, dfz = 0.0, dpe = 0.0, dvir = 0.0;
-      int gi = 0;
-      if (valid) {
-        const int l = S.own0 + o;
-        gi = S.gown0 + o;
-        uint2 row;
-        const uint16_t* el;
-        if (WHOLE) {
-          row = rows[gi];
-          el = ent;
-        } else {
-          row = s_rows[S.row_off + o];
-          row.x -= S.list_base;
-          el = s_ent;
-          if (row.x + row.y > S.list_len) {  // inconsistent row: record and skip
-            if (lane == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
-            row.y = 0;
-          }
-        }
-        if (MIXED) {
-          const float4 hi_i = ((const float4*)sh_pos)[l], lo_i = sh_lo[l];
-          for (unsigned e = lane; e < row.y; e += LANES) {
-            const int j = el[row.x + e];
-            const float4 hj = ((const float4*)sh_pos)[j], lj = sh_lo[j];
-            float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;  // exact
-            if (WHOLE) {
-              const float mx = rintf(dx * g.inv_L), my = rintf(dy * g.inv_L), mz = rintf(dz * g.inv_L);
-              dx = fmaf(-mx, g.L_hi, dx) + fmaf(-mx, g.L_lo, lj.x - lo_i.x);
-              dy = fmaf(-my, g.L_hi, dy) + fmaf(-my, g.L_lo, lj.y - lo_i.y);
-              dz = fmaf(-mz, g.L_hi, dz) + fmaf(-mz, g.L_lo, lj.z - lo_i.z);
-            } else {
-              dx += lj.x - lo_i.x;
-              dy += lj.y - lo_i.y;
-              dz += lj.z - lo_i.z;
-            }
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri2 = __frcp_rn(r2);
-            const float si = c.sig2f * ri2;
-            const float s3i = si * si * si;
-            const bool in = r2 < c.rc2f;
-            float ff = fmaf(ri2 * s3i, fmaf(-c.f48, s3i, c.f24), c.f8c2);
-            ff = in ? ff : 0.0f;
-            fx = fmaf(ff, dx, fx);
-            fy = fmaf(ff, dy, fy);
-            fz = fmaf(ff, dz, fz);
-            if (HALF) atomicAdd(&((float4*)fout)[sh_gid[j]], make_float4(-ff * dx, -ff * dy, -ff * dz, 0.0f));
-            if (ENERGY) {
-              const float v = c.e4 * fmaf(s3i, s3i - 1.0f, fmaf(c.c2f, r2, c.c0f));
-              pe += in ? v : 0.0f;
-              vir = fmaf(-ff, r2, vir);
-            }
-          }
-        } else {
-          const dvec4 qi = ((const dvec4*)sh_pos)[l];
-          for (unsigned e = lane; e < row.y; e += LANES) {
-            const int j = el[row.x + e];
-            const dvec4 qj = ((const dvec4*)sh_pos)[j];
-            double dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;  // exact
-            if (!WHOLE) {
-              double sx, sy, sz;
-              shift_of(qj.w, g, sx, sy, sz);
-              dx += sx;
-              dy += sy;
-              dz += sz;
-            } else {
-              dx = fma(-rint(dx * g.inv_L64), g.L, dx);
-              dy = fma(-rint(dy * g.inv_L64), g.L, dy);
-              dz = fma(-rint(dz * g.inv_L64), g.L, dz);
-            }
-            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            const double ri2 = __drcp_rn(r2);
-            const double si = c.sig2 * ri2;
-            const double s3i = si * si * si;
-            const bool in = r2 < c.rc2;
-            double ff = fma(ri2 * s3i, fma(-f48d, s3i, f24d), f8c2d);
-            ff = in ? ff : 0.0;
-            dfx = fma(ff, dx, dfx);
-            dfy = fma(ff, dy, dfy);
-            dfz = fma(ff, dz, dfz);
-            if (HALF) {
-              dvec4* F = (dvec4*)fout;
-              const int gj = sh_gid[j];
-              atomicAdd(&F[gj].x, -ff * dx);
-              atomicAdd(&F[gj].y, -ff * dy);
-              atomicAdd(&F[gj].z, -ff * dz);
-            }
-            if (ENERGY) {
-              const double v = e4d * fma(s3i, s3i - 1.0, fma(c2sd, r2, c.c0));
-              dpe += in ? v : 0.0;
-              dvir = fma(-ff, r2, dvir);
-            }
-          }
+  const int n_own = S.own1 - S.own0;
+  for (int o = grp; __any_sync(0xffffffffu, o < n_own); o += kGroups) {
+    const bool valid = o < n_own;
+    AccF a0{0.f, 0.f, 0.f, 0.f, 0.f}, a1{0.f, 0.f, 0.f, 0.f, 0.f};
+    double dfx = 0.0, dfy = 0.0, dfz = 0.0, dpe = 0.0, dvir = 0.0;
+    int gi = 0;
+    if (valid) {
+      const int l = S.own0 + o;
+      gi = S.gown0 + o;
+      uint2 row;
+      const uint16_t* el;
+      if (WHOLE) {
+        row = rows[gi];
+        el = ent;
+      } else {
+        row = s_rows[S.row_off + o];
+        row.x -= S.list_base;
+        el = s_ent;
+        if (row.x + row.y > S.list_len) {  // inconsistent row: record and skip
+          if (lane == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+          row.y = 0;
         }
       }
       if (MIXED) {
-        fx = gsum<LANES>(fx);
-        fy = gsum<LANES>(fy);
-        fz = gsum<LANES>(fz);
-        if (valid && lane == 0) {
-          if (HALF) atomicAdd(&((float4*)fout)[gi], make_float4(fx, fy, fz, 0.0f));
-          else ((float4*)fout)[gi] = make_float4(fx, fy, fz, 0.0f);
+        const float4 hi_i = ((const float4*)sh_pos)[l], lo_i = sh_lo[l];
+        float4* F = (float4*)fout;
+        unsigned e = lane;
+        // two independent entries per iteration
+        for (; e + LANES < row.y; e += 2 * LANES) {
+          const int j0 = el[row.x + e], j1 = el[row.x + e + LANES];
+          const float4 h0 = ((const float4*)sh_pos)[j0], q0 = sh_lo[j0];
+          const float4 h1 = ((const float4*)sh_pos)[j1], q1 = sh_lo[j1];
+          pair_mixed<HALF, ENERGY, WHOLE>(hi_i, lo_i, h0, q0, c, g, a0, F, HALF ? sh_gid[j0] : 0);
+          pair_mixed<HALF, ENERGY, WHOLE>(hi_i, lo_i, h1, q1, c, g, a1, F, HALF ? sh_gid[j1] : 0);
         }
-        if (ENERGY) {
-          pe_acc += (double)pe;
-          vir_acc += (double)vir;
+        if (e < row.y) {
+          const int j0 = el[row.x + e];
+          pair_mixed<HALF, ENERGY, WHOLE>(hi_i, lo_i, ((const float4*)sh_pos)[j0], sh_lo[j0], c, g, a0, F,
+                                          HALF ? sh_gid[j0] : 0);
         }
       } else {
-        dfx = gsum<LANES>(dfx);
-        dfy = gsum<LANES>(dfy);
-        dfz = gsum<LANES>(dfz);
-        if (valid && lane == 0) {
-          dvec4* F = (dvec4*)fout;
-          if (HALF) {
-            atomicAdd(&F[gi].x, dfx);
-            atomicAdd(&F[gi].y, dfy);
-            atomicAdd(&F[gi].z, dfz);
+        const dvec4 qi = ((const dvec4*)sh_pos)[l];
+        for (unsigned e = lane; e < row.y; e += LANES) {
+          const int j = el[row.x + e];
+          const dvec4 qj = ((const dvec4*)sh_pos)[j];
+          double dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;  // exact
+          if (!WHOLE) {
+            double sx, sy, sz;
+            shift_of(qj.w, g, sx, sy, sz);
+            dx += sx;
+            dy += sy;
+            dz += sz;
           } else {
-            F[gi] = make_dvec4(dfx, dfy, dfz, 0.0);
+            dx = fma(-rint(dx * g.inv_L64), g.L, dx);
+            dy = fma(-rint(dy * g.inv_L64), g.L, dy);
+            dz = fma(-rint(dz * g.inv_L64), g.L, dz);
           }
-        }
-        if (ENERGY) {
-          pe_acc += dpe;
-          vir_acc += dvir;
+          const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+          const double ri2 = __drcp_rn(r2);
+          const double si = c.sig2 * ri2;
+          const double s3i = si * si * si;
+          const bool in = r2 < c.rc2;
+          double ff = fma(ri2 * s3i, fma(-f48d, s3i, f24d), f8c2d);
+          ff = in ? ff : 0.0;
+          dfx = fma(ff, dx, dfx);
+          dfy = fma(ff, dy, dfy);
+          dfz = fma(ff, dz, dfz);
+          if (HALF) {
+            dvec4* F = (dvec4*)fout;
+            const int gj = sh_gid[j];
+            atomicAdd(&F[gj].x, -ff * dx);
+            atomicAdd(&F[gj].y, -ff * dy);
+            atomicAdd(&F[gj].z, -ff * dz);
+          }
+          if (ENERGY) {
+            const double v = e4d * fma(s3i, s3i - 1.0, fma(c2sd, r2, c.c0));
+            dpe += in ? v : 0.0;
+            dvir = fma(-ff, r2, dvir);
+          }
         }
       }
     }
+    if (MIXED) {
+      float fx = gsum<LANES>(a0.fx + a1.fx);
+      float fy = gsum<LANES>(a0.fy + a1.fy);
+      float fz = gsum<LANES>(a0.fz + a1.fz);
+      if (valid && lane == 0) {
+        if (HALF) atomicAdd(&((float4*)fout)[gi], make_float4(fx, fy, fz, 0.0f));
+        else ((float4*)fout)[gi] = make_float4(fx, fy, fz, 0.0f);
+      }
+      if (ENERGY) {
+        pe_acc += (double)a0.pe + (double)a1.pe;
+        vir_acc += (double)a0.vir + (double)a1.vir;
+      }
+    } else {
+      dfx = gsum<LANES>(dfx);
+      dfy = gsum<LANES>(dfy);
+      dfz = gsum<LANES>(dfz);
+      if (valid && lane == 0) {
+        dvec4* F = (dvec4*)fout;
+        if (HALF) {
+          atomicAdd(&F[gi].x, dfx);
+          atomicAdd(&F[gi].y, dfy);
+          atomicAdd(&F[gi].z, dfz);
+        } else {
+          F[gi] = make_dvec4(dfx, dfy, dfz, 0.0);
+        }
+      }
+      if (ENERGY) {
+        pe_acc += dpe;
+        vir_acc += dvir;
+      }
+    }
+  }
+}
+
+// Bookkeeping of one tile before its copies are issued: segment of the list, cell bounds,
+// capacity checks (identical in every thread).  Returns whether the tile can be staged.
+__device__ __forceinline__ bool force_tile_prepare(int64_t t, const TileArgs& ta, const uint32_t* __restrict__ cs,
+                                                   const uint2* __restrict__ tile_list, TileShared& S,
+                                                   int32_t* __restrict__ status) {
+  const TileInfo ti = tile_info(t, ta);
+  if (threadIdx.x == blockDim.x - 1) {
+    const uint2 tl = tile_list[t];
+    S.list_base = tl.x;
+    S.list_len = tl.y;
+  }
+  if (!stage_offsets(ti, ta, cs, S)) {
+    if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
+    return false;
+  }
+  if (S.own1 - S.own0 > ta.max_own || S.list_len > (unsigned)ta.max_list) {
+    if (threadIdx.x == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+    return false;
+  }
+  return true;
+}
+
+// Force over the list, tile by tile.  With nbuf = 2 each CTA walks its tiles with two
+// shared-memory buffers: the copies of tile t + gridDim.x are issued before tile t is computed,
+// so the copy latency overlaps the pair arithmetic; with nbuf = 1 the tiles are staged one after
+// the other and the overlap comes from the other CTAs of the SM.  Energies: per-thread FP64
+// sums -> one partial per block.
+template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_force_tile(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
+                 int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows,
+                 const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent, void* __restrict__ fout,
+                 double* __restrict__ part, int32_t* __restrict__ status, int nbuf) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileShared SS[2];
+  __shared__ __align__(8) uint64_t bars[2];
+  const TileLayout L = tile_layout(ta, MIXED, true);
+  const size_t buf_bytes = align16(L.total);
+  double pe_acc = 0.0, vir_acc = 0.0;
+  if (WHOLE) {
+    if (blockIdx.x == 0) {
+      stage_whole<MIXED, true>(N, pos, lo, SS[0], smem, L);
+      __syncthreads();
+      force_tile_compute<MIXED, LANES, HALF, ENERGY, true>(SS[0], smem, L, rows, ent, c, g, fout, status, pe_acc,
+                                                           vir_acc);
+    }
+  } else {
+    const bool pipelined = nbuf == 2;
+    if (threadIdx.x == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      fence_proxy_async_smem();
+    }
     __syncthreads();
+    uint32_t ph0 = 0, ph1 = 0;
+    int64_t t = blockIdx.x;
+    int b = 0;
+    bool v_cur = false, v_next = false;
+    if (pipelined && t < ta.ntiles) {
+      v_cur = force_tile_prepare(t, ta, cs, tile_list, SS[0], status);
+      if (v_cur) stage_issue<MIXED, true>(tile_info(t, ta), ta, pos, lo, rows, ent, SS[0], smem, L, &bars[0]);
+    }
+    for (; t < ta.ntiles; t += gridDim.x) {
+      if (!pipelined) {
+        v_cur = force_tile_prepare(t, ta, cs, tile_list, SS[0], status);
+        if (v_cur) stage_issue<MIXED, true>(tile_info(t, ta), ta, pos, lo, rows, ent, SS[0], smem, L, &bars[0]);
+      } else {
+        const int64_t tn = t + gridDim.x;
+        v_next = false;
+        if (tn < ta.ntiles) {
+          v_next = force_tile_prepare(tn, ta, cs, tile_list, SS[b ^ 1], status);
+          if (v_next)
+            stage_issue<MIXED, true>(tile_info(tn, ta), ta, pos, lo, rows, ent, SS[b ^ 1],
+                                     smem + (b ^ 1) * buf_bytes, L, &bars[b ^ 1]);
+        }
+      }
+      if (v_cur) {
+        uint32_t& ph = b ? ph1 : ph0;
+        if (!stage_finish<MIXED, true>(tile_info(t, ta), ta, g, SS[b], smem + b * buf_bytes, L, &bars[b], ph, HALF,
+                                       status)) {
+          if (v_next) mbar_wait(&bars[b ^ 1], b ? ph0 : ph1, kWaitBudget);  // drain the other buffer's copies
+          return;
+        }
+        force_tile_compute<MIXED, LANES, HALF, ENERGY, false>(SS[b], smem + b * buf_bytes, L, rows, ent, c, g, fout,
+                                                              status, pe_acc, vir_acc);
+      }
+      __syncthreads();
+      if (pipelined) {
+        v_cur = v_next;
+        b ^= 1;
+      }
+    }
   }
   if (ENERGY) {
     __shared__ double sh[32];
@@ -836,56 +947,56 @@ void launch_list_tile(int precision, int half, const void* pos, const double* x,
 template <bool MIXED, int LANES, bool HALF, bool ENERGY>
 static void force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
                     const uint2* rows, const uint2* tl, const uint16_t* ent, void* f, double* part, int32_t* status,
-                    int grid, size_t sm, cudaStream_t s) {
+                    int nbuf, int grid, size_t sm, cudaStream_t s) {
   if (ta.whole) {
     set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, true>, sm);
     k_force_tile<MIXED, LANES, HALF, ENERGY, true><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c, rows, tl,
-                                                                                  ent, f, part, status);
+                                                                                  ent, f, part, status, nbuf);
   } else {
     set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, false>, sm);
     k_force_tile<MIXED, LANES, HALF, ENERGY, false><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c, rows, tl,
-                                                                                   ent, f, part, status);
+                                                                                   ent, f, part, status, nbuf);
   }
 }
 
 template <bool MIXED, int LANES>
 static void force_l(int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
                     TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
-                    double* part, int32_t* status, int grid, size_t sm, cudaStream_t s) {
+                    double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
   if (half) {
-    if (energy) force_w<MIXED, LANES, true, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s);
-    else force_w<MIXED, LANES, true, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s);
+    if (energy) force_w<MIXED, LANES, true, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    else force_w<MIXED, LANES, true, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
   } else {
-    if (energy) force_w<MIXED, LANES, false, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s);
-    else force_w<MIXED, LANES, false, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s);
+    if (energy) force_w<MIXED, LANES, false, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    else force_w<MIXED, LANES, false, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
   }
 }
 
 template <bool MIXED>
 static void force_p(int lanes, int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N,
                     Geom g, TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
-                    double* part, int32_t* status, int grid, size_t sm, cudaStream_t s) {
+                    double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
   switch (lanes) {
-    case 1: force_l<MIXED, 1>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
-    case 2: force_l<MIXED, 2>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
-    case 4: force_l<MIXED, 4>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
-    case 8: force_l<MIXED, 8>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
-    case 16: force_l<MIXED, 16>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
-    default: force_l<MIXED, 32>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, grid, sm, s); break;
+    case 1: force_l<MIXED, 1>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
+    case 2: force_l<MIXED, 2>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
+    case 4: force_l<MIXED, 4>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
+    case 8: force_l<MIXED, 8>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
+    case 16: force_l<MIXED, 16>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
+    default: force_l<MIXED, 32>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
   }
 }
 
 int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const float4* lo,
                       const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
                       const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
-                      cudaStream_t s) {
-  const size_t sm = force_smem_bytes(ta, precision);
+                      int nbuf, cudaStream_t s) {
+  const size_t sm = force_smem_bytes(ta, precision, nbuf);
   if (per_sm <= 0) per_sm = per_sm_for(sm);
   const int grid = tile_grid(ta, per_sm);
   if (precision == LJ_MIXED)
-    force_p<true>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, grid, sm, s);
+    force_p<true>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf, grid, sm, s);
   else
-    force_p<false>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, grid, sm, s);
+    force_p<false>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf, grid, sm, s);
   return grid;
 }
 

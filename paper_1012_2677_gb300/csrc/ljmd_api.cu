@@ -60,6 +60,7 @@ struct ljmd_sys {
   TileArgs ta{};
   int tile_T = 0;                // preferred cells per tile along z (0 = default)
   int force_per_sm = 0;          // force CTAs per SM (0 = as many as fit)
+  int force_nbuf = 1;            // tile buffers per force CTA (1 or 2)
   uint32_t* scan_tmp = nullptr;
   size_t scan_tmp_cap = 0;
   int64_t cap_n = 0;       // particle capacity of the per-particle buffers
@@ -359,7 +360,7 @@ static int ensure_tile_list(ljmd_sys* s) {
 
 // Tile geometry for the staged list/force kernels: T cells along z per tile, shared-memory
 // capacities from the actual largest tile of the current cell occupancy.
-static int choose_tiles(ljmd_sys* s) {
+static int choose_tiles(ljmd_sys* s, int t_cap) {
   ljmd_sys* sys = s;
   TileArgs& ta = s->ta;
   const int n = s->g.n;
@@ -380,6 +381,7 @@ static int choose_tiles(ljmd_sys* s) {
   }
   ta.whole = 0;
   int T = s->tile_T > 0 ? s->tile_T : 4;
+  if (T > t_cap) T = t_cap;
   if (T > n - 2) T = n - 2;
   if (T > kMaxTileT) T = kMaxTileT;
   if (T < 1) T = 1;
@@ -437,52 +439,59 @@ static int rebuild(ljmd_sys* s) {
   std::swap(s->f, s->f_alt);
   launch_shadow_all(s->x, N, s->precision == LJ_MIXED, s->hi, s->lo, s->pos64, s->ref, st);
   CKL();
-  TRY(choose_tiles(s));
   const int half = s->prm.list_form == LJ_LIST_HALF;
   uint64_t total = 0;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    if (s->ent_cap == 0) {
-      // first construction: the continuum estimate of partners within r_s, with headroom
-      const double est = 4.18879 * s->rs * s->rs * s->rs * (double)N / (s->L * s->L * s->L);
-      const size_t want = (size_t)((double)N * (est * (half ? 0.5 : 1.0) * 1.3 + 8.0)) + 4096;
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // the force kernel's two tile buffers must fit: a smaller tile is chosen if they do not
+  for (int t_cap = kMaxTileT;;) {
+    TRY(choose_tiles(s, t_cap));
+    bool built = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (s->ent_cap == 0) {
+        // first construction: the continuum estimate of partners within r_s, with headroom
+        const double est = 4.18879 * s->rs * s->rs * s->rs * (double)N / (s->L * s->L * s->L);
+        const size_t want = (size_t)((double)N * (est * (half ? 0.5 : 1.0) * 1.3 + 8.0)) + 4096;
+        TRY(dalloc_t(s, &s->ent, want));
+        s->ent_cap = want;
+      }
+      CK(cudaMemsetAsync(s->d_total64, 0, 2 * sizeof(unsigned long long), st));
+      CK(cudaMemsetAsync(s->d_sizes + 3, 0, sizeof(unsigned int), st));
+      launch_list_tile(s->precision, half, force_pos(s), s->x, s->cell_start, N, s->g, s->ta, s->band, s->rows,
+                       s->tile_list, s->ent, (uint64_t)s->ent_cap, s->d_total64, s->d_sizes + 3, s->d_status, st);
+      s->launches += 1;
+      CKL();
+      CK(cudaMemcpyAsync(s->h_u32 + 4, s->d_total64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(s->h_u32 + 12, s->d_sizes + 3, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      unsigned long long total64, actual64;
+      memcpy(&total64, s->h_u32 + 4, sizeof(total64));
+      memcpy(&actual64, s->h_u32 + 6, sizeof(actual64));
+      s->ta.max_list = (int32_t)s->h_u32[12];
+      if (total64 > 4294967295ULL) return LJ_ERANGE;  // row starts are 32-bit
+      total = total64;
+      if (total <= s->ent_cap) {
+        int32_t w = 0;
+        TRY(device_status(s, &w));
+        if (w) {
+          fprintf(stderr, "ljmd: list construction raised status %d (n=%d T=%d tiles=%lld staged<=%d own<=%d)\n", w,
+                  s->ta.n, s->ta.T, (long long)s->ta.ntiles, s->ta.max_staged, s->ta.max_own);
+          return LJ_EDEVICE;
+        }
+        s->list_actual = actual64;
+        built = true;
+        break;
+      }
+      // the rows did not fit: grow to the exact size plus headroom and construct again
+      const size_t want = (size_t)(total * 1.2) + 4096;
       TRY(dalloc_t(s, &s->ent, want));
       s->ent_cap = want;
     }
-    CK(cudaMemsetAsync(s->d_total64, 0, 2 * sizeof(unsigned long long), st));
-    CK(cudaMemsetAsync(s->d_sizes + 3, 0, sizeof(unsigned int), st));
-    launch_list_tile(s->precision, half, force_pos(s), s->x, s->cell_start, N, s->g, s->ta, s->band, s->rows,
-                     s->tile_list, s->ent, (uint64_t)s->ent_cap, s->d_total64, s->d_sizes + 3, s->d_status, st);
-    s->launches += 1;
-    CKL();
-    CK(cudaMemcpyAsync(s->h_u32 + 4, s->d_total64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(s->h_u32 + 12, s->d_sizes + 3, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    unsigned long long total64, actual64;
-    memcpy(&total64, s->h_u32 + 4, sizeof(total64));
-    memcpy(&actual64, s->h_u32 + 6, sizeof(actual64));
-    s->ta.max_list = (int32_t)s->h_u32[12];
-    if (total64 > 4294967295ULL) return LJ_ERANGE;  // row starts are 32-bit
-    total = total64;
-    if (total <= s->ent_cap) {
-      int32_t w = 0;
-      TRY(device_status(s, &w));
-      if (w) {
-        fprintf(stderr, "ljmd: list construction raised status %d (n=%d T=%d tiles=%lld staged<=%d own<=%d)\n", w,
-                s->ta.n, s->ta.T, (long long)s->ta.ntiles, s->ta.max_staged, s->ta.max_own);
-        return LJ_EDEVICE;
-      }
-      int dev = 0, smem_max = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if (force_smem_bytes(s->ta, s->precision) > (size_t)smem_max) return LJ_ERANGE;
-      s->list_actual = actual64;
-      break;
-    }
-    // the rows did not fit: grow to the exact size plus headroom and construct again
-    const size_t want = (size_t)(total * 1.2) + 4096;
-    TRY(dalloc_t(s, &s->ent, want));
-    s->ent_cap = want;
-    if (attempt == 1) return LJ_EDEVICE;
+    if (!built) return LJ_EDEVICE;
+    if (force_smem_bytes(s->ta, s->precision, s->force_nbuf) <= (size_t)smem_max) break;
+    if (s->ta.whole || s->ta.T <= 1) return LJ_ERANGE;
+    t_cap = s->ta.T - 1;
   }
   s->list_entries = total;
   s->have_list = true;
@@ -521,7 +530,7 @@ static int run_force(ljmd_sys* s, bool energy) {
     PhaseTimer timer(s, PH_FORCE);
     s->nb_force = launch_force_tile(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->lo, s->cell_start, s->n,
                                     s->g, s->ta, s->c, s->rows, s->tile_list, s->ent, s->f, s->part_force, s->d_status,
-                                    per_sm, s->st);
+                                    per_sm, s->force_nbuf, s->st);
   }
   s->launches += 1;
   CKL();
@@ -893,10 +902,12 @@ int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
   return LJ_OK;
 }
 
-int ljmd_set_tuning(ljmd_sys* sys, int32_t tile_cells, int32_t lanes, int32_t force_ctas_per_sm) {
+int ljmd_set_tuning(ljmd_sys* sys, int32_t tile_cells, int32_t lanes, int32_t force_ctas_per_sm,
+                    int32_t force_buffers) {
   if (!sys) return LJ_EINVAL;
   if (sys->broken) return LJ_EDEVICE;
   if (tile_cells < 0 || tile_cells > kMaxTileT || force_ctas_per_sm < 0 || force_ctas_per_sm > 4) return LJ_EINVAL;
+  if (force_buffers < 0 || force_buffers > 2) return LJ_EINVAL;
   if (!(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
     return LJ_EINVAL;
   if (tile_cells != sys->tile_T) {
@@ -906,6 +917,12 @@ int ljmd_set_tuning(ljmd_sys* sys, int32_t tile_cells, int32_t lanes, int32_t fo
   }
   if (lanes) sys->prm.lanes = lanes;
   sys->force_per_sm = force_ctas_per_sm;
+  const int nbuf = force_buffers ? force_buffers : 1;
+  if (nbuf != sys->force_nbuf) {
+    sys->force_nbuf = nbuf;
+    sys->have_list = false;  // the tile shape is re-checked against the larger shared-memory use
+    sys->forces_current = false;
+  }
   return LJ_OK;
 }
 

@@ -111,7 +111,7 @@ struct TileArgs {
   int32_t max_list;    // list entries per tile (padded to 8), at most (known after construction)
 };
 size_t list_smem_bytes(const TileArgs& ta, int precision);
-size_t force_smem_bytes(const TileArgs& ta, int precision);
+size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf);
 void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStream_t s);
 void launch_tile_sizes(const uint32_t* cs, TileArgs ta, unsigned int* out, cudaStream_t s);
 // counter[0] += padded tile segments (reservations), counter[1] += actual entries
@@ -122,7 +122,7 @@ void launch_list_tile(int precision, int half, const void* pos, const double* x,
 int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const float4* lo,
                       const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
                       const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
-                      cudaStream_t s);
+                      int nbuf, cudaStream_t s);
 void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,
                         uint64_t E, uint32_t* out, int32_t* status, cudaStream_t s);
 

@@ -73,7 +73,7 @@ _SIGS = {
     "ljmd_get_pairs_static": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_stats)]),
     "ljmd_set_profiling": (ctypes.c_int, [_P, _I32]),
-    "ljmd_set_tuning": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+    "ljmd_set_tuning": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),
     "ljmd_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_profile)]),
 }
 
@@ -217,8 +217,9 @@ def ljmd_get_stats(h) -> dict:
     return {name: getattr(st, name) for name, _ in ljmd_stats._fields_}
 
 
-def ljmd_set_tuning(h, tile_cells: int = 0, lanes: int = 0, force_ctas_per_sm: int = 0) -> None:
-    _chk(load().ljmd_set_tuning(h, int(tile_cells), int(lanes), int(force_ctas_per_sm)), "ljmd_set_tuning")
+def ljmd_set_tuning(h, tile_cells: int = 0, lanes: int = 0, force_ctas_per_sm: int = 0, force_buffers: int = 0) -> None:
+    _chk(load().ljmd_set_tuning(h, int(tile_cells), int(lanes), int(force_ctas_per_sm), int(force_buffers)),
+         "ljmd_set_tuning")
 
 
 def ljmd_set_profiling(h, enable: bool) -> None:
@@ -312,8 +313,8 @@ class System:
     def stats(self):
         return ljmd_get_stats(self.h)
 
-    def set_tuning(self, tile_cells=0, lanes=0, force_ctas_per_sm=0):
-        ljmd_set_tuning(self.h, tile_cells, lanes, force_ctas_per_sm)
+    def set_tuning(self, tile_cells=0, lanes=0, force_ctas_per_sm=0, force_buffers=0):
+        ljmd_set_tuning(self.h, tile_cells, lanes, force_ctas_per_sm, force_buffers)
 
     def set_profiling(self, enable=True):
         ljmd_set_profiling(self.h, enable)

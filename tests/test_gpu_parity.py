@@ -146,6 +146,26 @@ def test_forces_and_energies_match_oracle(precision, list_form, lanes):
     assert np.abs(gf.sum(0)).max() < (1e-4 if precision == ljmd.LJ_MIXED else 1e-9) * rms
 
 
+@pytest.mark.parametrize("precision,list_form", FORMS)
+@pytest.mark.parametrize("tile,lanes,nbuf", [(1, 4, 1), (2, 2, 2), (4, 8, 2), (8, 4, 1), (14, 16, 2), (5, 1, 2)])
+def test_forces_and_list_under_tuning_knobs(precision, list_form, tile, lanes, nbuf):
+    """Every tile shape / lanes / buffering choice gives the oracle's forces and the exact list."""
+    x, v, L = thermal(8, 0.6, 1.2, 9)  # 2048 particles, 5 cells per side (ragged tiles for T = 2, 4)
+    F, pe, vir = O.forces(x, L)
+    with _system(precision, list_form) as s:
+        s.set_tuning(tile, lanes, 0, nbuf)
+        s.set_state(x, v, L)
+        s.compute_forces()
+        _, _, gf, _ = s.get_state()
+        gpe, _, gvir = s.energies()
+        got = s.pairs()
+    rms = np.sqrt((F ** 2).sum(1).mean())
+    assert np.sqrt(((gf - F) ** 2).sum(1)).max() / rms <= FORCE_TOL[precision]
+    etol = 1e-6 if precision == ljmd.LJ_MIXED else 1e-12
+    assert gpe == pytest.approx(pe, rel=etol) and gvir == pytest.approx(vir, rel=etol)
+    assert np.array_equal(got, O.pairs_within(x, L, 3.0))
+
+
 @pytest.mark.parametrize("precision", [ljmd.LJ_MIXED, ljmd.LJ_FP64])
 def test_forces_dense_liquid(precision):
     x, v, L = thermal(8, 0.8, 0.9, 4)
