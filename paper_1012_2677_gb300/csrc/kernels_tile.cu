@@ -148,7 +148,8 @@ struct TileLayout {
 
 static __host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-__host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, bool mixed, bool force) {
+__host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, bool mixed, bool force,
+                                                           bool gid = true) {
   TileLayout L;
   const size_t ms = (size_t)ta.max_staged;
   L.pos = 0;
@@ -156,7 +157,7 @@ __host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, b
   L.lo = o;
   if (mixed && force) o += align16(ms * 16);
   L.gid = o;
-  o += align16(ms * 4);
+  if (gid) o += align16(ms * 4);  // the full-list force kernel needs no sorted indices
   L.rows = o;
   L.ent = o;
   L.cnt = o;
@@ -393,7 +394,40 @@ __device__ __forceinline__ int own_cell(const TileShared& S, int l, int Tp) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Shared-memory layout of the thread-per-key list kernel (mixed form, staged tiles).
+constexpr int kListSplit = 2;  // candidate sub-ranges per neighbour column (work balance)
+constexpr size_t kListSmemTarget = 52 * 1024;  // 4 CTAs per SM
+struct KeyListLayout {
+  size_t pos;    // hi float4 [max_staged]
+  size_t gid;    // int [max_staged]
+  size_t cnt;    // int [nch * 9 * kListSplit * 32]: per (key, column part) counts, then offsets in the row
+  size_t kst;    // int [nch * 32] row start within the tile segment, then int [nch * 32] row length
+  size_t seg;    // uint16 [seg_cap]: the tile's list segment before it is copied out
+  int nch;       // 32-key chunks per tile, at most
+  int seg_cap;   // entries (a multiple of 8)
+  size_t total;
+};
+__host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs& ta) {
+  KeyListLayout K;
+  const size_t ms = (size_t)ta.max_staged;
+  K.nch = (ta.max_own + 31) / 32;
+  K.pos = 0;
+  size_t o = align16(ms * 16);
+  K.gid = o;
+  o += align16(ms * 4);
+  K.cnt = o;
+  o += align16((size_t)K.nch * 9 * kListSplit * 32 * 4);
+  K.kst = o;
+  o += align16((size_t)K.nch * 32 * 8);
+  K.seg = o;
+  size_t room = o + 8192 < kListSmemTarget ? kListSmemTarget - o : 8192;
+  K.seg_cap = (int)((room / 2) & ~(size_t)7);
+  K.total = o + 2 * (size_t)K.seg_cap;
+  return K;
+}
+
 size_t list_smem_bytes(const TileArgs& ta, int precision) {
+  if (precision == LJ_MIXED && !ta.whole) return key_list_layout(ta).total;
   return tile_layout(ta, precision == LJ_MIXED, false).total;
 }
 
@@ -526,6 +560,202 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Candidates of one work item for the lane's key: part `h` (of kListSplit) of the range of
+// cells m_a - 1 .. m_b + 1 of neighbour column k (m_a, m_b: own cells of the first and last key
+// of the 32-key chunk c), tested in ascending staged order.  Partners beyond the key's own 3
+// cells fail the distance test (cells are at least r_s wide), so the chunk can share one
+// candidate range.  With WRITE the kept partners go to dst[p], dst[p + 1], ...  Returns the
+// number kept.
+__device__ __forceinline__ bool key_test(float r2, const ListBand& band, bool& maybe) {
+  const bool in = r2 < band.lo;
+  maybe = !in && r2 < band.hi;
+  return in;
+}
+
+template <bool HALF, bool WRITE>
+__device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float4* sh_pos, const int* sh_gid,
+                                        const double* __restrict__ x, int64_t N, const Geom& g,
+                                        const ListBand& band, int c, int k, int h, int n_own, uint16_t* dst, int p) {
+  const int lane = threadIdx.x & 31;
+  const int ncol = S.ncol;
+  const int o = 32 * c + lane;
+  const bool valid = o < n_own;
+  const int o_last = min(32 * c + 31, n_own - 1);
+  const int ma = own_cell(S, S.own0 + 32 * c, Tp), mb = own_cell(S, S.own0 + o_last, Tp);
+  const int r0 = S.offq[k * ncol + ma - 1], r1 = S.offq[k * ncol + mb + 2];
+  const int j0 = r0 + ((r1 - r0) * h) / kListSplit, j1 = r0 + ((r1 - r0) * (h + 1)) / kListSplit;
+  const int l = S.own0 + (valid ? o : o_last);
+  const float4 pi = sh_pos[l];
+  const int gi = sh_gid[l];
+  int cnt = 0;
+  int j = j0;
+  for (; j + 1 < j1; j += 2) {  // two candidates per iteration (same address in every lane: broadcasts)
+    const float4 pa = sh_pos[j], pb = sh_pos[j + 1];
+    const float ax = pa.x - pi.x, ay = pa.y - pi.y, az = pa.z - pi.z;  // exact
+    const float bx = pb.x - pi.x, by = pb.y - pi.y, bz = pb.z - pi.z;
+    bool ma_, mb_;
+    bool ina = key_test(fmaf(ax, ax, fmaf(ay, ay, az * az)), band, ma_);
+    bool inb = key_test(fmaf(bx, bx, fmaf(by, by, bz * bz)), band, mb_);
+    if (__any_sync(0xffffffffu, ma_ || mb_)) {
+      if (ma_) ina = pair_in_exact(x, N, gi, sh_gid[j], g, band.rs2);
+      if (mb_) inb = pair_in_exact(x, N, gi, sh_gid[j + 1], g, band.rs2);
+    }
+    ina = ina && valid && j != l;
+    inb = inb && valid && j + 1 != l;
+    if (HALF) {
+      ina = ina && sh_gid[j] > gi;
+      inb = inb && sh_gid[j + 1] > gi;
+    }
+    if (WRITE) {
+      if (ina) dst[p++] = (uint16_t)j;
+      if (inb) dst[p++] = (uint16_t)(j + 1);
+    }
+    cnt += (ina ? 1 : 0) + (inb ? 1 : 0);
+  }
+  if (j < j1) {
+    const float4 pa = sh_pos[j];
+    const float ax = pa.x - pi.x, ay = pa.y - pi.y, az = pa.z - pi.z;
+    bool ma_;
+    bool ina = key_test(fmaf(ax, ax, fmaf(ay, ay, az * az)), band, ma_);
+    if (__any_sync(0xffffffffu, ma_)) {
+      if (ma_) ina = pair_in_exact(x, N, gi, sh_gid[j], g, band.rs2);
+    }
+    ina = ina && valid && j != l;
+    if (HALF) ina = ina && sh_gid[j] > gi;
+    if (WRITE && ina) dst[p++] = (uint16_t)j;
+    cnt += ina ? 1 : 0;
+  }
+  return cnt;
+}
+
+// Pair-list construction, mixed form, staged tiles: one thread per key particle.  Work items
+// are (32-key chunk, neighbour column); a first pass counts each key's partners per column, a
+// prefix gives every key its row and every column its place in the row (columns in order,
+// partners ascending: the list is deterministic), one atomic reserves the tile's segment
+// (padded to 8 entries), and a second pass writes the entries into shared memory, from where
+// they are copied out with 16-byte stores (directly to global memory if the segment does not
+// fit).
+template <bool HALF>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_list_keys(const float4* __restrict__ pos, const double* __restrict__ x, const uint32_t* __restrict__ cs,
+                int64_t N, Geom g, TileArgs ta, ListBand band, uint2* __restrict__ rows,
+                uint2* __restrict__ tile_list, uint16_t* __restrict__ ent, uint64_t cap,
+                unsigned long long* __restrict__ counter, unsigned int* __restrict__ max_list,
+                int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileShared S;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ unsigned int s_base, s_total, s_padded;
+  __shared__ int s_ok;
+  const KeyListLayout K = key_list_layout(ta);
+  TileLayout L;  // the staging helpers' view: positions and sorted indices
+  L.pos = K.pos;
+  L.lo = K.pos;
+  L.gid = K.gid;
+  L.rows = L.ent = L.cnt = L.total = 0;
+  const float4* sh_pos = (const float4*)(smem + K.pos);
+  const int* sh_gid = (const int*)(smem + K.gid);
+  int* s_cnt = (int*)(smem + K.cnt);
+  int* s_kst = (int*)(smem + K.kst);
+  int* s_len = s_kst + K.nch * 32;
+  uint16_t* s_seg = (uint16_t*)(smem + K.seg);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t phase = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+
+  for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
+    const TileInfo ti = tile_info(t, ta);
+    if (!stage_offsets(ti, ta, cs, S)) {
+      if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
+      __syncthreads();
+      continue;
+    }
+    if (!stage_copy_async<true, false>(ti, ta, g, pos, nullptr, nullptr, nullptr, S, smem, L, &bar, phase, true,
+                                       status))
+      return;
+    const int n_own = S.own1 - S.own0;
+    if (n_own > ta.max_own) {  // sizing inconsistency: record and skip the tile
+      if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
+      __syncthreads();
+      continue;
+    }
+    const int nch = (n_own + 31) / 32;
+    // pass 1: counts per (key, column part)
+    constexpr int kItems = 9 * kListSplit;
+    for (int item = warp; item < nch * kItems; item += kWarps) {
+      const int c = item / kItems, r = item - kItems * c;
+      s_cnt[item * 32 + lane] = key_item<HALF, false>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit,
+                                                      r % kListSplit, n_own, nullptr, 0);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // column offsets within each row, row lengths, exclusive prefix of the rows; one atomic
+      // reserves the tile's segment, padded to a multiple of 8 entries (16 bytes)
+      unsigned run = 0;
+      for (int c = 0; c < nch; ++c) {
+        const int o = 32 * c + lane;
+        int tot = 0;
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+          const int v = s_cnt[(c * kItems + r) * 32 + lane];
+          s_cnt[(c * kItems + r) * 32 + lane] = tot;
+          tot += v;
+        }
+        if (o >= n_own) tot = 0;
+        unsigned inc = (unsigned)tot;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, inc, d);
+          if (lane >= d) inc += y;
+        }
+        s_kst[o] = (int)(run + inc - (unsigned)tot);
+        s_len[o] = tot;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) {
+        const unsigned padded = (run + 7u) & ~7u;
+        const unsigned long long b = atomicAdd(counter, (unsigned long long)padded);
+        atomicAdd(counter + 1, (unsigned long long)run);
+        const bool fits = b + padded <= cap;
+        s_base = (unsigned)b;
+        s_total = run;
+        s_padded = padded;
+        s_ok = fits;
+        tile_list[t] = fits ? make_uint2((unsigned)b, padded) : make_uint2(0u, 0u);
+        atomicMax(max_list, padded);
+      }
+    }
+    __syncthreads();
+    const bool ok = s_ok != 0;
+    for (int o = threadIdx.x; o < n_own; o += blockDim.x)
+      rows[S.gown0 + o] = ok ? make_uint2(s_base + (unsigned)s_kst[o], (unsigned)s_len[o]) : make_uint2(0u, 0u);
+    if (ok) {
+      const bool staged = s_padded <= (unsigned)K.seg_cap;
+      uint16_t* dst = staged ? s_seg : ent + s_base;
+      // pass 2: the same tests, entries written
+      for (int item = warp; item < nch * kItems; item += kWarps) {
+        const int c = item / kItems, r = item - kItems * c;
+        const int o = 32 * c + lane;
+        const int p = o < n_own ? s_kst[o] + s_cnt[item * 32 + lane] : 0;
+        key_item<HALF, true>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit, n_own, dst,
+                             p);
+      }
+      if (staged) {
+        __syncthreads();
+        const uint4* src = (const uint4*)s_seg;
+        uint4* out = (uint4*)(ent + s_base);
+        for (unsigned w = threadIdx.x; w < s_padded / 8u; w += blockDim.x) out[w] = src[w];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 template <int LANES>
 __device__ __forceinline__ float gsum(float v) {
 #pragma unroll
@@ -541,11 +771,11 @@ __device__ __forceinline__ double gsum(double v) {
 
 // Shared memory of the force kernel: `nbuf` tile buffers (with two, the next tile's copies are in
 // flight while the current one is computed); one for the whole-box case.
-size_t force_buffer_bytes(const TileArgs& ta, int precision) {
-  return align16(tile_layout(ta, precision == LJ_MIXED, true).total);
+size_t force_buffer_bytes(const TileArgs& ta, int precision, int half) {
+  return align16(tile_layout(ta, precision == LJ_MIXED, true, half || ta.whole).total);
 }
-size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf) {
-  return (ta.whole ? 1 : (nbuf == 2 ? 2 : 1)) * force_buffer_bytes(ta, precision);
+size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf, int half) {
+  return (ta.whole ? 1 : (nbuf == 2 ? 2 : 1)) * force_buffer_bytes(ta, precision, half);
 }
 
 // 1/x from the hardware approximation (rcp.approx) refined by one Newton-Raphson step
@@ -702,9 +932,12 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
         if (HALF) atomicAdd(&((float4*)fout)[gi], make_float4(fx, fy, fz, 0.0f));
         else ((float4*)fout)[gi] = make_float4(fx, fy, fz, 0.0f);
       }
-      if (ENERGY) {
-        pe_acc += (double)a0.pe + (double)a1.pe;
-        vir_acc += (double)a0.vir + (double)a1.vir;
+      if (ENERGY) {  // the group's lanes reduce in FP32, one lane accumulates in FP64
+        const float pe = gsum<LANES>(a0.pe + a1.pe), vir = gsum<LANES>(a0.vir + a1.vir);
+        if (lane == 0) {
+          pe_acc += (double)pe;
+          vir_acc += (double)vir;
+        }
       }
     } else {
       dfx = gsum<LANES>(dfx);
@@ -764,7 +997,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared SS[2];
   __shared__ __align__(8) uint64_t bars[2];
-  const TileLayout L = tile_layout(ta, MIXED, true);
+  const TileLayout L = tile_layout(ta, MIXED, true, HALF || WHOLE);
   const size_t buf_bytes = align16(L.total);
   double pe_acc = 0.0, vir_acc = 0.0;
   if (WHOLE) {
@@ -934,8 +1167,15 @@ void launch_list_tile(int precision, int half, const void* pos, const double* x,
     }
   } else {
     if (mixed) {
-      if (half) LJ_LIST_LAUNCH(true, true, false);
-      else LJ_LIST_LAUNCH(true, false, false);
+      if (half) {
+        set_smem(k_list_keys<true>, sm);
+        k_list_keys<true><<<grid, kTileThreads, sm, s>>>((const float4*)pos, x, cs, N, g, ta, band, rows, tile_list,
+                                                         ent, cap, counter, max_list, status);
+      } else {
+        set_smem(k_list_keys<false>, sm);
+        k_list_keys<false><<<grid, kTileThreads, sm, s>>>((const float4*)pos, x, cs, N, g, ta, band, rows, tile_list,
+                                                          ent, cap, counter, max_list, status);
+      }
     } else {
       if (half) LJ_LIST_LAUNCH(false, true, false);
       else LJ_LIST_LAUNCH(false, false, false);
@@ -990,7 +1230,7 @@ int launch_force_tile(int precision, int half, int lanes, int energy, const void
                       const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
                       const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
                       int nbuf, cudaStream_t s) {
-  const size_t sm = force_smem_bytes(ta, precision, nbuf);
+  const size_t sm = force_smem_bytes(ta, precision, nbuf, half);
   if (per_sm <= 0) per_sm = per_sm_for(sm);
   const int grid = tile_grid(ta, per_sm);
   if (precision == LJ_MIXED)

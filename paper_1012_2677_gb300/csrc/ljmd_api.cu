@@ -489,7 +489,7 @@ static int rebuild(ljmd_sys* s) {
       s->ent_cap = want;
     }
     if (!built) return LJ_EDEVICE;
-    if (force_smem_bytes(s->ta, s->precision, s->force_nbuf) <= (size_t)smem_max) break;
+    if (force_smem_bytes(s->ta, s->precision, s->force_nbuf, half) <= (size_t)smem_max) break;
     if (s->ta.whole || s->ta.T <= 1) return LJ_ERANGE;
     t_cap = s->ta.T - 1;
   }

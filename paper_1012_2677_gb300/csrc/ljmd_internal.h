@@ -111,7 +111,7 @@ struct TileArgs {
   int32_t max_list;    // list entries per tile (padded to 8), at most (known after construction)
 };
 size_t list_smem_bytes(const TileArgs& ta, int precision);
-size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf);
+size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf, int half);
 void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStream_t s);
 void launch_tile_sizes(const uint32_t* cs, TileArgs ta, unsigned int* out, cudaStream_t s);
 // counter[0] += padded tile segments (reservations), counter[1] += actual entries
