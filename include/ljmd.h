@@ -234,6 +234,38 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
  */
 int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
 
+/*
+ * Adjoint pass at the current positions over the current list (the list is built first if there
+ * is none): hw = H(x) w, the Hessian of the potential energy (Eq. 2 summed over pairs with
+ * r < r_c) times w, from the pair energy u(s) as a function of s = r^2:
+ *   (H w)_i = sum_j [2 u'(s) (w_i - w_j) + 4 u''(s) d (d . (w_i - w_j))],  d = x_j - x_i.
+ * The force Jacobian is -H.  dtheta (4 doubles, may be NULL) receives w . dF/deps,
+ * w . dF/dsigma, dPE/deps and dPE/dsigma, with r_c = (cutoff / sigma) sigma scaling with sigma
+ * (the truncation constants c2, c0 of Eq. 2 stay fixed).  w and hw are 3N FP64 in id order, host
+ * (on_device = 0) or device (1).  The paper has no adjoint; this differentiates its pair force.
+ * Mixed form: FP32 pair arithmetic, FP64 results.  Synchronises the stream.
+ * Errors: LJ_EINVAL (NULL w or hw), LJ_ESTATE (no particles), LJ_ENOMEM, LJ_EDEVICE.
+ */
+int ljmd_hvp(ljmd_sys* sys, const double* w, double* hw, double* dtheta, int32_t on_device);
+
+/*
+ * Differentiable trajectory: from (x0, v0) (n particles, box side `box`, 3n FP64 each, id order,
+ * x0 unwrapped) run nsteps of velocity-Verlet (Sec. 4.4) with step dt and return
+ *   *loss = (1 / n_pe) sum_{t > nsteps - n_pe} PE(x_t) / n  +  (1 / n) sum_i |x_i(nsteps) - x_i(0)|^2
+ * (unwrapped positions), and, if any of gx0, gv0, gtheta is non-NULL, its gradients with respect
+ * to x0, v0 (3n FP64 each) and (eps, sigma) (gtheta[2]).  The gradients come from the reverse-time
+ * recurrences of velocity-Verlet with h = dt / 2 (one adjoint pass, i.e. one Hessian-vector
+ * product, per state), recomputing the states of each segment of ckpt_every steps from a
+ * checkpoint stored in the forward run.  Arrays are host (on_device = 0) or device (1).  The
+ * handle's state is replaced (it ends at x0 of the last recomputed segment).  The paper has no
+ * adjoint; this differentiates its integrator and pair force.  Synchronises the stream.
+ * Errors: LJ_EINVAL (n <= 0, nsteps < 1, n_pe outside [0, nsteps], ckpt_every < 1, NULL x0, v0 or
+ * loss, box too small), LJ_ENOMEM, LJ_EDEVICE.
+ */
+int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, const double* v0, double dt,
+                        int64_t nsteps, int64_t n_pe, int64_t ckpt_every, double* loss, double* gx0, double* gv0,
+                        double* gtheta, int32_t on_device);
+
 /* Counters and state of the handle (synchronises the stream). */
 int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out);
 

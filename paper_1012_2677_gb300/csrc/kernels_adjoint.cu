@@ -1,0 +1,83 @@
+// Element-wise kernels of the reverse-time (adjoint) pass through velocity-Verlet: moving adjoint
+// vectors between the caller's id order and the library's cell-sorted order, the unwrapped
+// trajectory state, and the vector updates of the recurrences.  The pair work (Hessian-vector
+// product, forces and parameter derivatives) is the adjoint tile kernel of kernels_tile.cu.
+#include "common.cuh"
+
+namespace ljmd {
+
+static int grid_of(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  return (int)(b < 65535 ? b : 65535);
+}
+
+// w_sorted[s] = (w[3 id[s]], w[3 id[s] + 1], w[3 id[s] + 2]) (or zero when w is null)
+__global__ void k_to_sorted(const double* __restrict__ w, const int32_t* __restrict__ id, int64_t N,
+                            dvec4* __restrict__ out) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    if (w) {
+      const int64_t p = id[s];
+      out[s] = make_dvec4(w[3 * p], w[3 * p + 1], w[3 * p + 2], 0.0);
+    } else {
+      out[s] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+    }
+  }
+}
+void launch_to_sorted(const double* w_id, const int32_t* id, int64_t N, dvec4* out, cudaStream_t s) {
+  k_to_sorted<<<grid_of(N), 256, 0, s>>>(w_id, id, N, out);
+}
+
+// Unwrapped positions in id order: out[3 id[s] + k] = x[k N + s] - offset + img[k N + s] L.
+__global__ void k_unwrapped(const double* __restrict__ x, const int32_t* __restrict__ img,
+                            const int32_t* __restrict__ id, int64_t N, double offset, double L,
+                            double* __restrict__ out) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = id[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[3 * p + k] = (x[k * N + s] - offset) + (double)img[k * N + s] * L;
+  }
+}
+void launch_unwrapped(const double* x, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
+                      double* out, cudaStream_t s) {
+  k_unwrapped<<<grid_of(N), 256, 0, s>>>(x, img, id, N, offset, L, out);
+}
+
+// y += a x (n doubles)
+__global__ void k_axpy(double* __restrict__ y, double a, const double* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+void launch_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s) {
+  k_axpy<<<grid_of(n), 256, 0, s>>>(y, a, x, n);
+}
+
+// y = a (u - w) (n doubles)
+__global__ void k_scaled_diff(double* __restrict__ y, double a, const double* __restrict__ u,
+                              const double* __restrict__ w, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * (u[i] - w[i]);
+}
+void launch_scaled_diff(double* y, double a, const double* u, const double* w, int64_t n, cudaStream_t s) {
+  k_scaled_diff<<<grid_of(n), 256, 0, s>>>(y, a, u, w, n);
+}
+
+// Per-block partial sums of (u - w)^2 over n doubles (fixed grid, fixed order).
+__global__ void k_sqdiff(const double* __restrict__ u, const double* __restrict__ w, int64_t n,
+                         double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = u[i] - w[i];
+    acc = fma(d, d, acc);
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+int launch_sqdiff(const double* u, const double* w, int64_t n, double* part, cudaStream_t s) {
+  const int nb = red_blocks(n);
+  k_sqdiff<<<nb, kRedThreads, 0, s>>>(u, w, n, part);
+  return nb;
+}
+
+}  // namespace ljmd

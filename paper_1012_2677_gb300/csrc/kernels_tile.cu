@@ -1067,6 +1067,214 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Adjoint pass over the list (the derivatives the reverse-time recurrences need), for the pair
+// energy u(s) of Eq. 2 as a function of s = r^2 (a = sigma^2 / s):
+//   u   = 4 eps (a^6 - a^3 + c2 s / sigma^2 + c0)
+//   u'  = du/ds   = 4 eps ((3 a^3 - 6 a^6) / s + c2 / sigma^2)
+//   u'' = d2u/ds2 = 4 eps (42 a^6 - 12 a^3) / s^2
+//   du/dsigma  = (4 eps / sigma) (12 a^6 - 6 a^3 - 2 c2 s / sigma^2)
+//   du'/dsigma = (4 eps / sigma) ((18 a^3 - 72 a^6) / s - 2 c2 / sigma^2)
+// (c2, c0 fixed: r_c scales with sigma).  Per key i, with d = x_j - x_i and dw = w_i - w_j:
+//   (H w)_i += 2 u' dw + 4 u'' d (d . dw)        (Hessian of the potential energy times w)
+//   F_i     += 2 u' d                              (force, = -dPE/dx_i)
+//   w . dF/dsigma += w_i . (2 du'/dsigma d),  w . dF/deps += w_i . (2 u' d) / eps
+//   PE += u / 2,  dPE/deps += u / (2 eps),  dPE/dsigma += (du/dsigma) / 2   (full list: each pair twice)
+// all zero for s >= r_c^2.  Block partials: [w.dF/deps, w.dF/dsigma, dPE/deps, dPE/dsigma, PE].
+constexpr int kAdjLanes = 4;
+constexpr int kAdjParts = 5;
+
+template <bool MIXED, bool WHOLE>
+__device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const unsigned char* buf, const TileLayout& L,
+                                                     const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
+                                                     const LJConst& c, const Geom& g, const dvec4* __restrict__ w,
+                                                     dvec4* __restrict__ hw, dvec4* __restrict__ fo,
+                                                     int32_t* __restrict__ status, double* acc) {
+  const void* sh_pos = buf + L.pos;
+  const float4* sh_lo = (const float4*)(buf + L.lo);
+  const int* sh_gid = (const int*)(buf + L.gid);
+  const uint2* s_rows = (const uint2*)(buf + L.rows);
+  const uint16_t* s_ent = (const uint16_t*)(buf + L.ent);
+  const int lane = threadIdx.x & (kAdjLanes - 1);
+  const int grp = threadIdx.x / kAdjLanes;
+  constexpr int kGroups = kTileThreads / kAdjLanes;
+  const double e4 = 4.0 * c.eps, inv_sig = 1.0 / c.sigma, c2s = c.c2 / c.sig2;
+  const int n_own = S.own1 - S.own0;
+  for (int o = grp; __any_sync(0xffffffffu, o < n_own); o += kGroups) {
+    const bool valid = o < n_own;
+    double h[3] = {0.0, 0.0, 0.0}, f[3] = {0.0, 0.0, 0.0}, q[kAdjParts] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int gi = 0;
+    if (valid) {
+      const int l = S.own0 + o;
+      gi = S.gown0 + o;
+      uint2 row;
+      const uint16_t* el;
+      if (WHOLE) {
+        row = rows[gi];
+        el = ent;
+      } else {
+        row = s_rows[S.row_off + o];
+        row.x -= S.list_base;
+        el = s_ent;
+        if (row.x + row.y > S.list_len) {
+          if (lane == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+          row.y = 0;
+        }
+      }
+      const dvec4 wi = w[gi];
+      if (MIXED) {
+        const float4 hi_i = ((const float4*)sh_pos)[l], lo_i = sh_lo[l];
+        const float e4f = (float)e4, sig2f = (float)c.sig2, c2sf = (float)c2s, rc2f = (float)c.rc2,
+                    c0f = (float)c.c0, isgf = (float)inv_sig;
+        float ah[3] = {0.f, 0.f, 0.f}, af[3] = {0.f, 0.f, 0.f}, aq[kAdjParts] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        const float wx = (float)wi.x, wy = (float)wi.y, wz = (float)wi.z;
+        for (unsigned e = lane; e < row.y; e += kAdjLanes) {
+          const int j = el[row.x + e];
+          const float4 hj = ((const float4*)sh_pos)[j], lj = sh_lo[j];
+          float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;
+          if (WHOLE) {
+            const float mx = rintf(dx * g.inv_L), my = rintf(dy * g.inv_L), mz = rintf(dz * g.inv_L);
+            dx = fmaf(-mx, g.L_hi, dx) + fmaf(-mx, g.L_lo, lj.x - lo_i.x);
+            dy = fmaf(-my, g.L_hi, dy) + fmaf(-my, g.L_lo, lj.y - lo_i.y);
+            dz = fmaf(-mz, g.L_hi, dz) + fmaf(-mz, g.L_lo, lj.z - lo_i.z);
+          } else {
+            dx += lj.x - lo_i.x;
+            dy += lj.y - lo_i.y;
+            dz += lj.z - lo_i.z;
+          }
+          const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (!(s2 < rc2f)) continue;
+          const dvec4 wj = w[sh_gid[j]];
+          const float is = 1.0f / s2;
+          const float a = sig2f * is, a3 = a * a * a, a6 = a3 * a3;
+          const float u = e4f * (a6 - a3 + c2sf * s2 + c0f);
+          const float u1 = e4f * (is * (3.0f * a3 - 6.0f * a6) + c2sf);
+          const float u2 = e4f * is * is * (42.0f * a6 - 12.0f * a3);
+          const float dus = e4f * isgf * (12.0f * a6 - 6.0f * a3 - 2.0f * c2sf * s2);
+          const float du1s = e4f * isgf * (is * (18.0f * a3 - 72.0f * a6) - 2.0f * c2sf);
+          const float dwx = wx - (float)wj.x, dwy = wy - (float)wj.y, dwz = wz - (float)wj.z;
+          const float ddw = dx * dwx + dy * dwy + dz * dwz;
+          const float t1 = 2.0f * u1, t2 = 4.0f * u2 * ddw;
+          ah[0] += t1 * dwx + t2 * dx;
+          ah[1] += t1 * dwy + t2 * dy;
+          ah[2] += t1 * dwz + t2 * dz;
+          af[0] += t1 * dx;
+          af[1] += t1 * dy;
+          af[2] += t1 * dz;
+          const float wd = wx * dx + wy * dy + wz * dz;
+          aq[0] += t1 * wd;
+          aq[1] += 2.0f * du1s * wd;
+          aq[2] += 0.5f * u;
+          aq[3] += 0.5f * dus;
+          aq[4] += 0.5f * u;
+        }
+        for (int k = 0; k < 3; ++k) {
+          h[k] = ah[k];
+          f[k] = af[k];
+        }
+        for (int k = 0; k < kAdjParts; ++k) q[k] = aq[k];
+      } else {
+        const dvec4 qi = ((const dvec4*)sh_pos)[l];
+        for (unsigned e = lane; e < row.y; e += kAdjLanes) {
+          const int j = el[row.x + e];
+          const dvec4 qj = ((const dvec4*)sh_pos)[j];
+          double dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;
+          if (!WHOLE) {
+            double sx, sy, sz;
+            shift_of(qj.w, g, sx, sy, sz);
+            dx += sx;
+            dy += sy;
+            dz += sz;
+          } else {
+            dx = fma(-rint(dx * g.inv_L64), g.L, dx);
+            dy = fma(-rint(dy * g.inv_L64), g.L, dy);
+            dz = fma(-rint(dz * g.inv_L64), g.L, dz);
+          }
+          const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
+          if (!(s2 < c.rc2)) continue;
+          const dvec4 wj = w[sh_gid[j]];
+          const double is = 1.0 / s2;
+          const double a = c.sig2 * is, a3 = a * a * a, a6 = a3 * a3;
+          const double u = e4 * (a6 - a3 + c2s * s2 + c.c0);
+          const double u1 = e4 * (is * (3.0 * a3 - 6.0 * a6) + c2s);
+          const double u2 = e4 * is * is * (42.0 * a6 - 12.0 * a3);
+          const double dus = e4 * inv_sig * (12.0 * a6 - 6.0 * a3 - 2.0 * c2s * s2);
+          const double du1s = e4 * inv_sig * (is * (18.0 * a3 - 72.0 * a6) - 2.0 * c2s);
+          const double dwx = wi.x - wj.x, dwy = wi.y - wj.y, dwz = wi.z - wj.z;
+          const double ddw = dx * dwx + dy * dwy + dz * dwz;
+          const double t1 = 2.0 * u1, t2 = 4.0 * u2 * ddw;
+          h[0] += t1 * dwx + t2 * dx;
+          h[1] += t1 * dwy + t2 * dy;
+          h[2] += t1 * dwz + t2 * dz;
+          f[0] += t1 * dx;
+          f[1] += t1 * dy;
+          f[2] += t1 * dz;
+          const double wd = wi.x * dx + wi.y * dy + wi.z * dz;
+          q[0] += t1 * wd;
+          q[1] += 2.0 * du1s * wd;
+          q[2] += 0.5 * u;
+          q[3] += 0.5 * dus;
+          q[4] += 0.5 * u;
+        }
+      }
+    }
+    for (int k = 0; k < 3; ++k) {
+      h[k] = gsum<kAdjLanes>(h[k]);
+      f[k] = gsum<kAdjLanes>(f[k]);
+    }
+    if (valid && lane == 0) {
+      hw[gi] = make_dvec4(h[0], h[1], h[2], 0.0);
+      if (fo) fo[gi] = make_dvec4(f[0], f[1], f[2], 0.0);
+    }
+    for (int k = 0; k < kAdjParts; ++k) acc[k] += q[k];
+  }
+}
+
+template <bool MIXED, bool WHOLE>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_adjoint_tile(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
+                   int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows,
+                   const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent,
+                   const dvec4* __restrict__ w, dvec4* __restrict__ hw, dvec4* __restrict__ fo,
+                   double* __restrict__ part, int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileShared S;
+  __shared__ __align__(8) uint64_t bar;
+  const TileLayout L = tile_layout(ta, MIXED, true, true);
+  double acc[kAdjParts] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (WHOLE) {
+    if (blockIdx.x == 0) {
+      stage_whole<MIXED, true>(N, pos, lo, S, smem, L);
+      __syncthreads();
+      adjoint_tile_compute<MIXED, true>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc);
+    }
+  } else {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      fence_proxy_async_smem();
+    }
+    __syncthreads();
+    uint32_t ph = 0;
+    for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
+      const bool ok = force_tile_prepare(t, ta, cs, tile_list, S, status);
+      if (ok) {
+        const TileInfo ti = tile_info(t, ta);
+        stage_issue<MIXED, true>(ti, ta, pos, lo, rows, ent, S, smem, L, &bar);
+        if (!stage_finish<MIXED, true>(ti, ta, g, S, smem, L, &bar, ph, true, status)) return;
+        adjoint_tile_compute<MIXED, false>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc);
+      }
+      __syncthreads();
+    }
+  }
+  __shared__ double sh[32];
+  for (int k = 0; k < kAdjParts; ++k) {
+    const double t = block_sum(acc[k], sh);
+    if (threadIdx.x == 0) part[kAdjParts * (size_t)blockIdx.x + k] = t;
+    __syncthreads();
+  }
+}
+
+
+// ---------------------------------------------------------------------------------------------
 // Expand the list into (key, partner) sorted-index pairs (for inspection).  The whole-box case
 // is a template parameter: no barrier sits under a runtime branch.
 template <bool WHOLE>
@@ -1303,6 +1511,28 @@ void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStr
   if (b < 1) b = 1;
   if (b > 4096) b = 4096;
   k_max_count<<<(int)b, 256, 0, s>>>(cnt, n, out);
+}
+
+int launch_adjoint_tile(int precision, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
+                        TileArgs ta, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
+                        const void* w, void* hw, void* fo, double* part, int32_t* status, cudaStream_t s) {
+  const size_t sm = align16(tile_layout(ta, precision == LJ_MIXED, true, true).total);
+  const int grid = tile_grid(ta, min(per_sm_for(sm), 2));
+#define LJ_ADJ_LAUNCH(M, W)                                                                                 \
+  do {                                                                                                      \
+    set_smem(k_adjoint_tile<M, W>, sm);                                                                     \
+    k_adjoint_tile<M, W><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c, rows, tile_list, ent,     \
+                                                        (const dvec4*)w, (dvec4*)hw, (dvec4*)fo, part, status); \
+  } while (0)
+  if (precision == LJ_MIXED) {
+    if (ta.whole) LJ_ADJ_LAUNCH(true, true);
+    else LJ_ADJ_LAUNCH(true, false);
+  } else {
+    if (ta.whole) LJ_ADJ_LAUNCH(false, true);
+    else LJ_ADJ_LAUNCH(false, false);
+  }
+#undef LJ_ADJ_LAUNCH
+  return grid;
 }
 
 }  // namespace ljmd

@@ -79,6 +79,11 @@ struct ljmd_sys {
   double prof_ms[4] = {0, 0, 0, 0};
   int64_t prof_n[4] = {0, 0, 0, 0};
   int64_t launches = 0;
+  // adjoint pass (allocated on first use)
+  dvec4 *adj_w = nullptr, *adj_hw = nullptr, *adj_f = nullptr;
+  double* part_adj = nullptr;
+  double* d_adj = nullptr;
+  int64_t adj_cap = 0;
   // pinned host mirrors
   uint32_t* h_u32 = nullptr;
   double* h_f64 = nullptr;
@@ -123,7 +128,8 @@ static void free_all(ljmd_sys* s) {
   void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->lo, s->pos64, s->ref, s->id,
                   s->id_alt, s->img, s->img_alt, s->cell_of, s->cell_alt, s->perm, s->cell_count, s->cell_start,
                   s->cell_fill, s->rows, s->tile_list, s->ent, s->scan_tmp, s->part_force, s->part_ke,
-                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64, s->d_sizes};
+                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64, s->d_sizes,
+                  s->adj_w, s->adj_hw, s->adj_f, s->part_adj, s->d_adj};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& p : s->ev_pending) {
@@ -1002,6 +1008,231 @@ int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npai
     }
   }
   *npairs = count;
+  return check_status(sys);
+}
+
+
+// ---- adjoint: Hessian-vector product and the reverse-time pass through velocity-Verlet --------
+}  // extern "C"
+
+static int ensure_adjoint(ljmd_sys* s) {
+  ljmd_sys* sys = s;
+  if (s->adj_cap < s->n) {
+    TRY(dalloc_t(s, &s->adj_w, s->n));
+    TRY(dalloc_t(s, &s->adj_hw, s->n));
+    TRY(dalloc_t(s, &s->adj_f, s->n));
+    s->adj_cap = s->n;
+  }
+  if (!s->part_adj) TRY(dalloc_t(s, &s->part_adj, 5 * (size_t)kMaxRedBlocks));
+  if (!s->d_adj) TRY(dalloc_t(s, &s->d_adj, 8));
+  (void)sys;
+  return LJ_OK;
+}
+
+// One adjoint pass at the current positions with the vector w (device, id order; null = 0):
+// hw = H w and f = F (device, id order; either may be null), q = [w.F, w.dF/dsigma, PE,
+// dPE/dsigma, PE] (host; w.dF/deps = w.F / eps, dPE/deps = PE / eps).  Synchronises.
+static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* f_id, double q[5]) {
+  ljmd_sys* sys = s;
+  if (!s->have_list) TRY(rebuild(s));
+  TRY(ensure_adjoint(s));
+  const int64_t N = s->n;
+  cudaStream_t st = s->st;
+  launch_to_sorted(w_id, s->id, N, s->adj_w, st);
+  const int nb = launch_adjoint_tile(s->precision, force_pos(s), s->lo, s->cell_start, N, s->g, s->ta, s->c, s->rows,
+                                     s->tile_list, s->ent, s->adj_w, s->adj_hw, f_id ? s->adj_f : nullptr,
+                                     s->part_adj, s->d_status, st);
+  launch_final_reduce(s->part_adj, nb, 5, s->d_adj, st);
+  s->launches += 3;
+  if (hw_id) {
+    launch_scatter_back_f64x4_to_f64x3(s->adj_hw, hw_id, s->id, N, st);
+    s->launches += 1;
+  }
+  if (f_id) {
+    launch_scatter_back_f64x4_to_f64x3(s->adj_f, f_id, s->id, N, st);
+    s->launches += 1;
+  }
+  CKL();
+  CK(cudaMemcpyAsync(s->h_f64, s->d_adj, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int k = 0; k < 5; ++k) q[k] = s->h_f64[k];
+  return check_status(s);
+}
+
+template <class T>
+struct DevBuf {  // device scratch owned by one call
+  T* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  int alloc(size_t n) {
+    if (cudaMalloc(&p, (n ? n : 1) * sizeof(T)) != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return LJ_ENOMEM;
+    }
+    return LJ_OK;
+  }
+};
+
+extern "C" {
+
+int ljmd_hvp(ljmd_sys* sys, const double* w, double* hw, double* dtheta, int32_t on_device) {
+  if (!sys || !w || !hw) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0) return LJ_ESTATE;
+  const int64_t N = sys->n;
+  const size_t bytes = sizeof(double) * 3 * (size_t)N;
+  DevBuf<double> wd, hd;
+  const double* w_dev = w;
+  double* hw_dev = hw;
+  if (!on_device) {
+    TRY(wd.alloc(3 * (size_t)N));
+    TRY(hd.alloc(3 * (size_t)N));
+    CK(cudaMemcpyAsync(wd.p, w, bytes, cudaMemcpyHostToDevice, sys->st));
+    w_dev = wd.p;
+    hw_dev = hd.p;
+  }
+  double q[5];
+  TRY(adjoint_pass(sys, w_dev, hw_dev, nullptr, q));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(hw, hd.p, bytes, cudaMemcpyDeviceToHost, sys->st));
+    CK(cudaStreamSynchronize(sys->st));
+  }
+  if (dtheta) {
+    const double eps = sys->prm.eps;
+    dtheta[0] = q[0] / eps;
+    dtheta[1] = q[1];
+    dtheta[2] = q[4] / eps;
+    dtheta[3] = q[3];
+  }
+  return LJ_OK;
+}
+
+int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, const double* v0, double dt,
+                        int64_t nsteps, int64_t n_pe, int64_t ckpt_every, double* loss, double* gx0, double* gv0,
+                        double* gtheta, int32_t on_device) {
+  if (!sys || n <= 0 || !x0 || !v0 || !loss || nsteps < 1 || n_pe < 0 || n_pe > nsteps || ckpt_every < 1 ||
+      !isfinite(dt))
+    return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  const size_t n3 = 3 * (size_t)n;
+  const size_t bytes = sizeof(double) * n3;
+  const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+  cudaStream_t st = sys->st;
+  DevBuf<double> ck_x, ck_v, seg_x, x0u, xNu, lx, lv, b, f, part;
+  TRY(ck_x.alloc(n3 * (size_t)nseg));
+  TRY(ck_v.alloc(n3 * (size_t)nseg));
+  TRY(seg_x.alloc(n3 * (size_t)ckpt_every));
+  TRY(x0u.alloc(n3));
+  TRY(xNu.alloc(n3));
+  TRY(lx.alloc(n3));
+  TRY(lv.alloc(n3));
+  TRY(b.alloc(n3));
+  TRY(f.alloc(n3));
+  TRY(part.alloc(kMaxRedBlocks + 8));
+  // the initial state on the device
+  if (on_device) {
+    CK(cudaMemcpyAsync(x0u.p, x0, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ck_v.p, v0, bytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK(cudaMemcpyAsync(x0u.p, x0, bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ck_v.p, v0, bytes, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(ck_x.p, x0u.p, bytes, cudaMemcpyDeviceToDevice, st));
+  auto capture = [&](double* xu, double* vv) -> int {
+    launch_unwrapped(sys->x, sys->img, sys->id, sys->n, sys->g.offset, sys->L, xu, st);
+    if (vv) launch_scatter_back_f64x3(sys->v, vv, sys->id, sys->n, 0.0, st);
+    sys->launches += vv ? 2 : 1;
+    CK(cudaGetLastError());
+    return LJ_OK;
+  };
+  const double h = 0.5 * dt, wpe = n_pe > 0 ? 1.0 / ((double)n_pe * (double)n) : 0.0;
+  const int saved_ee = sys->prm.energy_every;
+  sys->prm.energy_every = 0;
+  // ---- forward: checkpoints every ckpt_every steps, PE over the last n_pe states
+  TRY(ljmd_set_state(sys, n, box, ck_x.p, ck_v.p, 1));
+  double acc_pe = 0.0;
+  for (int64_t t = 1; t <= nsteps; ++t) {
+    int r = ljmd_step(sys, dt, 1);
+    if (r != LJ_OK) {
+      sys->prm.energy_every = saved_ee;
+      return r;
+    }
+    if (t > nsteps - n_pe) {
+      double pe = 0.0;
+      TRY(ljmd_energies(sys, &pe, nullptr, nullptr));
+      acc_pe += pe;
+    }
+    if (t % ckpt_every == 0 && t < nsteps) TRY(capture(ck_x.p + n3 * (size_t)(t / ckpt_every), ck_v.p + n3 * (size_t)(t / ckpt_every)));
+  }
+  sys->prm.energy_every = saved_ee;
+  TRY(capture(xNu.p, nullptr));
+  const int nb = launch_sqdiff(xNu.p, x0u.p, (int64_t)n3, part.p, st);
+  launch_final_reduce(part.p, nb, 1, part.p + kMaxRedBlocks, st);
+  CKL();
+  CK(cudaMemcpyAsync(sys->h_f64, part.p + kMaxRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double msd = sys->h_f64[0] / (double)n;
+  *loss = acc_pe * wpe + msd;
+  if (!gx0 && !gv0 && !gtheta) return check_status(sys);
+
+  // ---- reverse: lx = dloss/dx_n, lv = 0; then state by state back to t = 0
+  double gth[2] = {0.0, 0.0};
+  const double eps = sys->prm.eps;
+  double q[5];
+  launch_scaled_diff(lx.p, 2.0 / (double)n, xNu.p, x0u.p, (int64_t)n3, st);
+  CK(cudaMemsetAsync(lv.p, 0, bytes, st));
+  if (n_pe > 0) {
+    TRY(adjoint_pass(sys, nullptr, nullptr, f.p, q));  // at x_n: F and dPE
+    launch_axpy(lx.p, -wpe, f.p, (int64_t)n3, st);
+    gth[0] += wpe * q[4] / eps;
+    gth[1] += wpe * q[3];
+  }
+  for (int64_t seg = nseg - 1; seg >= 0; --seg) {
+    const int64_t t0 = seg * ckpt_every, t1 = std::min<int64_t>(t0 + ckpt_every, nsteps);
+    // recompute the segment's states t0 .. t1 - 1 from its checkpoint
+    TRY(ljmd_set_state(sys, n, box, ck_x.p + n3 * (size_t)seg, ck_v.p + n3 * (size_t)seg, 1));
+    CK(cudaMemcpyAsync(seg_x.p, ck_x.p + n3 * (size_t)seg, bytes, cudaMemcpyDeviceToDevice, st));
+    sys->prm.energy_every = 0;
+    for (int64_t t = t0 + 1; t < t1; ++t) {
+      int r = ljmd_step(sys, dt, 1);
+      if (r != LJ_OK) {
+        sys->prm.energy_every = saved_ee;
+        return r;
+      }
+      TRY(capture(seg_x.p + n3 * (size_t)(t - t0), nullptr));
+    }
+    sys->prm.energy_every = saved_ee;
+    for (int64_t t = t1 - 1; t >= t0; --t) {
+      launch_axpy(lv.p, dt, lx.p, (int64_t)n3, st);  // x_{t+1} = x_t + dt v'
+      TRY(ljmd_set_state(sys, n, box, seg_x.p + n3 * (size_t)(t - t0), nullptr, 1));
+      TRY(adjoint_pass(sys, lv.p, b.p, f.p, q));
+      const double c = t == 0 ? h : dt;  // both half-kicks touching state t (one at t = 0)
+      launch_axpy(lx.p, -c, b.p, (int64_t)n3, st);
+      gth[0] += c * q[0] / eps;
+      gth[1] += c * q[1];
+      if (t > nsteps - n_pe) {
+        launch_axpy(lx.p, -wpe, f.p, (int64_t)n3, st);
+        gth[0] += wpe * q[4] / eps;
+        gth[1] += wpe * q[3];
+      }
+      if (t == 0) {
+        // MSD term at t = 0: -2 (x_n - x_0) / N
+        launch_scaled_diff(b.p, -2.0 / (double)n, xNu.p, x0u.p, (int64_t)n3, st);
+        launch_axpy(lx.p, 1.0, b.p, (int64_t)n3, st);
+      }
+      sys->launches += 3;
+      CKL();
+    }
+  }
+  if (gx0) CK(cudaMemcpyAsync(gx0, lx.p, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (gv0) CK(cudaMemcpyAsync(gv0, lv.p, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (gtheta) {
+    gtheta[0] = gth[0];
+    gtheta[1] = gth[1];
+  }
   return check_status(sys);
 }
 

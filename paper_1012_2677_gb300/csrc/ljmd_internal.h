@@ -123,6 +123,12 @@ int launch_force_tile(int precision, int half, int lanes, int energy, const void
                       const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
                       const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
                       int nbuf, cudaStream_t s);
+// Adjoint pass (HVP, forces, parameter derivatives) over the list; w, hw, fo are dvec4 [N] in sorted
+// order (fo may be null).  Writes 5 partials per block [w.dF/deps, w.dF/dsigma, dPE/deps,
+// dPE/dsigma, PE]; returns the number of blocks.
+int launch_adjoint_tile(int precision, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
+                        TileArgs ta, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
+                        const void* w, void* hw, void* fo, double* part, int32_t* status, cudaStream_t s);
 void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,
                         uint64_t E, uint32_t* out, int32_t* status, cudaStream_t s);
 
@@ -147,5 +153,13 @@ void launch_entries_to_keys(unsigned long long* keys, uint64_t E, const int32_t*
                             unsigned int* counter, int32_t* status, cudaStream_t s);
 // Ascending bitonic sort of P = 2^m keys in place; returns the number of kernel launches.
 int launch_bitonic_sort(unsigned long long* keys, uint32_t P, cudaStream_t s);
+
+// ---- adjoint pass helpers (kernels_adjoint.cu) ----------------------------------------
+void launch_to_sorted(const double* w_id, const int32_t* id, int64_t N, dvec4* out, cudaStream_t s);
+void launch_unwrapped(const double* x, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
+                      double* out, cudaStream_t s);
+void launch_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s);
+void launch_scaled_diff(double* y, double a, const double* u, const double* w, int64_t n, cudaStream_t s);
+int launch_sqdiff(const double* u, const double* w, int64_t n, double* part, cudaStream_t s);
 
 }  // namespace ljmd

@@ -71,6 +71,8 @@ _SIGS = {
     "ljmd_set_energy_log": (ctypes.c_int, [_P, _P, _I64]),
     "ljmd_get_pairs": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_get_pairs_static": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ljmd_hvp": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
+    "ljmd_traj_loss_grad": (ctypes.c_int, [_P, _I64, _D, _P, _P, _D, _I64, _I64, _I64, _P, _P, _P, _P, _I32]),
     "ljmd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_stats)]),
     "ljmd_set_profiling": (ctypes.c_int, [_P, _I32]),
     "ljmd_set_tuning": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),
@@ -211,6 +213,38 @@ def ljmd_get_pairs_static(h, cap=None):
     return out[:min(n.value, cap)], n.value
 
 
+def ljmd_hvp(h, w, hw, dtheta=None) -> None:
+    """hw = H(x) w (Hessian of the potential energy); dtheta (4 doubles, optional) =
+    (w.dF/deps, w.dF/dsigma, dPE/deps, dPE/dsigma).  w, hw: both host or both device, 3N FP64."""
+    pw, dw, kw = _arr_ptr(w, np.float64)
+    ph, dh, kh = _arr_ptr(hw, np.float64)
+    if dw != dh:
+        raise ValueError("w and hw must both be host or both be device arrays")
+    dth = np.zeros(4) if dtheta is None else dtheta
+    _chk(load().ljmd_hvp(h, pw, ph, dth.ctypes.data_as(_P), dw), "ljmd_hvp")
+    return dth
+
+
+def ljmd_traj_loss_grad(h, n: int, box: float, x0, v0, dt: float, nsteps: int, n_pe: int, ckpt_every: int,
+                        gx0=None, gv0=None):
+    """Loss of the differentiable trajectory (mean PE/N over the last n_pe steps + MSD) and its
+    gradients by the reverse-time pass with checkpoints every ckpt_every steps.  x0, v0 (and gx0,
+    gv0 when given) are all host or all device arrays of 3n FP64.  Returns (loss, (deps, dsigma))."""
+    px, dx, kx = _arr_ptr(x0, np.float64, 3 * n)
+    pv, dv, kv = _arr_ptr(v0, np.float64, 3 * n)
+    pgx, dgx, kgx = _arr_ptr(gx0, np.float64, 3 * n)
+    pgv, dgv, kgv = _arr_ptr(gv0, np.float64, 3 * n)
+    for d, a in ((dv, v0), (dgx, gx0), (dgv, gv0)):
+        if a is not None and d != dx:
+            raise ValueError("all arrays must be host or all device")
+    loss = _D()
+    gth = np.zeros(2)
+    _chk(load().ljmd_traj_loss_grad(h, int(n), float(box), px, pv, float(dt), int(nsteps), int(n_pe),
+                                    int(ckpt_every), ctypes.byref(loss), pgx, pgv, gth.ctypes.data_as(_P), dx),
+         "ljmd_traj_loss_grad")
+    return loss.value, (float(gth[0]), float(gth[1]))
+
+
 def ljmd_get_stats(h) -> dict:
     st = ljmd_stats()
     _chk(load().ljmd_get_stats(h, ctypes.byref(st)), "ljmd_get_stats")
@@ -309,6 +343,24 @@ class System:
     def pairs_static(self, cap=None):
         """(pairs, npairs) from the allocation-free export; pairs holds the first min(cap, npairs)."""
         return ljmd_get_pairs_static(self.h, cap)
+
+    def hvp(self, w):
+        """(H w, (w.dF/deps, w.dF/dsigma, dPE/deps, dPE/dsigma)) at the current positions, id order."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        hw = np.empty_like(w)
+        dth = ljmd_hvp(self.h, w, hw)
+        return hw, tuple(float(t) for t in dth)
+
+    def traj_loss_grad(self, x0, v0, box, dt, nsteps, n_pe, ckpt_every):
+        """(loss, g_x0, g_v0, (dloss/deps, dloss/dsigma)) of the differentiable trajectory (host arrays)."""
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        n = x0.size // 3
+        gx = np.empty_like(x0)
+        gv = np.empty_like(v0)
+        loss, gth = ljmd_traj_loss_grad(self.h, n, box, x0, v0, dt, nsteps, n_pe, ckpt_every, gx, gv)
+        self.n, self.box = n, float(box)
+        return loss, gx, gv, gth
 
     def stats(self):
         return ljmd_get_stats(self.h)
