@@ -291,6 +291,90 @@ int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out);
 int ljmd_set_tuning(ljmd_sys* sys, int32_t tile_cells, int32_t lanes, int32_t force_ctas_per_sm,
                     int32_t force_buffers);
 
+/* ---- batched replicas ------------------------------------------------------------------- */
+
+/*
+ * Many independent periodic LJ systems (replicas) of uneven size, density and temperature,
+ * advanced together with the same method (mixed form, full list): every phase of the step is one
+ * launch over all replicas, the list-validity rule (rebuild when the largest displacement of any
+ * replica exceeds margin/2) is evaluated on the device, and K steps can be captured once as a
+ * CUDA graph and replayed.  Replica r owns particles [base_r, base_r + n[r]) of every array, with
+ * base_r = n[0] + ... + n[r-1]; all arrays are in that concatenated order.  The paper treats one
+ * system; batching is this library's extension of the same per-system method.
+ */
+typedef struct ljmd_batch ljmd_batch;
+
+typedef struct ljmd_batch_stats {
+  int64_t replicas;        /* R */
+  int64_t n;               /* particles over all replicas */
+  int64_t steps;           /* steps since the state was set */
+  int64_t rebuilds;        /* list constructions (host-driven and device-decided) */
+  int64_t list_entries;    /* entries of the current lists, all replicas */
+  int64_t tiles;           /* shared-memory tiles over all replicas */
+  int64_t cells;           /* cells over all replicas */
+  int64_t kernel_launches; /* kernels launched (graph replays count their kernels) */
+  int32_t status_word;     /* LJ_ST_* bits raised on the device */
+  int32_t tile_cells;      /* preferred cells per tile along z */
+  int32_t lanes;           /* threads per key particle in the force kernel */
+  int32_t pad;
+} ljmd_batch_stats;
+
+/*
+ * Create a batch of `replicas` systems with common potential and list parameters p (cutoff,
+ * margin, eps, sigma, truncation; list_form is full; p->lanes 2, 4 or 8 or 0 for the default)
+ * and per-replica particle counts n[r] and box sides box[r] (host arrays).  Every box needs
+ * L >= 2 (r_s + margin) and at least 3 cells per side (L >= 3 r_s).  The batch works on its own
+ * stream; every call first waits for the work queued so far on cuda_stream (a cudaStream_t, NULL =
+ * legacy default stream).  Errors: LJ_EINVAL, LJ_ERANGE (a box under 3 cells per side, more than
+ * 2^32 - 1 cells, more than 10^9 particles), LJ_ENOMEM, LJ_EDEVICE.
+ */
+int ljmd_batch_create(ljmd_batch** out, const ljmd_params* p, int32_t replicas, const int64_t* n, const double* box,
+                      void* cuda_stream);
+
+/* Free every resource of the batch (NULL is ignored). */
+void ljmd_batch_destroy(ljmd_batch* b);
+
+/*
+ * Set all replicas' states: x[3 i + k] positions (folded into the replica's box), v velocities
+ * (NULL = 0), i over the concatenated particles; host (on_device = 0) or device arrays.  The
+ * lists are rebuilt (with capacities sized for the following steps) before the next force.
+ */
+int ljmd_batch_set_state(ljmd_batch* b, const double* x, const double* v, int32_t on_device);
+
+/*
+ * Advance every replica nsteps velocity-Verlet steps (Sec. 4.4) with step dt.  graph_steps = K > 0:
+ * the K-step sequence (kick-drift with displacement check, device-decided rebuild, force; final
+ * kick) is captured once as a CUDA graph (re-captured when dt or K changes) and replayed
+ * floor(nsteps / K) times, the rest run as plain launches; K = 0: plain launches.  No host
+ * synchronisation between steps; synchronises once at the end.  Capacities of the lists are fixed
+ * at the last host construction (with headroom); if a device-side construction exceeds them the
+ * status word is raised and LJ_EDEVICE is returned (set the state again to resize).
+ */
+int ljmd_batch_step(ljmd_batch* b, double dt, int64_t nsteps, int32_t graph_steps);
+
+/* Per-replica PE (Eq. 2), kinetic energy and virial of the current state (host arrays of R). */
+int ljmd_batch_energies(ljmd_batch* b, double* pe, double* ke, double* virial);
+
+/* Positions (as stored, folded at the last construction), velocities and forces in the
+ * concatenated caller order; any pointer may be NULL.  Synchronises. */
+int ljmd_batch_get_state(ljmd_batch* b, double* x, double* v, double* f, int32_t on_device);
+
+/* Unique pairs (i, j), i < j, of replica r's current list in its own particle numbering, sorted;
+ * as ljmd_get_pairs.  Synchronises. */
+int ljmd_batch_get_pairs(ljmd_batch* b, int32_t replica, int64_t* ij, int64_t cap, int64_t* npairs);
+
+int ljmd_batch_get_stats(ljmd_batch* b, ljmd_batch_stats* out);
+
+/* Kernel shape: tile_cells (1..14, 0 keeps) and force lanes (2, 4, 8; 0 keeps).  Drops the graph. */
+int ljmd_batch_set_tuning(ljmd_batch* b, int32_t tile_cells, int32_t lanes);
+
+/*
+ * Autotuner: for tile_cells in {2, 3, 4, 6} and lanes in {2, 4, 8}, construct the lists at the
+ * current positions and time `trials` force launches and the construction (CUDA events); keep the
+ * shape with the least force + construction / 10.  The state is unchanged.  Outputs may be NULL.
+ */
+int ljmd_batch_autotune(ljmd_batch* b, int32_t trials, int32_t* best_tile, int32_t* best_lanes, double* best_ms);
+
 /* Human-readable name of a status code. */
 const char* ljmd_strerror(int code);
 

@@ -54,7 +54,8 @@ void launch_wrap_label(double* x, int32_t* img, int64_t N, Geom g, uint32_t* cel
 // Exclusive scan, three passes: per-tile sums, scan of the tile sums (recursively), tile scan.
 constexpr int kScanTile = 2048;  // 256 threads x 8 values
 
-__global__ void k_tile_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+__global__ void k_tile_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   __shared__ uint32_t sh[8];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   uint32_t s = 0;
@@ -75,7 +76,8 @@ __global__ void k_tile_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t
 
 // Scan of one tile: each thread owns 8 consecutive values; out[i] = base + exclusive prefix.
 __global__ void k_tile_scan(const uint32_t* __restrict__ in, int64_t n, const uint32_t* __restrict__ tile_base,
-                            uint32_t* __restrict__ out) {
+                            uint32_t* __restrict__ out, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   __shared__ uint32_t sh[8];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * 8;
   uint32_t v[8], t = 0;
@@ -116,17 +118,17 @@ size_t scan_tmp_words(int64_t n) {
   return words + 1;
 }
 
-int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s) {
+int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s, const int* pred) {
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles <= 1) {
-    k_tile_scan<<<1, 256, 0, s>>>(in, n, nullptr, out);
+    k_tile_scan<<<1, 256, 0, s>>>(in, n, nullptr, out, pred);
     return 1;
   }
   uint32_t* sums = tmp;                // [tiles]
   uint32_t* base = tmp + tiles;        // [tiles + 1]
-  k_tile_sums<<<(int)tiles, 256, 0, s>>>(in, n, sums);
-  const int inner = launch_scan_u32(sums, base, tiles, tmp + 2 * tiles + 1, s);
-  k_tile_scan<<<(int)tiles, 256, 0, s>>>(in, n, base, out);
+  k_tile_sums<<<(int)tiles, 256, 0, s>>>(in, n, sums, pred);
+  const int inner = launch_scan_u32(sums, base, tiles, tmp + 2 * tiles + 1, s, pred);
+  k_tile_scan<<<(int)tiles, 256, 0, s>>>(in, n, base, out, pred);
   return inner + 2;
 }
 
@@ -134,7 +136,8 @@ int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
 // Scatter (Fig. 3 (ii)-(iii)): place each particle at its cell's pointer and advance it.
 // The arrival order inside a cell is made deterministic afterwards by k_cell_order.
 __global__ void k_scatter(const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ start,
-                          uint32_t* __restrict__ fill, uint32_t* __restrict__ perm, int64_t N) {
+                          uint32_t* __restrict__ fill, uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t c = cell_of[i];
     const uint32_t slot = atomicAdd(&fill[c], 1u);
@@ -143,14 +146,15 @@ __global__ void k_scatter(const uint32_t* __restrict__ cell_of, const uint32_t* 
 }
 
 void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_t* cell_fill, uint32_t* perm,
-                    int64_t N, cudaStream_t s) {
-  k_scatter<<<grid_for(N, 256), 256, 0, s>>>(cell_of, cell_start, cell_fill, perm, N);
+                    int64_t N, cudaStream_t s, const int* pred) {
+  k_scatter<<<grid_for(N, 256), 256, 0, s>>>(cell_of, cell_start, cell_fill, perm, N, pred);
 }
 
 // Inside each cell order the particles by id (insertion sort of the cell's slice of perm):
 // the sorted order then depends only on the positions, not on atomic arrival order.
 __global__ void k_cell_order(const uint32_t* __restrict__ start, int64_t ncells, uint32_t* __restrict__ perm,
-                             const int32_t* __restrict__ id) {
+                             const int32_t* __restrict__ id, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t b = start[c], e = start[c + 1];
@@ -168,14 +172,15 @@ __global__ void k_cell_order(const uint32_t* __restrict__ start, int64_t ncells,
 }
 
 void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* perm, const int32_t* id,
-                       cudaStream_t s) {
-  k_cell_order<<<grid_for(ncells, 128), 128, 0, s>>>(cell_start, ncells, perm, id);
+                       cudaStream_t s, const int* pred) {
+  k_cell_order<<<grid_for(ncells, 128), 128, 0, s>>>(cell_start, ncells, perm, id, pred);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Gathers: out[k] = in[perm[k]].
 __global__ void k_gather_f64x3(const double* __restrict__ in, double* __restrict__ out,
-                               const uint32_t* __restrict__ perm, int64_t N) {
+                               const uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t p = perm[k];
     out[k] = in[p];
@@ -183,12 +188,13 @@ __global__ void k_gather_f64x3(const double* __restrict__ in, double* __restrict
     out[2 * N + k] = in[2 * N + p];
   }
 }
-void launch_gather_f64x3(const double* in, double* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
-  k_gather_f64x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N);
+void launch_gather_f64x3(const double* in, double* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
+  k_gather_f64x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N, pred);
 }
 
 __global__ void k_gather_i32x3(const int32_t* __restrict__ in, int32_t* __restrict__ out,
-                               const uint32_t* __restrict__ perm, int64_t N) {
+                               const uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t p = perm[k];
     out[k] = in[p];
@@ -196,47 +202,51 @@ __global__ void k_gather_i32x3(const int32_t* __restrict__ in, int32_t* __restri
     out[2 * N + k] = in[2 * N + p];
   }
 }
-void launch_gather_i32x3(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
-  k_gather_i32x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N);
+void launch_gather_i32x3(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
+  k_gather_i32x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N, pred);
 }
 
 __global__ void k_gather_i32(const int32_t* __restrict__ in, int32_t* __restrict__ out,
-                             const uint32_t* __restrict__ perm, int64_t N) {
+                             const uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
     out[k] = in[perm[k]];
 }
-void launch_gather_i32(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
-  k_gather_i32<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N);
+void launch_gather_i32(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
+  k_gather_i32<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N, pred);
 }
 
 __global__ void k_gather_u32(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                             const uint32_t* __restrict__ perm, int64_t N) {
+                             const uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
     out[k] = in[perm[k]];
 }
-void launch_gather_u32(const uint32_t* in, uint32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
-  k_gather_u32<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N);
+void launch_gather_u32(const uint32_t* in, uint32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
+  k_gather_u32<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N, pred);
 }
 
 __global__ void k_gather_16B(const uint4* __restrict__ in, uint4* __restrict__ out, const uint32_t* __restrict__ perm,
-                             int64_t N) {
+                             int64_t N, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
     out[k] = in[perm[k]];
 }
-void launch_gather_16B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
-  k_gather_16B<<<grid_for(N, 256), 256, 0, s>>>((const uint4*)in, (uint4*)out, perm, N);
+void launch_gather_16B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
+  k_gather_16B<<<grid_for(N, 256), 256, 0, s>>>((const uint4*)in, (uint4*)out, perm, N, pred);
 }
 
 __global__ void k_gather_32B(const uint4* __restrict__ in, uint4* __restrict__ out, const uint32_t* __restrict__ perm,
-                             int64_t N) {
+                             int64_t N, const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t p = perm[k];
     out[2 * k] = in[2 * (size_t)p];
     out[2 * k + 1] = in[2 * (size_t)p + 1];
   }
 }
-void launch_gather_32B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s) {
-  k_gather_32B<<<grid_for(N, 256), 256, 0, s>>>((const uint4*)in, (uint4*)out, perm, N);
+void launch_gather_32B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
+  k_gather_32B<<<grid_for(N, 256), 256, 0, s>>>((const uint4*)in, (uint4*)out, perm, N, pred);
 }
 
 // ---------------------------------------------------------------------------------------------

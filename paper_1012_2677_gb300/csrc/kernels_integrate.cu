@@ -108,7 +108,8 @@ int launch_integrate(int precision, double* x, double* v, const void* f, void* p
 // the hi/lo split always (the list build uses it in both forms); for FP64 also the dvec4
 // copy; and the displacement reference (hi for mixed, the dvec4 for FP64) if ref != NULL.
 __global__ void k_shadow(const double* __restrict__ x, int64_t N, int mixed, float4* __restrict__ hi,
-                         float4* __restrict__ lo, dvec4* __restrict__ pos64, void* __restrict__ ref) {
+                         float4* __restrict__ lo, dvec4* __restrict__ pos64, void* __restrict__ ref, const int* __restrict__ pred) {
+  if (pred && !*pred) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double a = x[i], b = x[N + i], c = x[2 * N + i];
     float4 h, l;
@@ -128,10 +129,10 @@ __global__ void k_shadow(const double* __restrict__ x, int64_t N, int mixed, flo
 }
 
 void launch_shadow_all(const double* x, int64_t N, int mixed, float4* hi, float4* lo, dvec4* pos64, void* ref,
-                       cudaStream_t s) {
+                       cudaStream_t s, const int* pred) {
   int64_t b = (N + 255) / 256;
   if (b < 1) b = 1;
-  k_shadow<<<(int)(b < 1048576 ? b : 1048576), 256, 0, s>>>(x, N, mixed, hi, lo, pos64, ref);
+  k_shadow<<<(int)(b < 1048576 ? b : 1048576), 256, 0, s>>>(x, N, mixed, hi, lo, pos64, ref, pred);
 }
 
 }  // namespace ljmd

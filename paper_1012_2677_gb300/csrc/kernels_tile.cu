@@ -394,6 +394,26 @@ __device__ __forceinline__ int own_cell(const TileShared& S, int l, int Tp) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Batched replicas: the replica owning global tile t (tile_base ascending), and the tile geometry
+// of that replica (capacities stay the batch's).
+__device__ __forceinline__ int replica_of_tile(const ReplicaGeo* __restrict__ reps, int R, int64_t t) {
+  int lo = 0, hi = R - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (reps[mid].tile_base <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ void replica_view(const ReplicaGeo& rg, TileArgs& ta, Geom& g) {
+  ta.n = rg.n;
+  ta.T = rg.T;
+  ta.ntz = rg.ntz;
+  ta.whole = 0;
+  ta.ntiles = (int64_t)rg.n * rg.n * rg.ntz;
+  g = rg.g;
+}
+
 // Shared-memory layout of the thread-per-key list kernel (mixed form, staged tiles).
 constexpr int kListSplit = 2;  // candidate sub-ranges per neighbour column (work balance)
 constexpr size_t kListSmemTarget = 52 * 1024;  // 4 CTAs per SM
@@ -635,19 +655,21 @@ __device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float
 // (padded to 8 entries), and a second pass writes the entries into shared memory, from where
 // they are copied out with 16-byte stores (directly to global memory if the segment does not
 // fit).
-template <bool HALF>
+template <bool HALF, bool BATCHED>
 __global__ void __launch_bounds__(kTileThreads, 4)
-    k_list_keys(const float4* __restrict__ pos, const double* __restrict__ x, const uint32_t* __restrict__ cs,
-                int64_t N, Geom g, TileArgs ta, ListBand band, uint2* __restrict__ rows,
+    k_list_keys(const float4* __restrict__ pos, const double* __restrict__ x, const uint32_t* __restrict__ cs_in,
+                int64_t N, Geom g_in, TileArgs ta_in, ListBand band, uint2* __restrict__ rows,
                 uint2* __restrict__ tile_list, uint16_t* __restrict__ ent, uint64_t cap,
                 unsigned long long* __restrict__ counter, unsigned int* __restrict__ max_list,
-                int32_t* __restrict__ status) {
+                int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps, int R,
+                const int* __restrict__ pred) {
+  if (pred && !*pred) return;  // predicated (batched rebuild inside a graph)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared S;
   __shared__ __align__(8) uint64_t bar;
   __shared__ unsigned int s_base, s_total, s_padded;
   __shared__ int s_ok;
-  const KeyListLayout K = key_list_layout(ta);
+  const KeyListLayout K = key_list_layout(ta_in);
   TileLayout L;  // the staging helpers' view: positions and sorted indices
   L.pos = K.pos;
   L.lo = K.pos;
@@ -667,8 +689,18 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   }
   __syncthreads();
 
-  for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
-    const TileInfo ti = tile_info(t, ta);
+  for (int64_t t = blockIdx.x; t < ta_in.ntiles; t += gridDim.x) {
+    TileArgs ta = ta_in;
+    Geom g = g_in;
+    const uint32_t* cs = cs_in;
+    int64_t tl = t;
+    if (BATCHED) {  // the tile's replica: its box, grid and cells
+      const ReplicaGeo& rg = reps[replica_of_tile(reps, R, t)];
+      replica_view(rg, ta, g);
+      cs = cs_in + rg.cell_base;
+      tl = t - rg.tile_base;
+    }
+    const TileInfo ti = tile_info(tl, ta);
     if (!stage_offsets(ti, ta, cs, S)) {
       if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
       __syncthreads();
@@ -727,6 +759,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         s_ok = fits;
         tile_list[t] = fits ? make_uint2((unsigned)b, padded) : make_uint2(0u, 0u);
         atomicMax(max_list, padded);
+        if (BATCHED && !fits) atomicOr(status, LJ_ST_LIST_OVERFLOW);  // no host retry inside a graph
       }
     }
     __syncthreads();
@@ -963,10 +996,10 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
 
 // Bookkeeping of one tile before its copies are issued: segment of the list, cell bounds,
 // capacity checks (identical in every thread).  Returns whether the tile can be staged.
-__device__ __forceinline__ bool force_tile_prepare(int64_t t, const TileArgs& ta, const uint32_t* __restrict__ cs,
+__device__ __forceinline__ bool force_tile_prepare(const TileInfo& ti, int64_t t, const TileArgs& ta,
+                                                   const uint32_t* __restrict__ cs,
                                                    const uint2* __restrict__ tile_list, TileShared& S,
                                                    int32_t* __restrict__ status) {
-  const TileInfo ti = tile_info(t, ta);
   if (threadIdx.x == blockDim.x - 1) {
     const uint2 tl = tile_list[t];
     S.list_base = tl.x;
@@ -1020,18 +1053,18 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     int b = 0;
     bool v_cur = false, v_next = false;
     if (pipelined && t < ta.ntiles) {
-      v_cur = force_tile_prepare(t, ta, cs, tile_list, SS[0], status);
+      v_cur = force_tile_prepare(tile_info(t, ta), t, ta, cs, tile_list, SS[0], status);
       if (v_cur) stage_issue<MIXED, true>(tile_info(t, ta), ta, pos, lo, rows, ent, SS[0], smem, L, &bars[0]);
     }
     for (; t < ta.ntiles; t += gridDim.x) {
       if (!pipelined) {
-        v_cur = force_tile_prepare(t, ta, cs, tile_list, SS[0], status);
+        v_cur = force_tile_prepare(tile_info(t, ta), t, ta, cs, tile_list, SS[0], status);
         if (v_cur) stage_issue<MIXED, true>(tile_info(t, ta), ta, pos, lo, rows, ent, SS[0], smem, L, &bars[0]);
       } else {
         const int64_t tn = t + gridDim.x;
         v_next = false;
         if (tn < ta.ntiles) {
-          v_next = force_tile_prepare(tn, ta, cs, tile_list, SS[b ^ 1], status);
+          v_next = force_tile_prepare(tile_info(tn, ta), tn, ta, cs, tile_list, SS[b ^ 1], status);
           if (v_next)
             stage_issue<MIXED, true>(tile_info(tn, ta), ta, pos, lo, rows, ent, SS[b ^ 1],
                                      smem + (b ^ 1) * buf_bytes, L, &bars[b ^ 1]);
@@ -1063,6 +1096,91 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       part[2 * (size_t)blockIdx.x] = tp;
       part[2 * (size_t)blockIdx.x + 1] = tv;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched replicas (mixed form, full list): one persistent launch walks the tiles of all
+// replicas; each tile takes its replica's box and grid from the replica table.  Energies: the
+// tile's PE and virial are reduced over the CTA and added to its replica's totals (e_rep[2 r],
+// e_rep[2 r + 1]).
+template <int LANES, bool ENERGY>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_force_batch(const float4* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs_in,
+                  int64_t N, TileArgs caps, LJConst c, const uint2* __restrict__ rows,
+                  const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent, float4* __restrict__ fout,
+                  double* __restrict__ e_rep, int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps,
+                  int R) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileShared S;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ double sh[32];
+  const TileLayout L = tile_layout(caps, true, true, false);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  uint32_t ph = 0;
+  for (int64_t t = blockIdx.x; t < caps.ntiles; t += gridDim.x) {
+    const int r = replica_of_tile(reps, R, t);
+    const ReplicaGeo& rg = reps[r];
+    TileArgs ta = caps;
+    Geom g;
+    replica_view(rg, ta, g);
+    const uint32_t* cs = cs_in + rg.cell_base;
+    const TileInfo ti = tile_info(t - rg.tile_base, ta);
+    double pe_acc = 0.0, vir_acc = 0.0;
+    if (force_tile_prepare(ti, t, ta, cs, tile_list, S, status)) {
+      stage_issue<true, true>(ti, ta, pos, lo, rows, ent, S, smem, L, &bar);
+      if (!stage_finish<true, true>(ti, ta, g, S, smem, L, &bar, ph, false, status)) return;
+      force_tile_compute<true, LANES, false, ENERGY, false>(S, smem, L, rows, ent, c, g, fout, status, pe_acc,
+                                                            vir_acc);
+    }
+    if (ENERGY) {
+      const double tp = block_sum(pe_acc, sh);
+      __syncthreads();
+      const double tv = block_sum(vir_acc, sh);
+      if (threadIdx.x == 0) {
+        atomicAdd(&e_rep[2 * r], 0.5 * tp);  // full list: each pair twice
+        atomicAdd(&e_rep[2 * r + 1], 0.5 * tv);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Largest staged and own counts over the tiles of all replicas.
+__global__ void k_tile_sizes_batch(const uint32_t* __restrict__ cs_in, TileArgs caps,
+                                   const ReplicaGeo* __restrict__ reps, int R, unsigned int* __restrict__ out) {
+  unsigned int mst = 0, mown = 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < caps.ntiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const ReplicaGeo& rg = reps[replica_of_tile(reps, R, t)];
+    TileArgs ta = caps;
+    Geom g;
+    replica_view(rg, ta, g);
+    const uint32_t* cs = cs_in + rg.cell_base;
+    const TileInfo ti = tile_info(t - rg.tile_base, ta);
+    const int ncol = ti.Tp + 2;
+    unsigned int tot = 0;
+    for (int q = 0; q < 9 * ncol; ++q) {
+      int sx, sy, sz;
+      const uint32_t cq = cell_of_q(ti, ta.n, ncol, q, sx, sy, sz);
+      tot += cs[cq + 1] - cs[cq];
+    }
+    const uint32_t c0 = ((uint32_t)ti.cx * (uint32_t)ta.n + (uint32_t)ti.cy) * (uint32_t)ta.n + (uint32_t)ti.z0;
+    mst = max(mst, tot);
+    mown = max(mown, cs[c0 + ti.Tp] - cs[c0]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mst = max(mst, __shfl_xor_sync(0xffffffffu, mst, o));
+    mown = max(mown, __shfl_xor_sync(0xffffffffu, mown, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], mst);
+    atomicMax(&out[1], mown);
   }
 }
 
@@ -1255,7 +1373,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     __syncthreads();
     uint32_t ph = 0;
     for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
-      const bool ok = force_tile_prepare(t, ta, cs, tile_list, S, status);
+      const bool ok = force_tile_prepare(tile_info(t, ta), t, ta, cs, tile_list, S, status);
       if (ok) {
         const TileInfo ti = tile_info(t, ta);
         stage_issue<MIXED, true>(ti, ta, pos, lo, rows, ent, S, smem, L, &bar);
@@ -1376,13 +1494,15 @@ void launch_list_tile(int precision, int half, const void* pos, const double* x,
   } else {
     if (mixed) {
       if (half) {
-        set_smem(k_list_keys<true>, sm);
-        k_list_keys<true><<<grid, kTileThreads, sm, s>>>((const float4*)pos, x, cs, N, g, ta, band, rows, tile_list,
-                                                         ent, cap, counter, max_list, status);
+        set_smem(k_list_keys<true, false>, sm);
+        k_list_keys<true, false><<<grid, kTileThreads, sm, s>>>((const float4*)pos, x, cs, N, g, ta, band, rows,
+                                                                tile_list, ent, cap, counter, max_list, status,
+                                                                nullptr, 0, nullptr);
       } else {
-        set_smem(k_list_keys<false>, sm);
-        k_list_keys<false><<<grid, kTileThreads, sm, s>>>((const float4*)pos, x, cs, N, g, ta, band, rows, tile_list,
-                                                          ent, cap, counter, max_list, status);
+        set_smem(k_list_keys<false, false>, sm);
+        k_list_keys<false, false><<<grid, kTileThreads, sm, s>>>((const float4*)pos, x, cs, N, g, ta, band, rows,
+                                                                 tile_list, ent, cap, counter, max_list, status,
+                                                                 nullptr, 0, nullptr);
       }
     } else {
       if (half) LJ_LIST_LAUNCH(false, true, false);
@@ -1532,6 +1652,56 @@ int launch_adjoint_tile(int precision, const void* pos, const float4* lo, const 
     else LJ_ADJ_LAUNCH(false, false);
   }
 #undef LJ_ADJ_LAUNCH
+  return grid;
+}
+
+
+// ---- batched replicas -----------------------------------------------------------------------
+size_t batch_list_smem_bytes(const TileArgs& caps) { return key_list_layout(caps).total; }
+size_t batch_force_smem_bytes(const TileArgs& caps) { return align16(tile_layout(caps, true, true, false).total); }
+
+void launch_tile_sizes_batch(const uint32_t* cs, TileArgs caps, const ReplicaGeo* reps, int R, unsigned int* out,
+                             cudaStream_t s) {
+  int64_t b = (caps.ntiles + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 4096) b = 4096;
+  k_tile_sizes_batch<<<(int)b, 256, 0, s>>>(cs, caps, reps, R, out);
+}
+
+void launch_list_batch(const float4* hi, const double* x, const uint32_t* cs, int64_t N, Geom g, TileArgs caps,
+                       ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
+                       unsigned long long* counter, unsigned int* max_list, int32_t* status, const ReplicaGeo* reps,
+                       int R, const int* pred, cudaStream_t s) {
+  const size_t sm = key_list_layout(caps).total;
+  const int grid = tile_grid(caps, per_sm_for(sm));
+  set_smem(k_list_keys<false, true>, sm);
+  k_list_keys<false, true><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, caps, band, rows, tile_list, ent, cap,
+                                                          counter, max_list, status, reps, R, pred);
+}
+
+int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo, const uint32_t* cs, int64_t N,
+                       TileArgs caps, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
+                       float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R, cudaStream_t s) {
+  const size_t sm = batch_force_smem_bytes(caps);
+  const int grid = tile_grid(caps, per_sm_for(sm));
+#define LJ_FB(LN)                                                                                               \
+  do {                                                                                                          \
+    if (energy) {                                                                                               \
+      set_smem(k_force_batch<LN, true>, sm);                                                                    \
+      k_force_batch<LN, true><<<grid, kTileThreads, sm, s>>>(hi, lo, cs, N, caps, c, rows, tile_list, ent, f,   \
+                                                             e_rep, status, reps, R);                          \
+    } else {                                                                                                    \
+      set_smem(k_force_batch<LN, false>, sm);                                                                   \
+      k_force_batch<LN, false><<<grid, kTileThreads, sm, s>>>(hi, lo, cs, N, caps, c, rows, tile_list, ent, f,  \
+                                                              e_rep, status, reps, R);                         \
+    }                                                                                                           \
+  } while (0)
+  switch (lanes) {
+    case 2: LJ_FB(2); break;
+    case 8: LJ_FB(8); break;
+    default: LJ_FB(4); break;
+  }
+#undef LJ_FB
   return grid;
 }
 

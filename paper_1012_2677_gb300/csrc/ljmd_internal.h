@@ -69,17 +69,26 @@ void launch_wrap_label(double* x, int32_t* img, int64_t N, Geom g, uint32_t* cel
 // exclusive scan of n uint32 values into out[0..n] (out[n] = total); tmp >= scan_tmp_words(n)
 size_t scan_tmp_words(int64_t n);
 // returns the number of kernels launched
-int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
+int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s,
+    const int* pred = nullptr);
 void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_t* cell_fill, uint32_t* perm,
-                    int64_t N, cudaStream_t s);
+                    int64_t N, cudaStream_t s,
+    const int* pred = nullptr);
 void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* perm, const int32_t* id,
-                       cudaStream_t s);
-void launch_gather_f64x3(const double* in, double* out, const uint32_t* perm, int64_t N, cudaStream_t s);
-void launch_gather_i32x3(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s);
-void launch_gather_i32(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s);
-void launch_gather_u32(const uint32_t* in, uint32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s);
-void launch_gather_16B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s);
-void launch_gather_32B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s);
+                       cudaStream_t s,
+    const int* pred = nullptr);
+void launch_gather_f64x3(const double* in, double* out, const uint32_t* perm, int64_t N, cudaStream_t s,
+    const int* pred = nullptr);
+void launch_gather_i32x3(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s,
+    const int* pred = nullptr);
+void launch_gather_i32(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s,
+    const int* pred = nullptr);
+void launch_gather_u32(const uint32_t* in, uint32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s,
+    const int* pred = nullptr);
+void launch_gather_16B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s,
+    const int* pred = nullptr);
+void launch_gather_32B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s,
+    const int* pred = nullptr);
 void launch_scatter_back_f64x3(const double* in, double* out_idorder, const int32_t* id, int64_t N,
                                double sub, cudaStream_t s);
 void launch_scatter_back_f32x4_to_f64x3(const float4* in, double* out, const int32_t* id, int64_t N,
@@ -95,7 +104,8 @@ void launch_load_state(const double* x_in, const double* v_in, double* x, double
 // mixed: hi/lo FP32 split of x_state; fp64: dvec4 copy.  ref (optional) receives hi
 // (mixed) or the dvec4 (fp64) as the displacement reference.
 void launch_shadow_all(const double* x, int64_t N, int mixed, float4* hi, float4* lo, dvec4* pos64, void* ref,
-                       cudaStream_t s);
+                       cudaStream_t s,
+                       const int* pred = nullptr);
 
 // ---- staged cell-column tiles: list and force ---------------------------------------------
 constexpr int kMaxTileT = 14;  // cells per tile along z, at most
@@ -109,6 +119,15 @@ struct TileArgs {
   int32_t max_own;     // own particles per tile, at most
   int32_t max_chunks;  // 32-candidate chunks per own particle, at most
   int32_t max_list;    // list entries per tile (padded to 8), at most (known after construction)
+};
+// One replica of a batch: its box (offset and p are the batch's), grid, tiles and particles.
+// Global tiles, cells and particles are the replicas' ranges concatenated in replica order.
+struct ReplicaGeo {
+  Geom g;
+  int32_t n, T, ntz, pad;  // cells per side, cells per tile along z, tiles per column
+  int64_t tile_base;       // first global tile
+  int64_t cell_base;       // first global cell
+  int64_t base, count;     // first global particle, particles
 };
 size_t list_smem_bytes(const TileArgs& ta, int precision);
 size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf, int half);
@@ -161,5 +180,28 @@ void launch_unwrapped(const double* x, const int32_t* img, const int32_t* id, in
 void launch_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s);
 void launch_scaled_diff(double* y, double a, const double* u, const double* w, int64_t n, cudaStream_t s);
 int launch_sqdiff(const double* u, const double* w, int64_t n, double* part, cudaStream_t s);
+
+// ---- batched replicas (kernels_tile.cu, kernels_batch.cu) ----------------------------------
+size_t batch_list_smem_bytes(const TileArgs& caps);
+size_t batch_force_smem_bytes(const TileArgs& caps);
+void launch_tile_sizes_batch(const uint32_t* cs, TileArgs caps, const ReplicaGeo* reps, int R, unsigned int* out,
+                             cudaStream_t s);
+void launch_list_batch(const float4* hi, const double* x, const uint32_t* cs, int64_t N, Geom g, TileArgs caps,
+                       ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
+                       unsigned long long* counter, unsigned int* max_list, int32_t* status, const ReplicaGeo* reps,
+                       int R, const int* pred, cudaStream_t s);
+int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo, const uint32_t* cs, int64_t N,
+                       TileArgs caps, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
+                       float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R, cudaStream_t s);
+void launch_wrap_label_batch(double* x, int32_t* img, int64_t N, const int32_t* rep_of, const ReplicaGeo* reps,
+                             double offset, uint32_t* cell_of, uint32_t* cell_count, int32_t* status,
+                             const int* pred, cudaStream_t s);
+void launch_rebuild_flag(const uint32_t* dmax_bits, float limit2, int* flag, long long* rebuilds, cudaStream_t s);
+void launch_copy_words(const void* in, void* out, int64_t bytes, const int* pred, cudaStream_t s);
+void launch_zero_words(void* out, int64_t bytes, const int* pred, cudaStream_t s);
+void launch_replica_ke(const double* v, int64_t N, const ReplicaGeo* reps, int R, double* ke_rep, cudaStream_t s);
+void launch_set_flag(int* flag, int value, cudaStream_t s);
+void launch_load_batch(const double* xin, const double* vin, double* x, double* v, int32_t* id, int32_t* img,
+                       int64_t N, const int32_t* rep_of, const ReplicaGeo* reps, double offset, cudaStream_t s);
 
 }  // namespace ljmd

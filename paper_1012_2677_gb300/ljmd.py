@@ -53,6 +53,13 @@ class ljmd_profile(ctypes.Structure):
                 ("energy_ms", ctypes.c_double), ("energy_launches", ctypes.c_int64)]
 
 
+class ljmd_batch_stats(ctypes.Structure):
+    _fields_ = [("replicas", ctypes.c_int64), ("n", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("rebuilds", ctypes.c_int64), ("list_entries", ctypes.c_int64), ("tiles", ctypes.c_int64),
+                ("cells", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("status_word", ctypes.c_int32),
+                ("tile_cells", ctypes.c_int32), ("lanes", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _I32, _I64, _U64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
@@ -72,6 +79,16 @@ _SIGS = {
     "ljmd_get_pairs": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_get_pairs_static": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_hvp": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
+    "ljmd_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ljmd_params), _I32, _P, _P, _P]),
+    "ljmd_batch_destroy": (None, [_P]),
+    "ljmd_batch_set_state": (ctypes.c_int, [_P, _P, _P, _I32]),
+    "ljmd_batch_step": (ctypes.c_int, [_P, _D, _I64, _I32]),
+    "ljmd_batch_energies": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ljmd_batch_get_state": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
+    "ljmd_batch_get_pairs": (ctypes.c_int, [_P, _I32, _P, _I64, _P]),
+    "ljmd_batch_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_batch_stats)]),
+    "ljmd_batch_set_tuning": (ctypes.c_int, [_P, _I32, _I32]),
+    "ljmd_batch_autotune": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "ljmd_traj_loss_grad": (ctypes.c_int, [_P, _I64, _D, _P, _P, _D, _I64, _I64, _I64, _P, _P, _P, _P, _I32]),
     "ljmd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_stats)]),
     "ljmd_set_profiling": (ctypes.c_int, [_P, _I32]),
@@ -381,3 +398,85 @@ class System:
             return
         self._keep = [tensor]
         ljmd_set_energy_log(self.h, ctypes.c_void_p(tensor.data_ptr()), tensor.shape[0])
+
+
+# ---- batched replicas ----------------------------------------------------------------------------
+
+class Batch:
+    """Independent LJ systems of uneven size advanced together (ljmd_batch_*).  Replica r owns the
+    particles [base_r, base_r + n[r]) of the concatenated arrays."""
+
+    def __init__(self, n, box, eps=1.0, sigma=1.0, cutoff=2.5, margin=0.3, truncation=LJ_TRUNC_QUADRATIC, lanes=0,
+                 stream=None):
+        self.n = np.ascontiguousarray(n, dtype=np.int64)
+        self.box = np.ascontiguousarray(box, dtype=np.float64)
+        self.R = len(self.n)
+        self.N = int(self.n.sum())
+        self.base = np.concatenate([[0], np.cumsum(self.n)[:-1]]).astype(np.int64)
+        self.params = ljmd_params(eps, sigma, cutoff, margin, truncation, LJ_LIST_FULL, 0, lanes)
+        h = _P()
+        _chk(load().ljmd_batch_create(ctypes.byref(h), ctypes.byref(self.params), self.R,
+                                      self.n.ctypes.data_as(_P), self.box.ctypes.data_as(_P), _stream_handle(stream)),
+             "ljmd_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ljmd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, x, v=None):
+        px, dx, kx = _arr_ptr(x, np.float64, 3 * self.N)
+        pv, dv, kv = _arr_ptr(v, np.float64, 3 * self.N)
+        if v is not None and dv != dx:
+            raise ValueError("x and v must both be host or both be device arrays")
+        _chk(load().ljmd_batch_set_state(self.h, px, pv, dx), "ljmd_batch_set_state")
+
+    def step(self, dt, nsteps=1, graph_steps=0):
+        _chk(load().ljmd_batch_step(self.h, float(dt), int(nsteps), int(graph_steps)), "ljmd_batch_step")
+
+    def energies(self):
+        pe, ke, vir = (np.empty(self.R) for _ in range(3))
+        _chk(load().ljmd_batch_energies(self.h, pe.ctypes.data_as(_P), ke.ctypes.data_as(_P), vir.ctypes.data_as(_P)),
+             "ljmd_batch_energies")
+        return pe, ke, vir
+
+    def get_state(self):
+        x, v, f = (np.empty((self.N, 3)) for _ in range(3))
+        _chk(load().ljmd_batch_get_state(self.h, x.ctypes.data_as(_P), v.ctypes.data_as(_P), f.ctypes.data_as(_P), 0),
+             "ljmd_batch_get_state")
+        return x, v, f
+
+    def pairs(self, r):
+        n = _I64()
+        _chk(load().ljmd_batch_get_pairs(self.h, int(r), None, 0, ctypes.byref(n)), "ljmd_batch_get_pairs")
+        out = np.empty((max(n.value, 1), 2), dtype=np.int64)
+        _chk(load().ljmd_batch_get_pairs(self.h, int(r), out.ctypes.data_as(_P), n.value, ctypes.byref(n)),
+             "ljmd_batch_get_pairs")
+        return out[:n.value]
+
+    def stats(self):
+        st = ljmd_batch_stats()
+        _chk(load().ljmd_batch_get_stats(self.h, ctypes.byref(st)), "ljmd_batch_get_stats")
+        return {name: getattr(st, name) for name, _ in ljmd_batch_stats._fields_}
+
+    def set_tuning(self, tile_cells=0, lanes=0):
+        _chk(load().ljmd_batch_set_tuning(self.h, int(tile_cells), int(lanes)), "ljmd_batch_set_tuning")
+
+    def autotune(self, trials=5):
+        t, l, ms = _I32(), _I32(), _D()
+        _chk(load().ljmd_batch_autotune(self.h, int(trials), ctypes.byref(t), ctypes.byref(l), ctypes.byref(ms)),
+             "ljmd_batch_autotune")
+        return t.value, l.value, ms.value

@@ -54,3 +54,39 @@ def dyadic(x, bits: int = 40) -> np.ndarray:
     2^(52 - bits) is exact (inputs then survive any offset storage bit for bit)."""
     s = float(2 ** bits)
     return np.round(np.asarray(x, dtype=np.float64) * s) / s
+
+
+def fcc_thinned(N: int, rho: float, seed: int):
+    """Positions of N particles in a cubic box of side L = (N / rho)^(1/3): an FCC lattice of
+    M = ceil((N / 4)^(1/3)) cells of side L / M with a seeded random N-subset of its 4 M^3 sites
+    kept.  Returns (x[N, 3], L)."""
+    L = (N / rho) ** (1.0 / 3.0)
+    M = int(np.ceil((N / 4.0) ** (1.0 / 3.0)))
+    a = L / M
+    basis = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+    g = np.arange(M)
+    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 1, 3)
+    sites = ((cells + basis[None]) * a).reshape(-1, 3)
+    keep = subset(len(sites), N, seed)
+    return sites[keep].copy(), L
+
+
+def thermal_velocities(N: int, T: float, seed: int) -> np.ndarray:
+    """Seeded Gaussian velocities with the mean removed and sum v^2 = 3 (N - 1) T."""
+    v = gaussian((N, 3), seed)
+    v -= v.mean(0)
+    return v * np.sqrt(3.0 * (N - 1) * T / (v ** 2).sum())
+
+
+def batch_workload(R: int, seed: int, n_range=(500, 50000)):
+    """The batched-replica workload: R replicas with (N, rho, T) from replica_table, FCC-thinned
+    positions and thermal velocities (replica seeds seed + r).  Returns (n[R], box[R], x[sum n, 3],
+    v[sum n, 3], T[R])."""
+    n, rho, T = replica_table(R, seed, n_range=n_range)
+    xs, vs, box = [], [], []
+    for r in range(R):
+        x, L = fcc_thinned(int(n[r]), float(rho[r]), seed + r)
+        xs.append(x)
+        vs.append(thermal_velocities(int(n[r]), float(T[r]), seed + 7919 + r))
+        box.append(L)
+    return n, np.array(box), np.concatenate(xs), np.concatenate(vs), T
