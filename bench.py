@@ -275,6 +275,9 @@ def run_ours(args, wl, world, rank, local):
                "note": "set_state from pinned host + K steps + get_state/energies to host, per K-step job"}
         s2.close()
 
+    batched = None if args.no_batch else run_batched(args, stream, world, rank, barrier)
+    adjoint = None if args.no_adjoint else run_adjoint(stream)
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -291,6 +294,8 @@ def run_ours(args, wl, world, rank, local):
         "list": {"entries_per_particle": entries / N, "rebuilds": st1["rebuilds"] - st0["rebuilds"],
                  "mean_lifetime_steps": args.steps / max(st1["rebuilds"] - st0["rebuilds"], 1)},
         "energies_final": {"pe_per_particle": pe / N, "ke_per_particle": ke / N, "virial": vir},
+        "batched": batched,
+        "adjoint": adjoint,
         "pair_interactions_per_s": entries * args.steps * world / (ms * 1e-3),
     }
     if rank == 0 and not args.no_cpu_baseline and not args.skip_cpu:
@@ -299,6 +304,58 @@ def run_ours(args, wl, world, rank, local):
         dist.barrier()
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def run_batched(args, stream, world, rank, barrier):
+    """Batched-replica workload: 256 replicas, N ~ U[500, 50000], rho ~ U[0.3, 0.9], T ~ U[0.7, 1.5]
+    (FCC filled then thinned), r_c 2.5, margin 0.3, dt 0.004, mixed form; tiles autotuned, steps
+    replayed as a captured 10-step CUDA graph.  Timed with CUDA events on the library's stream."""
+    import torch
+    from paper_1012_2677_gb300 import ljmd, synth
+    n, box, x, v, _ = synth.batch_workload(256, 1000 + 100 * rank)
+    K = 10
+    steps = max(K, (args.batch_steps // K) * K)
+    with ljmd.Batch(n, box, cutoff=2.5, margin=0.3, stream=stream) as b:
+        b.set_state(x, v)
+        tile, lanes, tune_ms = b.autotune(trials=3)
+        b.step(0.004, 2 * K, graph_steps=K)  # warm-up: capture and first replays
+        torch.cuda.synchronize()
+        st0 = b.stats()
+        barrier()
+        t0 = time.perf_counter()
+        b.step(0.004, steps, graph_steps=K)  # returns after the stream is synchronised
+        dt_s = time.perf_counter() - t0
+        st1 = b.stats()
+    N = int(n.sum())
+    return {"workload": "256 replicas, N in [500, 50000] (%d particles), rho in [0.3, 0.9], T in [0.7, 1.5], "
+                        "margin 0.3, dt 0.004" % N,
+            "value": N * steps * world / dt_s, "unit": UNIT, "steps": steps, "ms_per_step": dt_s / steps * 1e3,
+            "graph_steps": K, "autotuned": {"tile_cells": tile, "lanes": lanes, "cost_ms": round(tune_ms, 4)},
+            "rebuilds": st1["rebuilds"] - st0["rebuilds"],
+            "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+            "timing": "host clock around one ljmd_batch_step call (graph replays, one synchronisation at the end)"}
+
+
+def run_adjoint(stream):
+    """Differentiable-trajectory workload: 32,000 particles (FCC 20^3 x 4), rho 0.6, T 1.2,
+    50 steps, loss over the last 10, checkpoints every 10; forward + checkpointed reverse pass."""
+    import numpy as np
+    import torch
+    from paper_1012_2677_gb300 import ljmd, synth
+    x, L = synth.fcc_thinned(32000, 0.6, 5)
+    v = synth.thermal_velocities(len(x), 1.2, 5)
+    res = {}
+    for name, prec in (("mixed", ljmd.LJ_MIXED), ("fp64", ljmd.LJ_FP64)):
+        with ljmd.System(cutoff=2.5, margin=0.5, precision=prec, energy_every=0, stream=stream) as s:
+            s.traj_loss_grad(x, v, L, 0.005, 10, 2, 5)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss, gx, gv, gth = s.traj_loss_grad(x, v, L, 0.005, 50, 10, 10)
+            t = time.perf_counter() - t0
+        res[name] = {"seconds": t, "particle_steps_per_s": len(x) * 50 / t, "loss": loss,
+                     "grad_norm_x0": float(np.linalg.norm(gx)), "dloss_deps": gth[0], "dloss_dsigma": gth[1]}
+    res["note"] = "forward 50 steps + reverse pass (one Hessian-vector product per state, segments recomputed)"
+    return res
 
 
 def _oracle_sample_rate(wl, target_s, sample_seed=7):
@@ -374,6 +431,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--skip-cpu", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -113,12 +113,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+// try_wait with a suspend-time hint: the thread may sleep up to `hint_ns` nanoseconds inside the
+// instruction until the phase completes, instead of spinning on issue slots.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity, uint32_t hint_ns = 1000000u) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(r)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
       : "memory");
   return r != 0;
 }
