@@ -416,14 +416,18 @@ __device__ __forceinline__ void replica_view(const ReplicaGeo& rg, TileArgs& ta,
 
 // Shared-memory layout of the thread-per-key list kernel (mixed form, staged tiles).
 constexpr int kListSplit = 2;  // candidate sub-ranges per neighbour column (work balance)
-constexpr size_t kListSmemTarget = 52 * 1024;  // 4 CTAs per SM
+constexpr int kListItems = 9 * kListSplit;     // work items per 32-key chunk
+constexpr size_t kListSmemTarget = 64 * 1024;  // 3 CTAs per SM
 struct KeyListLayout {
   size_t pos;    // hi float4 [max_staged]
   size_t gid;    // int [max_staged]
-  size_t cnt;    // int [nch * 9 * kListSplit * 32]: per (key, column part) counts, then offsets in the row
+  size_t cnt;    // int [nch * kListItems * 32]: per (key, column part) counts, then offsets in the row
   size_t kst;    // int [nch * 32] row start within the tile segment, then int [nch * 32] row length
+  size_t ibase;  // int [nch * kListItems + 1]: first mask word of each item
+  size_t mask;   // uint32 [mask_words * 32]: kept-candidate bits, word-major, lane-minor
   size_t seg;    // uint16 [seg_cap]: the tile's list segment before it is copied out
   int nch;       // 32-key chunks per tile, at most
+  int mask_words;  // mask words per lane for one tile
   int seg_cap;   // entries (a multiple of 8)
   size_t total;
 };
@@ -436,9 +440,16 @@ __host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs
   K.gid = o;
   o += align16(ms * 4);
   K.cnt = o;
-  o += align16((size_t)K.nch * 9 * kListSplit * 32 * 4);
+  o += align16((size_t)K.nch * kListItems * 32 * 4);
   K.kst = o;
   o += align16((size_t)K.nch * 32 * 8);
+  K.ibase = o;
+  o += align16(((size_t)K.nch * kListItems + 1) * 4);
+  // every item needs ceil(len / 32) words; the items of a chunk cover at most all staged slots
+  int mw = K.nch * ((int)(ms / 32) + kListItems + 1);
+  K.mask_words = mw < 192 ? mw : 192;
+  K.mask = o;
+  o += (size_t)K.mask_words * 32 * 4;
   K.seg = o;
   size_t room = o + 8192 < kListSmemTarget ? kListSmemTarget - o : 8192;
   K.seg_cap = (int)((room / 2) & ~(size_t)7);
@@ -592,22 +603,35 @@ __device__ __forceinline__ bool key_test(float r2, const ListBand& band, bool& m
   return in;
 }
 
-template <bool HALF, bool WRITE>
-__device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float4* sh_pos, const int* sh_gid,
-                                        const double* __restrict__ x, int64_t N, const Geom& g,
-                                        const ListBand& band, int c, int k, int h, int n_own, uint16_t* dst, int p) {
-  const int lane = threadIdx.x & 31;
+// Candidate range [j0, j1) of item (chunk c, column k, part h).
+__device__ __forceinline__ void key_item_range(const TileShared& S, int Tp, int c, int k, int h, int n_own, int& j0,
+                                               int& j1) {
   const int ncol = S.ncol;
-  const int o = 32 * c + lane;
-  const bool valid = o < n_own;
   const int o_last = min(32 * c + 31, n_own - 1);
   const int ma = own_cell(S, S.own0 + 32 * c, Tp), mb = own_cell(S, S.own0 + o_last, Tp);
   const int r0 = S.offq[k * ncol + ma - 1], r1 = S.offq[k * ncol + mb + 2];
-  const int j0 = r0 + ((r1 - r0) * h) / kListSplit, j1 = r0 + ((r1 - r0) * (h + 1)) / kListSplit;
+  j0 = r0 + ((r1 - r0) * h) / kListSplit;
+  j1 = r0 + ((r1 - r0) * (h + 1)) / kListSplit;
+}
+
+// MODE 0: count; 1: count and store the kept-candidate bits (word w of the item at
+// mask[(wbase + w) * 32 + lane]); 2: write the kept partners to dst[p], dst[p + 1], ...
+template <bool HALF, int MODE>
+__device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float4* sh_pos, const int* sh_gid,
+                                        const double* __restrict__ x, int64_t N, const Geom& g,
+                                        const ListBand& band, int c, int k, int h, int n_own, uint16_t* dst, int p,
+                                        uint32_t* mask, int wbase) {
+  const int lane = threadIdx.x & 31;
+  const int o = 32 * c + lane;
+  const bool valid = o < n_own;
+  const int o_last = min(32 * c + 31, n_own - 1);
+  int j0, j1;
+  key_item_range(S, Tp, c, k, h, n_own, j0, j1);
   const int l = S.own0 + (valid ? o : o_last);
   const float4 pi = sh_pos[l];
   const int gi = sh_gid[l];
   int cnt = 0;
+  uint32_t bits = 0;
   int j = j0;
   for (; j + 1 < j1; j += 2) {  // two candidates per iteration (same address in every lane: broadcasts)
     const float4 pa = sh_pos[j], pb = sh_pos[j + 1];
@@ -626,9 +650,17 @@ __device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float
       ina = ina && sh_gid[j] > gi;
       inb = inb && sh_gid[j + 1] > gi;
     }
-    if (WRITE) {
+    if (MODE == 2) {
       if (ina) dst[p++] = (uint16_t)j;
       if (inb) dst[p++] = (uint16_t)(j + 1);
+    }
+    if (MODE == 1) {  // q = j - j0 is even, so a pair never straddles a word
+      const int q = j - j0;
+      bits |= ((ina ? 1u : 0u) | (inb ? 2u : 0u)) << (q & 31);
+      if ((q & 31) == 30) {
+        mask[(wbase + (q >> 5)) * 32 + lane] = bits;
+        bits = 0;
+      }
     }
     cnt += (ina ? 1 : 0) + (inb ? 1 : 0);
   }
@@ -642,10 +674,89 @@ __device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float
     }
     ina = ina && valid && j != l;
     if (HALF) ina = ina && sh_gid[j] > gi;
-    if (WRITE && ina) dst[p++] = (uint16_t)j;
+    if (MODE == 2 && ina) dst[p++] = (uint16_t)j;
+    if (MODE == 1) bits |= (ina ? 1u : 0u) << ((j - j0) & 31);
     cnt += ina ? 1 : 0;
+    ++j;
+  }
+  if (MODE == 1 && ((j - j0) & 31) != 0) mask[(wbase + ((j - j0) >> 5)) * 32 + lane] = bits;
+  return cnt;
+}
+
+// Count pass with bits, 32 candidates per word: the FP32 filter sets `bits` (r^2 < lo) and
+// `mbits` (r^2 < hi) with compile-time bit positions, then the rare band members get the exact
+// FP64 test, the key itself and the slots past the range are cleared, and the word is stored.
+// Slots past the range read whatever follows in shared memory; their bits are masked off.
+template <bool HALF>
+__device__ __forceinline__ int key_item_bits(const TileShared& S, int Tp, const float4* sh_pos, const int* sh_gid,
+                                             const double* __restrict__ x, int64_t N, const Geom& g,
+                                             const ListBand& band, int c, int k, int h, int n_own, uint32_t* mask,
+                                             int wbase) {
+  const int lane = threadIdx.x & 31;
+  const int o = 32 * c + lane;
+  const bool valid = o < n_own;
+  const int o_last = min(32 * c + 31, n_own - 1);
+  int j0, j1;
+  key_item_range(S, Tp, c, k, h, n_own, j0, j1);
+  const int l = S.own0 + (valid ? o : o_last);
+  const float4 pi = sh_pos[l];
+  const int gi = sh_gid[l];
+  int cnt = 0;
+  for (int jb = j0, w = 0; jb < j1; jb += 32, ++w) {
+    uint32_t bits = 0, mbits = 0;
+#pragma unroll
+    for (int u = 0; u < 32; u += 8) {
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const float4 pj = sh_pos[jb + u + v];  // same address in every lane: one broadcast
+        const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;  // exact
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r2 < band.lo) bits |= 1u << (u + v);
+        if (r2 < band.hi) mbits |= 1u << (u + v);
+      }
+    }
+    const int nv = j1 - jb;
+    const uint32_t tail = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+    bits &= tail;
+    mbits &= tail & ~bits;
+    if (__any_sync(0xffffffffu, mbits != 0u)) {
+      while (mbits) {
+        const int bit = __ffs(mbits) - 1;
+        mbits &= mbits - 1;
+        if (pair_in_exact(x, N, gi, sh_gid[jb + bit], g, band.rs2)) bits |= 1u << bit;
+      }
+    }
+    if (l >= jb && l < jb + 32) bits &= ~(1u << (l - jb));  // the key itself
+    if (HALF) {
+      uint32_t m = bits;
+      while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        if (sh_gid[jb + bit] <= gi) bits &= ~(1u << bit);
+      }
+    }
+    if (!valid) bits = 0u;
+    mask[(wbase + w) * 32 + lane] = bits;
+    cnt += __popc(bits);
   }
   return cnt;
+}
+
+// Write pass from stored bits: the kept partners of the lane's key in ascending order.
+__device__ __forceinline__ void key_item_from_mask(const TileShared& S, int Tp, int c, int k, int h, int n_own,
+                                                   uint16_t* dst, int p, const uint32_t* mask, int wbase) {
+  const int lane = threadIdx.x & 31;
+  int j0, j1;
+  key_item_range(S, Tp, c, k, h, n_own, j0, j1);
+  const int nw = (j1 - j0 + 31) >> 5;
+  for (int w = 0; w < nw; ++w) {
+    uint32_t m = mask[(wbase + w) * 32 + lane];
+    while (m) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1;
+      dst[p++] = (uint16_t)(j0 + 32 * w + bit);
+    }
+  }
 }
 
 // Pair-list construction, mixed form, staged tiles: one thread per key particle.  Work items
@@ -680,6 +791,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   int* s_cnt = (int*)(smem + K.cnt);
   int* s_kst = (int*)(smem + K.kst);
   int* s_len = s_kst + K.nch * 32;
+  int* s_ibase = (int*)(smem + K.ibase);
+  uint32_t* s_mask = (uint32_t*)(smem + K.mask);
   uint16_t* s_seg = (uint16_t*)(smem + K.seg);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t phase = 0;
@@ -716,12 +829,39 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       continue;
     }
     const int nch = (n_own + 31) / 32;
-    // pass 1: counts per (key, column part)
-    constexpr int kItems = 9 * kListSplit;
+    constexpr int kItems = kListItems;
+    // first mask word of every item (warp 0); the bits are kept only if the tile's words fit
+    if (warp == 0) {
+      int run = 0;
+      for (int base = 0; base < nch * kItems; base += 32) {
+        const int item = base + lane;
+        int nw = 0;
+        if (item < nch * kItems) {
+          int j0, j1;
+          key_item_range(S, ti.Tp, item / kItems, (item % kItems) / kListSplit, item % kListSplit, n_own, j0, j1);
+          nw = (j1 - j0 + 31) >> 5;
+        }
+        int inc = nw;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, d);
+          if (lane >= d) inc += y;
+        }
+        if (item < nch * kItems) s_ibase[item] = run + inc - nw;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) s_ibase[nch * kItems] = run;
+    }
+    __syncthreads();
+    const bool keep_bits = s_ibase[nch * kItems] <= K.mask_words;
+    // pass 1: counts per (key, column part), kept-candidate bits
     for (int item = warp; item < nch * kItems; item += kWarps) {
       const int c = item / kItems, r = item - kItems * c;
-      s_cnt[item * 32 + lane] = key_item<HALF, false>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit,
-                                                      r % kListSplit, n_own, nullptr, 0);
+      s_cnt[item * 32 + lane] =
+          keep_bits ? key_item_bits<HALF>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit,
+                                          n_own, s_mask, s_ibase[item])
+                    : key_item<HALF, 0>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit,
+                                        n_own, nullptr, 0, nullptr, 0);
     }
     __syncthreads();
     if (warp == 0) {
@@ -774,8 +914,11 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         const int c = item / kItems, r = item - kItems * c;
         const int o = 32 * c + lane;
         const int p = o < n_own ? s_kst[o] + s_cnt[item * 32 + lane] : 0;
-        key_item<HALF, true>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit, n_own, dst,
-                             p);
+        if (keep_bits)
+          key_item_from_mask(S, ti.Tp, c, r / kListSplit, r % kListSplit, n_own, dst, p, s_mask, s_ibase[item]);
+        else
+          key_item<HALF, 2>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit, n_own, dst,
+                            p, nullptr, 0);
       }
       if (staged) {
         __syncthreads();
