@@ -55,6 +55,12 @@ extern "C" {
 #define LJ_LIST_FULL 0  /* every particle lists all partners; force kernel writes without atomics */
 #define LJ_LIST_HALF 1  /* each pair once, key = lower index (Sec. 2.4); Newton-3 scatter with atomics */
 
+/* ---- list validity rules (Sec. 2.3, Alg. 2) ---- */
+#define LJ_VALID_HALF_MARGIN 0     /* rebuild when the largest displacement since the build > margin/2 */
+#define LJ_VALID_DUTC 1            /* DUTC: buffer = margin at the build, -= 2 v_max dt per step, rebuild at <= 0 */
+#define LJ_VALID_DUTC_LDC 2        /* Alg. 2: DUTC first; when it expires, the large displacement check */
+#define LJ_VALID_HALF_MARGIN_LDC 3 /* the margin/2 rule first; when it fires, the large displacement check */
+
 /* ---- truncation of the potential (Sec. 2.1) ---- */
 #define LJ_TRUNC_QUADRATIC 0  /* Eq. 2: 4 eps [c2 (r/sigma)^2 + c0] added, V(r_c) = V'(r_c) = 0 */
 #define LJ_TRUNC_SHIFT 1      /* c2 = 0, c0 from V(r_c) = 0 (force identical to Eq. 1) */
@@ -83,6 +89,10 @@ typedef struct ljmd_stats {
   int32_t status_word;     /* LJ_ST_* bits raised on the device (synchronises) */
   int32_t precision;       /* LJ_FP64 / LJ_MIXED */
   int64_t kernel_launches; /* CUDA kernels this handle has launched */
+  int64_t ldc_checks;      /* large displacement checks run (LDC rules) */
+  int64_t ldc_kept;        /* of those, checks that kept the list */
+  int32_t validity;        /* LJ_VALID_* rule in use */
+  int32_t pad;
 } ljmd_stats;
 
 /* Per-phase device time (CUDA events on the handle's stream), accumulated while profiling is on. */
@@ -374,6 +384,21 @@ int ljmd_batch_set_tuning(ljmd_batch* b, int32_t tile_cells, int32_t lanes);
  * shape with the least force + construction / 10.  The state is unchanged.  Outputs may be NULL.
  */
 int ljmd_batch_autotune(ljmd_batch* b, int32_t trials, int32_t* best_tile, int32_t* best_lanes, double* best_ms);
+
+/*
+ * List-validity rule (Sec. 2.3, Alg. 2); the list is rebuilt when the rule says it expired.
+ *  LJ_VALID_HALF_MARGIN (default): the largest displacement since the build exceeds margin/2.
+ *  LJ_VALID_DUTC: the dynamical upper time cutoff, buffer_length = margin at the build, reduced by
+ *    2 v_max dt every step (v_max: largest drift speed of the step), expired at <= 0.
+ *  LJ_VALID_DUTC_LDC: Alg. 2: when DUTC expires, the large displacement check (LDC) decides: the
+ *    particles that moved more than margin - (largest displacement) form L_D; the list is kept if
+ *    |L_D| <= max_ld (N_l) and no pair of L_D is unlisted yet closer than r_c now.  Rerun every
+ *    step until it fails.
+ *  LJ_VALID_HALF_MARGIN_LDC: the margin/2 rule first, then the LDC as above.
+ * max_ld: N_l (0 keeps the current, default 1024).  A new rule takes effect at the next list
+ * construction (forced at the next force evaluation).  Errors: LJ_EINVAL.
+ */
+int ljmd_set_validity(ljmd_sys* sys, int32_t mode, int32_t max_ld);
 
 /* Human-readable name of a status code. */
 const char* ljmd_strerror(int code);

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
   const double kk = a.kpre + a.kpost;
   const float kpre_f = (float)a.kpre;
   double ke_acc = 0.0;
-  float d2max = 0.0f;
+  float d2max = 0.0f, v2max = 0.0f;
   bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     double F[3];
@@ -61,6 +61,9 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
     }
     ke_acc += MIXED ? 0.5 * (double)ke_i : 0.5 * ke_d;
     if (a.shadow) {
+      // speed of the drift (the velocity that moved the particle this step), for the DUTC rule
+      const float vx = (float)v[i], vy = (float)v[N + i], vz = (float)v[2 * N + i];
+      v2max = fmaxf(v2max, fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
       if (MIXED) {
         float4 h, l;
         split_hi_lo(xs[0], h.x, l.x);
@@ -90,6 +93,9 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
   if (a.shadow) {
     const float m = block_max(d2max, shf);
     if (threadIdx.x == 0) atomicMax(dmax_bits, __float_as_uint(m));
+    __syncthreads();
+    const float mv = block_max(v2max, shf);
+    if (threadIdx.x == 0) atomicMax(dmax_bits + 1, __float_as_uint(mv));
   }
 }
 

@@ -1848,4 +1848,53 @@ int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo
   return grid;
 }
 
+
+// ---- list validity: the large displacement check (LDC) of Alg. 2 -----------------------------
+// L_D = { i : |x_i - x_ref_i| > th } with th = margin - (an upper bound of the largest
+// displacement); x_ref are the FP64 positions the list was built from.  Indices beyond `cap` are
+// counted but not stored.
+__global__ void k_ldc_collect(const double* __restrict__ x, const double* __restrict__ xref, int64_t N, double th2,
+                              int32_t* __restrict__ list, unsigned int cap, unsigned int* __restrict__ count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double dx = x[i] - xref[i], dy = x[N + i] - xref[N + i], dz = x[2 * N + i] - xref[2 * N + i];
+    if (dx * dx + dy * dy + dz * dz > th2) {
+      const unsigned int k = atomicAdd(count, 1u);
+      if (k < cap) list[k] = (int32_t)i;
+    }
+  }
+}
+
+// Every pair of L_D: unlisted (the list's own exact FP64 test on the build positions says r >= r_s)
+// and now closer than r_c (FP64, with a relative safety of 1e-6) raises *flag.
+__global__ void k_ldc_pairs(const double* __restrict__ x, const double* __restrict__ xref, int64_t N, Geom g,
+                            const int32_t* __restrict__ list, int m, double rs2, double rc2, int* __restrict__ flag) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x) {
+    const int i = list[a];
+    for (int b = a + 1; b < m; ++b) {
+      const int j = list[b];
+      double d2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double t = x[k * N + j] - x[k * N + i];
+        if (t > g.half_L) t -= g.L;
+        else if (t < -g.half_L) t += g.L;
+        d2 += t * t;
+      }
+      if (d2 < rc2 * (1.0 + 1e-6) && !pair_in_exact(xref, N, i, j, g, rs2)) atomicOr(flag, 1);
+    }
+  }
+}
+
+void launch_ldc_collect(const double* x, const double* xref, int64_t N, double th2, int32_t* list, unsigned int cap,
+                        unsigned int* count, cudaStream_t s) {
+  int64_t b = (N + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 65535) b = 65535;
+  k_ldc_collect<<<(int)b, 256, 0, s>>>(x, xref, N, th2, list, cap, count);
+}
+void launch_ldc_pairs(const double* x, const double* xref, int64_t N, Geom g, const int32_t* list, int m, double rs2,
+                      double rc2, int* flag, cudaStream_t s) {
+  const int b = (m + 127) / 128;
+  k_ldc_pairs<<<b < 1 ? 1 : b, 128, 0, s>>>(x, xref, N, g, list, m, rs2, rc2, flag);
+}
 }  // namespace ljmd

@@ -79,6 +79,16 @@ struct ljmd_sys {
   double prof_ms[4] = {0, 0, 0, 0};
   int64_t prof_n[4] = {0, 0, 0, 0};
   int64_t launches = 0;
+  // list validity rule (Sec. 2.3 / Alg. 2)
+  int valid_mode = LJ_VALID_HALF_MARGIN;
+  int max_ld = 1024;          // N_l of the LDC method
+  double dutc_buffer = 0.0;   // buffer_length of the DUTC method
+  double last_vmax = 0.0;     // largest drift speed of the last step
+  double* xref64 = nullptr;   // FP64 positions the list was built from (LDC)
+  int64_t xref_cap = 0;
+  int32_t* ldc_list = nullptr;
+  unsigned int* d_ldc = nullptr;  // [0] |L_D|, [1] invalid flag
+  int64_t ldc_checks = 0, ldc_kept = 0;
   // adjoint pass (allocated on first use)
   dvec4 *adj_w = nullptr, *adj_hw = nullptr, *adj_f = nullptr;
   double* part_adj = nullptr;
@@ -129,7 +139,7 @@ static void free_all(ljmd_sys* s) {
                   s->id_alt, s->img, s->img_alt, s->cell_of, s->cell_alt, s->perm, s->cell_count, s->cell_start,
                   s->cell_fill, s->rows, s->tile_list, s->ent, s->scan_tmp, s->part_force, s->part_ke,
                   s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64, s->d_sizes,
-                  s->adj_w, s->adj_hw, s->adj_f, s->part_adj, s->d_adj};
+                  s->adj_w, s->adj_hw, s->adj_f, s->part_adj, s->d_adj, s->xref64, s->ldc_list, s->d_ldc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& p : s->ev_pending) {
@@ -330,6 +340,8 @@ static int ensure_cells(ljmd_sys* s) {
 }
 
 static void reset_counters(ljmd_sys* s) {
+  s->ldc_checks = 0;
+  s->ldc_kept = 0;
   s->have_list = false;
   s->forces_current = false;
   s->pe_step = -1;
@@ -502,6 +514,15 @@ static int rebuild(ljmd_sys* s) {
   s->list_entries = total;
   s->have_list = true;
   s->rebuilds += 1;
+  s->dutc_buffer = s->prm.margin;
+  if (s->valid_mode == LJ_VALID_DUTC_LDC || s->valid_mode == LJ_VALID_HALF_MARGIN_LDC) {
+    if (s->xref_cap < s->n) {
+      TRY(dalloc_t(s, &s->xref64, 3 * (size_t)s->n));
+      s->xref_cap = s->n;
+    }
+    launch_copy_words(s->x, s->xref64, 24 * s->n, nullptr, s->st);
+    s->launches += 1;
+  }
   s->pe_step = -1;
   return LJ_OK;
 }
@@ -548,12 +569,76 @@ static int run_force(ljmd_sys* s, bool energy) {
 // Largest displacement since the list was built, as measured by the last integrate launch.
 static int read_dmax(ljmd_sys* s, double* out) {
   ljmd_sys* sys = s;
-  CK(cudaMemcpyAsync(s->h_u32, s->d_dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(s->h_u32, s->d_dmax, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
-  float d2;
+  float d2, v2;
   memcpy(&d2, s->h_u32, sizeof(float));
+  memcpy(&v2, s->h_u32 + 1, sizeof(float));
   *out = sqrt((double)d2);
+  s->last_vmax = sqrt((double)v2);
   return LJ_OK;
+}
+
+// Large displacement check (Alg. 2): L_D = particles that moved more than margin - d_max (d_max
+// taken as an upper bound of the measured largest displacement); the list stays valid if |L_D| <=
+// N_l and no pair of L_D is both unlisted and now closer than r_c.  Synchronises twice.
+static int ldc_valid(ljmd_sys* s, bool* valid) {
+  ljmd_sys* sys = s;
+  *valid = false;
+  s->ldc_checks += 1;
+  const double slack = (s->precision == LJ_MIXED) ? 2.0 * sqrt(3.0) * ldexp(1.0, s->g.p - 23) + 1e-6 : 1e-12;
+  const double th = s->prm.margin - (s->last_dmax + slack) - 1e-9;
+  if (!(th > 0.0) || !s->xref64) return LJ_OK;
+  if (!s->ldc_list) TRY(dalloc_t(s, &s->ldc_list, (size_t)s->max_ld));
+  if (!s->d_ldc) TRY(dalloc_t(s, &s->d_ldc, 2));
+  CK(cudaMemsetAsync(s->d_ldc, 0, 2 * sizeof(unsigned int), s->st));
+  launch_ldc_collect(s->x, s->xref64, s->n, th * th, s->ldc_list, (unsigned)s->max_ld, s->d_ldc, s->st);
+  s->launches += 1;
+  CKL();
+  CK(cudaMemcpyAsync(s->h_u32, s->d_ldc, sizeof(unsigned int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  const unsigned int m = s->h_u32[0];
+  if (m > (unsigned)s->max_ld) return LJ_OK;
+  if (m >= 2) {
+    launch_ldc_pairs(s->x, s->xref64, s->n, s->g, s->ldc_list, (int)m, s->band.rs2, s->c.rc2, (int*)s->d_ldc + 1,
+                     s->st);
+    s->launches += 1;
+    CKL();
+    CK(cudaMemcpyAsync(s->h_u32, s->d_ldc + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    if (s->h_u32[0]) return LJ_OK;
+  }
+  *valid = true;
+  s->ldc_kept += 1;
+  return LJ_OK;
+}
+
+// The list-validity rule after a drift of length dt (measured maxima of the step are current).
+static int list_expired(ljmd_sys* s, double dt, bool* expired) {
+  *expired = false;
+  switch (s->valid_mode) {
+    case LJ_VALID_HALF_MARGIN:
+      *expired = s->last_dmax > s->disp_limit;
+      return LJ_OK;
+    case LJ_VALID_DUTC:
+      s->dutc_buffer -= 2.0 * s->last_vmax * (1.0 + 1e-6) * fabs(dt);
+      *expired = !(s->dutc_buffer > 0.0);
+      return LJ_OK;
+    default: {
+      bool first_ok;
+      if (s->valid_mode == LJ_VALID_DUTC_LDC) {
+        s->dutc_buffer -= 2.0 * s->last_vmax * (1.0 + 1e-6) * fabs(dt);
+        first_ok = s->dutc_buffer > 0.0;
+      } else {
+        first_ok = s->last_dmax <= s->disp_limit;
+      }
+      if (first_ok) return LJ_OK;
+      bool ok = false;
+      TRY(ldc_valid(s, &ok));
+      *expired = !ok;
+      return LJ_OK;
+    }
+  }
 }
 
 static int ensure_forces(ljmd_sys* s, bool energy) {
@@ -614,7 +699,7 @@ int ljmd_create(ljmd_sys** out, const ljmd_params* p, int32_t precision, void* c
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_energies, 4);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_log_count, 1);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_status, 1);
-  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_dmax, 1);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_dmax, 2);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_total64, 2);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_sizes, 4);
   if (r == LJ_OK && cudaMallocHost(&sys->h_u32, 64) != cudaSuccess) r = LJ_ENOMEM;
@@ -762,11 +847,17 @@ int ljmd_compute_forces(ljmd_sys* sys) {
   } else {
     // displacement since the list was built (shadow copies are current): rebuild if invalid
     IntegrateArgs a{0.0, 0.0, 0.0, 0, 1};
-    CK(cudaMemsetAsync(sys->d_dmax, 0, 4, sys->st));
+    CK(cudaMemsetAsync(sys->d_dmax, 0, 8, sys->st));
     integrate(sys, a);
     CKL();
     TRY(read_dmax(sys, &sys->last_dmax));
-    if (sys->last_dmax > sys->disp_limit) TRY(rebuild(sys));
+    bool expired = sys->last_dmax > sys->disp_limit;
+    if (expired && (sys->valid_mode == LJ_VALID_DUTC_LDC || sys->valid_mode == LJ_VALID_HALF_MARGIN_LDC)) {
+      bool ok = false;
+      TRY(ldc_valid(sys, &ok));
+      expired = !ok;
+    }
+    if (expired) TRY(rebuild(sys));
   }
   return run_force(sys, true);
 }
@@ -784,7 +875,7 @@ int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
   for (int64_t s = 0; s < nsteps; ++s) {
     const bool rec = sys->pe_step == sys->steps && want_energy(sys->steps);
     IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, rec ? 1 : 0, 1};
-    CK(cudaMemsetAsync(sys->d_dmax, 0, 4, st));
+    CK(cudaMemsetAsync(sys->d_dmax, 0, 8, st));
     const int nb = integrate(sys, a);
     CKL();
     if (rec) {
@@ -794,7 +885,9 @@ int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
     sys->steps += 1;
     sys->forces_current = false;
     TRY(read_dmax(sys, &sys->last_dmax));
-    if (sys->last_dmax > sys->disp_limit) TRY(rebuild(sys));
+    bool expired = false;
+    TRY(list_expired(sys, dt, &expired));
+    if (expired) TRY(rebuild(sys));
     TRY(run_force(sys, want_energy(sys->steps)));
   }
   // final half-kick: v at the full step of the last state
@@ -898,6 +991,9 @@ int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
   out->max_displacement = sys->last_dmax;
   out->precision = sys->precision;
   out->kernel_launches = sys->launches;
+  out->ldc_checks = sys->ldc_checks;
+  out->ldc_kept = sys->ldc_kept;
+  out->validity = sys->valid_mode;
   if (sys->broken) {
     out->status_word = -1;
     return LJ_EDEVICE;
@@ -1234,6 +1330,24 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
     gtheta[1] = gth[1];
   }
   return check_status(sys);
+}
+
+
+int ljmd_set_validity(ljmd_sys* sys, int32_t mode, int32_t max_ld) {
+  if (!sys) return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (mode < LJ_VALID_HALF_MARGIN || mode > LJ_VALID_HALF_MARGIN_LDC || max_ld < 0) return LJ_EINVAL;
+  if (max_ld > 0 && max_ld != sys->max_ld) {
+    if (sys->ldc_list) cudaFree(sys->ldc_list);
+    sys->ldc_list = nullptr;
+    sys->max_ld = max_ld;
+  }
+  if (mode != sys->valid_mode) {
+    sys->valid_mode = mode;
+    sys->have_list = false;  // the next construction records what the new rule needs
+    sys->forces_current = false;
+  }
+  return LJ_OK;
 }
 
 

@@ -357,7 +357,7 @@ static int enqueue_steps(ljmd_batch* b, double dt, int64_t k) {
   const double h = 0.5 * dt;
   const float limit2 = (float)(b->disp_limit * b->disp_limit);
   for (int64_t s = 0; s < k; ++s) {
-    BK(cudaMemsetAsync(b->dmax, 0, sizeof(uint32_t), b->st));
+    BK(cudaMemsetAsync(b->dmax, 0, 2 * sizeof(uint32_t), b->st));
     IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, 0, 1};
     launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->hi, b->lo, b->ref, b->N, a, nullptr, b->dmax, b->status, b->st);
     launch_rebuild_flag(b->dmax, limit2, b->flag, b->d_rebuilds, b->st);
@@ -442,7 +442,7 @@ int ljmd_batch_create(ljmd_batch** out, const ljmd_params* p, int32_t replicas, 
   A(&b->e_rep, 2 * (size_t)replicas);
   A(&b->ke_rep, (size_t)replicas);
   A(&b->status, 1);
-  A(&b->dmax, 1);
+  A(&b->dmax, 2);
   A(&b->flag, 1);
   A(&b->d_rebuilds, 1);
   A(&b->counter, 2);

@@ -159,7 +159,9 @@ struct IntegrateArgs {
   int ke;          // accumulate the kinetic energy of the full-step velocity
   int shadow;      // rewrite the force kernel's position copy after the drift
 };
-// Returns the number of blocks used for KE partials.
+// Returns the number of blocks used for KE partials.  With a.shadow, dmax_bits[0] and [1] receive
+// (atomic max) the float bits of the largest squared displacement since the list build and of the
+// largest squared drift speed.
 int launch_integrate(int precision, double* x, double* v, const void* f, void* hi_or_pos, float4* lo,
                      const void* ref, int64_t N, IntegrateArgs a, double* ke_part, uint32_t* dmax_bits,
                      int32_t* status, cudaStream_t s);
@@ -203,5 +205,11 @@ void launch_replica_ke(const double* v, int64_t N, const ReplicaGeo* reps, int R
 void launch_set_flag(int* flag, int value, cudaStream_t s);
 void launch_load_batch(const double* xin, const double* vin, double* x, double* v, int32_t* id, int32_t* img,
                        int64_t N, const int32_t* rep_of, const ReplicaGeo* reps, double offset, cudaStream_t s);
+
+// ---- list validity (kernels_tile.cu) --------------------------------------------------------
+void launch_ldc_collect(const double* x, const double* xref, int64_t N, double th2, int32_t* list, unsigned int cap,
+                        unsigned int* count, cudaStream_t s);
+void launch_ldc_pairs(const double* x, const double* xref, int64_t N, Geom g, const int32_t* list, int m, double rs2,
+                      double rc2, int* flag, cudaStream_t s);
 
 }  // namespace ljmd

@@ -22,6 +22,7 @@ LJ_OK, LJ_EINVAL, LJ_ENOMEM, LJ_EDEVICE, LJ_ESTATE, LJ_ERANGE = 0, -1, -2, -3, -
 LJ_FP64, LJ_MIXED = 0, 1
 LJ_LIST_FULL, LJ_LIST_HALF = 0, 1
 LJ_TRUNC_QUADRATIC, LJ_TRUNC_SHIFT, LJ_TRUNC_CUT = 0, 1, 2
+LJ_VALID_HALF_MARGIN, LJ_VALID_DUTC, LJ_VALID_DUTC_LDC, LJ_VALID_HALF_MARGIN_LDC = 0, 1, 2, 3
 LJ_PAIRS_STATIC_MAX_ENTRIES = 524288  # static scratch of ljmd_get_pairs_static, in list entries
 LJ_ST_NONFINITE, LJ_ST_LIST_OVERFLOW, LJ_ST_TIMEOUT, LJ_ST_CELL_RANGE = 1, 2, 4, 8
 
@@ -43,7 +44,8 @@ class ljmd_stats(ctypes.Structure):
                 ("list_entries", ctypes.c_int64), ("cells_per_side", ctypes.c_int64), ("box", ctypes.c_double),
                 ("mean_lifetime", ctypes.c_double), ("max_displacement", ctypes.c_double),
                 ("status_word", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("ldc_checks", ctypes.c_int64), ("ldc_kept", ctypes.c_int64),
+                ("validity", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class ljmd_profile(ctypes.Structure):
@@ -79,6 +81,7 @@ _SIGS = {
     "ljmd_get_pairs": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_get_pairs_static": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_hvp": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
+    "ljmd_set_validity": (ctypes.c_int, [_P, _I32, _I32]),
     "ljmd_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ljmd_params), _I32, _P, _P, _P]),
     "ljmd_batch_destroy": (None, [_P]),
     "ljmd_batch_set_state": (ctypes.c_int, [_P, _P, _P, _I32]),
@@ -360,6 +363,10 @@ class System:
     def pairs_static(self, cap=None):
         """(pairs, npairs) from the allocation-free export; pairs holds the first min(cap, npairs)."""
         return ljmd_get_pairs_static(self.h, cap)
+
+    def set_validity(self, mode, max_ld=0):
+        """List-validity rule (LJ_VALID_*) and N_l of the large displacement check."""
+        _chk(load().ljmd_set_validity(self.h, int(mode), int(max_ld)), "ljmd_set_validity")
 
     def hvp(self, w):
         """(H w, (w.dF/deps, w.dF/dsigma, dPE/deps, dPE/dsigma)) at the current positions, id order."""

@@ -284,3 +284,44 @@ def test_invalid_box_rejected():
         with pytest.raises(ljmd.LjmdError) as e:
             s.set_state(np.zeros((4, 3)), None, 6.9)  # < 2 (r_s + margin) = 7
         assert e.value.code == ljmd.LJ_EINVAL
+
+
+# ------------------------------------------------------------------------------------ list validity rules
+
+@pytest.mark.parametrize("mode", [ljmd.LJ_VALID_HALF_MARGIN, ljmd.LJ_VALID_DUTC, ljmd.LJ_VALID_DUTC_LDC,
+                                  ljmd.LJ_VALID_HALF_MARGIN_LDC])
+def test_validity_rules_never_miss_a_pair(mode):
+    """Under every rule (Sec. 2.3, Alg. 2), after every step each pair within r_c is listed."""
+    x, v, L = thermal(6, 0.6, 1.5, 6)
+    rc, margin = 2.5, 0.3
+    with _system(ljmd.LJ_MIXED, cutoff=rc, margin=margin) as s:
+        s.set_validity(mode, 256)
+        s.set_state(x, v, L)
+        for _ in range(60):
+            s.step(0.005, 1)
+            gx, _, _, _ = s.get_state()
+            listed = _pairs_set(s.pairs())
+            assert _pairs_set(_brute_pairs_numpy(gx, L, rc)) <= listed
+        st = s.stats()
+    assert st["validity"] == mode and st["status_word"] == 0 and st["rebuilds"] >= 2
+
+
+def test_ldc_extends_list_lifetime_with_same_trajectory():
+    """The large displacement check keeps lists the margin/2 rule would drop (fewer rebuilds, Alg. 2)
+    and the trajectory is the same to FP32 summation order; DUTC alone rebuilds at least as often
+    as the displacement rule."""
+    x, v, L = thermal(8, 0.5, 1.0, 12)
+    out = {}
+    for mode in (ljmd.LJ_VALID_HALF_MARGIN, ljmd.LJ_VALID_HALF_MARGIN_LDC, ljmd.LJ_VALID_DUTC, ljmd.LJ_VALID_DUTC_LDC):
+        with _system(ljmd.LJ_MIXED, cutoff=2.5, margin=0.5) as s:
+            s.set_validity(mode, 4096)
+            s.set_state(x, v, L)
+            s.step(0.005, 150)
+            gx, _, _, img = s.get_state()
+            out[mode] = (s.stats(), gx + img * L)
+    base = out[ljmd.LJ_VALID_HALF_MARGIN]
+    ldc = out[ljmd.LJ_VALID_HALF_MARGIN_LDC]
+    assert ldc[0]["rebuilds"] < base[0]["rebuilds"] and ldc[0]["ldc_kept"] > 0
+    assert np.abs(ldc[1] - base[1]).max() < 1e-4
+    assert out[ljmd.LJ_VALID_DUTC][0]["rebuilds"] >= base[0]["rebuilds"]
+    assert out[ljmd.LJ_VALID_DUTC_LDC][0]["rebuilds"] <= out[ljmd.LJ_VALID_DUTC][0]["rebuilds"]
