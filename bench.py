@@ -276,6 +276,7 @@ def run_ours(args, wl, world, rank, local):
         s2.close()
 
     batched = None if args.no_batch else run_batched(args, stream, world, rank, barrier)
+    replica = None if args.no_replica else run_paper_replica(stream)
     adjoint = None if args.no_adjoint else run_adjoint(stream)
 
     out = {
@@ -295,6 +296,7 @@ def run_ours(args, wl, world, rank, local):
                  "mean_lifetime_steps": args.steps / max(st1["rebuilds"] - st0["rebuilds"], 1)},
         "energies_final": {"pe_per_particle": pe / N, "ke_per_particle": ke / N, "virial": vir},
         "batched": batched,
+        "paper_replica": replica,
         "adjoint": adjoint,
         "pair_interactions_per_s": entries * args.steps * world / (ms * 1e-3),
     }
@@ -304,6 +306,39 @@ def run_ours(args, wl, world, rank, local):
         dist.barrier()
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def run_paper_replica(stream):
+    """The paper's benchmark configuration on one GPU (Sec. 4.4): 500,000 particles (FCC 50^3 x 4) in
+    a 100^3 box (rho = 0.5), r_c = 2.5, r_s = 2.8, dt = 0.001, |v| = 0.9 in random directions,
+    150 warm-up steps and 1000 timed steps; MUPS = N steps / (1e6 s).  The list rule is the margin/2
+    displacement rule and, beside it, the large displacement check of Alg. 2."""
+    import torch
+    from paper_1012_2677_gb300 import ljmd, synth
+    out = {}
+    for name, mode in (("half_margin", ljmd.LJ_VALID_HALF_MARGIN), ("half_margin_ldc", ljmd.LJ_VALID_HALF_MARGIN_LDC)):
+        with ljmd.System(cutoff=2.5, margin=0.3, precision=ljmd.LJ_MIXED, energy_every=0, stream=stream) as s:
+            s.init_lattice(50, 0.5, 1.0, 6)
+            x, _, _, _ = s.get_state()
+            v = 0.9 * synth.unit_vectors(len(x), 6)
+            s.set_validity(mode, 16384)
+            s.set_state(x, v, 100.0)
+            s.step(0.001, 150)
+            torch.cuda.synchronize()
+            st0 = s.stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(0.001, 1000)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st1 = s.stats()
+        nr = st1["rebuilds"] - st0["rebuilds"]
+        out[name] = {"mups": len(x) * 1000 / (ms * 1e-3) / 1e6, "ms_per_step": ms / 1000, "rebuilds": nr,
+                     "mean_lifetime_steps": 1000 / max(nr, 1)}
+    out["paper_context"] = {"mups_per_xeon_x5570_core": 2.73, "mups_per_power6_process": 1.65,
+                            "lifetime_steps_power6": 51.2, "note": "FP64 CPU figures of Tables 2-3 and Sec. 5.2"}
+    return out
 
 
 def run_batched(args, stream, world, rank, barrier):
@@ -433,6 +468,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-replica", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--skip-cpu", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
       F[2] = f.z;
     }
     double xs[3];
-    float ke_i = 0.0f;
+    float ke_i = 0.0f, vd2 = 0.0f;
     double ke_d = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
         }
       }
       if (kk != 0.0) vk = fma(kk, F[k], vk);
+      vd2 = fmaf((float)vk, (float)vk, vd2);
       double xk = x[k * N + i];
       if (a.dt != 0.0) xk = fma(a.dt, vk, xk);
       v[k * N + i] = vk;
@@ -62,8 +63,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
     ke_acc += MIXED ? 0.5 * (double)ke_i : 0.5 * ke_d;
     if (a.shadow) {
       // speed of the drift (the velocity that moved the particle this step), for the DUTC rule
-      const float vx = (float)v[i], vy = (float)v[N + i], vz = (float)v[2 * N + i];
-      v2max = fmaxf(v2max, fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+      v2max = fmaxf(v2max, vd2);
       if (MIXED) {
         float4 h, l;
         split_hi_lo(xs[0], h.x, l.x);
@@ -90,12 +90,25 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
   __shared__ float shf[32];
   const double tk = block_sum(ke_acc, sh);
   if (threadIdx.x == 0 && a.ke) ke_part[blockIdx.x] = tk;
-  if (a.shadow) {
-    const float m = block_max(d2max, shf);
-    if (threadIdx.x == 0) atomicMax(dmax_bits, __float_as_uint(m));
+  if (a.shadow) {  // both maxima in one pass over the warps
+    __shared__ float shv[32];
+    d2max = warp_max(d2max);
+    v2max = warp_max(v2max);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
-    const float mv = block_max(v2max, shf);
-    if (threadIdx.x == 0) atomicMax(dmax_bits + 1, __float_as_uint(mv));
+    if (l == 0) {
+      shf[w] = d2max;
+      shv[w] = v2max;
+    }
+    __syncthreads();
+    if (w == 0) {
+      const bool in = l < (int)(blockDim.x >> 5);
+      const float md = warp_max(in ? shf[l] : 0.0f), mv = warp_max(in ? shv[l] : 0.0f);
+      if (l == 0) {
+        atomicMax(dmax_bits, __float_as_uint(md));
+        atomicMax(dmax_bits + 1, __float_as_uint(mv));
+      }
+    }
   }
 }
 

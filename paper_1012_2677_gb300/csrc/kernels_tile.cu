@@ -417,7 +417,7 @@ __device__ __forceinline__ void replica_view(const ReplicaGeo& rg, TileArgs& ta,
 // Shared-memory layout of the thread-per-key list kernel (mixed form, staged tiles).
 constexpr int kListSplit = 2;  // candidate sub-ranges per neighbour column (work balance)
 constexpr int kListItems = 9 * kListSplit;     // work items per 32-key chunk
-constexpr size_t kListSmemTarget = 64 * 1024;  // 3 CTAs per SM
+constexpr size_t kListSmemTarget = 48 * 1024;  // 4 CTAs per SM for typical liquids
 struct KeyListLayout {
   size_t pos;    // hi float4 [max_staged]
   size_t gid;    // int [max_staged]
@@ -447,7 +447,7 @@ __host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs
   o += align16(((size_t)K.nch * kListItems + 1) * 4);
   // every item needs ceil(len / 32) words; the items of a chunk cover at most all staged slots
   int mw = K.nch * ((int)(ms / 32) + kListItems + 1);
-  K.mask_words = mw < 192 ? mw : 192;
+  K.mask_words = mw < 128 ? mw : 128;
   K.mask = o;
   o += (size_t)K.mask_words * 32 * 4;
   K.seg = o;
@@ -759,6 +759,51 @@ __device__ __forceinline__ void key_item_from_mask(const TileShared& S, int Tp, 
   }
 }
 
+// One work unit of the list construction: 32 consecutive staged candidates [j0, j0 + len) against
+// the lane's key l (sorted index gi); bit b set iff j0 + b is listed for the key.  Same tests as
+// key_item_bits.
+template <bool HALF>
+__device__ __forceinline__ uint32_t unit_bits(const float4* sh_pos, const int* sh_gid, const double* __restrict__ x,
+                                              int64_t N, const Geom& g, const ListBand& band, int j0, int len, int l,
+                                              int gi, bool valid) {
+  const float4 pi = sh_pos[l];
+  uint32_t bits = 0, mbits = 0;
+#pragma unroll
+  for (int u = 0; u < 32; u += 8) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const float4 pj = sh_pos[j0 + u + v];  // same address in every lane: one broadcast
+      const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;  // exact
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (r2 < band.lo) bits |= 1u << (u + v);
+      if (r2 < band.hi) mbits |= 1u << (u + v);
+    }
+  }
+  const uint32_t tail = len >= 32 ? 0xffffffffu : ((1u << len) - 1u);
+  bits &= tail;
+  mbits &= tail & ~bits;
+  if (__any_sync(0xffffffffu, mbits != 0u)) {
+    while (mbits) {
+      const int bit = __ffs(mbits) - 1;
+      mbits &= mbits - 1;
+      if (pair_in_exact(x, N, gi, sh_gid[j0 + bit], g, band.rs2)) bits |= 1u << bit;
+    }
+  }
+  if (l >= j0 && l < j0 + 32) bits &= ~(1u << (l - j0));  // the key itself
+  if (HALF) {
+    uint32_t m = bits;
+    while (m) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1;
+      if (sh_gid[j0 + bit] <= gi) bits &= ~(1u << bit);
+    }
+  }
+  return valid ? bits : 0u;
+}
+
+constexpr int kUnitChunks = 24;   // chunks per tile in the unit path
+constexpr int kUnitMax = 160;     // work units per tile in the unit path
+
 // Pair-list construction, mixed form, staged tiles: one thread per key particle.  Work items
 // are (32-key chunk, neighbour column); a first pass counts each key's partners per column, a
 // prefix gives every key its row and every column its place in the row (columns in order,
@@ -780,6 +825,9 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   __shared__ __align__(8) uint64_t bar;
   __shared__ unsigned int s_base, s_total, s_padded;
   __shared__ int s_ok;
+  __shared__ int u_ck0[kUnitChunks + 1], u_ub[kUnitChunks + 1], u_info[kUnitMax];
+  __shared__ unsigned char u_chunk[kUnitMax];
+  __shared__ int s_nchunk, s_nunit;
   const KeyListLayout K = key_list_layout(ta_in);
   TileLayout L;  // the staging helpers' view: positions and sorted indices
   L.pos = K.pos;
@@ -828,6 +876,166 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       __syncthreads();
       continue;
     }
+    // ---- unit path: chunks of whole own cells (at most 32 keys), one 32-candidate word per unit
+    if (threadIdx.x == 0) {
+      const int base4 = 4 * S.ncol;
+      int nc = 0, kpos = 0, acc = 0;
+      bool ok = true;
+      u_ck0[0] = 0;
+      for (int m = 1; m <= ti.Tp && ok; ++m) {
+        int nm = S.offq[base4 + m + 1] - S.offq[base4 + m];
+        if (acc + nm <= 32) {
+          acc += nm;
+          continue;
+        }
+        if (acc > 0) {
+          kpos += acc;
+          if (nc + 1 > kUnitChunks) ok = false;
+          else u_ck0[++nc] = kpos;
+          acc = 0;
+        }
+        while (nm > 32 && ok) {
+          kpos += 32;
+          if (nc + 1 > kUnitChunks) ok = false;
+          else u_ck0[++nc] = kpos;
+          nm -= 32;
+        }
+        acc = nm;
+      }
+      if (ok && acc > 0) {
+        kpos += acc;
+        if (nc + 1 > kUnitChunks) ok = false;
+        else u_ck0[++nc] = kpos;
+      }
+      s_nchunk = ok ? nc : -1;
+    }
+    __syncwarp();
+    if (warp == 0) {
+      // units in (chunk, column, word) order: lane p takes the pairs (c, k) = (p / 9, p % 9), ...
+      const int nc = s_nchunk;
+      const int ucap = min(kUnitMax, K.mask_words);
+      int run = 0;
+      bool ok = nc >= 0;
+      for (int base = 0; ok && base < nc * 9; base += 32) {
+        const int pk = base + lane;
+        int r0 = 0, r1 = 0;
+        if (pk < nc * 9) {
+          const int c = pk / 9, k = pk - 9 * (pk / 9);
+          const int ma = own_cell(S, S.own0 + u_ck0[c], ti.Tp), mb = own_cell(S, S.own0 + u_ck0[c + 1] - 1, ti.Tp);
+          r0 = S.offq[k * S.ncol + ma - 1];
+          r1 = S.offq[k * S.ncol + mb + 2];
+        }
+        const int nw = (r1 - r0 + 31) >> 5;
+        int inc = nw;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, d);
+          if (lane >= d) inc += y;
+        }
+        const int first = run + inc - nw;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+        if (run > ucap) {
+          ok = false;
+          break;
+        }
+        if (pk < nc * 9) {
+          const int c = pk / 9;
+          if (pk % 9 == 0) u_ub[c] = first;
+          for (int w = 0; w < nw; ++w) {
+            const int j0 = r0 + 32 * w;
+            u_info[first + w] = j0 | (min(32, r1 - j0) << 16);
+            u_chunk[first + w] = (unsigned char)c;
+          }
+        }
+      }
+      if (lane == 0) {
+        if (ok && nc >= 0) u_ub[nc] = run;
+        s_nunit = ok ? run : -1;
+        if (!ok) s_nchunk = -1;
+      }
+    }
+    __syncthreads();
+    if (s_nchunk >= 0) {
+      const int nc = s_nchunk, nu = s_nunit;
+      // phase A: the bits of every unit
+      for (int u = warp; u < nu; u += kWarps) {
+        const int c = u_chunk[u];
+        const int o = u_ck0[c] + lane;
+        const bool valid = o < u_ck0[c + 1];
+        const int l = S.own0 + (valid ? o : u_ck0[c + 1] - 1);
+        s_mask[u * 32 + lane] = unit_bits<HALF>(sh_pos, sh_gid, x, N, g, band, u_info[u] & 0xffff, u_info[u] >> 16,
+                                                l, sh_gid[l], valid);
+      }
+      __syncthreads();
+      // phase B: row lengths (one warp per chunk)
+      for (int c = warp; c < nc; c += kWarps) {
+        int len = 0;
+        for (int u = u_ub[c]; u < u_ub[c + 1]; ++u) len += __popc(s_mask[u * 32 + lane]);
+        const int o = u_ck0[c] + lane;
+        if (o < u_ck0[c + 1]) s_len[o] = len;
+      }
+      __syncthreads();
+      // phase C: exclusive prefix of the rows, one atomic reserves the tile's padded segment
+      if (warp == 0) {
+        unsigned run = 0;
+        for (int base = 0; base < n_own; base += 32) {
+          const int o = base + lane;
+          const unsigned v = o < n_own ? (unsigned)s_len[o] : 0u;
+          unsigned inc = v;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += y;
+          }
+          if (o < n_own) s_kst[o] = (int)(run + inc - v);
+          run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) {
+          const unsigned padded = (run + 7u) & ~7u;
+          const unsigned long long b = atomicAdd(counter, (unsigned long long)padded);
+          atomicAdd(counter + 1, (unsigned long long)run);
+          const bool fits = b + padded <= cap;
+          s_base = (unsigned)b;
+          s_total = run;
+          s_padded = padded;
+          s_ok = fits;
+          tile_list[t] = fits ? make_uint2((unsigned)b, padded) : make_uint2(0u, 0u);
+          atomicMax(max_list, padded);
+          if (BATCHED && !fits) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+        }
+      }
+      __syncthreads();
+      const bool ok = s_ok != 0;
+      for (int o = threadIdx.x; o < n_own; o += blockDim.x)
+        rows[S.gown0 + o] = ok ? make_uint2(s_base + (unsigned)s_kst[o], (unsigned)s_len[o]) : make_uint2(0u, 0u);
+      if (ok) {
+        const bool staged = s_padded <= (unsigned)K.seg_cap;
+        uint16_t* dst = staged ? s_seg : ent + s_base;
+        // phase D: entries in row order (units of a chunk in column order), one warp per chunk
+        for (int c = warp; c < nc; c += kWarps) {
+          const int o = u_ck0[c] + lane;
+          int p = o < u_ck0[c + 1] ? s_kst[o] : 0;
+          for (int u = u_ub[c]; u < u_ub[c + 1]; ++u) {
+            uint32_t m = s_mask[u * 32 + lane];
+            const int j0 = u_info[u] & 0xffff;
+            while (m) {
+              const int bit = __ffs(m) - 1;
+              m &= m - 1;
+              dst[p++] = (uint16_t)(j0 + bit);
+            }
+          }
+        }
+        if (staged) {
+          __syncthreads();
+          const uint4* src = (const uint4*)s_seg;
+          uint4* out = (uint4*)(ent + s_base);
+          for (unsigned w = threadIdx.x; w < s_padded / 8u; w += blockDim.x) out[w] = src[w];
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    // ---- item path (tiles whose chunk or unit tables do not fit)
     const int nch = (n_own + 31) / 32;
     constexpr int kItems = kListItems;
     // first mask word of every item (warp 0); the bits are kept only if the tile's words fit
@@ -1865,24 +2073,41 @@ __global__ void k_ldc_collect(const double* __restrict__ x, const double* __rest
 }
 
 // Every pair of L_D: unlisted (the list's own exact FP64 test on the build positions says r >= r_s)
-// and now closer than r_c (FP64, with a relative safety of 1e-6) raises *flag.
-__global__ void k_ldc_pairs(const double* __restrict__ x, const double* __restrict__ xref, int64_t N, Geom g,
-                            const int32_t* __restrict__ list, int m, double rs2, double rc2, int* __restrict__ flag) {
-  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x) {
-    const int i = list[a];
-    for (int b = a + 1; b < m; ++b) {
-      const int j = list[b];
-      double d2 = 0.0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        double t = x[k * N + j] - x[k * N + i];
-        if (t > g.half_L) t -= g.L;
-        else if (t < -g.half_L) t += g.L;
-        d2 += t * t;
-      }
-      if (d2 < rc2 * (1.0 + 1e-6) && !pair_in_exact(xref, N, i, j, g, rs2)) atomicOr(flag, 1);
-    }
+// and now closer than r_c (FP64, with a relative safety of 1e-6) raises *flag.  Block (x, y) takes
+// the 16 members 16 x .. 16 x + 15 against the 256 members 256 y + threadIdx.x; pairs a < b only.
+constexpr int kLdcRows = 16;
+__global__ void __launch_bounds__(256) k_ldc_pairs(const double* __restrict__ x, const double* __restrict__ xref,
+                                                   int64_t N, Geom g, const int32_t* __restrict__ list, int m,
+                                                   double rs2, double rc2, int* __restrict__ flag) {
+  __shared__ double sa[kLdcRows][3];
+  __shared__ int ia[kLdcRows];
+  const int a0 = blockIdx.x * kLdcRows;
+  if (threadIdx.x < kLdcRows) {
+    const int a = a0 + threadIdx.x;
+    const int i = a < m ? list[a] : 0;
+    ia[threadIdx.x] = i;
+    for (int k = 0; k < 3; ++k) sa[threadIdx.x][k] = x[k * N + i];
   }
+  __syncthreads();
+  const int b = blockIdx.y * blockDim.x + threadIdx.x;
+  if (b >= m || b <= a0) return;  // some a < b remains only if b > a0
+  const int j = list[b];
+  const double xj = x[j], yj = x[N + j], zj = x[2 * N + j];
+  bool hit = false;
+  for (int r = 0; r < kLdcRows; ++r) {
+    const int a = a0 + r;
+    if (a >= m || a >= b) break;
+    double t[3] = {xj - sa[r][0], yj - sa[r][1], zj - sa[r][2]};
+    double d2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (t[k] > g.half_L) t[k] -= g.L;
+      else if (t[k] < -g.half_L) t[k] += g.L;
+      d2 += t[k] * t[k];
+    }
+    if (d2 < rc2 * (1.0 + 1e-6) && !pair_in_exact(xref, N, ia[r], j, g, rs2)) hit = true;
+  }
+  if (hit) atomicOr(flag, 1);
 }
 
 void launch_ldc_collect(const double* x, const double* xref, int64_t N, double th2, int32_t* list, unsigned int cap,
@@ -1894,7 +2119,7 @@ void launch_ldc_collect(const double* x, const double* xref, int64_t N, double t
 }
 void launch_ldc_pairs(const double* x, const double* xref, int64_t N, Geom g, const int32_t* list, int m, double rs2,
                       double rc2, int* flag, cudaStream_t s) {
-  const int b = (m + 127) / 128;
-  k_ldc_pairs<<<b < 1 ? 1 : b, 128, 0, s>>>(x, xref, N, g, list, m, rs2, rc2, flag);
+  dim3 grid((unsigned)((m + kLdcRows - 1) / kLdcRows), (unsigned)((m + 255) / 256));
+  k_ldc_pairs<<<grid, 256, 0, s>>>(x, xref, N, g, list, m, rs2, rc2, flag);
 }
 }  // namespace ljmd

@@ -81,7 +81,7 @@ struct ljmd_sys {
   int64_t launches = 0;
   // list validity rule (Sec. 2.3 / Alg. 2)
   int valid_mode = LJ_VALID_HALF_MARGIN;
-  int max_ld = 1024;          // N_l of the LDC method
+  int max_ld = 4096;          // N_l of the LDC method
   double dutc_buffer = 0.0;   // buffer_length of the DUTC method
   double last_vmax = 0.0;     // largest drift speed of the last step
   double* xref64 = nullptr;   // FP64 positions the list was built from (LDC)
