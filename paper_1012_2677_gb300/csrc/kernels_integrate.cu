@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
         }
       }
       if (kk != 0.0) vk = fma(kk, F[k], vk);
-      vd2 = fmaf((float)vk, (float)vk, vd2);
+      if (a.speed) vd2 = fmaf((float)vk, (float)vk, vd2);
       double xk = x[k * N + i];
       if (a.dt != 0.0) xk = fma(a.dt, vk, xk);
       v[k * N + i] = vk;
@@ -90,7 +90,10 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
   __shared__ float shf[32];
   const double tk = block_sum(ke_acc, sh);
   if (threadIdx.x == 0 && a.ke) ke_part[blockIdx.x] = tk;
-  if (a.shadow) {  // both maxima in one pass over the warps
+  if (a.shadow && !a.speed) {
+    const float m = block_max(d2max, shf);
+    if (threadIdx.x == 0) atomicMax(dmax_bits, __float_as_uint(m));
+  } else if (a.shadow) {  // both maxima in one pass over the warps
     __shared__ float shv[32];
     d2max = warp_max(d2max);
     v2max = warp_max(v2max);

@@ -874,7 +874,8 @@ int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
   cudaStream_t st = sys->st;
   for (int64_t s = 0; s < nsteps; ++s) {
     const bool rec = sys->pe_step == sys->steps && want_energy(sys->steps);
-    IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, rec ? 1 : 0, 1};
+    const int dutc = sys->valid_mode == LJ_VALID_DUTC || sys->valid_mode == LJ_VALID_DUTC_LDC;
+    IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, rec ? 1 : 0, 1, dutc};
     CK(cudaMemsetAsync(sys->d_dmax, 0, 8, st));
     const int nb = integrate(sys, a);
     CKL();

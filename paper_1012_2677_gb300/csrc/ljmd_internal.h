@@ -158,6 +158,7 @@ struct IntegrateArgs {
   double dt;       // drift length (0 = no drift)
   int ke;          // accumulate the kinetic energy of the full-step velocity
   int shadow;      // rewrite the force kernel's position copy after the drift
+  int speed;       // also reduce the largest drift speed (DUTC rules)
 };
 // Returns the number of blocks used for KE partials.  With a.shadow, dmax_bits[0] and [1] receive
 // (atomic max) the float bits of the largest squared displacement since the list build and of the
