@@ -395,7 +395,7 @@ int ljmd_batch_autotune(ljmd_batch* b, int32_t trials, int32_t* best_tile, int32
  *    |L_D| <= max_ld (N_l) and no pair of L_D is unlisted yet closer than r_c now.  Rerun every
  *    step until it fails.
  *  LJ_VALID_HALF_MARGIN_LDC: the margin/2 rule first, then the LDC as above.
- * max_ld: N_l (0 keeps the current, default 1024).  A new rule takes effect at the next list
+ * max_ld: N_l (0 keeps the current, default 4096).  A new rule takes effect at the next list
  * construction (forced at the next force evaluation).  Errors: LJ_EINVAL.
  */
 int ljmd_set_validity(ljmd_sys* sys, int32_t mode, int32_t max_ld);
