@@ -458,7 +458,7 @@ __host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs
 }
 
 size_t list_smem_bytes(const TileArgs& ta, int precision) {
-  if (precision == LJ_MIXED && !ta.whole) return key_list_layout(ta).total;
+  if (!ta.whole) return key_list_layout(ta).total;  // both forms: the FP32 filter on the hi copies
   return tile_layout(ta, precision == LJ_MIXED, false).total;
 }
 
@@ -1822,9 +1822,10 @@ static int per_sm_for(size_t smem_bytes) {
   return k < 1 ? 1 : (k > 4 ? 4 : k);
 }
 
-void launch_list_tile(int precision, int half, const void* pos, const double* x, const uint32_t* cs, int64_t N,
-                      Geom g, TileArgs ta, ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
-                      unsigned long long* counter, unsigned int* max_list, int32_t* status, cudaStream_t s) {
+void launch_list_tile(int precision, int half, const void* pos, const float4* hi, const double* x, const uint32_t* cs,
+                      int64_t N, Geom g, TileArgs ta, ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent,
+                      uint64_t cap, unsigned long long* counter, unsigned int* max_list, int32_t* status,
+                      cudaStream_t s) {
   const size_t sm = list_smem_bytes(ta, precision);
   const int grid = tile_grid(ta, per_sm_for(sm));
 #define LJ_LIST_LAUNCH(M, H, W)                                                                                 \
@@ -1842,23 +1843,14 @@ void launch_list_tile(int precision, int half, const void* pos, const double* x,
       if (half) LJ_LIST_LAUNCH(false, true, true);
       else LJ_LIST_LAUNCH(false, false, true);
     }
+  } else if (half) {  // tiles, either form: one thread per key on the hi copies (the list is the same)
+    set_smem(k_list_keys<true, false>, sm);
+    k_list_keys<true, false><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
+                                                            counter, max_list, status, nullptr, 0, nullptr);
   } else {
-    if (mixed) {
-      if (half) {
-        set_smem(k_list_keys<true, false>, sm);
-        k_list_keys<true, false><<<grid, kTileThreads, sm, s>>>((const float4*)pos, x, cs, N, g, ta, band, rows,
-                                                                tile_list, ent, cap, counter, max_list, status,
-                                                                nullptr, 0, nullptr);
-      } else {
-        set_smem(k_list_keys<false, false>, sm);
-        k_list_keys<false, false><<<grid, kTileThreads, sm, s>>>((const float4*)pos, x, cs, N, g, ta, band, rows,
-                                                                 tile_list, ent, cap, counter, max_list, status,
-                                                                 nullptr, 0, nullptr);
-      }
-    } else {
-      if (half) LJ_LIST_LAUNCH(false, true, false);
-      else LJ_LIST_LAUNCH(false, false, false);
-    }
+    set_smem(k_list_keys<false, false>, sm);
+    k_list_keys<false, false><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
+                                                             counter, max_list, status, nullptr, 0, nullptr);
   }
 #undef LJ_LIST_LAUNCH
 }

@@ -476,7 +476,7 @@ static int rebuild(ljmd_sys* s) {
       }
       CK(cudaMemsetAsync(s->d_total64, 0, 2 * sizeof(unsigned long long), st));
       CK(cudaMemsetAsync(s->d_sizes + 3, 0, sizeof(unsigned int), st));
-      launch_list_tile(s->precision, half, force_pos(s), s->x, s->cell_start, N, s->g, s->ta, s->band, s->rows,
+      launch_list_tile(s->precision, half, force_pos(s), s->hi, s->x, s->cell_start, N, s->g, s->ta, s->band, s->rows,
                        s->tile_list, s->ent, (uint64_t)s->ent_cap, s->d_total64, s->d_sizes + 3, s->d_status, st);
       s->launches += 1;
       CKL();

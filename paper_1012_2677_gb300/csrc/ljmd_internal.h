@@ -134,9 +134,10 @@ size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf, int half);
 void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStream_t s);
 void launch_tile_sizes(const uint32_t* cs, TileArgs ta, unsigned int* out, cudaStream_t s);
 // counter[0] += padded tile segments (reservations), counter[1] += actual entries
-void launch_list_tile(int precision, int half, const void* pos, const double* x, const uint32_t* cs, int64_t N,
-                      Geom g, TileArgs ta, ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
-                      unsigned long long* counter, unsigned int* max_list, int32_t* status, cudaStream_t s);
+void launch_list_tile(int precision, int half, const void* pos, const float4* hi, const double* x, const uint32_t* cs,
+                      int64_t N, Geom g, TileArgs ta, ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent,
+                      uint64_t cap, unsigned long long* counter, unsigned int* max_list, int32_t* status,
+                      cudaStream_t s);
 // Returns the number of blocks (energy partials written to part[2 b], part[2 b + 1]).
 int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const float4* lo,
                       const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
