@@ -53,6 +53,26 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(x, dist=None, device="cuda"):
+    """Largest x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
+def replica_seed(base, rank):
+    """Each rank advances an independent replica (no data-path exchange between ranks)."""
+    return base + 1000 * rank
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -157,7 +177,7 @@ def run_ours(args, wl, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
-    seed = wl["seed"] + 1000 * rank  # independent replica per rank
+    seed = replica_seed(wl["seed"], rank)  # independent replica per rank
 
     def barrier():
         if dist is not None:
@@ -187,11 +207,8 @@ def run_ours(args, wl, world, rank, local):
     st1 = s.stats()
     pe, ke, vir = s.energies()
     s.set_profiling(False)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * args.steps * world / (ms * 1e-3)
+    ms = reduce_max(ms, dist)
+    value = job_value(N * args.steps, world, ms * 1e-3)
 
     # dominant kernel: the force kernel (CUDA events around each launch on the library's stream)
     f_ms = prof["force_ms"] / max(prof["force_launches"], 1)
@@ -266,11 +283,8 @@ def run_ours(args, wl, world, rank, local):
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         barrier()
-        if dist is not None:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": N * args.steps * world / t_e2e, "unit": UNIT,
+        t_e2e = reduce_max(t_e2e, dist)
+        e2e = {"value": job_value(N * args.steps, world, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": 2 * 24 * N / args.steps, "d2h_bytes_per_step": (2 * 24 * N + 24) / args.steps,
                "note": "set_state from pinned host + K steps + get_state/energies to host, per K-step job"}
         s2.close()
