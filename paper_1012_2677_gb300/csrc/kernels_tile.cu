@@ -141,7 +141,7 @@ struct TileLayout {
   size_t lo;     // MIXED: lo float4 [ms] (force only)
   size_t gid;    // int [ms]
   size_t rows;   // uint2 [max_own + 2] (force only)
-  size_t ent;    // uint16 [max_list] (force only)
+  size_t ent;    // uint16 [list_cap] (force only)
   size_t cnt;    // int [max_own] (list only), then pre [max_own], then masks [max_own * max_chunks]
   size_t total;
 };
@@ -164,7 +164,7 @@ __host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, b
   if (force) {
     o += align16(8 * ((size_t)ta.max_own + 2));
     L.ent = o;
-    if (!ta.whole) o += align16(2 * (size_t)ta.max_list);
+    if (!ta.whole) o += align16(2 * (size_t)ta.list_cap);
   } else {
     o += align16(8 * (size_t)ta.max_own + 4 * (size_t)ta.max_own * ta.max_chunks);
   }
@@ -190,7 +190,7 @@ __device__ __forceinline__ void stage_issue(const TileInfo& ti, const TileArgs& 
     r0 = S.gown0 & ~1;
     r1 = (S.gown0 + n_own + 1) & ~1;
     if (n_own > 0) bytes += 8u * (unsigned)(r1 - r0);
-    bytes += 2u * S.list_len;
+    if (S.list_len <= (unsigned)ta.list_cap) bytes += 2u * S.list_len;
   }
   if (lane == 0) {
     fence_proxy_async_smem();
@@ -224,7 +224,8 @@ __device__ __forceinline__ void stage_issue(const TileInfo& ti, const TileArgs& 
     }
   } else if (FORCE && lane == 9) {
     if (n_own > 0) bulk_g2s(smem + L.rows, rows + r0, 8u * (unsigned)(r1 - r0), bar);
-    if (S.list_len > 0) bulk_g2s(smem + L.ent, ent + S.list_base, 2u * S.list_len, bar);
+    if (S.list_len > 0 && S.list_len <= (unsigned)ta.list_cap)
+      bulk_g2s(smem + L.ent, ent + S.list_base, 2u * S.list_len, bar);
     S.row_off = S.gown0 - r0;
   }
 }
@@ -1211,11 +1212,12 @@ __device__ __forceinline__ void pair_mixed(const float4& hi_i, const float4& lo_
 
 // Forces of the own particles of one staged tile (buffer `buf`); group `grp` of LANES threads per
 // key particle, lanes striding over its row.
-template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE>
+template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST>
 __device__ __forceinline__ void force_tile_compute(const TileShared& S, const unsigned char* buf, const TileLayout& L,
                                                    const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
                                                    const LJConst& c, const Geom& g, void* __restrict__ fout,
-                                                   int32_t* __restrict__ status, double& pe_acc, double& vir_acc) {
+                                                   int32_t* __restrict__ status, double& pe_acc, double& vir_acc,
+                                                   int list_cap) {
   const void* sh_pos = buf + L.pos;
   const float4* sh_lo = (const float4*)(buf + L.lo);
   const int* sh_gid = (const int*)(buf + L.gid);
@@ -1236,19 +1238,18 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
       const int l = S.own0 + o;
       gi = S.gown0 + o;
       uint2 row;
-      const uint16_t* el;
       if (WHOLE) {
         row = rows[gi];
-        el = ent;
       } else {
         row = s_rows[S.row_off + o];
         row.x -= S.list_base;
-        el = s_ent;
         if (row.x + row.y > S.list_len) {  // inconsistent row: record and skip
           if (lane == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
           row.y = 0;
         }
       }
+      // the row's pairs; one instance per memory space of the list (shared: staged segment)
+      auto row_pairs = [&](const uint16_t* __restrict__ el) {
       if (MIXED) {
         const float4 hi_i = ((const float4*)sh_pos)[l], lo_i = sh_lo[l];
         float4* F = (float4*)fout;
@@ -1307,6 +1308,10 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
           }
         }
       }
+      };
+      if (WHOLE) row_pairs(ent);
+      else if (!LONGLIST || S.list_len <= (unsigned)list_cap) row_pairs(s_ent);
+      else row_pairs(ent + S.list_base);  // a long segment stays in HBM
     }
     if (MIXED) {
       float fx = gsum<LANES>(a0.fx + a1.fx);
@@ -1372,7 +1377,7 @@ __device__ __forceinline__ bool force_tile_prepare(const TileInfo& ti, int64_t t
 // so the copy latency overlaps the pair arithmetic; with nbuf = 1 the tiles are staged one after
 // the other and the overlap comes from the other CTAs of the SM.  Energies: per-thread FP64
 // sums -> one partial per block.
-template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE>
+template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST>
 __global__ void __launch_bounds__(kTileThreads, 4)
     k_force_tile(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
                  int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows,
@@ -1388,8 +1393,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     if (blockIdx.x == 0) {
       stage_whole<MIXED, true>(N, pos, lo, SS[0], smem, L);
       __syncthreads();
-      force_tile_compute<MIXED, LANES, HALF, ENERGY, true>(SS[0], smem, L, rows, ent, c, g, fout, status, pe_acc,
-                                                           vir_acc);
+      force_tile_compute<MIXED, LANES, HALF, ENERGY, true, false>(SS[0], smem, L, rows, ent, c, g, fout, status, pe_acc,
+                                                           vir_acc, ta.list_cap);
     }
   } else {
     const bool pipelined = nbuf == 2;
@@ -1428,8 +1433,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
           if (v_next) mbar_wait(&bars[b ^ 1], b ? ph0 : ph1, kWaitBudget);  // drain the other buffer's copies
           return;
         }
-        force_tile_compute<MIXED, LANES, HALF, ENERGY, false>(SS[b], smem + b * buf_bytes, L, rows, ent, c, g, fout,
-                                                              status, pe_acc, vir_acc);
+        force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST>(SS[b], smem + b * buf_bytes, L, rows, ent, c, g, fout,
+                                                              status, pe_acc, vir_acc, ta.list_cap);
       }
       __syncthreads();
       if (pipelined) {
@@ -1485,8 +1490,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     if (force_tile_prepare(ti, t, ta, cs, tile_list, S, status)) {
       stage_issue<true, true>(ti, ta, pos, lo, rows, ent, S, smem, L, &bar);
       if (!stage_finish<true, true>(ti, ta, g, S, smem, L, &bar, ph, false, status)) return;
-      force_tile_compute<true, LANES, false, ENERGY, false>(S, smem, L, rows, ent, c, g, fout, status, pe_acc,
-                                                            vir_acc);
+      force_tile_compute<true, LANES, false, ENERGY, false, true>(S, smem, L, rows, ent, c, g, fout, status, pe_acc,
+                                                            vir_acc, ta.list_cap);
     }
     if (ENERGY) {
       const double tp = block_sum(pe_acc, sh);
@@ -1557,7 +1562,7 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
                                                      const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
                                                      const LJConst& c, const Geom& g, const dvec4* __restrict__ w,
                                                      dvec4* __restrict__ hw, dvec4* __restrict__ fo,
-                                                     int32_t* __restrict__ status, double* acc) {
+                                                     int32_t* __restrict__ status, double* acc, int list_cap) {
   const void* sh_pos = buf + L.pos;
   const float4* sh_lo = (const float4*)(buf + L.lo);
   const int* sh_gid = (const int*)(buf + L.gid);
@@ -1583,7 +1588,7 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
       } else {
         row = s_rows[S.row_off + o];
         row.x -= S.list_base;
-        el = s_ent;
+        el = S.list_len <= (unsigned)list_cap ? s_ent : ent + S.list_base;  // long segments stay in HBM
         if (row.x + row.y > S.list_len) {
           if (lane == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
           row.y = 0;
@@ -1714,7 +1719,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     if (blockIdx.x == 0) {
       stage_whole<MIXED, true>(N, pos, lo, S, smem, L);
       __syncthreads();
-      adjoint_tile_compute<MIXED, true>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc);
+      adjoint_tile_compute<MIXED, true>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc, ta.list_cap);
     }
   } else {
     if (threadIdx.x == 0) {
@@ -1729,7 +1734,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const TileInfo ti = tile_info(t, ta);
         stage_issue<MIXED, true>(ti, ta, pos, lo, rows, ent, S, smem, L, &bar);
         if (!stage_finish<MIXED, true>(ti, ta, g, S, smem, L, &bar, ph, true, status)) return;
-        adjoint_tile_compute<MIXED, false>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc);
+        adjoint_tile_compute<MIXED, false>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc, ta.list_cap);
       }
       __syncthreads();
     }
@@ -1859,15 +1864,17 @@ template <bool MIXED, int LANES, bool HALF, bool ENERGY>
 static void force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
                     const uint2* rows, const uint2* tl, const uint16_t* ent, void* f, double* part, int32_t* status,
                     int nbuf, int grid, size_t sm, cudaStream_t s) {
-  if (ta.whole) {
-    set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, true>, sm);
-    k_force_tile<MIXED, LANES, HALF, ENERGY, true><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c, rows, tl,
-                                                                                  ent, f, part, status, nbuf);
-  } else {
-    set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, false>, sm);
-    k_force_tile<MIXED, LANES, HALF, ENERGY, false><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c, rows, tl,
-                                                                                   ent, f, part, status, nbuf);
-  }
+#define LJ_FW(W, LONG)                                                                                           \
+  do {                                                                                                           \
+    set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, W, LONG>, sm);                                             \
+    k_force_tile<MIXED, LANES, HALF, ENERGY, W, LONG><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c,     \
+                                                                                    rows, tl, ent, f, part, status, \
+                                                                                    nbuf);                          \
+  } while (0)
+  if (ta.whole) LJ_FW(true, false);
+  else if (ta.list_cap < ta.max_list) LJ_FW(false, true);  // some segments longer than the staged capacity
+  else LJ_FW(false, false);
+#undef LJ_FW
 }
 
 template <bool MIXED, int LANES>
@@ -1974,6 +1981,10 @@ void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStr
   if (b < 1) b = 1;
   if (b > 4096) b = 4096;
   k_max_count<<<(int)b, 256, 0, s>>>(cnt, n, out);
+}
+
+size_t adjoint_smem_bytes(const TileArgs& ta, int precision) {
+  return align16(tile_layout(ta, precision == LJ_MIXED, true, true).total);
 }
 
 int launch_adjoint_tile(int precision, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,

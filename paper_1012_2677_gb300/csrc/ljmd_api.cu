@@ -507,7 +507,17 @@ static int rebuild(ljmd_sys* s) {
       s->ent_cap = want;
     }
     if (!built) return LJ_EDEVICE;
-    if (force_smem_bytes(s->ta, s->precision, s->force_nbuf, half) <= (size_t)smem_max) break;
+    // the force kernel stages a tile's list segment if it fits; longer segments are read from HBM
+    TileArgs tz = s->ta;
+    tz.list_cap = 0;
+    const size_t base_bytes = std::max(force_smem_bytes(tz, s->precision, s->force_nbuf, 1),
+                                       adjoint_smem_bytes(tz, s->precision));
+    const int nbuf = s->ta.whole ? 1 : (s->force_nbuf == 2 ? 2 : 1);
+    if (base_bytes <= (size_t)smem_max) {
+      const int64_t room = ((int64_t)smem_max - (int64_t)base_bytes) / (2 * nbuf) - 16;
+      s->ta.list_cap = (int32_t)std::max<int64_t>(0, std::min<int64_t>(s->ta.max_list, room) & ~(int64_t)7);
+      break;
+    }
     if (s->ta.whole || s->ta.T <= 1) return LJ_ERANGE;
     t_cap = s->ta.T - 1;
   }

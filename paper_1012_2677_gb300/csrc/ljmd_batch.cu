@@ -335,7 +335,14 @@ static int host_build(ljmd_batch* b) {
     if (attempt == 1) return LJ_EDEVICE;
   }
   if (b->caps.max_list == 0) return LJ_EDEVICE;
-  if (batch_force_smem_bytes(b->caps) > (size_t)smem_max) return LJ_ERANGE;
+  {  // list segments beyond what fits next to the staged positions are read from HBM
+    TileArgs tz = b->caps;
+    tz.list_cap = 0;
+    const size_t base_bytes = batch_force_smem_bytes(tz);
+    if (base_bytes > (size_t)smem_max) return LJ_ERANGE;
+    const int64_t room = ((int64_t)smem_max - (int64_t)base_bytes) / 2 - 16;
+    b->caps.list_cap = (int32_t)std::max<int64_t>(0, std::min<int64_t>(b->caps.max_list, room) & ~(int64_t)7);
+  }
   b->have_list = true;
   b->forces_current = false;
   b->host_rebuilds += 1;

@@ -119,6 +119,7 @@ struct TileArgs {
   int32_t max_own;     // own particles per tile, at most
   int32_t max_chunks;  // 32-candidate chunks per own particle, at most
   int32_t max_list;    // list entries per tile (padded to 8), at most (known after construction)
+  int32_t list_cap;    // entries of a tile's segment the force kernel stages; longer ones stay in HBM
 };
 // One replica of a batch: its box (offset and p are the batch's), grid, tiles and particles.
 // Global tiles, cells and particles are the replicas' ranges concatenated in replica order.
@@ -143,6 +144,7 @@ int launch_force_tile(int precision, int half, int lanes, int energy, const void
                       const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
                       const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
                       int nbuf, cudaStream_t s);
+size_t adjoint_smem_bytes(const TileArgs& ta, int precision);
 // Adjoint pass (HVP, forces, parameter derivatives) over the list; w, hw, fo are dvec4 [N] in sorted
 // order (fo may be null).  Writes 5 partials per block [w.dF/deps, w.dF/dsigma, dPE/deps,
 // dPE/dsigma, PE]; returns the number of blocks.

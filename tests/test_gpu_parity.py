@@ -325,3 +325,20 @@ def test_ldc_extends_list_lifetime_with_same_trajectory():
     assert np.abs(ldc[1] - base[1]).max() < 1e-4
     assert out[ljmd.LJ_VALID_DUTC][0]["rebuilds"] >= base[0]["rebuilds"]
     assert out[ljmd.LJ_VALID_DUTC_LDC][0]["rebuilds"] <= out[ljmd.LJ_VALID_DUTC][0]["rebuilds"]
+
+
+@pytest.mark.parametrize("list_form", [ljmd.LJ_LIST_FULL, ljmd.LJ_LIST_HALF])
+@pytest.mark.parametrize("precision", [ljmd.LJ_MIXED, ljmd.LJ_FP64])
+def test_pair_list_clustered(list_form, precision):
+    """A dense blob over a dilute background: cells far above the mean occupancy take the list
+    kernel's fallback path (too many work units for the unit tables); the list stays bit-exact."""
+    L = 21.0
+    rng = synth.rng(41)
+    blob = 10.0 + 1.5 * rng.standard_normal((1200, 3))
+    back = synth.uniform_positions(1500, L, 42)
+    x = synth.dyadic(np.vstack([blob, back]) % L)
+    with _system(precision, list_form, cutoff=2.5, margin=0.5) as s:
+        s.set_state(x, None, L)
+        s.build_pairlist()
+        got = s.pairs()
+    assert np.array_equal(got, O.pairs_within(x, L, 3.0))
