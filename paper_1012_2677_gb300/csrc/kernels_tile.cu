@@ -395,17 +395,7 @@ __device__ __forceinline__ int own_cell(const TileShared& S, int l, int Tp) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Batched replicas: the replica owning global tile t (tile_base ascending), and the tile geometry
-// of that replica (capacities stay the batch's).
-__device__ __forceinline__ int replica_of_tile(const ReplicaGeo* __restrict__ reps, int R, int64_t t) {
-  int lo = 0, hi = R - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (reps[mid].tile_base <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
+// Batched replicas: the tile geometry of a replica (capacities stay the batch's).
 __device__ __forceinline__ void replica_view(const ReplicaGeo& rg, TileArgs& ta, Geom& g) {
   ta.n = rg.n;
   ta.T = rg.T;
@@ -819,7 +809,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
                 uint2* __restrict__ tile_list, uint16_t* __restrict__ ent, uint64_t cap,
                 unsigned long long* __restrict__ counter, unsigned int* __restrict__ max_list,
                 int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps, int R,
-                const int* __restrict__ pred) {
+                const int* __restrict__ pred, const int32_t* __restrict__ tile_rep) {
   if (pred && !*pred) return;  // predicated (batched rebuild inside a graph)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared S;
@@ -857,7 +847,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     const uint32_t* cs = cs_in;
     int64_t tl = t;
     if (BATCHED) {  // the tile's replica: its box, grid and cells
-      const ReplicaGeo& rg = reps[replica_of_tile(reps, R, t)];
+      const ReplicaGeo& rg = reps[tile_rep[t]];
       replica_view(rg, ta, g);
       cs = cs_in + rg.cell_base;
       tl = t - rg.tile_base;
@@ -1466,7 +1456,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
                   int64_t N, TileArgs caps, LJConst c, const uint2* __restrict__ rows,
                   const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent, float4* __restrict__ fout,
                   double* __restrict__ e_rep, int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps,
-                  int R) {
+                  int R, const int32_t* __restrict__ tile_rep) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared S;
   __shared__ __align__(8) uint64_t bar;
@@ -1479,7 +1469,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   __syncthreads();
   uint32_t ph = 0;
   for (int64_t t = blockIdx.x; t < caps.ntiles; t += gridDim.x) {
-    const int r = replica_of_tile(reps, R, t);
+    const int r = tile_rep[t];
     const ReplicaGeo& rg = reps[r];
     TileArgs ta = caps;
     Geom g;
@@ -1508,11 +1498,12 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 
 // Largest staged and own counts over the tiles of all replicas.
 __global__ void k_tile_sizes_batch(const uint32_t* __restrict__ cs_in, TileArgs caps,
-                                   const ReplicaGeo* __restrict__ reps, int R, unsigned int* __restrict__ out) {
+                                   const ReplicaGeo* __restrict__ reps, int R, const int32_t* __restrict__ tile_rep,
+                                   unsigned int* __restrict__ out) {
   unsigned int mst = 0, mown = 0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < caps.ntiles;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const ReplicaGeo& rg = reps[replica_of_tile(reps, R, t)];
+    const ReplicaGeo& rg = reps[tile_rep[t]];
     TileArgs ta = caps;
     Geom g;
     replica_view(rg, ta, g);
@@ -1851,11 +1842,11 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
   } else if (half) {  // tiles, either form: one thread per key on the hi copies (the list is the same)
     set_smem(k_list_keys<true, false>, sm);
     k_list_keys<true, false><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
-                                                            counter, max_list, status, nullptr, 0, nullptr);
+                                                            counter, max_list, status, nullptr, 0, nullptr, nullptr);
   } else {
     set_smem(k_list_keys<false, false>, sm);
     k_list_keys<false, false><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
-                                                             counter, max_list, status, nullptr, 0, nullptr);
+                                                             counter, max_list, status, nullptr, 0, nullptr, nullptr);
   }
 #undef LJ_LIST_LAUNCH
 }
@@ -2014,28 +2005,29 @@ int launch_adjoint_tile(int precision, const void* pos, const float4* lo, const 
 size_t batch_list_smem_bytes(const TileArgs& caps) { return key_list_layout(caps).total; }
 size_t batch_force_smem_bytes(const TileArgs& caps) { return align16(tile_layout(caps, true, true, false).total); }
 
-void launch_tile_sizes_batch(const uint32_t* cs, TileArgs caps, const ReplicaGeo* reps, int R, unsigned int* out,
-                             cudaStream_t s) {
+void launch_tile_sizes_batch(const uint32_t* cs, TileArgs caps, const ReplicaGeo* reps, int R,
+                             const int32_t* tile_rep, unsigned int* out, cudaStream_t s) {
   int64_t b = (caps.ntiles + 255) / 256;
   if (b < 1) b = 1;
   if (b > 4096) b = 4096;
-  k_tile_sizes_batch<<<(int)b, 256, 0, s>>>(cs, caps, reps, R, out);
+  k_tile_sizes_batch<<<(int)b, 256, 0, s>>>(cs, caps, reps, R, tile_rep, out);
 }
 
 void launch_list_batch(const float4* hi, const double* x, const uint32_t* cs, int64_t N, Geom g, TileArgs caps,
                        ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
                        unsigned long long* counter, unsigned int* max_list, int32_t* status, const ReplicaGeo* reps,
-                       int R, const int* pred, cudaStream_t s) {
+                       int R, const int32_t* tile_rep, const int* pred, cudaStream_t s) {
   const size_t sm = key_list_layout(caps).total;
   const int grid = tile_grid(caps, per_sm_for(sm));
   set_smem(k_list_keys<false, true>, sm);
   k_list_keys<false, true><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, caps, band, rows, tile_list, ent, cap,
-                                                          counter, max_list, status, reps, R, pred);
+                                                          counter, max_list, status, reps, R, pred, tile_rep);
 }
 
 int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo, const uint32_t* cs, int64_t N,
                        TileArgs caps, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
-                       float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R, cudaStream_t s) {
+                       float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R,
+                       const int32_t* tile_rep, cudaStream_t s) {
   const size_t sm = batch_force_smem_bytes(caps);
   const int grid = tile_grid(caps, per_sm_for(sm));
 #define LJ_FB(LN)                                                                                               \
@@ -2043,11 +2035,11 @@ int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo
     if (energy) {                                                                                               \
       set_smem(k_force_batch<LN, true>, sm);                                                                    \
       k_force_batch<LN, true><<<grid, kTileThreads, sm, s>>>(hi, lo, cs, N, caps, c, rows, tile_list, ent, f,   \
-                                                             e_rep, status, reps, R);                          \
+                                                             e_rep, status, reps, R, tile_rep);                          \
     } else {                                                                                                    \
       set_smem(k_force_batch<LN, false>, sm);                                                                   \
       k_force_batch<LN, false><<<grid, kTileThreads, sm, s>>>(hi, lo, cs, N, caps, c, rows, tile_list, ent, f,  \
-                                                              e_rep, status, reps, R);                         \
+                                                              e_rep, status, reps, R, tile_rep);                         \
     }                                                                                                           \
   } while (0)
   switch (lanes) {

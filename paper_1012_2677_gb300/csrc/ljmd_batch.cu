@@ -32,6 +32,7 @@ struct ljmd_batch {
   Geom g0{};  // the batch's common offset / p (box fields of replica 0)
   std::vector<ReplicaGeo> reps_h;
   ReplicaGeo* reps = nullptr;
+  int32_t* tile_rep = nullptr;  // replica of every global tile
   TileArgs caps{};
   int64_t ncells = 0;
   int tile_T = 4;  // preferred cells per tile along z
@@ -102,7 +103,7 @@ static void drop_graph(ljmd_batch* b) {
 
 static void free_batch(ljmd_batch* b) {
   drop_graph(b);
-  void* ptrs[] = {b->reps, b->x, b->v, b->x_alt, b->v_alt, b->f, b->hi, b->lo, b->ref, b->id, b->id_alt, b->img,
+  void* ptrs[] = {b->reps, b->tile_rep, b->x, b->v, b->x_alt, b->v_alt, b->f, b->hi, b->lo, b->ref, b->id, b->id_alt, b->img,
                   b->img_alt, b->rep_of, b->cell_of, b->perm, b->cell_count, b->cell_start, b->cell_fill,
                   b->scan_tmp, b->rows, b->tile_list, b->ent, b->e_rep, b->ke_rep, b->status, b->dmax, b->flag,
                   b->d_rebuilds, b->counter, b->sizes};
@@ -118,6 +119,30 @@ static void free_batch(ljmd_batch* b) {
 static int join_user(ljmd_batch* b) {
   BK(cudaEventRecord(b->user_ev, b->user_st));
   BK(cudaStreamWaitEvent(b->st, b->user_ev, 0));
+  return LJ_OK;
+}
+
+// Cells per tile along z for one replica: the preferred T at density 0.5, scaled by 0.5 / rho so that
+// a tile stages about the same number of particles in every replica (the shared-memory capacity is
+// set by the densest replica's tiles).
+static int replica_tile(int pref, int64_t n_cells, int64_t count, double L) {
+  const double rho = (double)count / (L * L * L);
+  int T = (int)lround((double)pref * 0.5 / std::max(rho, 1e-9));
+  T = std::max(1, std::min(T, pref));
+  T = std::min<int>(T, (int)n_cells - 2);
+  return std::max(1, std::min(T, kMaxTileT));
+}
+
+// Replica index of every global tile (tiles are the replicas' ranges in order), for the kernels.
+static int upload_tile_rep(ljmd_batch* b) {
+  std::vector<int32_t> tr((size_t)b->caps.ntiles);
+  for (int r = 0; r < b->R; ++r) {
+    const ReplicaGeo& rg = b->reps_h[r];
+    const int64_t nt = (int64_t)rg.n * rg.n * rg.ntz;
+    for (int64_t t = 0; t < nt; ++t) tr[(size_t)(rg.tile_base + t)] = r;
+  }
+  BTRY(balloc(&b->tile_rep, tr.size()));
+  BK(cudaMemcpy(b->tile_rep, tr.data(), sizeof(int32_t) * tr.size(), cudaMemcpyHostToDevice));
   return LJ_OK;
 }
 
@@ -170,8 +195,7 @@ static int setup_replicas(ljmd_batch* b) {
     g.L_lo = (float)(L - Lhi);
     g.inv_L = (float)(1.0 / L);
     g.inv_L64 = 1.0 / L;
-    int T = std::min<int>(b->tile_T, (int)n - 2);
-    T = std::max(1, std::min(T, kMaxTileT));
+    const int T = replica_tile(b->tile_T, n, b->count[r], L);
     rg.n = (int32_t)n;
     rg.T = T;
     rg.ntz = (int32_t)((n + T - 1) / T);
@@ -218,6 +242,7 @@ static int setup_replicas(ljmd_batch* b) {
   b->disp_limit = 0.5 * p.margin - (2.0 * sqrt(3.0) * ldexp(1.0, pw - 23) + 1e-6);
   BTRY(balloc(&b->reps, b->R));
   BK(cudaMemcpyAsync(b->reps, b->reps_h.data(), sizeof(ReplicaGeo) * b->R, cudaMemcpyHostToDevice, b->st));
+  BTRY(upload_tile_rep(b));
   BTRY(balloc(&b->cell_count, b->ncells));
   BTRY(balloc(&b->cell_start, b->ncells + 1));
   BTRY(balloc(&b->cell_fill, b->ncells));
@@ -251,7 +276,7 @@ static int enqueue_rebuild(ljmd_batch* b, const int* pred) {
   launch_zero_words(b->counter, 2 * sizeof(unsigned long long), pred, st);
   launch_zero_words(b->sizes, 4 * sizeof(unsigned int), pred, st);
   launch_list_batch(b->hi, b->x, b->cell_start, N, b->g0, b->caps, b->band, b->rows, b->tile_list, b->ent,
-                    (uint64_t)b->ent_cap, b->counter, b->sizes + 3, b->status, b->reps, b->R, pred, st);
+                    (uint64_t)b->ent_cap, b->counter, b->sizes + 3, b->status, b->reps, b->R, b->tile_rep, pred, st);
   b->launches += 17;
   BKL();
   return LJ_OK;
@@ -275,7 +300,7 @@ static int host_build(ljmd_batch* b) {
                           nullptr, st);
   b->launches += 1 + launch_scan_u32(b->cell_count, b->cell_start, b->ncells, b->scan_tmp, st);
   BK(cudaMemsetAsync(b->sizes, 0, 4 * sizeof(unsigned int), st));
-  launch_tile_sizes_batch(b->cell_start, b->caps, b->reps, b->R, b->sizes, st);
+  launch_tile_sizes_batch(b->cell_start, b->caps, b->reps, b->R, b->tile_rep, b->sizes, st);
   b->launches += 1;
   BKL();
   BK(cudaMemcpyAsync(b->h_u64, b->sizes, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
@@ -340,7 +365,9 @@ static int host_build(ljmd_batch* b) {
     tz.list_cap = 0;
     const size_t base_bytes = batch_force_smem_bytes(tz);
     if (base_bytes > (size_t)smem_max) return LJ_ERANGE;
-    const int64_t room = ((int64_t)smem_max - (int64_t)base_bytes) / 2 - 16;
+    // room for the list next to the positions so that 4 CTAs share an SM where possible
+    const int64_t target = std::max<int64_t>((int64_t)base_bytes + 4096, 54 * 1024);
+    const int64_t room = (std::min<int64_t>(smem_max, target) - (int64_t)base_bytes) / 2 - 16;
     b->caps.list_cap = (int32_t)std::max<int64_t>(0, std::min<int64_t>(b->caps.max_list, room) & ~(int64_t)7);
   }
   b->have_list = true;
@@ -352,7 +379,7 @@ static int host_build(ljmd_batch* b) {
 static int enqueue_force(ljmd_batch* b, bool energy) {
   if (energy) BK(cudaMemsetAsync(b->e_rep, 0, 2 * sizeof(double) * b->R, b->st));
   launch_force_batch(b->lanes, energy ? 1 : 0, b->hi, b->lo, b->cell_start, b->N, b->caps, b->c, b->rows,
-                     b->tile_list, b->ent, b->f, b->e_rep, b->status, b->reps, b->R, b->st);
+                     b->tile_list, b->ent, b->f, b->e_rep, b->status, b->reps, b->R, b->tile_rep, b->st);
   b->launches += 1;
   BKL();
   return LJ_OK;
@@ -716,8 +743,7 @@ int ljmd_batch_set_tuning(ljmd_batch* b, int32_t tile_cells, int32_t lanes) {
   if (tile_cells && tile_cells != b->tile_T) {
     b->tile_T = tile_cells;
     for (ReplicaGeo& rg : b->reps_h) {
-      int T = std::min<int>(tile_cells, rg.n - 2);
-      rg.T = std::max(1, std::min(T, kMaxTileT));
+      rg.T = replica_tile(tile_cells, rg.n, rg.count, rg.g.L);
       rg.ntz = (rg.n + rg.T - 1) / rg.T;
     }
     int64_t tiles = 0;
@@ -728,6 +754,7 @@ int ljmd_batch_set_tuning(ljmd_batch* b, int32_t tile_cells, int32_t lanes) {
     b->caps.ntiles = tiles;
     BK(cudaMemcpyAsync(b->reps, b->reps_h.data(), sizeof(ReplicaGeo) * b->R, cudaMemcpyHostToDevice, b->st));
     BTRY(balloc(&b->tile_list, (size_t)tiles));
+    BTRY(upload_tile_rep(b));
     b->have_list = false;
     b->forces_current = false;
   }

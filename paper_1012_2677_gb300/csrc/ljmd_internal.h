@@ -190,15 +190,16 @@ int launch_sqdiff(const double* u, const double* w, int64_t n, double* part, cud
 // ---- batched replicas (kernels_tile.cu, kernels_batch.cu) ----------------------------------
 size_t batch_list_smem_bytes(const TileArgs& caps);
 size_t batch_force_smem_bytes(const TileArgs& caps);
-void launch_tile_sizes_batch(const uint32_t* cs, TileArgs caps, const ReplicaGeo* reps, int R, unsigned int* out,
-                             cudaStream_t s);
+void launch_tile_sizes_batch(const uint32_t* cs, TileArgs caps, const ReplicaGeo* reps, int R,
+                             const int32_t* tile_rep, unsigned int* out, cudaStream_t s);
 void launch_list_batch(const float4* hi, const double* x, const uint32_t* cs, int64_t N, Geom g, TileArgs caps,
                        ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
                        unsigned long long* counter, unsigned int* max_list, int32_t* status, const ReplicaGeo* reps,
-                       int R, const int* pred, cudaStream_t s);
+                       int R, const int32_t* tile_rep, const int* pred, cudaStream_t s);
 int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo, const uint32_t* cs, int64_t N,
                        TileArgs caps, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
-                       float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R, cudaStream_t s);
+                       float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R,
+                       const int32_t* tile_rep, cudaStream_t s);
 void launch_wrap_label_batch(double* x, int32_t* img, int64_t N, const int32_t* rep_of, const ReplicaGeo* reps,
                              double offset, uint32_t* cell_of, uint32_t* cell_count, int32_t* status,
                              const int* pred, cudaStream_t s);
