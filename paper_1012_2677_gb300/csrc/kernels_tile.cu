@@ -124,6 +124,107 @@ __device__ __forceinline__ bool stage_offsets(const TileInfo& ti, const TileArgs
   return S.total <= ta.max_staged;
 }
 
+// The same bookkeeping done by one warp alone (the producer warp of the pipelined force kernel):
+// no CTA barrier, the other warps keep computing.
+__device__ __forceinline__ bool stage_offsets_warp(const TileInfo& ti, const TileArgs& ta,
+                                                   const uint32_t* __restrict__ cs, TileShared& S, int lane) {
+  const int ncol = ti.Tp + 2;
+  const int ncell = 9 * ncol;
+  int run = 0;
+  for (int base = 0; base < ncell; base += 32) {
+    const int q = base + lane;
+    int v = 0;
+    if (q < ncell) {
+      int sx, sy, sz;
+      const uint32_t c = cell_of_q(ti, ta.n, ncol, q, sx, sy, sz);
+      const uint32_t a = cs[c], b = cs[c + 1];
+      S.g0[q] = (int)a;
+      v = (int)(b - a);
+    }
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (q < ncell) S.offq[q + 1] = run + inc;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    S.offq[0] = 0;
+    S.ncol = ncol;
+    S.ncell = ncell;
+    S.total = run;
+    S.own0 = S.offq[4 * ncol + 1];
+    S.own1 = S.offq[4 * ncol + ti.Tp + 1];
+    S.gown0 = S.g0[4 * ncol + 1];
+  }
+  __syncwarp();
+  return run <= ta.max_staged;
+}
+
+// Cell bounds of a tile's staged cells held in one warp's registers (lane l: cells l, l + 32, ...),
+// loaded a tile ahead of their use so the bookkeeping never waits on memory.
+constexpr int kPfRounds = (kMaxCells + 31) / 32;
+struct TilePrefetch {
+  TileInfo ti;
+  uint2 tl;
+  uint32_t a[kPfRounds], b[kPfRounds];
+};
+
+__device__ __forceinline__ void tile_prefetch(int64_t t, const TileArgs& ta, const uint32_t* __restrict__ cs,
+                                              const uint2* __restrict__ tile_list, TilePrefetch& pf, int lane) {
+  pf.ti = tile_info(t, ta);
+  const int ncol = pf.ti.Tp + 2, ncell = 9 * ncol;
+  pf.tl = tile_list ? tile_list[t] : make_uint2(0u, 0u);
+#pragma unroll
+  for (int r = 0; r < kPfRounds; ++r) {
+    const int q = 32 * r + lane;
+    pf.a[r] = pf.b[r] = 0u;
+    if (q < ncell) {
+      int sx, sy, sz;
+      const uint32_t c = cell_of_q(pf.ti, ta.n, ncol, q, sx, sy, sz);
+      pf.a[r] = cs[c];
+      pf.b[r] = cs[c + 1];
+    }
+  }
+}
+
+// stage_offsets_warp from prefetched bounds; also the tile's list segment.
+__device__ __forceinline__ bool tile_prepare_pf(const TilePrefetch& pf, const TileArgs& ta, TileShared& S, int lane) {
+  const int ncol = pf.ti.Tp + 2, ncell = 9 * ncol;
+  int run = 0;
+#pragma unroll
+  for (int r = 0; r < kPfRounds; ++r) {
+    if (32 * r >= ncell) break;
+    const int q = 32 * r + lane;
+    int inc = q < ncell ? (int)(pf.b[r] - pf.a[r]) : 0;
+    if (q < ncell) S.g0[q] = (int)pf.a[r];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (q < ncell) S.offq[q + 1] = run + inc;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    S.offq[0] = 0;
+    S.ncol = ncol;
+    S.ncell = ncell;
+    S.total = run;
+    S.own0 = S.offq[4 * ncol + 1];
+    S.own1 = S.offq[4 * ncol + pf.ti.Tp + 1];
+    S.gown0 = S.g0[4 * ncol + 1];
+    S.list_base = pf.tl.x;
+    S.list_len = pf.tl.y;
+  }
+  __syncwarp();
+  return run <= ta.max_staged;
+}
+
 // Staged cell of staged slot s: the largest q with offq[q] <= s.
 __device__ __forceinline__ int slot_cell(const TileShared& S, int s) {
   int lo = 0, hi = S.ncell - 1;
@@ -172,17 +273,17 @@ __host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, b
   return L;
 }
 
-// Issue the bulk copies of one tile (warp 0; lane k < 9 handles column k, lane 9 the rows and
-// list segment), all completing on `bar`.  Copies: positions (hi [+ lo] or FP64), and for the
+// Issue the bulk copies of one tile (warp `issuer`; lane k < 9 handles column k, lane 9 the rows
+// and list segment), all completing on `bar`.  Copies: positions (hi [+ lo] or FP64), and for the
 // force kernel the own rows and the list segment.  No barrier inside: the other warps go on.
 template <bool MIXED, bool FORCE>
 __device__ __forceinline__ void stage_issue(const TileInfo& ti, const TileArgs& ta, const void* __restrict__ pos,
                                             const float4* __restrict__ lo, const uint2* __restrict__ rows,
                                             const uint16_t* __restrict__ ent, TileShared& S, unsigned char* smem,
-                                            const TileLayout& L, uint64_t* bar) {
+                                            const TileLayout& L, uint64_t* bar, int issuer = 0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned bpp = MIXED ? 16u : 32u;
-  if (warp != 0) return;
+  if (warp != issuer) return;
   unsigned bytes = (unsigned)S.total * bpp * ((MIXED && FORCE) ? 2u : 1u);
   int r0 = 0, r1 = 0;
   const int n_own = S.own1 - S.own0;
@@ -230,6 +331,19 @@ __device__ __forceinline__ void stage_issue(const TileInfo& ti, const TileArgs& 
   }
 }
 
+// Image shift of one staged hi/lo coordinate by S = s L_hi (+ s L_lo into lo), exact in hi + lo:
+// hi + S can round when it leaves the binade of hi (a particle that drifted below the offset
+// since the last wrap sits on the finer grid of the binade below), so the rounding error is
+// recovered with Knuth's two-sum and moved into lo.
+__device__ __forceinline__ void shift_hi_lo(float& h, float& l, float s, const Geom& g) {
+  const float S = s * g.L_hi;  // exact: s is -1, 0 or +1
+  const float t = __fadd_rn(h, S);
+  const float bv = __fsub_rn(t, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bv)), __fsub_rn(S, bv));
+  h = t;
+  l = __fadd_rn(l, __fadd_rn(err, s * g.L_lo));
+}
+
 // Wait (all threads, bounded) for the copies of a staged tile, then fill in the image shifts
 // (mixed: added to hi/lo; FP64: code in w) and, if wanted, the sorted indices.  Returns false
 // (all threads) on timeout, after recording it; the caller drains any other copies in flight.
@@ -255,7 +369,7 @@ __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs&
   const bool interior = ti.cx >= 1 && ti.cx <= ta.n - 2 && ti.cy >= 1 && ti.cy <= ta.n - 2 && ti.z0 >= 1 &&
                         ti.z0 + ti.Tp <= ta.n - 1;
   if (MIXED && interior && !want_gid) return true;
-  for (int q = warp; q < S.ncell; q += kWarps) {
+  for (int q = warp; q < S.ncell; q += (int)(blockDim.x >> 5)) {
     int sx = 0, sy = 0, sz = 0;
     if (!interior) cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
     const bool shifted = (sx | sy | sz) != 0;
@@ -265,14 +379,15 @@ __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs&
       if (MIXED) {
         if (shifted) {
           float4* h = (float4*)(smem + L.pos) + s;
-          h->x = fmaf((float)sx, g.L_hi, h->x);  // exact
-          h->y = fmaf((float)sy, g.L_hi, h->y);
-          h->z = fmaf((float)sz, g.L_hi, h->z);
           if (FORCE) {
             float4* l = (float4*)(smem + L.lo) + s;
-            l->x = fmaf((float)sx, g.L_lo, l->x);
-            l->y = fmaf((float)sy, g.L_lo, l->y);
-            l->z = fmaf((float)sz, g.L_lo, l->z);
+            shift_hi_lo(h->x, l->x, (float)sx, g);
+            shift_hi_lo(h->y, l->y, (float)sy, g);
+            shift_hi_lo(h->z, l->z, (float)sz, g);
+          } else {  // list filter: hi only; a rounding of hi stays inside the FP32 band
+            h->x = fmaf((float)sx, g.L_hi, h->x);
+            h->y = fmaf((float)sy, g.L_hi, h->y);
+            h->z = fmaf((float)sz, g.L_hi, h->z);
           }
         }
       } else {
@@ -409,6 +524,7 @@ __device__ __forceinline__ void replica_view(const ReplicaGeo& rg, TileArgs& ta,
 constexpr int kListSplit = 2;  // candidate sub-ranges per neighbour column (work balance)
 constexpr int kListItems = 9 * kListSplit;     // work items per 32-key chunk
 constexpr size_t kListSmemTarget = 48 * 1024;  // 4 CTAs per SM for typical liquids
+constexpr int kListThreads = 256;               // threads of a list-construction CTA (128 or 256)
 struct KeyListLayout {
   size_t pos;    // hi float4 [max_staged]
   size_t gid;    // int [max_staged]
@@ -422,7 +538,7 @@ struct KeyListLayout {
   int seg_cap;   // entries (a multiple of 8)
   size_t total;
 };
-__host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs& ta) {
+__host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs& ta, int nt = kListThreads) {
   KeyListLayout K;
   const size_t ms = (size_t)ta.max_staged;
   K.nch = (ta.max_own + 31) / 32;
@@ -442,7 +558,9 @@ __host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs
   K.mask = o;
   o += (size_t)K.mask_words * 32 * 4;
   K.seg = o;
-  size_t room = o + 8192 < kListSmemTarget ? kListSmemTarget - o : 8192;
+  // 128-thread CTAs: smaller footprint, more of them per SM
+  const size_t target = nt == 128 ? kListSmemTarget * 3 / 4 : kListSmemTarget;
+  size_t room = o + 8192 < target ? target - o : 8192;
   K.seg_cap = (int)((room / 2) & ~(size_t)7);
   K.total = o + 2 * (size_t)K.seg_cap;
   return K;
@@ -802,8 +920,8 @@ constexpr int kUnitMax = 160;     // work units per tile in the unit path
 // (padded to 8 entries), and a second pass writes the entries into shared memory, from where
 // they are copied out with 16-byte stores (directly to global memory if the segment does not
 // fit).
-template <bool HALF, bool BATCHED>
-__global__ void __launch_bounds__(kTileThreads, 4)
+template <bool HALF, bool BATCHED, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
     k_list_keys(const float4* __restrict__ pos, const double* __restrict__ x, const uint32_t* __restrict__ cs_in,
                 int64_t N, Geom g_in, TileArgs ta_in, ListBand band, uint2* __restrict__ rows,
                 uint2* __restrict__ tile_list, uint16_t* __restrict__ ent, uint64_t cap,
@@ -819,7 +937,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   __shared__ int u_ck0[kUnitChunks + 1], u_ub[kUnitChunks + 1], u_info[kUnitMax];
   __shared__ unsigned char u_chunk[kUnitMax];
   __shared__ int s_nchunk, s_nunit;
-  const KeyListLayout K = key_list_layout(ta_in);
+  constexpr int kLW = NT / 32;  // warps of the CTA
+  const KeyListLayout K = key_list_layout(ta_in, NT);
   TileLayout L;  // the staging helpers' view: positions and sorted indices
   L.pos = K.pos;
   L.lo = K.pos;
@@ -835,25 +954,46 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   uint16_t* s_seg = (uint16_t*)(smem + K.seg);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t phase = 0;
+  __shared__ int s_staged_ok;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_proxy_async_smem();
   }
+  // warp 0 holds the cell bounds of the CTA's next tile, loaded one tile ahead of their use
+  TilePrefetch pf;
+  auto prefetch = [&](int64_t tp) {
+    TileArgs tap = ta_in;
+    Geom gp = g_in;
+    const uint32_t* csp = cs_in;
+    int64_t tlp = tp;
+    if (BATCHED) {
+      const ReplicaGeo& rg = reps[tile_rep[tp]];
+      replica_view(rg, tap, gp);
+      csp = cs_in + rg.cell_base;
+      tlp = tp - rg.tile_base;
+    }
+    tile_prefetch(tlp, tap, csp, nullptr, pf, lane);
+  };
+  if (warp == 0 && blockIdx.x < ta_in.ntiles) prefetch(blockIdx.x);
   __syncthreads();
 
   for (int64_t t = blockIdx.x; t < ta_in.ntiles; t += gridDim.x) {
     TileArgs ta = ta_in;
     Geom g = g_in;
-    const uint32_t* cs = cs_in;
     int64_t tl = t;
     if (BATCHED) {  // the tile's replica: its box, grid and cells
       const ReplicaGeo& rg = reps[tile_rep[t]];
       replica_view(rg, ta, g);
-      cs = cs_in + rg.cell_base;
       tl = t - rg.tile_base;
     }
     const TileInfo ti = tile_info(tl, ta);
-    if (!stage_offsets(ti, ta, cs, S)) {
+    if (warp == 0) {
+      const bool okp = tile_prepare_pf(pf, ta, S, lane);
+      if (lane == 0) s_staged_ok = okp ? 1 : 0;
+      if (t + gridDim.x < ta_in.ntiles) prefetch(t + gridDim.x);
+    }
+    __syncthreads();
+    if (!s_staged_ok) {
       if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
       __syncthreads();
       continue;
@@ -949,7 +1089,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     if (s_nchunk >= 0) {
       const int nc = s_nchunk, nu = s_nunit;
       // phase A: the bits of every unit
-      for (int u = warp; u < nu; u += kWarps) {
+      for (int u = warp; u < nu; u += kLW) {
         const int c = u_chunk[u];
         const int o = u_ck0[c] + lane;
         const bool valid = o < u_ck0[c + 1];
@@ -959,7 +1099,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       }
       __syncthreads();
       // phase B: row lengths (one warp per chunk)
-      for (int c = warp; c < nc; c += kWarps) {
+      for (int c = warp; c < nc; c += kLW) {
         int len = 0;
         for (int u = u_ub[c]; u < u_ub[c + 1]; ++u) len += __popc(s_mask[u * 32 + lane]);
         const int o = u_ck0[c] + lane;
@@ -1002,11 +1142,14 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       if (ok) {
         const bool staged = s_padded <= (unsigned)K.seg_cap;
         uint16_t* dst = staged ? s_seg : ent + s_base;
-        // phase D: entries in row order (units of a chunk in column order), one warp per chunk
-        for (int c = warp; c < nc; c += kWarps) {
+        // phase D: entries in row order (units of a chunk in column order), one warp per unit;
+        // a unit's entries start after the key's entries in the chunk's earlier units
+        for (int u = warp; u < nu; u += kLW) {
+          const int c = u_chunk[u];
           const int o = u_ck0[c] + lane;
-          int p = o < u_ck0[c + 1] ? s_kst[o] : 0;
-          for (int u = u_ub[c]; u < u_ub[c + 1]; ++u) {
+          if (o < u_ck0[c + 1]) {
+            int p = s_kst[o];
+            for (int v = u_ub[c]; v < u; ++v) p += __popc(s_mask[v * 32 + lane]);
             uint32_t m = s_mask[u * 32 + lane];
             const int j0 = u_info[u] & 0xffff;
             while (m) {
@@ -1054,7 +1197,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     __syncthreads();
     const bool keep_bits = s_ibase[nch * kItems] <= K.mask_words;
     // pass 1: counts per (key, column part), kept-candidate bits
-    for (int item = warp; item < nch * kItems; item += kWarps) {
+    for (int item = warp; item < nch * kItems; item += kLW) {
       const int c = item / kItems, r = item - kItems * c;
       s_cnt[item * 32 + lane] =
           keep_bits ? key_item_bits<HALF>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit,
@@ -1109,7 +1252,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       const bool staged = s_padded <= (unsigned)K.seg_cap;
       uint16_t* dst = staged ? s_seg : ent + s_base;
       // pass 2: the same tests, entries written
-      for (int item = warp; item < nch * kItems; item += kWarps) {
+      for (int item = warp; item < nch * kItems; item += kLW) {
         const int c = item / kItems, r = item - kItems * c;
         const int o = 32 * c + lane;
         const int p = o < n_own ? s_kst[o] + s_cnt[item * 32 + lane] : 0;
@@ -1202,7 +1345,7 @@ __device__ __forceinline__ void pair_mixed(const float4& hi_i, const float4& lo_
 
 // Forces of the own particles of one staged tile (buffer `buf`); group `grp` of LANES threads per
 // key particle, lanes striding over its row.
-template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST>
+template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST, int UNR = 2>
 __device__ __forceinline__ void force_tile_compute(const TileShared& S, const unsigned char* buf, const TileLayout& L,
                                                    const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
                                                    const LJConst& c, const Geom& g, void* __restrict__ fout,
@@ -1238,24 +1381,46 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
           row.y = 0;
         }
       }
-      // the row's pairs; one instance per memory space of the list (shared: staged segment)
-      auto row_pairs = [&](const uint16_t* __restrict__ el) {
+      // the row's pairs; one instance per memory space of the list (in_smem: staged segment)
+      auto row_pairs = [&](const uint16_t* __restrict__ el, bool in_smem) {
       if (MIXED) {
-        const float4 hi_i = ((const float4*)sh_pos)[l], lo_i = sh_lo[l];
+        // staged positions by 32-bit shared address: hi at a_pos + 16 j, lo at a_pos + d_lo + 16 j
+        const uint32_t a_pos = smem_addr(sh_pos), d_lo = smem_addr(sh_lo) - a_pos, a_gid = smem_addr(sh_gid);
+        const float4 hi_i = lds_f4(a_pos + 16u * l), lo_i = lds_f4(a_pos + d_lo + 16u * l);
         float4* F = (float4*)fout;
-        unsigned e = lane;
-        // two independent entries per iteration
-        for (; e + LANES < row.y; e += 2 * LANES) {
-          const int j0 = el[row.x + e], j1 = el[row.x + e + LANES];
-          const float4 h0 = ((const float4*)sh_pos)[j0], q0 = sh_lo[j0];
-          const float4 h1 = ((const float4*)sh_pos)[j1], q1 = sh_lo[j1];
-          pair_mixed<HALF, ENERGY, WHOLE>(hi_i, lo_i, h0, q0, c, g, a0, F, HALF ? sh_gid[j0] : 0);
-          pair_mixed<HALF, ENERGY, WHOLE>(hi_i, lo_i, h1, q1, c, g, a1, F, HALF ? sh_gid[j1] : 0);
-        }
-        if (e < row.y) {
-          const int j0 = el[row.x + e];
-          pair_mixed<HALF, ENERGY, WHOLE>(hi_i, lo_i, ((const float4*)sh_pos)[j0], sh_lo[j0], c, g, a0, F,
-                                          HALF ? sh_gid[j0] : 0);
+        auto pair_at = [&](uint32_t j, AccF& acc) {
+          const uint32_t b = a_pos + (j << 4);
+          pair_mixed<HALF, ENERGY, WHOLE>(hi_i, lo_i, lds_f4(b), lds_f4(b + d_lo), c, g, acc, F,
+                                          HALF ? lds_s32(a_gid + 4u * j) : 0);
+        };
+        if (in_smem) {
+          // list segment staged: entries by 32-bit shared address, two independent per iteration
+          uint32_t p = smem_addr(s_ent) + 2u * (row.x + lane);
+          const uint32_t pend = smem_addr(s_ent) + 2u * (row.x + row.y);
+          if (UNR == 4) {  // four independent entries per iteration (more loads in flight)
+            for (; p + 6u * LANES < pend; p += 8u * LANES) {
+              const uint32_t j0 = lds_u16(p), j1 = lds_u16(p + 2u * LANES), j2 = lds_u16(p + 4u * LANES),
+                             j3 = lds_u16(p + 6u * LANES);
+              pair_at(j0, a0);
+              pair_at(j1, a1);
+              pair_at(j2, a0);
+              pair_at(j3, a1);
+            }
+          }
+          for (; p + 2u * LANES < pend; p += 4u * LANES) {
+            const uint32_t j0 = lds_u16(p), j1 = lds_u16(p + 2u * LANES);
+            pair_at(j0, a0);
+            pair_at(j1, a1);
+          }
+          if (p < pend) pair_at(lds_u16(p), a0);
+        } else {
+          unsigned e = lane;
+          for (; e + LANES < row.y; e += 2 * LANES) {
+            const uint32_t j0 = el[row.x + e], j1 = el[row.x + e + LANES];
+            pair_at(j0, a0);
+            pair_at(j1, a1);
+          }
+          if (e < row.y) pair_at(el[row.x + e], a0);
         }
       } else {
         const dvec4 qi = ((const dvec4*)sh_pos)[l];
@@ -1299,9 +1464,9 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
         }
       }
       };
-      if (WHOLE) row_pairs(ent);
-      else if (!LONGLIST || S.list_len <= (unsigned)list_cap) row_pairs(s_ent);
-      else row_pairs(ent + S.list_base);  // a long segment stays in HBM
+      if (WHOLE) row_pairs(ent, false);
+      else if (!LONGLIST || S.list_len <= (unsigned)list_cap) row_pairs(s_ent, true);
+      else row_pairs(ent + S.list_base, false);  // a long segment stays in HBM
     }
     if (MIXED) {
       float fx = gsum<LANES>(a0.fx + a1.fx);
@@ -1433,6 +1598,192 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       }
     }
   }
+  if (ENERGY) {
+    __shared__ double sh[32];
+    const double tp = block_sum(pe_acc, sh);
+    __syncthreads();
+    const double tv = block_sum(vir_acc, sh);
+    if (threadIdx.x == 0) {
+      part[2 * (size_t)blockIdx.x] = tp;
+      part[2 * (size_t)blockIdx.x + 1] = tv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pipelined force (mixed form, full list, tiled box): two producer warps stage tiles into two
+// shared-memory buffers (producer p handles the tiles k = p mod 2, in buffer p) while the consumer
+// warps compute, so neither the copies nor the tile-end stragglers hold the CTA at a barrier.
+// Per tile k (buffer k % 2, bookkeeping slot k % 4):
+//   producer: wait empty[b] (tile k - 2 released) -> issue the copies of tile k -> bookkeeping of
+//             tile k + 2 from cell bounds loaded one tile earlier, and the loads for tile k + 4 ->
+//             wait full[b] -> arrive ready[b];
+//   consumers: wait ready[b] -> (periodic tiles: image shifts, consumer barrier) -> forces of
+//             the tile's own particles -> arrive empty[b].
+// Every wait is bounded; a producer that gives up marks the slot aborted and releases the
+// consumers, which then leave.  No copy is in flight when a warp leaves.
+constexpr int kPipeConsumers = kWarps;                 // consumer warps (the 256 threads of a tile)
+constexpr int kPipeProducers = 2;
+constexpr int kPipeThreads = kTileThreads + 32 * kPipeProducers;
+constexpr int kPipeSlots = 4;
+
+__device__ __forceinline__ bool tile_interior(const TileInfo& ti, const TileArgs& ta) {
+  return ti.cx >= 1 && ti.cx <= ta.n - 2 && ti.cy >= 1 && ti.cy <= ta.n - 2 && ti.z0 >= 1 && ti.z0 + ti.Tp <= ta.n - 1;
+}
+
+// Image shifts of a staged tile's periodic cells by the consumer warps (warp per cell, lanes over
+// its particles).  Every writer orders its writes before later bulk copies into the same bytes;
+// the caller then waits for all consumer warps (a bounded mbarrier wait, not bar.sync, so that a
+// warp that left on a timeout cannot hold the others forever).
+__device__ __forceinline__ void stage_shift_consumers(const TileInfo& ti, const TileArgs& ta, const Geom& g,
+                                                      const TileShared& S, unsigned char* smem, const TileLayout& L) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = warp; q < S.ncell; q += kPipeConsumers) {
+    int sx, sy, sz;
+    cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
+    if ((sx | sy | sz) == 0) continue;
+    for (int e = S.offq[q] + lane; e < S.offq[q + 1]; e += 32) {
+      float4* h = (float4*)(smem + L.pos) + e;
+      float4* l = (float4*)(smem + L.lo) + e;
+      shift_hi_lo(h->x, l->x, (float)sx, g);
+      shift_hi_lo(h->y, l->y, (float)sy, g);
+      shift_hi_lo(h->z, l->z, (float)sz, g);
+    }
+  }
+  fence_proxy_async_smem();
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+template <int LANES, bool ENERGY, bool LONGLIST>
+__global__ void __launch_bounds__(kPipeThreads, 2)
+    k_force_pipe(const float4* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
+                 Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
+                 const uint16_t* __restrict__ ent, float4* __restrict__ fout, double* __restrict__ part,
+                 int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileShared SS[kPipeSlots];
+  __shared__ TileInfo s_ti[kPipeSlots];
+  __shared__ int s_valid[kPipeSlots];  // 1: interior tile, 2: periodic tile (shifts), 0: skip, -1: abort
+  __shared__ __align__(8) uint64_t full[2], ready[2], empty[2], shifted[2];
+  const TileLayout L = tile_layout(ta, true, true, false);
+  const size_t buf_bytes = align16(L.total);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&ready[b], 1);
+      mbar_init(&empty[b], kPipeConsumers);
+      mbar_init(&shifted[b], kPipeConsumers);
+    }
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  double pe_acc = 0.0, vir_acc = 0.0;
+  const int64_t stride = gridDim.x;
+  if (warp >= kPipeConsumers) {
+    // ---- producer p: tiles k = p, p + 2, ... in buffer p ----
+    const int p = warp - kPipeConsumers, b = p;
+    int64_t t = blockIdx.x + p * stride;
+    TilePrefetch pf;
+    bool ok_next = false;
+    TileInfo ti_cur{0, 0, 0, 0};
+    if (t < ta.ntiles) {
+      tile_prefetch(t, ta, cs, tile_list, pf, lane);
+      ti_cur = pf.ti;
+      ok_next = tile_prepare_pf(pf, ta, SS[p], lane);
+      if (t + 2 * stride < ta.ntiles) tile_prefetch(t + 2 * stride, ta, cs, tile_list, pf, lane);
+    }
+    for (int k = p; t < ta.ntiles; t += 2 * stride, k += 2) {
+      const int slot = k % kPipeSlots;
+      const uint32_t use = (uint32_t)(k >> 1);
+      TileShared& S = SS[slot];
+      unsigned char* buf = smem + b * buf_bytes;
+      bool ok = true;
+      if (k >= 2) {
+        if (lane == 0) ok = mbar_wait(&empty[b], (use - 1u) & 1u, kWaitBudget);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
+      if (!ok) {  // the consumers did not release the buffer: give up (nothing in flight)
+        if (lane == 0) {
+          atomicOr(status, LJ_ST_TIMEOUT);
+          s_valid[slot] = -1;
+          mbar_arrive(&ready[b]);
+        }
+        break;
+      }
+      const TileInfo ti = ti_cur;
+      bool staged = ok_next;
+      if (staged && (S.own1 - S.own0 > ta.max_own || S.list_len > (unsigned)ta.max_list)) {
+        if (lane == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
+        staged = false;
+      }
+      if (!staged && lane == 0 && !ok_next) atomicOr(status, LJ_ST_CELL_RANGE);
+      if (staged) stage_issue<true, true>(ti, ta, pos, lo, rows, ent, S, buf, L, &full[b], warp);
+      // bookkeeping of this producer's next tile (its slot was released with tile k - 2), then
+      // the loads for the one after it
+      const int64_t tn = t + 2 * stride;
+      if (tn < ta.ntiles) {
+        ti_cur = pf.ti;
+        ok_next = tile_prepare_pf(pf, ta, SS[(k + 2) % kPipeSlots], lane);
+        if (tn + 2 * stride < ta.ntiles) tile_prefetch(tn + 2 * stride, ta, cs, tile_list, pf, lane);
+      }
+      if (staged) {
+        bool landed = true;
+        if (lane == 0) landed = mbar_wait(&full[b], use & 1u, kWaitBudget);
+        landed = __shfl_sync(0xffffffffu, landed ? 1 : 0, 0) != 0;
+        if (!landed) {
+          if (lane == 0) {
+            atomicOr(status, LJ_ST_TIMEOUT);
+            mbar_wait(&full[b], use & 1u, kWaitBudget);  // let copies in flight land before leaving
+            s_valid[slot] = -1;
+            mbar_arrive(&ready[b]);
+          }
+          break;
+        }
+      }
+      if (lane == 0) {
+        s_ti[slot] = ti;
+        s_valid[slot] = staged ? (tile_interior(ti, ta) ? 1 : 2) : 0;
+        mbar_arrive(&ready[b]);  // release: bookkeeping and copies visible to the consumers
+      }
+    }
+  } else {
+    // ---- consumers ----
+    int k = 0;
+    uint32_t shpar = 0u;  // bit b: phase of shifted[b] (every consumer warp sees the same tiles)
+    for (int64_t t = blockIdx.x; t < ta.ntiles; t += stride, ++k) {
+      const int b = k & 1, slot = k % kPipeSlots;
+      const uint32_t use = (uint32_t)(k >> 1);
+      bool ok = __all_sync(0xffffffffu, mbar_wait(&ready[b], use & 1u, kWaitBudget)) != 0;
+      if (!ok) {
+        if (lane == 0) atomicOr(status, LJ_ST_TIMEOUT);
+        break;
+      }
+      const int v = s_valid[slot];
+      if (v < 0) break;
+      unsigned char* buf = smem + b * buf_bytes;
+      if (v == 2) {  // periodic tile: shifts by all consumer warps, then wait for all of them
+        stage_shift_consumers(s_ti[slot], ta, g, SS[slot], buf, L);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&shifted[b]);
+        ok = __all_sync(0xffffffffu, mbar_wait(&shifted[b], (shpar >> b) & 1u, kWaitBudget)) != 0;
+        shpar ^= 1u << b;
+        if (!ok) {
+          if (lane == 0) atomicOr(status, LJ_ST_TIMEOUT);
+          break;
+        }
+      }
+      if (v > 0)
+        force_tile_compute<true, LANES, false, ENERGY, false, LONGLIST>(SS[slot], buf, L, rows, ent, c, g, fout, status,
+                                                                        pe_acc, vir_acc, ta.list_cap);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+    }
+  }
+  __syncthreads();
   if (ENERGY) {
     __shared__ double sh[32];
     const double tp = block_sum(pe_acc, sh);
@@ -1810,6 +2161,14 @@ static void set_smem(K kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// CTAs of a kernel resident per SM at the given dynamic shared memory (registers included).
+template <class K>
+static int resident_per_sm(K kernel, int threads, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1) nb = 1;
+  return nb;
+}
+
 static int per_sm_for(size_t smem_bytes) {
   int dev = 0, smem_sm = 0;
   cudaGetDevice(&dev);
@@ -1823,7 +2182,11 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
                       uint64_t cap, unsigned long long* counter, unsigned int* max_list, int32_t* status,
                       cudaStream_t s) {
   const size_t sm = list_smem_bytes(ta, precision);
-  const int grid = tile_grid(ta, per_sm_for(sm));
+  int grid = tile_grid(ta, per_sm_for(sm));
+  if (!ta.whole) {  // the key kernel: as many CTAs as are resident
+    set_smem(k_list_keys<false, false, kListThreads>, sm);
+    grid = tile_grid(ta, resident_per_sm(k_list_keys<false, false, kListThreads>, kListThreads, sm));
+  }
 #define LJ_LIST_LAUNCH(M, H, W)                                                                                 \
   do {                                                                                                          \
     set_smem(k_list_tile<M, H, W>, sm);                                                                         \
@@ -1840,21 +2203,22 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
       else LJ_LIST_LAUNCH(false, false, true);
     }
   } else if (half) {  // tiles, either form: one thread per key on the hi copies (the list is the same)
-    set_smem(k_list_keys<true, false>, sm);
-    k_list_keys<true, false><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
+    set_smem(k_list_keys<true, false, kListThreads>, sm);
+    k_list_keys<true, false, kListThreads><<<grid, kListThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
                                                             counter, max_list, status, nullptr, 0, nullptr, nullptr);
   } else {
-    set_smem(k_list_keys<false, false>, sm);
-    k_list_keys<false, false><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
+    set_smem(k_list_keys<false, false, kListThreads>, sm);
+    k_list_keys<false, false, kListThreads><<<grid, kListThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
                                                              counter, max_list, status, nullptr, 0, nullptr, nullptr);
   }
 #undef LJ_LIST_LAUNCH
 }
 
+// Returns the grid launched (the number of energy partials written).
 template <bool MIXED, int LANES, bool HALF, bool ENERGY>
-static void force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
-                    const uint2* rows, const uint2* tl, const uint16_t* ent, void* f, double* part, int32_t* status,
-                    int nbuf, int grid, size_t sm, cudaStream_t s) {
+static int force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
+                   const uint2* rows, const uint2* tl, const uint16_t* ent, void* f, double* part, int32_t* status,
+                   int nbuf, int grid, size_t sm, cudaStream_t s) {
 #define LJ_FW(W, LONG)                                                                                           \
   do {                                                                                                           \
     set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, W, LONG>, sm);                                             \
@@ -1862,36 +2226,52 @@ static void force_w(const void* pos, const float4* lo, const uint32_t* cs, int64
                                                                                     rows, tl, ent, f, part, status, \
                                                                                     nbuf);                          \
   } while (0)
+  if constexpr (MIXED && !HALF) {
+    if (!ta.whole && nbuf == 2) {  // producer warp + consumer warps over two buffers
+#define LJ_FP(LONG)                                                                                              \
+  do {                                                                                                           \
+    set_smem(k_force_pipe<LANES, ENERGY, LONG>, sm);                                                             \
+    const int64_t want = (int64_t)sm_count() * resident_per_sm(k_force_pipe<LANES, ENERGY, LONG>, kPipeThreads, sm); \
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, ta.ntiles), (int64_t)kMaxRedBlocks));            \
+    k_force_pipe<LANES, ENERGY, LONG><<<grid, kPipeThreads, sm, s>>>((const float4*)pos, lo, cs, g, ta, c, rows, \
+                                                                     tl, ent, (float4*)f, part, status);          \
+  } while (0)
+      if (ta.list_cap < ta.max_list) LJ_FP(true);
+      else LJ_FP(false);
+#undef LJ_FP
+      return grid;
+    }
+  }
   if (ta.whole) LJ_FW(true, false);
   else if (ta.list_cap < ta.max_list) LJ_FW(false, true);  // some segments longer than the staged capacity
   else LJ_FW(false, false);
 #undef LJ_FW
+  return grid;
 }
 
 template <bool MIXED, int LANES>
-static void force_l(int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
-                    TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
-                    double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
+static int force_l(int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
+                   TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
+                   double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
   if (half) {
-    if (energy) force_w<MIXED, LANES, true, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    else force_w<MIXED, LANES, true, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-  } else {
-    if (energy) force_w<MIXED, LANES, false, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    else force_w<MIXED, LANES, false, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    if (energy) return force_w<MIXED, LANES, true, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    return force_w<MIXED, LANES, true, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
   }
+  if (energy) return force_w<MIXED, LANES, false, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+  return force_w<MIXED, LANES, false, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
 }
 
 template <bool MIXED>
-static void force_p(int lanes, int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N,
+static int force_p(int lanes, int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N,
                     Geom g, TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
                     double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
   switch (lanes) {
-    case 1: force_l<MIXED, 1>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
-    case 2: force_l<MIXED, 2>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
-    case 4: force_l<MIXED, 4>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
-    case 8: force_l<MIXED, 8>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
-    case 16: force_l<MIXED, 16>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
-    default: force_l<MIXED, 32>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s); break;
+    case 1: return force_l<MIXED, 1>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 2: return force_l<MIXED, 2>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 4: return force_l<MIXED, 4>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 8: return force_l<MIXED, 8>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 16: return force_l<MIXED, 16>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    default: return force_l<MIXED, 32>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
   }
 }
 
@@ -1903,10 +2283,10 @@ int launch_force_tile(int precision, int half, int lanes, int energy, const void
   if (per_sm <= 0) per_sm = per_sm_for(sm);
   const int grid = tile_grid(ta, per_sm);
   if (precision == LJ_MIXED)
-    force_p<true>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf, grid, sm, s);
-  else
-    force_p<false>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf, grid, sm, s);
-  return grid;
+    return force_p<true>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf,
+                         grid, sm, s);
+  return force_p<false>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf,
+                        grid, sm, s);
 }
 
 void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,
@@ -2018,9 +2398,9 @@ void launch_list_batch(const float4* hi, const double* x, const uint32_t* cs, in
                        unsigned long long* counter, unsigned int* max_list, int32_t* status, const ReplicaGeo* reps,
                        int R, const int32_t* tile_rep, const int* pred, cudaStream_t s) {
   const size_t sm = key_list_layout(caps).total;
-  const int grid = tile_grid(caps, per_sm_for(sm));
-  set_smem(k_list_keys<false, true>, sm);
-  k_list_keys<false, true><<<grid, kTileThreads, sm, s>>>(hi, x, cs, N, g, caps, band, rows, tile_list, ent, cap,
+  set_smem(k_list_keys<false, true, kListThreads>, sm);
+  const int grid = tile_grid(caps, resident_per_sm(k_list_keys<false, true, kListThreads>, kListThreads, sm));
+  k_list_keys<false, true, kListThreads><<<grid, kListThreads, sm, s>>>(hi, x, cs, N, g, caps, band, rows, tile_list, ent, cap,
                                                           counter, max_list, status, reps, R, pred, tile_rep);
 }
 

@@ -60,7 +60,7 @@ struct ljmd_sys {
   TileArgs ta{};
   int tile_T = 0;                // preferred cells per tile along z (0 = default)
   int force_per_sm = 0;          // force CTAs per SM (0 = as many as fit)
-  int force_nbuf = 1;            // tile buffers per force CTA (1 or 2)
+  int force_nbuf = 0;            // tile buffers per force CTA (1 or 2; 0 = default)
   uint32_t* scan_tmp = nullptr;
   size_t scan_tmp_cap = 0;
   int64_t cap_n = 0;       // particle capacity of the per-particle buffers
@@ -274,11 +274,12 @@ static int setup_geometry(ljmd_sys* s, double L) {
   c.c0f = (float)c0;
 
   // FP32 list filter on hi parts: each hi difference is exact and differs from the exact
-  // difference by at most eps = 2^(p-22) (two dropped lo parts and the split of L), so
+  // difference by at most eps = 2^(p-22) + 2^(p-24) (two dropped lo parts, the split of L and
+  // the rounding of an image shift of hi that leaves its binade), so
   // |r2f - r^2| <= eps (2 sqrt(3) r_s + 3 eps) + 4 ulp(r_s^2).  Twice that bound plus 1e-6
   // relative is the band around r_s^2 inside which the exact FP64 test decides.
   {
-    const double eps = ldexp(1.0, pw - 22);
+    const double eps = ldexp(1.0, pw - 22) + ldexp(1.0, pw - 24);
     const double bound = eps * (2.0 * sqrt(3.0) * rs + 3.0 * eps) + 4.0 * 1.2e-7 * rs * rs;
     const double band = 2.0 * bound + 1e-6 * rs * rs;
     s->band.rs2 = rs * rs;
@@ -378,6 +379,14 @@ static int ensure_tile_list(ljmd_sys* s) {
 
 // Tile geometry for the staged list/force kernels: T cells along z per tile, shared-memory
 // capacities from the actual largest tile of the current cell occupancy.
+// Tile buffers per force CTA: the requested number, else two for the mixed form with the full
+// list (the pipelined kernel: producer warps stage the next tile while consumer warps compute)
+// and one otherwise.
+static int force_buffers(const ljmd_sys* s) {
+  if (s->force_nbuf) return s->force_nbuf;
+  return (s->precision == LJ_MIXED && s->prm.list_form == LJ_LIST_FULL) ? 2 : 1;
+}
+
 static int choose_tiles(ljmd_sys* s, int t_cap) {
   ljmd_sys* sys = s;
   TileArgs& ta = s->ta;
@@ -510,9 +519,9 @@ static int rebuild(ljmd_sys* s) {
     // the force kernel stages a tile's list segment if it fits; longer segments are read from HBM
     TileArgs tz = s->ta;
     tz.list_cap = 0;
-    const size_t base_bytes = std::max(force_smem_bytes(tz, s->precision, s->force_nbuf, 1),
+    const size_t base_bytes = std::max(force_smem_bytes(tz, s->precision, force_buffers(s), 1),
                                        adjoint_smem_bytes(tz, s->precision));
-    const int nbuf = s->ta.whole ? 1 : (s->force_nbuf == 2 ? 2 : 1);
+    const int nbuf = s->ta.whole ? 1 : force_buffers(s);
     if (base_bytes <= (size_t)smem_max) {
       const int64_t room = ((int64_t)smem_max - (int64_t)base_bytes) / (2 * nbuf) - 16;
       s->ta.list_cap = (int32_t)std::max<int64_t>(0, std::min<int64_t>(s->ta.max_list, room) & ~(int64_t)7);
@@ -567,7 +576,7 @@ static int run_force(ljmd_sys* s, bool energy) {
     PhaseTimer timer(s, PH_FORCE);
     s->nb_force = launch_force_tile(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->lo, s->cell_start, s->n,
                                     s->g, s->ta, s->c, s->rows, s->tile_list, s->ent, s->f, s->part_force, s->d_status,
-                                    per_sm, s->force_nbuf, s->st);
+                                    per_sm, force_buffers(s), s->st);
   }
   s->launches += 1;
   CKL();
@@ -1030,9 +1039,8 @@ int ljmd_set_tuning(ljmd_sys* sys, int32_t tile_cells, int32_t lanes, int32_t fo
   }
   if (lanes) sys->prm.lanes = lanes;
   sys->force_per_sm = force_ctas_per_sm;
-  const int nbuf = force_buffers ? force_buffers : 1;
-  if (nbuf != sys->force_nbuf) {
-    sys->force_nbuf = nbuf;
+  if (force_buffers != sys->force_nbuf) {
+    sys->force_nbuf = force_buffers;
     sys->have_list = false;  // the tile shape is re-checked against the larger shared-memory use
     sys->forces_current = false;
   }

@@ -233,7 +233,7 @@ static int setup_replicas(ljmd_batch* b) {
   c.c0f = (float)c0;
   // band of the FP32 list filter and the displacement limit: the single-system derivation with
   // the batch's common p
-  const double eps = ldexp(1.0, pw - 22);
+  const double eps = ldexp(1.0, pw - 22) + ldexp(1.0, pw - 24);
   const double bound = eps * (2.0 * sqrt(3.0) * rs + 3.0 * eps) + 4.0 * 1.2e-7 * rs * rs;
   const double band = 2.0 * bound + 1e-6 * rs * rs;
   b->band.rs2 = rs * rs;

@@ -166,6 +166,26 @@ def test_forces_and_list_under_tuning_knobs(precision, list_form, tile, lanes, n
     assert np.array_equal(got, O.pairs_within(x, L, 3.0))
 
 
+@pytest.mark.parametrize("precision,list_form", FORMS)
+@pytest.mark.parametrize("nbuf", [1, 2])
+def test_forces_after_face_layer_drifts_below_offset(precision, list_form, nbuf):
+    """FCC start: one lattice layer lies exactly on each lower face, so within a few steps half of
+    it drifts below the position offset (the finer hi grid of the binade below) while the list
+    is kept; its +L images meet the upper-face layer at nearest-neighbour distance, where an
+    inexact image shift of hi would show as ~1e-4 relative force error."""
+    with _system(precision, list_form) as s:
+        s.set_tuning(0, 0, 0, nbuf)
+        s.init_lattice(8, 0.5, 1.0, 5)
+        s.step(0.005, 4)
+        x, _, gf, _ = s.get_state()
+        L = s.stats()["box"]
+        assert s.stats()["rebuilds"] == 1
+    assert (x.min(0) < 0).all()  # some particles left through every lower face
+    F, _, _ = O.forces(x, L)
+    rms = np.sqrt((F ** 2).sum(1).mean())
+    assert np.sqrt(((gf - F) ** 2).sum(1)).max() / rms <= FORCE_TOL[precision]
+
+
 @pytest.mark.parametrize("precision", [ljmd.LJ_MIXED, ljmd.LJ_FP64])
 def test_forces_dense_liquid(precision):
     x, v, L = thermal(8, 0.8, 0.9, 4)
