@@ -73,6 +73,41 @@ __device__ __forceinline__ bool finite_f(float v) {
   return (__float_as_int(v) & 0x7f800000) != 0x7f800000;
 }
 
+// Format conversions between binary32 and binary64 with integer operations only, so that they
+// take no slots of the FP64 pipe (2 operations per clock per SM on this part).  From the IEEE 754
+// layouts: binary32 has an 8-bit exponent with bias 127 and 23 stored mantissa bits, binary64 an
+// 11-bit exponent with bias 1023 and 52 stored mantissa bits.
+//
+// f32_to_f64: exact.  Zero keeps its sign; binary32 subnormals (below 1.2e-38) become zero of the
+// same sign; infinities and NaNs map to infinities and NaNs.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int u = (unsigned int)__float_as_int(f);
+  const unsigned int e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  unsigned long long bits = sign;
+  if (e == 0xffu) bits |= 0x7ff0000000000000ULL | ((unsigned long long)(u & 0x7fffffu) << 29);
+  else if (e != 0u) bits |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// f64_to_f32: rounded to nearest (ties away from zero) at the 24th significant bit.  Magnitudes
+// below 2^-126 give zero of the same sign, magnitudes that round to 2^128 or more give infinity;
+// infinities and NaNs map to infinities and NaNs.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0x7ff) return __int_as_float((int)(sign | 0x7f800000u | (unsigned int)((b >> 29) & 0x7fffffu) |
+                                              ((b & 0xfffffffffffffULL) ? 0x400000u : 0u)));
+  if (e < 1023 - 126) return __int_as_float((int)sign);
+  // exponent and top 23 mantissa bits, plus the rounding bit (bit 28); a carry into the exponent
+  // is the correct result (and gives infinity past the largest binary32)
+  unsigned int r = ((unsigned int)(e - 896) << 23) + (unsigned int)((b >> 29) & 0x7fffffu) +
+                   (unsigned int)((b >> 28) & 1u);
+  if (e - 896 >= 0xff || r >= 0x7f800000u) r = 0x7f800000u;
+  return __int_as_float((int)(sign | r));
+}
+
 // FP32 split of a stored coordinate x_state in [2^(p-1), 2^(p+1)):
 // hi = x_state truncated to 24 significant bits (exact as a float),
 // lo = x_state - hi rounded to FP32.  Integer operations only (no FP64 pipe):

@@ -8,6 +8,9 @@
 // last list construction is reduced (device-wide max) for the margin/2 validity rule.
 // State x, v is FP64 (positions stored as offset + x).  Per component the FP64 pipe does two
 // FMAs; the kinetic energy of the mixed form is taken in FP32 per particle and summed in FP64.
+// In the mixed form every FP32 <-> FP64 conversion is done with integer operations (exact for
+// FP32 -> FP64, rounded to nearest for FP64 -> FP32), which keeps the FP64 pipe for the seven
+// operations per particle that need it.
 #include "common.cuh"
 
 namespace ljmd {
@@ -25,11 +28,15 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
   bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     double F[3];
+    float Ff[3] = {0.0f, 0.0f, 0.0f};
     if (MIXED) {
       const float4 f = ((const float4*)fptr)[i];
-      F[0] = f.x;
-      F[1] = f.y;
-      F[2] = f.z;
+      Ff[0] = f.x;
+      Ff[1] = f.y;
+      Ff[2] = f.z;
+      F[0] = f32_to_f64(f.x);
+      F[1] = f32_to_f64(f.y);
+      F[2] = f32_to_f64(f.z);
     } else {
       const dvec4 f = ((const dvec4*)fptr)[i];
       F[0] = f.x;
@@ -44,7 +51,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
       double vk = v[k * N + i];
       if (a.ke) {
         if (MIXED) {
-          const float vf = fmaf(kpre_f, (float)F[k], (float)vk);
+          const float vf = fmaf(kpre_f, Ff[k], f64_to_f32(vk));
           ke_i = fmaf(vf, vf, ke_i);
         } else {
           const double vf = fma(a.kpre, F[k], vk);
@@ -52,7 +59,10 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
         }
       }
       if (kk != 0.0) vk = fma(kk, F[k], vk);
-      if (a.speed) vd2 = fmaf((float)vk, (float)vk, vd2);
+      if (a.speed) {
+        const float vs = MIXED ? f64_to_f32(vk) : (float)vk;
+        vd2 = fmaf(vs, vs, vd2);
+      }
       double xk = x[k * N + i];
       if (a.dt != 0.0) xk = fma(a.dt, vk, xk);
       v[k * N + i] = vk;
@@ -60,7 +70,8 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
       xs[k] = xk;
       bad |= !finite_d(xk) || !finite_d(vk);
     }
-    ke_acc += MIXED ? 0.5 * (double)ke_i : 0.5 * ke_d;
+    if (MIXED) ke_acc += f32_to_f64(0.5f * ke_i);  // exact halving and conversion, one FP64 add
+    else ke_acc += 0.5 * ke_d;
     if (a.shadow) {
       // speed of the drift (the velocity that moved the particle this step), for the DUTC rule
       v2max = fmaxf(v2max, vd2);
@@ -115,10 +126,27 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
   }
 }
 
+// Blocks of one resident wave (at most red_blocks(N)): the grid-stride loop then ends in step on
+// every SM instead of leaving a partial second wave.
+template <bool MIXED>
+static int one_wave(int64_t N) {
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<MIXED>, kRedThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  const int b = red_blocks(N);
+  return b < per_sm * sms ? b : per_sm * sms;
+}
+
 int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, float4* lo, const void* ref,
                      int64_t N, IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status,
                      cudaStream_t s) {
-  const int blocks = red_blocks(N);
+  const int blocks = precision == LJ_MIXED ? one_wave<true>(N) : one_wave<false>(N);
   if (precision == LJ_MIXED)
     k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, lo, ref, N, a, ke_part, dmax_bits, status);
   else
