@@ -1098,10 +1098,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
                                                 l, sh_gid[l], valid);
       }
       __syncthreads();
-      // phase B: row lengths (one warp per chunk)
+      // phase B: row lengths (one warp per chunk), and each unit's offset in its keys' rows
+      // (kept in the count area, which the unit path does not use otherwise, when it holds them)
+      int* s_upre = s_cnt;
+      const bool keep_pre = nu <= K.nch * kListItems;
       for (int c = warp; c < nc; c += kLW) {
         int len = 0;
-        for (int u = u_ub[c]; u < u_ub[c + 1]; ++u) len += __popc(s_mask[u * 32 + lane]);
+        for (int u = u_ub[c]; u < u_ub[c + 1]; ++u) {
+          if (keep_pre) s_upre[u * 32 + lane] = len;
+          len += __popc(s_mask[u * 32 + lane]);
+        }
         const int o = u_ck0[c] + lane;
         if (o < u_ck0[c + 1]) s_len[o] = len;
       }
@@ -1149,7 +1155,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
           const int o = u_ck0[c] + lane;
           if (o < u_ck0[c + 1]) {
             int p = s_kst[o];
-            for (int v = u_ub[c]; v < u; ++v) p += __popc(s_mask[v * 32 + lane]);
+            if (keep_pre) p += s_upre[u * 32 + lane];
+            else
+              for (int v = u_ub[c]; v < u; ++v) p += __popc(s_mask[v * 32 + lane]);
             uint32_t m = s_mask[u * 32 + lane];
             const int j0 = u_info[u] & 0xffff;
             while (m) {
