@@ -245,6 +245,20 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
 int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
 
 /*
+ * Budget of the bounded device-side waits, in SM clock cycles, for every system and batch of
+ * the process on the current device (0 restores the default of 4e9 cycles, about 2 s).  No
+ * counterpart in the paper: the waits are those of the staged tiles of the list, force and
+ * adjoint kernels (a tile's bulk copies) and of the pipelined force kernel (producer and
+ * consumer warps waiting for each other).  A wait that exceeds the budget records LJ_ST_TIMEOUT
+ * in the device status word and its CTA leaves after the copies it issued have landed (those
+ * final waits keep the default budget), so the call returns LJ_EDEVICE and the device stays
+ * usable.  A budget below the default also stops the waits from suspending, so a small budget
+ * makes them give up before their copies land: a test of the timeout paths.  Synchronises the
+ * device.  Errors: LJ_EINVAL (cycles < 0), LJ_EDEVICE (CUDA error).
+ */
+int ljmd_set_wait_budget(int64_t cycles);
+
+/*
  * Adjoint pass at the current positions over the current list (the list is built first if there
  * is none): hw = H(x) w, the Hessian of the potential energy (Eq. 2 summed over pairs with
  * r < r_c) times w, from the pair energy u(s) as a function of s = r^2:

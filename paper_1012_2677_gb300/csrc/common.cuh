@@ -179,14 +179,17 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity, uint32
   return r != 0;
 }
 
-// Wait for phase `parity` of bar to complete, giving up after `budget` clock cycles (false).
+constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz: a wait that long means a fault
+
+// Wait for phase `parity` of bar to complete, giving up after `budget` clock cycles (false).  A
+// budget below the default also drops the suspend hint, so that a short budget is not outlasted
+// by one suspended try_wait.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget) {
+  const uint32_t hint = budget < kWaitBudget ? 0u : 1000000u;
   const long long t0 = clock64();
-  while (!mbar_test(bar, parity))
+  while (!mbar_test(bar, parity, hint))
     if (clock64() - t0 > budget) return false;
   return true;
 }
-
-constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz: a wait that long means a fault
 
 }  // namespace ljmd

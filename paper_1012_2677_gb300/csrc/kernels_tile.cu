@@ -32,6 +32,12 @@ constexpr int kTileThreads = 256;
 constexpr int kWarps = kTileThreads / 32;
 constexpr int kMaxCells = 9 * (kMaxTileT + 2);
 
+// Budget of the waits for a tile's copies and for the other warps of the pipelined kernel (SM
+// clock cycles); the waits that let copies in flight land before a CTA leaves keep kWaitBudget.
+// Lowered only by ljmd_set_wait_budget, to drive the timeout paths in tests.
+__device__ long long g_wait_budget = kWaitBudget;
+__device__ __forceinline__ long long wait_budget() { return g_wait_budget; }
+
 struct TileInfo {
   int cx, cy, z0, Tp;
 };
@@ -354,7 +360,7 @@ __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs&
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // one thread polls the barrier; the others wait at the CTA barrier without taking issue slots
   bool ok = true;
-  if (threadIdx.x == 0) ok = mbar_wait(bar, phase, kWaitBudget);
+  if (threadIdx.x == 0) ok = mbar_wait(bar, phase, wait_budget());
   ok = __syncthreads_and(ok) != 0;
   if (!ok) {
     if (threadIdx.x == 0) {
@@ -1711,7 +1717,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
       unsigned char* buf = smem + b * buf_bytes;
       bool ok = true;
       if (k >= 2) {
-        if (lane == 0) ok = mbar_wait(&empty[b], (use - 1u) & 1u, kWaitBudget);
+        if (lane == 0) ok = mbar_wait(&empty[b], (use - 1u) & 1u, wait_budget());
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       }
       if (!ok) {  // the consumers did not release the buffer: give up (nothing in flight)
@@ -1740,7 +1746,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
       }
       if (staged) {
         bool landed = true;
-        if (lane == 0) landed = mbar_wait(&full[b], use & 1u, kWaitBudget);
+        if (lane == 0) landed = mbar_wait(&full[b], use & 1u, wait_budget());
         landed = __shfl_sync(0xffffffffu, landed ? 1 : 0, 0) != 0;
         if (!landed) {
           if (lane == 0) {
@@ -1765,7 +1771,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     for (int64_t t = blockIdx.x; t < ta.ntiles; t += stride, ++k) {
       const int b = k & 1, slot = k % kPipeSlots;
       const uint32_t use = (uint32_t)(k >> 1);
-      bool ok = __all_sync(0xffffffffu, mbar_wait(&ready[b], use & 1u, kWaitBudget)) != 0;
+      bool ok = __all_sync(0xffffffffu, mbar_wait(&ready[b], use & 1u, wait_budget())) != 0;
       if (!ok) {
         if (lane == 0) atomicOr(status, LJ_ST_TIMEOUT);
         break;
@@ -1777,7 +1783,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         stage_shift_consumers(s_ti[slot], ta, g, SS[slot], buf, L);
         __syncwarp();
         if (lane == 0) mbar_arrive(&shifted[b]);
-        ok = __all_sync(0xffffffffu, mbar_wait(&shifted[b], (shpar >> b) & 1u, kWaitBudget)) != 0;
+        ok = __all_sync(0xffffffffu, mbar_wait(&shifted[b], (shpar >> b) & 1u, wait_budget())) != 0;
         shpar ^= 1u << b;
         if (!ok) {
           if (lane == 0) atomicOr(status, LJ_ST_TIMEOUT);
@@ -2150,6 +2156,14 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Sets the budget of the bounded device waits (0: the default).  Synchronises the device.
+int set_wait_budget(long long cycles) {
+  const long long v = cycles > 0 ? cycles : kWaitBudget;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(g_wait_budget, &v, sizeof(v)) != cudaSuccess) return -1;
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
+}
+
 static int sm_count() {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);

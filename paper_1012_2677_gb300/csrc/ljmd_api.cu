@@ -1075,6 +1075,11 @@ int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out) {
 }
 
 
+int ljmd_set_wait_budget(int64_t cycles) {
+  if (cycles < 0) return LJ_EINVAL;
+  return set_wait_budget((long long)cycles) == 0 ? LJ_OK : LJ_EDEVICE;
+}
+
 int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
   if (!sys || !npairs || cap < 0 || (cap > 0 && !ij)) return LJ_EINVAL;
   if (sys->broken) return LJ_EDEVICE;

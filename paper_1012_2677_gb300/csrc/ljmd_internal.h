@@ -212,6 +212,8 @@ void launch_load_batch(const double* xin, const double* vin, double* x, double* 
                        int64_t N, const int32_t* rep_of, const ReplicaGeo* reps, double offset, cudaStream_t s);
 
 // ---- list validity (kernels_tile.cu) --------------------------------------------------------
+// Budget of the bounded device waits of the tile kernels (0: default); 0 on success.
+int set_wait_budget(long long cycles);
 void launch_ldc_collect(const double* x, const double* xref, int64_t N, double th2, int32_t* list, unsigned int cap,
                         unsigned int* count, cudaStream_t s);
 void launch_ldc_pairs(const double* x, const double* xref, int64_t N, Geom g, const int32_t* list, int m, double rs2,

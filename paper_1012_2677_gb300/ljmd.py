@@ -79,6 +79,7 @@ _SIGS = {
     "ljmd_energies": (ctypes.c_int, [_P, _P, _P, _P]),
     "ljmd_set_energy_log": (ctypes.c_int, [_P, _P, _I64]),
     "ljmd_get_pairs": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ljmd_set_wait_budget": (ctypes.c_int, [_I64]),
     "ljmd_get_pairs_static": (ctypes.c_int, [_P, _P, _I64, _P]),
     "ljmd_hvp": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
     "ljmd_set_validity": (ctypes.c_int, [_P, _I32, _I32]),
@@ -269,6 +270,11 @@ def ljmd_get_stats(h) -> dict:
     st = ljmd_stats()
     _chk(load().ljmd_get_stats(h, ctypes.byref(st)), "ljmd_get_stats")
     return {name: getattr(st, name) for name, _ in ljmd_stats._fields_}
+
+
+def ljmd_set_wait_budget(cycles: int) -> None:
+    """Budget of the bounded device waits in SM clock cycles (0: the default); a test knob."""
+    _chk(load().ljmd_set_wait_budget(int(cycles)), "ljmd_set_wait_budget")
 
 
 def ljmd_set_tuning(h, tile_cells: int = 0, lanes: int = 0, force_ctas_per_sm: int = 0, force_buffers: int = 0) -> None:

@@ -39,6 +39,7 @@ def test_argument_checks_before_any_device_work():
     for fn, args in (("ljmd_step", (None, 0.005, 1)), ("ljmd_compute_forces", (None,)),
                      ("ljmd_build_pairlist", (None, 2.5, 0.5)), ("ljmd_get_stats", (None, None))):
         assert getattr(lib, fn)(*args) == ljmd.LJ_EINVAL
+    assert lib.ljmd_set_wait_budget(-1) == ljmd.LJ_EINVAL
 
 
 def test_product_path_has_no_oracle_dependency():
