@@ -72,16 +72,24 @@ void launch_rebuild_flag(const uint32_t* dmax_bits, float limit2, int* flag, lon
 __global__ void k_set_flag(int* flag, int value) { *flag = value; }
 void launch_set_flag(int* flag, int value, cudaStream_t s) { k_set_flag<<<1, 1, 0, s>>>(flag, value); }
 
-// Predicated copy of `bytes` (a multiple of 4) from in to out.
+// Predicated copy of `bytes` (a multiple of 4) from in to out: 16-byte words while both
+// addresses are 16-byte aligned (the device allocations are), then the 4-byte tail.
 __global__ void k_copy_words(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
                              const int* __restrict__ pred) {
   if (pred && !*pred) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = in[i];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t n16 = 0;
+  if ((((uintptr_t)in | (uintptr_t)out) & 15u) == 0) {
+    n16 = n / 4;
+    const uint4* __restrict__ a = (const uint4*)in;
+    uint4* __restrict__ b = (uint4*)out;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += stride) b[i] = a[i];
+  }
+  for (int64_t i = 4 * n16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) out[i] = in[i];
 }
 void launch_copy_words(const void* in, void* out, int64_t bytes, const int* pred, cudaStream_t s) {
   const int64_t n = bytes / 4;
-  k_copy_words<<<grid_of(n), 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, n, pred);
+  k_copy_words<<<grid_of((n + 3) / 4), 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, n, pred);
 }
 
 // Predicated zero fill of `bytes` (a multiple of 4).
