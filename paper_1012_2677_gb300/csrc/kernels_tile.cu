@@ -1359,7 +1359,7 @@ __device__ __forceinline__ void pair_mixed(const float4& hi_i, const float4& lo_
 
 // Forces of the own particles of one staged tile (buffer `buf`); group `grp` of LANES threads per
 // key particle, lanes striding over its row.
-template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST, int UNR = 2>
+template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST, int UNR = 2, int NTH = kTileThreads>
 __device__ __forceinline__ void force_tile_compute(const TileShared& S, const unsigned char* buf, const TileLayout& L,
                                                    const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
                                                    const LJConst& c, const Geom& g, void* __restrict__ fout,
@@ -1372,7 +1372,7 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
   const uint16_t* s_ent = (const uint16_t*)(buf + L.ent);
   const int lane = threadIdx.x & (LANES - 1);
   const int grp = threadIdx.x / LANES;
-  constexpr int kGroups = kTileThreads / LANES;
+  constexpr int kGroups = NTH / LANES;  // groups of the computing threads
   const double f24d = 24.0 * c.eps, f48d = 48.0 * c.eps, f8c2d = 8.0 * c.eps * c.c2 / c.sig2;
   const double e4d = 4.0 * c.eps, c2sd = c.c2 / c.sig2;
   const int n_own = S.own1 - S.own0;
@@ -1636,10 +1636,9 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 //             the tile's own particles -> arrive empty[b].
 // Every wait is bounded; a producer that gives up marks the slot aborted and releases the
 // consumers, which then leave.  No copy is in flight when a warp leaves.
-constexpr int kPipeConsumers = kWarps;                 // consumer warps (the 256 threads of a tile)
 constexpr int kPipeProducers = 2;
-constexpr int kPipeThreads = kTileThreads + 32 * kPipeProducers;
 constexpr int kPipeSlots = 4;
+__host__ __device__ constexpr int pipe_threads(int cw) { return 32 * (cw + kPipeProducers); }
 
 __device__ __forceinline__ bool tile_interior(const TileInfo& ti, const TileArgs& ta) {
   return ti.cx >= 1 && ti.cx <= ta.n - 2 && ti.cy >= 1 && ti.cy <= ta.n - 2 && ti.z0 >= 1 && ti.z0 + ti.Tp <= ta.n - 1;
@@ -1650,9 +1649,10 @@ __device__ __forceinline__ bool tile_interior(const TileInfo& ti, const TileArgs
 // the caller then waits for all consumer warps (a bounded mbarrier wait, not bar.sync, so that a
 // warp that left on a timeout cannot hold the others forever).
 __device__ __forceinline__ void stage_shift_consumers(const TileInfo& ti, const TileArgs& ta, const Geom& g,
-                                                      const TileShared& S, unsigned char* smem, const TileLayout& L) {
+                                                      const TileShared& S, unsigned char* smem, const TileLayout& L,
+                                                      int consumers) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int q = warp; q < S.ncell; q += kPipeConsumers) {
+  for (int q = warp; q < S.ncell; q += consumers) {
     int sx, sy, sz;
     cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
     if ((sx | sy | sz) == 0) continue;
@@ -1671,8 +1671,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-template <int LANES, bool ENERGY, bool LONGLIST>
-__global__ void __launch_bounds__(kPipeThreads, 2)
+// CW consumer warps: 8 for tiles of up to 4 cells, 12 for larger tiles (more keys per tile).
+template <int LANES, bool ENERGY, bool LONGLIST, int CW>
+__global__ void __launch_bounds__(pipe_threads(CW), 2)
     k_force_pipe(const float4* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
                  Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
                  const uint16_t* __restrict__ ent, float4* __restrict__ fout, double* __restrict__ part,
@@ -1689,17 +1690,17 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&full[b], 1);
       mbar_init(&ready[b], 1);
-      mbar_init(&empty[b], kPipeConsumers);
-      mbar_init(&shifted[b], kPipeConsumers);
+      mbar_init(&empty[b], CW);
+      mbar_init(&shifted[b], CW);
     }
     fence_proxy_async_smem();
   }
   __syncthreads();
   double pe_acc = 0.0, vir_acc = 0.0;
   const int64_t stride = gridDim.x;
-  if (warp >= kPipeConsumers) {
+  if (warp >= CW) {
     // ---- producer p: tiles k = p, p + 2, ... in buffer p ----
-    const int p = warp - kPipeConsumers, b = p;
+    const int p = warp - CW, b = p;
     int64_t t = blockIdx.x + p * stride;
     TilePrefetch pf;
     bool ok_next = false;
@@ -1780,7 +1781,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
       if (v < 0) break;
       unsigned char* buf = smem + b * buf_bytes;
       if (v == 2) {  // periodic tile: shifts by all consumer warps, then wait for all of them
-        stage_shift_consumers(s_ti[slot], ta, g, SS[slot], buf, L);
+        stage_shift_consumers(s_ti[slot], ta, g, SS[slot], buf, L, CW);
         __syncwarp();
         if (lane == 0) mbar_arrive(&shifted[b]);
         ok = __all_sync(0xffffffffu, mbar_wait(&shifted[b], (shpar >> b) & 1u, wait_budget())) != 0;
@@ -1791,8 +1792,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         }
       }
       if (v > 0)
-        force_tile_compute<true, LANES, false, ENERGY, false, LONGLIST>(SS[slot], buf, L, rows, ent, c, g, fout, status,
-                                                                        pe_acc, vir_acc, ta.list_cap);
+        force_tile_compute<true, LANES, false, ENERGY, false, LONGLIST, 2, 32 * CW>(SS[slot], buf, L, rows, ent, c, g,
+                                                                                    fout, status, pe_acc, vir_acc,
+                                                                                    ta.list_cap);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
     }
@@ -2250,16 +2252,23 @@ static int force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_
   } while (0)
   if constexpr (MIXED && !HALF) {
     if (!ta.whole && nbuf == 2) {  // producer warp + consumer warps over two buffers
-#define LJ_FP(LONG)                                                                                              \
+#define LJ_FP(LONG, CW)                                                                                          \
   do {                                                                                                           \
-    set_smem(k_force_pipe<LANES, ENERGY, LONG>, sm);                                                             \
-    const int64_t want = (int64_t)sm_count() * resident_per_sm(k_force_pipe<LANES, ENERGY, LONG>, kPipeThreads, sm); \
-    grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, ta.ntiles), (int64_t)kMaxRedBlocks));            \
-    k_force_pipe<LANES, ENERGY, LONG><<<grid, kPipeThreads, sm, s>>>((const float4*)pos, lo, cs, g, ta, c, rows, \
-                                                                     tl, ent, (float4*)f, part, status);          \
+    set_smem(k_force_pipe<LANES, ENERGY, LONG, CW>, sm);                                                         \
+    const int64_t want =                                                                                         \
+        (int64_t)sm_count() * resident_per_sm(k_force_pipe<LANES, ENERGY, LONG, CW>, pipe_threads(CW), sm);     \
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, ta.ntiles), (int64_t)kMaxRedBlocks)); \
+    k_force_pipe<LANES, ENERGY, LONG, CW><<<grid, pipe_threads(CW), sm, s>>>((const float4*)pos, lo, cs, g, ta, c, \
+                                                                             rows, tl, ent, (float4*)f, part, status); \
   } while (0)
-      if (ta.list_cap < ta.max_list) LJ_FP(true);
-      else LJ_FP(false);
+      const bool lg = ta.list_cap < ta.max_list;
+      if (ta.T <= 4) {
+        if (lg) LJ_FP(true, 8);
+        else LJ_FP(false, 8);
+      } else {
+        if (lg) LJ_FP(true, 12);
+        else LJ_FP(false, 12);
+      }
 #undef LJ_FP
       return grid;
     }
