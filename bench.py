@@ -183,7 +183,7 @@ def run_ours(args, wl, world, rank, local):
         if dist is not None:
             dist.barrier()
 
-    s = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=ljmd.LJ_MIXED, list_form=ljmd.LJ_LIST_FULL,
+    s = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=ljmd.LJ_MIXED, list_form=ljmd.LJ_LIST_AUTO,
                     energy_every=1, stream=stream)
     s.init_lattice(wl["M"], wl["rho"], wl["T"], seed)
     N = s.n
@@ -219,7 +219,9 @@ def run_ours(args, wl, world, rank, local):
     ach_tf = fl / (f_ms * 1e-3) / 1e12
     hbm_frac = ach_gbs / peaks["hbm_gbs"]
     alu_frac = ach_tf / FP32_PEAK_TFLOPS
-    kernel_name = "k_force_pipe"  # the mixed form with the full list on tiles: the pipelined kernel
+    half = st1["list_form"] == ljmd.LJ_LIST_HALF  # the automatic list form of this density
+    # the mixed form on tiles: the pipelined kernel with the full list, the single-buffer one with the half
+    kernel_name = "k_force_tile" if half else "k_force_pipe"
     traffic = recorded_traffic(kernel_name, N)
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": round(ach_tf, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
@@ -266,7 +268,7 @@ def run_ours(args, wl, world, rank, local):
     e2e = None
     if not args.no_e2e:
         s2 = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=ljmd.LJ_MIXED,
-                         list_form=ljmd.LJ_LIST_FULL, energy_every=1, stream=stream)
+                         list_form=ljmd.LJ_LIST_AUTO, energy_every=1, stream=stream)
         s2.init_lattice(wl["M"], wl["rho"], wl["T"], seed)
         x0 = torch.empty((N, 3), dtype=torch.float64).pin_memory()
         v0 = torch.empty((N, 3), dtype=torch.float64).pin_memory()
@@ -298,7 +300,8 @@ def run_ours(args, wl, world, rank, local):
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 pair arithmetic, f64 state and sums", "data": "synthetic FCC start, Gaussian velocities",
         "config": {"workload": args.workload, "N": N, "density": wl["rho"], "T": wl["T"], "cutoff": wl["cutoff"],
-                   "margin": wl["margin"], "dt": wl["dt"], "list": "full", "parallelism": "replicas x%d" % world,
+                   "margin": wl["margin"], "dt": wl["dt"], "list": "half" if half else "full",
+                   "parallelism": "replicas x%d" % world,
                    "l2": "inputs larger than L2 (state and list ~%.1f GB)" % ((N * 250 + 4 * entries) / 1e9)},
         "roofline": roof,
         "fp64": fp64,

@@ -54,6 +54,12 @@ extern "C" {
 /* ---- pair-list forms ---- */
 #define LJ_LIST_FULL 0  /* every particle lists all partners; force kernel writes without atomics */
 #define LJ_LIST_HALF 1  /* each pair once, key = lower index (Sec. 2.4); Newton-3 scatter with atomics */
+/* The form chosen per box: the half list in the FP64 form and, in the mixed form, when the full list
+ * would hold 75 or more partners per particle ((4/3) pi r_s^3 N / L^3), the full list otherwise.
+ * The crossover was measured on GB300 at 16.4M particles, r_s = 3.0: the full list is faster at
+ * density 0.5 (56 partners per particle; force 3.04 against 3.91 ms), the half list at density
+ * 0.8 (87 partners; 4.60 against 5.26 ms).  ljmd_stats.list_form reports the form in use. */
+#define LJ_LIST_AUTO 2
 
 /* ---- list validity rules (Sec. 2.3, Alg. 2) ---- */
 #define LJ_VALID_HALF_MARGIN 0     /* rebuild when the largest displacement since the build > margin/2 */
@@ -72,7 +78,7 @@ typedef struct ljmd_params {
   double cutoff;       /* r_c (absolute length), > 0 */
   double margin;       /* r_s - r_c (Sec. 2.3), >= 0 */
   int32_t truncation;  /* LJ_TRUNC_* */
-  int32_t list_form;   /* LJ_LIST_FULL or LJ_LIST_HALF */
+  int32_t list_form;   /* LJ_LIST_FULL, LJ_LIST_HALF or LJ_LIST_AUTO */
   int32_t energy_every; /* inside ljmd_step: evaluate PE and virial every k-th step (0 = only on request) */
   int32_t lanes;       /* threads per key particle in the force kernel: 1,2,4,8,16,32; 0 = tuned default */
 } ljmd_params;
@@ -92,7 +98,7 @@ typedef struct ljmd_stats {
   int64_t ldc_checks;      /* large displacement checks run (LDC rules) */
   int64_t ldc_kept;        /* of those, checks that kept the list */
   int32_t validity;        /* LJ_VALID_* rule in use */
-  int32_t pad;
+  int32_t list_form;       /* LJ_LIST_FULL or LJ_LIST_HALF: the form in use (LJ_LIST_AUTO resolved) */
 } ljmd_stats;
 
 /* Per-phase device time (CUDA events on the handle's stream), accumulated while profiling is on. */
@@ -268,7 +274,10 @@ int ljmd_set_wait_budget(int64_t cycles);
  * (the truncation constants c2, c0 of Eq. 2 stay fixed).  w and hw are 3N FP64 in id order, host
  * (on_device = 0) or device (1).  The paper has no adjoint; this differentiates its pair force.
  * Mixed form: FP32 pair arithmetic, FP64 results.  Synchronises the stream.
- * Errors: LJ_EINVAL (NULL w or hw), LJ_ESTATE (no particles), LJ_ENOMEM, LJ_EDEVICE.
+ * The adjoint needs the full list: a handle created with LJ_LIST_HALF gets LJ_ESTATE, and one
+ * created with LJ_LIST_AUTO uses the full list from this call on.
+ * Errors: LJ_EINVAL (NULL w or hw), LJ_ESTATE (no particles, or an LJ_LIST_HALF handle),
+ * LJ_ENOMEM, LJ_EDEVICE.
  */
 int ljmd_hvp(ljmd_sys* sys, const double* w, double* hw, double* dtheta, int32_t on_device);
 
@@ -283,8 +292,9 @@ int ljmd_hvp(ljmd_sys* sys, const double* w, double* hw, double* dtheta, int32_t
  * checkpoint stored in the forward run.  Arrays are host (on_device = 0) or device (1).  The
  * handle's state is replaced (it ends at x0 of the last recomputed segment).  The paper has no
  * adjoint; this differentiates its integrator and pair force.  Synchronises the stream.
+ * Like ljmd_hvp it needs the full list (LJ_LIST_HALF: LJ_ESTATE; LJ_LIST_AUTO: full from now on).
  * Errors: LJ_EINVAL (n <= 0, nsteps < 1, n_pe outside [0, nsteps], ckpt_every < 1, NULL x0, v0 or
- * loss, box too small), LJ_ENOMEM, LJ_EDEVICE.
+ * loss, box too small), LJ_ESTATE (an LJ_LIST_HALF handle), LJ_ENOMEM, LJ_EDEVICE.
  */
 int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, const double* v0, double dt,
                         int64_t nsteps, int64_t n_pe, int64_t ckpt_every, double* loss, double* gx0, double* gv0,

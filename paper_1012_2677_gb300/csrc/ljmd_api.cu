@@ -61,6 +61,7 @@ struct ljmd_sys {
   int tile_T = 0;                // preferred cells per tile along z (0 = default)
   int force_per_sm = 0;          // force CTAs per SM (0 = as many as fit)
   int force_nbuf = 0;            // tile buffers per force CTA (1 or 2; 0 = default)
+  bool list_half = false;        // the list form in use (LJ_LIST_AUTO resolved)
   uint32_t* scan_tmp = nullptr;
   size_t scan_tmp_cap = 0;
   int64_t cap_n = 0;       // particle capacity of the per-particle buffers
@@ -220,7 +221,7 @@ static void truncation_terms(double x, int mode, double* c2, double* c0) {
 static int check_params(const ljmd_params* p) {
   if (!(p->cutoff > 0.0) || !(p->margin >= 0.0) || !(p->eps > 0.0) || !(p->sigma > 0.0)) return LJ_EINVAL;
   if (p->truncation < 0 || p->truncation > 2) return LJ_EINVAL;
-  if (p->list_form != LJ_LIST_FULL && p->list_form != LJ_LIST_HALF) return LJ_EINVAL;
+  if (p->list_form != LJ_LIST_FULL && p->list_form != LJ_LIST_HALF && p->list_form != LJ_LIST_AUTO) return LJ_EINVAL;
   if (p->energy_every < 0) return LJ_EINVAL;
   const int l = p->lanes;
   if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32)) return LJ_EINVAL;
@@ -291,6 +292,36 @@ static int setup_geometry(ljmd_sys* s, double L) {
   // <= 2^(p-23) per component), so the limit is lowered by twice that bound.
   const double slack = (s->precision == LJ_MIXED) ? 2.0 * sqrt(3.0) * ldexp(1.0, pw - 23) + 1e-6 : 1e-12;
   s->disp_limit = 0.5 * p.margin - slack;
+  return LJ_OK;
+}
+
+// The list form in use.  LJ_LIST_AUTO takes the half list in the FP64 form (its pair arithmetic
+// runs on the FP64 pipe, so halving the pairs pays for the atomics) and, in the mixed form, when
+// the full list would hold 75 or more partners per particle, (4/3) pi r_s^3 N / L^3: the crossover
+// measured on GB300 at 16.4M particles (full list faster at 56 partners, rho = 0.5; half list
+// faster at 87, rho = 0.8).  A change of form invalidates the list.
+static void resolve_list_form(ljmd_sys* s) {
+  bool half = s->prm.list_form == LJ_LIST_HALF;
+  if (s->prm.list_form == LJ_LIST_AUTO) {
+    const double per = 4.18879020478639 * s->rs * s->rs * s->rs * (double)s->n / (s->L * s->L * s->L);
+    half = s->precision != LJ_MIXED || per >= 75.0;
+  }
+  if (half != s->list_half) {
+    s->list_half = half;
+    s->have_list = false;
+    s->forces_current = false;
+  }
+}
+
+// The adjoint kernel writes each key's Hessian-vector row from the key's own list row, so it
+// needs the full list.  An explicit half list is refused (LJ_ESTATE); LJ_LIST_AUTO is fixed to the
+// full list from then on.
+static int adjoint_list_form(ljmd_sys* s) {
+  if (s->prm.list_form == LJ_LIST_HALF) return LJ_ESTATE;
+  if (s->prm.list_form == LJ_LIST_AUTO) {
+    s->prm.list_form = LJ_LIST_FULL;
+    resolve_list_form(s);
+  }
   return LJ_OK;
 }
 
@@ -384,7 +415,7 @@ static int ensure_tile_list(ljmd_sys* s) {
 // and one otherwise.
 static int force_buffers(const ljmd_sys* s) {
   if (s->force_nbuf) return s->force_nbuf;
-  return (s->precision == LJ_MIXED && s->prm.list_form == LJ_LIST_FULL) ? 2 : 1;
+  return (s->precision == LJ_MIXED && !s->list_half) ? 2 : 1;
 }
 
 static int choose_tiles(ljmd_sys* s, int t_cap) {
@@ -466,7 +497,7 @@ static int rebuild(ljmd_sys* s) {
   std::swap(s->f, s->f_alt);
   launch_shadow_all(s->x, N, s->precision == LJ_MIXED, s->hi, s->lo, s->pos64, s->ref, st);
   CKL();
-  const int half = s->prm.list_form == LJ_LIST_HALF;
+  const int half = s->list_half ? 1 : 0;
   uint64_t total = 0;
   int dev = 0, smem_max = 0;
   cudaGetDevice(&dev);
@@ -558,7 +589,7 @@ static int integrate(ljmd_sys* s, IntegrateArgs a) {
 static void energy_record(ljmd_sys* s, int nb_ke, bool to_log) {
   PhaseTimer timer(s, PH_ENERGY);
   s->launches += 1;
-  const double scale = s->prm.list_form == LJ_LIST_FULL ? 0.5 : 1.0;
+  const double scale = s->list_half ? 1.0 : 0.5;
   launch_energy_finalize(s->part_force, s->nb_force, s->part_ke, nb_ke, scale, s->d_energies,
                          to_log ? s->log_ptr : nullptr, to_log ? s->log_cap : 0, s->d_log_count, (double)s->steps,
                          s->st);
@@ -567,7 +598,7 @@ static void energy_record(ljmd_sys* s, int nb_ke, bool to_log) {
 
 static int run_force(ljmd_sys* s, bool energy) {
   ljmd_sys* sys = s;
-  const int half = s->prm.list_form == LJ_LIST_HALF;
+  const int half = s->list_half ? 1 : 0;
   if (half) CK(cudaMemsetAsync(s->f, 0, (s->precision == LJ_MIXED ? 16 : 32) * (size_t)s->n, s->st));
   int lanes = s->prm.lanes;
   if (lanes == 0) lanes = 4;
@@ -755,6 +786,7 @@ int ljmd_init_lattice(ljmd_sys* sys, int64_t M, double density, double T, uint64
   TRY(setup_geometry(sys, a * (double)M));
   TRY(ensure_particles(sys, N));
   sys->n = N;
+  resolve_list_form(sys);
   TRY(ensure_cells(sys));
   reset_counters(sys);
   launch_fcc(sys->x, M, a, sys->g.offset, sys->st);
@@ -782,6 +814,7 @@ int ljmd_set_state(ljmd_sys* sys, int64_t n, double box, const double* x, const 
   TRY(setup_geometry(sys, box));
   TRY(ensure_particles(sys, n));
   sys->n = n;
+  resolve_list_form(sys);
   TRY(ensure_cells(sys));
   reset_counters(sys);
   const double* xs = x;
@@ -853,6 +886,7 @@ int ljmd_build_pairlist(ljmd_sys* sys, double cutoff, double margin) {
     return r;
   }
   sys->forces_current = false;
+  resolve_list_form(sys);
   TRY(rebuild(sys));
   return LJ_OK;
 }
@@ -973,7 +1007,7 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
     return LJ_EDEVICE;
   }
   std::vector<std::pair<int64_t, int64_t>> pairs;
-  pairs.reserve(sys->prm.list_form == LJ_LIST_FULL ? sys->list_actual / 2 : sys->list_actual);
+  pairs.reserve(!sys->list_half ? sys->list_actual / 2 : sys->list_actual);
   for (uint64_t k = 0; k < E; ++k) {
     if (pr[2 * k] == 0xffffffffu) continue;  // padding between tile segments
     if (pr[2 * k] >= (uint64_t)N || pr[2 * k + 1] >= (uint64_t)N) {
@@ -982,7 +1016,7 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
       return LJ_EDEVICE;
     }
     const int64_t a = id[pr[2 * k]], b = id[pr[2 * k + 1]];
-    if (sys->prm.list_form == LJ_LIST_FULL) {
+    if (!sys->list_half) {
       if (a < b) pairs.emplace_back(a, b);
     } else {
       pairs.emplace_back(std::min(a, b), std::max(a, b));
@@ -1014,6 +1048,7 @@ int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
   out->ldc_checks = sys->ldc_checks;
   out->ldc_kept = sys->ldc_kept;
   out->validity = sys->valid_mode;
+  out->list_form = sys->list_half ? LJ_LIST_HALF : LJ_LIST_FULL;
   if (sys->broken) {
     out->status_word = -1;
     return LJ_EDEVICE;
@@ -1108,7 +1143,7 @@ int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npai
   launch_list_decode(sys->cell_start, sys->n, sys->ta, sys->rows, sys->ent, E, (uint32_t*)keys, sys->d_status,
                      sys->st);
   CKL();
-  launch_entries_to_keys(keys, E, sys->id, sys->n, sys->prm.list_form == LJ_LIST_FULL ? 1 : 0,
+  launch_entries_to_keys(keys, E, sys->id, sys->n, !sys->list_half ? 1 : 0,
                          (unsigned int*)counter, sys->d_status, sys->st);
   CKL();
   sys->launches += 2 + launch_bitonic_sort(keys, P, sys->st);
@@ -1201,6 +1236,7 @@ int ljmd_hvp(ljmd_sys* sys, const double* w, double* hw, double* dtheta, int32_t
   if (!sys || !w || !hw) return LJ_EINVAL;
   if (sys->broken) return LJ_EDEVICE;
   if (sys->n <= 0) return LJ_ESTATE;
+  TRY(adjoint_list_form(sys));
   const int64_t N = sys->n;
   const size_t bytes = sizeof(double) * 3 * (size_t)N;
   DevBuf<double> wd, hd;
@@ -1236,6 +1272,7 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
       !isfinite(dt))
     return LJ_EINVAL;
   if (sys->broken) return LJ_EDEVICE;
+  TRY(adjoint_list_form(sys));
   const size_t n3 = 3 * (size_t)n;
   const size_t bytes = sizeof(double) * n3;
   const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;

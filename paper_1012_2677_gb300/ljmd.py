@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ljmd.h")
 
 LJ_OK, LJ_EINVAL, LJ_ENOMEM, LJ_EDEVICE, LJ_ESTATE, LJ_ERANGE = 0, -1, -2, -3, -4, -5
 LJ_FP64, LJ_MIXED = 0, 1
-LJ_LIST_FULL, LJ_LIST_HALF = 0, 1
+LJ_LIST_FULL, LJ_LIST_HALF, LJ_LIST_AUTO = 0, 1, 2
 LJ_TRUNC_QUADRATIC, LJ_TRUNC_SHIFT, LJ_TRUNC_CUT = 0, 1, 2
 LJ_VALID_HALF_MARGIN, LJ_VALID_DUTC, LJ_VALID_DUTC_LDC, LJ_VALID_HALF_MARGIN_LDC = 0, 1, 2, 3
 LJ_PAIRS_STATIC_MAX_ENTRIES = 524288  # static scratch of ljmd_get_pairs_static, in list entries
@@ -45,7 +45,7 @@ class ljmd_stats(ctypes.Structure):
                 ("mean_lifetime", ctypes.c_double), ("max_displacement", ctypes.c_double),
                 ("status_word", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("ldc_checks", ctypes.c_int64), ("ldc_kept", ctypes.c_int64),
-                ("validity", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("validity", ctypes.c_int32), ("list_form", ctypes.c_int32)]
 
 
 class ljmd_profile(ctypes.Structure):

@@ -186,6 +186,50 @@ def test_forces_after_face_layer_drifts_below_offset(precision, list_form, nbuf)
     assert np.sqrt(((gf - F) ** 2).sum(1)).max() / rms <= FORCE_TOL[precision]
 
 
+@pytest.mark.parametrize("precision,rho,expect", [(ljmd.LJ_MIXED, 0.5, ljmd.LJ_LIST_FULL),
+                                                  (ljmd.LJ_MIXED, 0.8, ljmd.LJ_LIST_HALF),
+                                                  (ljmd.LJ_FP64, 0.5, ljmd.LJ_LIST_HALF)])
+def test_auto_list_form(precision, rho, expect):
+    """LJ_LIST_AUTO: the full list in the mixed form below 75 full-list partners per particle
+    ((4/3) pi r_s^3 rho: 56.5 at rho 0.5, 90 at rho 0.8), the half list above and in the FP64 form;
+    forces, energies and the pair set are the oracle's either way."""
+    x, v, L = thermal(8, rho, 1.0, 6)
+    F, pe, vir = O.forces(x, L)
+    with _system(precision, ljmd.LJ_LIST_AUTO) as s:
+        s.set_state(x, v, L)
+        s.compute_forces()
+        st = s.stats()
+        _, _, gf, _ = s.get_state()
+        gpe, _, gvir = s.energies()
+        got = s.pairs()
+    assert st["list_form"] == expect
+    rms = np.sqrt((F ** 2).sum(1).mean())
+    assert np.sqrt(((gf - F) ** 2).sum(1)).max() / rms <= FORCE_TOL[precision]
+    etol = 1e-6 if precision == ljmd.LJ_MIXED else 1e-12
+    assert gpe == pytest.approx(pe, rel=etol) and gvir == pytest.approx(vir, rel=etol)
+    assert np.array_equal(got, O.pairs_within(x, L, 3.0))
+
+
+def test_adjoint_requires_the_full_list():
+    """The adjoint kernel reads every partner of a key from the key's own row: an explicit half
+    list is refused, an automatic one switches to the full list and the HVP is the oracle's."""
+    x, v, L = thermal(8, 0.8, 1.0, 6)
+    w = np.random.default_rng(12).normal(size=x.shape)
+    with _system(ljmd.LJ_MIXED, ljmd.LJ_LIST_HALF) as s:
+        s.set_state(x, v, L)
+        with pytest.raises(ljmd.LjmdError) as e:
+            s.hvp(w)
+        assert e.value.code == ljmd.LJ_ESTATE
+    ref = O.hvp(x, L, w)
+    with _system(ljmd.LJ_MIXED, ljmd.LJ_LIST_AUTO) as s:
+        s.set_state(x, v, L)
+        assert s.stats()["list_form"] == ljmd.LJ_LIST_HALF
+        hw, _ = s.hvp(w)
+        assert s.stats()["list_form"] == ljmd.LJ_LIST_FULL
+    rms = np.sqrt((ref ** 2).sum(1).mean())
+    assert np.sqrt(((hw - ref) ** 2).sum(1)).max() / rms <= 2e-4
+
+
 @pytest.mark.parametrize("precision", [ljmd.LJ_MIXED, ljmd.LJ_FP64])
 def test_forces_dense_liquid(precision):
     x, v, L = thermal(8, 0.8, 0.9, 4)
