@@ -1318,6 +1318,16 @@ __device__ __forceinline__ float rcp_nr(float x) {
   return fmaf(r, fmaf(-x, r, 1.0f), r);
 }
 
+// 1/x in FP64 from the hardware approximation (rcp.approx.ftz.f64) refined by two Newton-Raphson
+// steps r' = r + r (1 - x r), each of which squares the relative error: full double precision to
+// within an ulp, in a handful of FP64 operations instead of a correctly rounded reciprocal.
+__device__ __forceinline__ double rcp_nr64(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
 struct AccF {
   float fx, fy, fz, pe, vir;
 };
@@ -1454,7 +1464,7 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
             dz = fma(-rint(dz * g.inv_L64), g.L, dz);
           }
           const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-          const double ri2 = __drcp_rn(r2);
+          const double ri2 = rcp_nr64(r2);
           const double si = c.sig2 * ri2;
           const double s3i = si * si * si;
           const bool in = r2 < c.rc2;
