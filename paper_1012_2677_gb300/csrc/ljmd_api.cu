@@ -1171,7 +1171,6 @@ int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npai
 }  // extern "C"
 
 static int ensure_adjoint(ljmd_sys* s) {
-  ljmd_sys* sys = s;
   if (s->adj_cap < s->n) {
     TRY(dalloc_t(s, &s->adj_w, s->n));
     TRY(dalloc_t(s, &s->adj_hw, s->n));
@@ -1180,7 +1179,6 @@ static int ensure_adjoint(ljmd_sys* s) {
   }
   if (!s->part_adj) TRY(dalloc_t(s, &s->part_adj, 5 * (size_t)kMaxRedBlocks));
   if (!s->d_adj) TRY(dalloc_t(s, &s->d_adj, 8));
-  (void)sys;
   return LJ_OK;
 }
 
