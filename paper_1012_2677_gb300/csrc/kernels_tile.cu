@@ -1654,6 +1654,25 @@ __device__ __forceinline__ bool tile_interior(const TileInfo& ti, const TileArgs
   return ti.cx >= 1 && ti.cx <= ta.n - 2 && ti.cy >= 1 && ti.cy <= ta.n - 2 && ti.z0 >= 1 && ti.z0 + ti.Tp <= ta.n - 1;
 }
 
+// Shift codes (FP64 form: every slot's w holds (sx + 1) + 3 (sy + 1) + 9 (sz + 1)) and, for the
+// half list, the sorted indices of a staged tile, written by one producer warp after the copies
+// land (the pipelined kernel's version of stage_finish for the FP64 form).
+__device__ __forceinline__ void stage_codes_warp(const TileInfo& ti, const TileArgs& ta, const TileShared& S,
+                                                 unsigned char* smem, const TileLayout& L, bool want_gid,
+                                                 int lane) {
+  const bool interior = tile_interior(ti, ta);
+  for (int q = 0; q < S.ncell; ++q) {
+    int sx = 0, sy = 0, sz = 0;
+    if (!interior) cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
+    const double code = (double)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
+    const int a = S.offq[q], b = S.offq[q + 1], gq = S.g0[q];
+    for (int e = a + lane; e < b; e += 32) {
+      ((dvec4*)(smem + L.pos))[e].w = code;
+      if (want_gid) ((int*)(smem + L.gid))[e] = gq + (e - a);
+    }
+  }
+}
+
 // Image shifts of a staged tile's periodic cells by the consumer warps (warp per cell, lanes over
 // its particles).  Every writer orders its writes before later bulk copies into the same bytes;
 // the caller then waits for all consumer warps (a bounded mbarrier wait, not bar.sync, so that a
@@ -1682,18 +1701,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // CW consumer warps: 8 for tiles of up to 4 cells, 12 for larger tiles (more keys per tile).
-template <int LANES, bool ENERGY, bool LONGLIST, int CW>
+// Forms: the mixed form with the full list (consumers apply the image shifts of periodic tiles)
+// and the FP64 form with the half list (the producer writes the shift codes and sorted indices;
+// the consumers scatter the partners' forces with atomics).
+template <bool MIXED, bool HALF, int LANES, bool ENERGY, bool LONGLIST, int CW>
 __global__ void __launch_bounds__(pipe_threads(CW), 2)
-    k_force_pipe(const float4* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
+    k_force_pipe(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
                  Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
-                 const uint16_t* __restrict__ ent, float4* __restrict__ fout, double* __restrict__ part,
+                 const uint16_t* __restrict__ ent, void* __restrict__ fout, double* __restrict__ part,
                  int32_t* __restrict__ status) {
+  static_assert(MIXED != HALF, "pipelined forms: mixed with the full list, FP64 with the half list");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared SS[kPipeSlots];
   __shared__ TileInfo s_ti[kPipeSlots];
   __shared__ int s_valid[kPipeSlots];  // 1: interior tile, 2: periodic tile (shifts), 0: skip, -1: abort
   __shared__ __align__(8) uint64_t full[2], ready[2], empty[2], shifted[2];
-  const TileLayout L = tile_layout(ta, true, true, false);
+  const TileLayout L = tile_layout(ta, MIXED, true, HALF);
   const size_t buf_bytes = align16(L.total);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -1746,7 +1769,7 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
         staged = false;
       }
       if (!staged && lane == 0 && !ok_next) atomicOr(status, LJ_ST_CELL_RANGE);
-      if (staged) stage_issue<true, true>(ti, ta, pos, lo, rows, ent, S, buf, L, &full[b], warp);
+      if (staged) stage_issue<MIXED, true>(ti, ta, pos, lo, rows, ent, S, buf, L, &full[b], warp);
       // bookkeeping of this producer's next tile (its slot was released with tile k - 2), then
       // the loads for the one after it
       const int64_t tn = t + 2 * stride;
@@ -1768,10 +1791,15 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
           }
           break;
         }
+        if (!MIXED) {  // shift codes and sorted indices by this warp; they precede later bulk copies
+          stage_codes_warp(ti, ta, S, buf, L, HALF, lane);
+          fence_proxy_async_smem();
+          __syncwarp();
+        }
       }
       if (lane == 0) {
         s_ti[slot] = ti;
-        s_valid[slot] = staged ? (tile_interior(ti, ta) ? 1 : 2) : 0;
+        s_valid[slot] = staged ? ((!MIXED || tile_interior(ti, ta)) ? 1 : 2) : 0;
         mbar_arrive(&ready[b]);  // release: bookkeeping and copies visible to the consumers
       }
     }
@@ -1802,7 +1830,7 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
         }
       }
       if (v > 0)
-        force_tile_compute<true, LANES, false, ENERGY, false, LONGLIST, 2, 32 * CW>(SS[slot], buf, L, rows, ent, c, g,
+        force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST, 2, 32 * CW>(SS[slot], buf, L, rows, ent, c, g,
                                                                                     fout, status, pe_acc, vir_acc,
                                                                                     ta.list_cap);
       __syncwarp();
@@ -2260,16 +2288,16 @@ static int force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_
                                                                                     rows, tl, ent, f, part, status, \
                                                                                     nbuf);                          \
   } while (0)
-  if constexpr (MIXED && !HALF) {
-    if (!ta.whole && nbuf == 2) {  // producer warp + consumer warps over two buffers
+  if constexpr (MIXED != HALF) {  // the pipelined forms: mixed + full list, FP64 + half list
+    if (!ta.whole && nbuf == 2) {  // producer warps + consumer warps over two buffers
 #define LJ_FP(LONG, CW)                                                                                          \
   do {                                                                                                           \
-    set_smem(k_force_pipe<LANES, ENERGY, LONG, CW>, sm);                                                         \
-    const int64_t want =                                                                                         \
-        (int64_t)sm_count() * resident_per_sm(k_force_pipe<LANES, ENERGY, LONG, CW>, pipe_threads(CW), sm);     \
+    set_smem(k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW>, sm);                                            \
+    const int64_t want = (int64_t)sm_count() *                                                                   \
+                         resident_per_sm(k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW>, pipe_threads(CW), sm); \
     grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, ta.ntiles), (int64_t)kMaxRedBlocks)); \
-    k_force_pipe<LANES, ENERGY, LONG, CW><<<grid, pipe_threads(CW), sm, s>>>((const float4*)pos, lo, cs, g, ta, c, \
-                                                                             rows, tl, ent, (float4*)f, part, status); \
+    k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW><<<grid, pipe_threads(CW), sm, s>>>(pos, lo, cs, g, ta, c,  \
+                                                                                       rows, tl, ent, f, part, status); \
   } while (0)
       const bool lg = ta.list_cap < ta.max_list;
       if (ta.T <= 4) {
