@@ -319,9 +319,9 @@ int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out);
  * in the force kernel (1, 2, 4, 8, 16, 32); force_ctas_per_sm: resident force CTAs per SM
  * (1..4; the pipelined kernel takes as many as fit); force_buffers: tile buffers per force CTA
  * (1: tiles staged one after the other; 2: the next tile's copies overlap the current tile's
- * arithmetic; for the mixed form with the full list this is the pipelined kernel, in which
- * producer warps stage tiles and consumer warps compute, and it is the default there; 1 is the
- * default otherwise).  A new tile_cells or force_buffers
+ * arithmetic; for the mixed form with the full list and the FP64 form with the half list this is
+ * the pipelined kernel, in which producer warps stage tiles and consumer warps compute, and it is
+ * the default there; 1 is the default otherwise).  A new tile_cells or force_buffers
  * takes effect at the next list construction (forced at the next force evaluation).  Results
  * do not depend on these knobs beyond FP32 summation order.
  */

@@ -410,12 +410,12 @@ static int ensure_tile_list(ljmd_sys* s) {
 
 // Tile geometry for the staged list/force kernels: T cells along z per tile, shared-memory
 // capacities from the actual largest tile of the current cell occupancy.
-// Tile buffers per force CTA: the requested number, else two for the mixed form with the full
-// list (the pipelined kernel: producer warps stage the next tile while consumer warps compute)
-// and one otherwise.
+// Tile buffers per force CTA: the requested number, else two for the forms with a pipelined
+// kernel (producer warps stage the next tile while consumer warps compute): the mixed form with
+// the full list and the FP64 form with the half list; one otherwise.
 static int force_buffers(const ljmd_sys* s) {
   if (s->force_nbuf) return s->force_nbuf;
-  return (s->precision == LJ_MIXED && !s->list_half) ? 2 : 1;
+  return ((s->precision == LJ_MIXED) != s->list_half) ? 2 : 1;
 }
 
 static int choose_tiles(ljmd_sys* s, int t_cap) {
