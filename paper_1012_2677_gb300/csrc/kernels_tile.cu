@@ -1654,37 +1654,46 @@ __device__ __forceinline__ bool tile_interior(const TileInfo& ti, const TileArgs
   return ti.cx >= 1 && ti.cx <= ta.n - 2 && ti.cy >= 1 && ti.cy <= ta.n - 2 && ti.z0 >= 1 && ti.z0 + ti.Tp <= ta.n - 1;
 }
 
-// Fix-ups of a staged tile after its copies land, by one producer warp (the pipelined kernel's
-// version of stage_finish): in the mixed form the image shifts of the periodic cells (exact
-// two-sum shifts of hi and lo); in the FP64 form every slot's shift code (sx + 1) + 3 (sy + 1) +
-// 9 (sz + 1) in w and, for the half list, the sorted indices.
-template <bool MIXED>
-__device__ __forceinline__ void stage_fix_warp(const TileInfo& ti, const TileArgs& ta, const Geom& g,
-                                               const TileShared& S, unsigned char* smem, const TileLayout& L,
-                                               bool want_gid, int lane) {
+// Shift codes (FP64 form: every slot's w holds (sx + 1) + 3 (sy + 1) + 9 (sz + 1)) and, for the
+// half list, the sorted indices of a staged tile, written by one producer warp after the copies
+// land (the pipelined kernel's version of stage_finish for the FP64 form).
+__device__ __forceinline__ void stage_codes_warp(const TileInfo& ti, const TileArgs& ta, const TileShared& S,
+                                                 unsigned char* smem, const TileLayout& L, bool want_gid,
+                                                 int lane) {
   const bool interior = tile_interior(ti, ta);
-  if (MIXED && interior) return;
   for (int q = 0; q < S.ncell; ++q) {
     int sx = 0, sy = 0, sz = 0;
     if (!interior) cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
+    const double code = (double)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
     const int a = S.offq[q], b = S.offq[q + 1], gq = S.g0[q];
-    if (MIXED) {
-      if ((sx | sy | sz) == 0) continue;
-      for (int e = a + lane; e < b; e += 32) {
-        float4* h = (float4*)(smem + L.pos) + e;
-        float4* l = (float4*)(smem + L.lo) + e;
-        shift_hi_lo(h->x, l->x, (float)sx, g);
-        shift_hi_lo(h->y, l->y, (float)sy, g);
-        shift_hi_lo(h->z, l->z, (float)sz, g);
-      }
-    } else {
-      const double code = (double)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
-      for (int e = a + lane; e < b; e += 32) {
-        ((dvec4*)(smem + L.pos))[e].w = code;
-        if (want_gid) ((int*)(smem + L.gid))[e] = gq + (e - a);
-      }
+    for (int e = a + lane; e < b; e += 32) {
+      ((dvec4*)(smem + L.pos))[e].w = code;
+      if (want_gid) ((int*)(smem + L.gid))[e] = gq + (e - a);
     }
   }
+}
+
+// Image shifts of a staged tile's periodic cells by the consumer warps (warp per cell, lanes over
+// its particles).  Every writer orders its writes before later bulk copies into the same bytes;
+// the caller then waits for all consumer warps (a bounded mbarrier wait, not bar.sync, so that a
+// warp that left on a timeout cannot hold the others forever).
+__device__ __forceinline__ void stage_shift_consumers(const TileInfo& ti, const TileArgs& ta, const Geom& g,
+                                                      const TileShared& S, unsigned char* smem, const TileLayout& L,
+                                                      int consumers) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = warp; q < S.ncell; q += consumers) {
+    int sx, sy, sz;
+    cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
+    if ((sx | sy | sz) == 0) continue;
+    for (int e = S.offq[q] + lane; e < S.offq[q + 1]; e += 32) {
+      float4* h = (float4*)(smem + L.pos) + e;
+      float4* l = (float4*)(smem + L.lo) + e;
+      shift_hi_lo(h->x, l->x, (float)sx, g);
+      shift_hi_lo(h->y, l->y, (float)sy, g);
+      shift_hi_lo(h->z, l->z, (float)sz, g);
+    }
+  }
+  fence_proxy_async_smem();
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -1692,27 +1701,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // CW consumer warps: 8 for tiles of up to 4 cells, 12 for larger tiles (more keys per tile).
-// Forms: the mixed form with the full list and the FP64 form with the half list (the consumers
-// scatter the partners' forces with atomics).  The producer of a tile writes its fix-ups (image
-// shifts, shift codes, sorted indices) after the copies land, so the consumers never wait for
-// each other.  BATCHED (mixed form): the tiles of all replicas of a batch in one launch; each
-// tile takes its replica's grid and box from the replica table, and its energy and virial go to
-// the replica's totals (part[2 r], part[2 r + 1]; one atomic per consumer warp and tile) instead
-// of per-block partials.
-template <bool MIXED, bool HALF, int LANES, bool ENERGY, bool LONGLIST, int CW, bool BATCHED>
+// Forms: the mixed form with the full list (consumers apply the image shifts of periodic tiles)
+// and the FP64 form with the half list (the producer writes the shift codes and sorted indices;
+// the consumers scatter the partners' forces with atomics).
+template <bool MIXED, bool HALF, int LANES, bool ENERGY, bool LONGLIST, int CW>
 __global__ void __launch_bounds__(pipe_threads(CW), 2)
     k_force_pipe(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
                  Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
                  const uint16_t* __restrict__ ent, void* __restrict__ fout, double* __restrict__ part,
-                 int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps,
-                 const int32_t* __restrict__ tile_rep) {
+                 int32_t* __restrict__ status) {
   static_assert(MIXED != HALF, "pipelined forms: mixed with the full list, FP64 with the half list");
-  static_assert(!BATCHED || MIXED, "batches use the mixed form");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared SS[kPipeSlots];
-  __shared__ int s_rep[kPipeSlots];
-  __shared__ int s_valid[kPipeSlots];  // 1: compute, 0: skip (bookkeeping failed), -1: abort
-  __shared__ __align__(8) uint64_t full[2], ready[2], empty[2];
+  __shared__ TileInfo s_ti[kPipeSlots];
+  __shared__ int s_valid[kPipeSlots];  // 1: interior tile, 2: periodic tile (shifts), 0: skip, -1: abort
+  __shared__ __align__(8) uint64_t full[2], ready[2], empty[2], shifted[2];
   const TileLayout L = tile_layout(ta, MIXED, true, HALF);
   const size_t buf_bytes = align16(L.total);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1721,6 +1724,7 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
       mbar_init(&full[b], 1);
       mbar_init(&ready[b], 1);
       mbar_init(&empty[b], CW);
+      mbar_init(&shifted[b], CW);
     }
     fence_proxy_async_smem();
   }
@@ -1732,31 +1736,13 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
     const int p = warp - CW, b = p;
     int64_t t = blockIdx.x + p * stride;
     TilePrefetch pf;
-    int rep_pf = 0;  // replica of the prefetched tile
-    auto prefetch = [&](int64_t tt) {
-      TileArgs tav = ta;
-      const uint32_t* csv = cs;
-      int64_t tl = tt;
-      rep_pf = 0;
-      if (BATCHED) {
-        rep_pf = tile_rep[tt];
-        const ReplicaGeo& rg = reps[rep_pf];
-        Geom gd;
-        replica_view(rg, tav, gd);
-        csv = cs + rg.cell_base;
-        tl = tt - rg.tile_base;
-      }
-      tile_prefetch(tl, tav, csv, tile_list + (tt - tl), pf, lane);
-    };
     bool ok_next = false;
     TileInfo ti_cur{0, 0, 0, 0};
-    int rep_cur = 0;
     if (t < ta.ntiles) {
-      prefetch(t);
+      tile_prefetch(t, ta, cs, tile_list, pf, lane);
       ti_cur = pf.ti;
-      rep_cur = rep_pf;
       ok_next = tile_prepare_pf(pf, ta, SS[p], lane);
-      if (t + 2 * stride < ta.ntiles) prefetch(t + 2 * stride);
+      if (t + 2 * stride < ta.ntiles) tile_prefetch(t + 2 * stride, ta, cs, tile_list, pf, lane);
     }
     for (int k = p; t < ta.ntiles; t += 2 * stride, k += 2) {
       const int slot = k % kPipeSlots;
@@ -1777,25 +1763,20 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
         break;
       }
       const TileInfo ti = ti_cur;
-      const int rep = rep_cur;
-      TileArgs tav = ta;  // the tile's grid (its replica's in a batch)
-      Geom gv = g;
-      if (BATCHED) replica_view(reps[rep], tav, gv);
       bool staged = ok_next;
       if (staged && (S.own1 - S.own0 > ta.max_own || S.list_len > (unsigned)ta.max_list)) {
         if (lane == 0) atomicOr(status, LJ_ST_LIST_OVERFLOW);
         staged = false;
       }
       if (!staged && lane == 0 && !ok_next) atomicOr(status, LJ_ST_CELL_RANGE);
-      if (staged) stage_issue<MIXED, true>(ti, tav, pos, lo, rows, ent, S, buf, L, &full[b], warp);
+      if (staged) stage_issue<MIXED, true>(ti, ta, pos, lo, rows, ent, S, buf, L, &full[b], warp);
       // bookkeeping of this producer's next tile (its slot was released with tile k - 2), then
       // the loads for the one after it
       const int64_t tn = t + 2 * stride;
       if (tn < ta.ntiles) {
         ti_cur = pf.ti;
-        rep_cur = rep_pf;
         ok_next = tile_prepare_pf(pf, ta, SS[(k + 2) % kPipeSlots], lane);
-        if (tn + 2 * stride < ta.ntiles) prefetch(tn + 2 * stride);
+        if (tn + 2 * stride < ta.ntiles) tile_prefetch(tn + 2 * stride, ta, cs, tile_list, pf, lane);
       }
       if (staged) {
         bool landed = true;
@@ -1810,48 +1791,54 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
           }
           break;
         }
-        // fix-ups of the tile by this warp; they precede later bulk copies into the same bytes
-        stage_fix_warp<MIXED>(ti, tav, gv, S, buf, L, HALF, lane);
-        fence_proxy_async_smem();
-        __syncwarp();
+        if (!MIXED) {  // shift codes and sorted indices by this warp; they precede later bulk copies
+          stage_codes_warp(ti, ta, S, buf, L, HALF, lane);
+          fence_proxy_async_smem();
+          __syncwarp();
+        }
       }
       if (lane == 0) {
-        s_rep[slot] = rep;
-        s_valid[slot] = staged ? 1 : 0;
-        mbar_arrive(&ready[b]);  // release: bookkeeping, copies and fix-ups visible to the consumers
+        s_ti[slot] = ti;
+        s_valid[slot] = staged ? ((!MIXED || tile_interior(ti, ta)) ? 1 : 2) : 0;
+        mbar_arrive(&ready[b]);  // release: bookkeeping and copies visible to the consumers
       }
     }
   } else {
     // ---- consumers ----
     int k = 0;
+    uint32_t shpar = 0u;  // bit b: phase of shifted[b] (every consumer warp sees the same tiles)
     for (int64_t t = blockIdx.x; t < ta.ntiles; t += stride, ++k) {
       const int b = k & 1, slot = k % kPipeSlots;
       const uint32_t use = (uint32_t)(k >> 1);
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&ready[b], use & 1u, wait_budget())) != 0;
+      bool ok = __all_sync(0xffffffffu, mbar_wait(&ready[b], use & 1u, wait_budget())) != 0;
       if (!ok) {
         if (lane == 0) atomicOr(status, LJ_ST_TIMEOUT);
         break;
       }
       const int v = s_valid[slot];
       if (v < 0) break;
-      if (v > 0)
-        force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST, 2, 32 * CW>(
-            SS[slot], smem + b * buf_bytes, L, rows, ent, c, g, fout, status, pe_acc, vir_acc, ta.list_cap);
-      if (BATCHED && ENERGY) {  // this tile's share of its replica's energy (full list: pairs twice)
-        const double tp = warp_sum(pe_acc), tv = warp_sum(vir_acc);
-        if (lane == 0 && (tp != 0.0 || tv != 0.0)) {
-          const int rep = s_rep[slot];
-          atomicAdd(&part[2 * rep], 0.5 * tp);
-          atomicAdd(&part[2 * rep + 1], 0.5 * tv);
+      unsigned char* buf = smem + b * buf_bytes;
+      if (v == 2) {  // periodic tile: shifts by all consumer warps, then wait for all of them
+        stage_shift_consumers(s_ti[slot], ta, g, SS[slot], buf, L, CW);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&shifted[b]);
+        ok = __all_sync(0xffffffffu, mbar_wait(&shifted[b], (shpar >> b) & 1u, wait_budget())) != 0;
+        shpar ^= 1u << b;
+        if (!ok) {
+          if (lane == 0) atomicOr(status, LJ_ST_TIMEOUT);
+          break;
         }
-        pe_acc = vir_acc = 0.0;
       }
+      if (v > 0)
+        force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST, 2, 32 * CW>(SS[slot], buf, L, rows, ent, c, g,
+                                                                                    fout, status, pe_acc, vir_acc,
+                                                                                    ta.list_cap);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
     }
   }
   __syncthreads();
-  if (ENERGY && !BATCHED) {
+  if (ENERGY) {
     __shared__ double sh[32];
     const double tp = block_sum(pe_acc, sh);
     __syncthreads();
@@ -2305,12 +2292,12 @@ static int force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_
     if (!ta.whole && nbuf == 2) {  // producer warps + consumer warps over two buffers
 #define LJ_FP(LONG, CW)                                                                                          \
   do {                                                                                                           \
-    set_smem(k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW, false>, sm);                                     \
+    set_smem(k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW>, sm);                                            \
     const int64_t want = (int64_t)sm_count() *                                                                   \
-                         resident_per_sm(k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW, false>, pipe_threads(CW), sm); \
+                         resident_per_sm(k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW>, pipe_threads(CW), sm); \
     grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, ta.ntiles), (int64_t)kMaxRedBlocks)); \
-    k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW, false><<<grid, pipe_threads(CW), sm, s>>>(                \
-        pos, lo, cs, g, ta, c, rows, tl, ent, f, part, status, nullptr, nullptr);                                \
+    k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW><<<grid, pipe_threads(CW), sm, s>>>(pos, lo, cs, g, ta, c,  \
+                                                                                       rows, tl, ent, f, part, status); \
   } while (0)
       const bool lg = ta.list_cap < ta.max_list;
       if (ta.T <= 4) {
@@ -2491,51 +2478,6 @@ int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo
                        float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R,
                        const int32_t* tile_rep, cudaStream_t s) {
   const size_t sm = batch_force_smem_bytes(caps);
-  int dev = 0, smem_max = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (2 * sm + 8192 <= (size_t)smem_max) {  // pipelined kernel: two tile buffers per CTA
-    const size_t sm2 = 2 * sm;
-    int gridp = 1;
-#define LJ_FP(LN, E, LONG, CW)                                                                                     \
-  do {                                                                                                             \
-    set_smem(k_force_pipe<true, false, LN, E, LONG, CW, true>, sm2);                                               \
-    const int64_t want =                                                                                           \
-        (int64_t)sm_count() * resident_per_sm(k_force_pipe<true, false, LN, E, LONG, CW, true>, pipe_threads(CW), sm2); \
-    gridp = (int)std::max<int64_t>(1, std::min<int64_t>(want, caps.ntiles));                                       \
-    k_force_pipe<true, false, LN, E, LONG, CW, true><<<gridp, pipe_threads(CW), sm2, s>>>(                         \
-        hi, lo, cs, Geom{}, caps, c, rows, tile_list, ent, f, e_rep, status, reps, tile_rep);                      \
-  } while (0)
-#define LJ_FPL(LN)                                        \
-  do {                                                    \
-    const bool lg = caps.list_cap < caps.max_list;        \
-    if (caps.T <= 4) {                                    \
-      if (energy) {                                       \
-        if (lg) LJ_FP(LN, true, true, 8);                 \
-        else LJ_FP(LN, true, false, 8);                   \
-      } else {                                            \
-        if (lg) LJ_FP(LN, false, true, 8);                \
-        else LJ_FP(LN, false, false, 8);                  \
-      }                                                   \
-    } else {                                              \
-      if (energy) {                                       \
-        if (lg) LJ_FP(LN, true, true, 12);                \
-        else LJ_FP(LN, true, false, 12);                  \
-      } else {                                            \
-        if (lg) LJ_FP(LN, false, true, 12);               \
-        else LJ_FP(LN, false, false, 12);                 \
-      }                                                   \
-    }                                                     \
-  } while (0)
-    switch (lanes) {
-      case 2: LJ_FPL(2); break;
-      case 8: LJ_FPL(8); break;
-      default: LJ_FPL(4); break;
-    }
-#undef LJ_FPL
-#undef LJ_FP
-    return gridp;
-  }
   const int grid = tile_grid(caps, per_sm_for(sm));
 #define LJ_FB(LN)                                                                                               \
   do {                                                                                                          \

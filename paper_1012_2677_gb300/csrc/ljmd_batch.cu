@@ -365,9 +365,8 @@ static int host_build(ljmd_batch* b) {
     tz.list_cap = 0;
     const size_t base_bytes = batch_force_smem_bytes(tz);
     if (base_bytes > (size_t)smem_max) return LJ_ERANGE;
-    // room for the list next to the positions so that two CTAs of the pipelined force kernel (two
-    // tile buffers each) share an SM where possible
-    const int64_t target = std::max<int64_t>((int64_t)base_bytes + 4096, 50 * 1024);
+    // room for the list next to the positions so that 4 CTAs share an SM where possible
+    const int64_t target = std::max<int64_t>((int64_t)base_bytes + 4096, 54 * 1024);
     const int64_t room = (std::min<int64_t>(smem_max, target) - (int64_t)base_bytes) / 2 - 16;
     b->caps.list_cap = (int32_t)std::max<int64_t>(0, std::min<int64_t>(b->caps.max_list, room) & ~(int64_t)7);
   }
