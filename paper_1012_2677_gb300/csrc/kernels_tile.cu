@@ -968,9 +968,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     fence_proxy_async_smem();
     s_issued = 0;
   }
-  // the last warp (idle in phase B, which has a warp per 32-key chunk) holds the cell bounds of the
-  // CTA's next tile, loaded one tile ahead of their use, and stages tiles
-  const int wp = kLW - 1;
+  // warp 0 holds the cell bounds of the CTA's next tile, loaded one tile ahead of their use
   TilePrefetch pf;
   auto prefetch = [&](int64_t tp) {
     TileArgs tap = ta_in;
@@ -985,7 +983,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     }
     tile_prefetch(tlp, tap, csp, nullptr, pf, lane);
   };
-  if (warp == wp && blockIdx.x < ta_in.ntiles) prefetch(blockIdx.x);
+  if (warp == 0 && blockIdx.x < ta_in.ntiles) prefetch(blockIdx.x);
   __syncthreads();
 
   for (int64_t t = blockIdx.x; t < ta_in.ntiles; t += gridDim.x) {
@@ -999,23 +997,23 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     }
     const TileInfo ti = tile_info(tl, ta);
     // a tile staged early by the previous iteration has its bookkeeping in the other slot and its
-    // copies in flight; otherwise the last warp prepares it now from the prefetched cell bounds
+    // copies in flight; otherwise warp 0 prepares it now from the prefetched cell bounds
     const bool issued = s_issued != 0;
     if (issued) cur ^= 1;
     TileShared& S = SL[cur];
-    if (!issued && warp == wp) {
+    if (!issued && warp == 0) {
       const bool okp = tile_prepare_pf(pf, ta, S, lane);
       if (lane == 0) s_staged_ok = okp ? 1 : 0;
       if (t + gridDim.x < ta_in.ntiles) prefetch(t + gridDim.x);
     }
     __syncthreads();  // every thread has read s_issued before it is cleared below
-    if (warp == wp && lane == 0) s_issued = 0;
+    if (threadIdx.x == 0) s_issued = 0;
     if (!s_staged_ok) {
       if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
       __syncthreads();
       continue;
     }
-    if (!issued) stage_issue<true, false>(ti, ta, pos, nullptr, nullptr, nullptr, S, smem, L, &bar, wp);
+    if (!issued) stage_issue<true, false>(ti, ta, pos, nullptr, nullptr, nullptr, S, smem, L, &bar);
     if (!stage_finish<true, false>(ti, ta, g, S, smem, L, &bar, phase, true, status)) return;
     const int n_own = S.own1 - S.own0;
     if (n_own > ta.max_own) {  // sizing inconsistency: record and skip the tile
@@ -1114,10 +1112,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
                                                 l, sh_gid[l], valid);
       }
       __syncthreads();
-      // this tile's staged positions and sorted indices are no longer read: the last warp prepares
-      // the next tile and issues its copies now, so that they land during phases B-D
+      // this tile's staged positions and sorted indices are no longer read: warp 0 prepares the
+      // next tile and issues its copies now, so that they land during phases B-D
       const int64_t tn = t + gridDim.x;
-      if (warp == wp && tn < ta_in.ntiles) {
+      if (warp == 0 && tn < ta_in.ntiles) {
         TileArgs tan = ta_in;
         Geom gn = g_in;
         int64_t tln = tn;
@@ -1128,8 +1126,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
         }
         TileShared& SN = SL[cur ^ 1];
         const bool okn = tile_prepare_pf(pf, tan, SN, lane);
-        if (okn)
-          stage_issue<true, false>(tile_info(tln, tan), tan, pos, nullptr, nullptr, nullptr, SN, smem, L, &bar, wp);
+        if (okn) stage_issue<true, false>(tile_info(tln, tan), tan, pos, nullptr, nullptr, nullptr, SN, smem, L, &bar);
         if (lane == 0) {
           s_staged_ok = okn ? 1 : 0;
           s_issued = 1;
