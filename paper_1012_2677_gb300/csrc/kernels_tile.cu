@@ -936,7 +936,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
                 const int* __restrict__ pred, const int32_t* __restrict__ tile_rep) {
   if (pred && !*pred) return;  // predicated (batched rebuild inside a graph)
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ TileShared SL[2];  // bookkeeping of the current tile and of the next one (staged early)
+  __shared__ TileShared S;
   __shared__ __align__(8) uint64_t bar;
   __shared__ unsigned int s_base, s_total, s_padded;
   __shared__ int s_ok;
@@ -961,12 +961,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t phase = 0;
   __shared__ int s_staged_ok;
-  __shared__ int s_issued;  // the next tile was prepared and its copies issued after phase A
-  int cur = 0;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_proxy_async_smem();
-    s_issued = 0;
   }
   // warp 0 holds the cell bounds of the CTA's next tile, loaded one tile ahead of their use
   TilePrefetch pf;
@@ -996,25 +993,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
       tl = t - rg.tile_base;
     }
     const TileInfo ti = tile_info(tl, ta);
-    // a tile staged early by the previous iteration has its bookkeeping in the other slot and its
-    // copies in flight; otherwise warp 0 prepares it now from the prefetched cell bounds
-    const bool issued = s_issued != 0;
-    if (issued) cur ^= 1;
-    TileShared& S = SL[cur];
-    if (!issued && warp == 0) {
+    if (warp == 0) {
       const bool okp = tile_prepare_pf(pf, ta, S, lane);
       if (lane == 0) s_staged_ok = okp ? 1 : 0;
       if (t + gridDim.x < ta_in.ntiles) prefetch(t + gridDim.x);
     }
-    __syncthreads();  // every thread has read s_issued before it is cleared below
-    if (threadIdx.x == 0) s_issued = 0;
+    __syncthreads();
     if (!s_staged_ok) {
       if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
       __syncthreads();
       continue;
     }
-    if (!issued) stage_issue<true, false>(ti, ta, pos, nullptr, nullptr, nullptr, S, smem, L, &bar);
-    if (!stage_finish<true, false>(ti, ta, g, S, smem, L, &bar, phase, true, status)) return;
+    if (!stage_copy_async<true, false>(ti, ta, g, pos, nullptr, nullptr, nullptr, S, smem, L, &bar, phase, true,
+                                       status))
+      return;
     const int n_own = S.own1 - S.own0;
     if (n_own > ta.max_own) {  // sizing inconsistency: record and skip the tile
       if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
@@ -1112,27 +1104,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
                                                 l, sh_gid[l], valid);
       }
       __syncthreads();
-      // this tile's staged positions and sorted indices are no longer read: warp 0 prepares the
-      // next tile and issues its copies now, so that they land during phases B-D
-      const int64_t tn = t + gridDim.x;
-      if (warp == 0 && tn < ta_in.ntiles) {
-        TileArgs tan = ta_in;
-        Geom gn = g_in;
-        int64_t tln = tn;
-        if (BATCHED) {
-          const ReplicaGeo& rg = reps[tile_rep[tn]];
-          replica_view(rg, tan, gn);
-          tln = tn - rg.tile_base;
-        }
-        TileShared& SN = SL[cur ^ 1];
-        const bool okn = tile_prepare_pf(pf, tan, SN, lane);
-        if (okn) stage_issue<true, false>(tile_info(tln, tan), tan, pos, nullptr, nullptr, nullptr, SN, smem, L, &bar);
-        if (lane == 0) {
-          s_staged_ok = okn ? 1 : 0;
-          s_issued = 1;
-        }
-        if (tn + gridDim.x < ta_in.ntiles) prefetch(tn + gridDim.x);
-      }
       // phase B: row lengths (one warp per chunk), and each unit's offset in its keys' rows
       // (kept in the count area, which the unit path does not use otherwise, when it holds them)
       int* s_upre = s_cnt;
