@@ -130,46 +130,6 @@ __device__ __forceinline__ bool stage_offsets(const TileInfo& ti, const TileArgs
   return S.total <= ta.max_staged;
 }
 
-// The same bookkeeping done by one warp alone (the producer warp of the pipelined force kernel):
-// no CTA barrier, the other warps keep computing.
-__device__ __forceinline__ bool stage_offsets_warp(const TileInfo& ti, const TileArgs& ta,
-                                                   const uint32_t* __restrict__ cs, TileShared& S, int lane) {
-  const int ncol = ti.Tp + 2;
-  const int ncell = 9 * ncol;
-  int run = 0;
-  for (int base = 0; base < ncell; base += 32) {
-    const int q = base + lane;
-    int v = 0;
-    if (q < ncell) {
-      int sx, sy, sz;
-      const uint32_t c = cell_of_q(ti, ta.n, ncol, q, sx, sy, sz);
-      const uint32_t a = cs[c], b = cs[c + 1];
-      S.g0[q] = (int)a;
-      v = (int)(b - a);
-    }
-    int inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (q < ncell) S.offq[q + 1] = run + inc;
-    run += __shfl_sync(0xffffffffu, inc, 31);
-  }
-  __syncwarp();
-  if (lane == 0) {
-    S.offq[0] = 0;
-    S.ncol = ncol;
-    S.ncell = ncell;
-    S.total = run;
-    S.own0 = S.offq[4 * ncol + 1];
-    S.own1 = S.offq[4 * ncol + ti.Tp + 1];
-    S.gown0 = S.g0[4 * ncol + 1];
-  }
-  __syncwarp();
-  return run <= ta.max_staged;
-}
-
 // Cell bounds of a tile's staged cells held in one warp's registers (lane l: cells l, l + 32, ...),
 // loaded a tile ahead of their use so the bookkeeping never waits on memory.
 constexpr int kPfRounds = (kMaxCells + 31) / 32;
@@ -197,7 +157,8 @@ __device__ __forceinline__ void tile_prefetch(int64_t t, const TileArgs& ta, con
   }
 }
 
-// stage_offsets_warp from prefetched bounds; also the tile's list segment.
+// The bookkeeping of stage_offsets done by one warp from prefetched bounds (no CTA barrier, the
+// other warps keep computing); also the tile's list segment.
 __device__ __forceinline__ bool tile_prepare_pf(const TilePrefetch& pf, const TileArgs& ta, TileShared& S, int lane) {
   const int ncol = pf.ti.Tp + 2, ncell = 9 * ncol;
   int run = 0;
@@ -1369,7 +1330,7 @@ __device__ __forceinline__ void pair_mixed(const float4& hi_i, const float4& lo_
 
 // Forces of the own particles of one staged tile (buffer `buf`); group `grp` of LANES threads per
 // key particle, lanes striding over its row.
-template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST, int UNR = 2, int NTH = kTileThreads>
+template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST, int NTH = kTileThreads>
 __device__ __forceinline__ void force_tile_compute(const TileShared& S, const unsigned char* buf, const TileLayout& L,
                                                    const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
                                                    const LJConst& c, const Geom& g, void* __restrict__ fout,
@@ -1421,16 +1382,6 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
           // list segment staged: entries by 32-bit shared address, two independent per iteration
           uint32_t p = smem_addr(s_ent) + 2u * (row.x + lane);
           const uint32_t pend = smem_addr(s_ent) + 2u * (row.x + row.y);
-          if (UNR == 4) {  // four independent entries per iteration (more loads in flight)
-            for (; p + 6u * LANES < pend; p += 8u * LANES) {
-              const uint32_t j0 = lds_u16(p), j1 = lds_u16(p + 2u * LANES), j2 = lds_u16(p + 4u * LANES),
-                             j3 = lds_u16(p + 6u * LANES);
-              pair_at(j0, a0);
-              pair_at(j1, a1);
-              pair_at(j2, a0);
-              pair_at(j3, a1);
-            }
-          }
           for (; p + 2u * LANES < pend; p += 4u * LANES) {
             const uint32_t j0 = lds_u16(p), j1 = lds_u16(p + 2u * LANES);
             pair_at(j0, a0);
@@ -1830,7 +1781,7 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
         }
       }
       if (v > 0)
-        force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST, 2, 32 * CW>(SS[slot], buf, L, rows, ent, c, g,
+        force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST, 32 * CW>(SS[slot], buf, L, rows, ent, c, g,
                                                                                     fout, status, pe_acc, vir_acc,
                                                                                     ta.list_cap);
       __syncwarp();
