@@ -50,3 +50,13 @@ def test_product_path_has_no_oracle_dependency():
     for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
         if path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
             assert not pat.search(open(path).read()), path
+
+
+def test_binding_constants_match_the_header():
+    """Every #define LJ_* of include/ljmd.h has the same value in the binding."""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "ljmd.h")).read()
+    defs = dict(re.findall(r"^#define (LJ_[A-Z0-9_]+) \(?(-?\d+)\)?", hdr, flags=re.M))
+    assert len(defs) >= 23  # status codes, device status bits, forms, list forms, rules, truncations
+    for name, value in defs.items():
+        assert getattr(ljmd, name) == int(value), name
