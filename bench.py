@@ -68,6 +68,12 @@ def job_value(units_per_rank, world, seconds):
     return units_per_rank * world / seconds
 
 
+def mups(n, steps, seconds):
+    """Speed in millions of particle updates per second (Sec. 3.3, Sec. 4.5): N k / (10^6 t) for
+    N particles advanced k steps in t seconds."""
+    return n * steps / (1e6 * seconds)
+
+
 def replica_seed(base, rank):
     """Each rank advances an independent replica (no data-path exchange between ranks)."""
     return base + 1000 * rank
@@ -326,7 +332,7 @@ def run_ours(args, wl, world, rank, local):
 
 
 def run_paper_replica(stream):
-    """The paper's benchmark configuration on one GPU (Sec. 4.4): 500,000 particles (FCC 50^3 x 4) in
+    """The paper's benchmark configuration on one GPU (Sec. 4.5): 500,000 particles (FCC 50^3 x 4) in
     a 100^3 box (rho = 0.5), r_c = 2.5, r_s = 2.8, dt = 0.001, |v| = 0.9 in random directions,
     150 warm-up steps and 1000 timed steps; MUPS = N steps / (1e6 s).  The list rule is the margin/2
     displacement rule and, beside it, the large displacement check of Alg. 2."""
@@ -351,7 +357,7 @@ def run_paper_replica(stream):
             ms = e0.elapsed_time(e1)
             st1 = s.stats()
         nr = st1["rebuilds"] - st0["rebuilds"]
-        out[name] = {"mups": len(x) * 1000 / (ms * 1e-3) / 1e6, "ms_per_step": ms / 1000, "rebuilds": nr,
+        out[name] = {"mups": mups(len(x), 1000, ms * 1e-3), "ms_per_step": ms / 1000, "rebuilds": nr,
                      "mean_lifetime_steps": 1000 / max(nr, 1)}
     out["paper_context"] = {"mups_per_xeon_x5570_core": 2.73, "mups_per_power6_process": 1.65,
                             "lifetime_steps_power6": 51.2, "note": "FP64 CPU figures of Tables 2-3 and Sec. 5.2"}

@@ -8,7 +8,7 @@
  * (Sec. 2.3), built from a cell grid whose counting sort also reorders the
  * particles for locality (Sec. 2.2, Sec. 3.3), stored as a sorted list
  * (Sec. 2.4, KeyPointer/SortedList), and driven by a second-order symplectic
- * (velocity-Verlet) integrator (Sec. 4.4).
+ * (velocity-Verlet) integrator (Sec. 4.5).
  *
  * Conventions for every call:
  *   - Reduced units (sigma, eps of the potential; m = 1, kB = 1).
@@ -128,7 +128,7 @@ int ljmd_create(ljmd_sys** out, const ljmd_params* p, int32_t precision, void* c
 void ljmd_destroy(ljmd_sys* sys);
 
 /*
- * FCC start of the benchmark (Sec. 4.4): M^3 cubic cells of side
+ * FCC start of the benchmark (Sec. 4.5): M^3 cubic cells of side
  * a = (4/density)^(1/3), four sites per cell, N = 4 M^3, L = M a; particle id
  * order ix, iy, iz, basis site.  Velocities: Gaussian components from the
  * counter-based SplitMix64 stream `seed` (draws 4i..4i+3 of particle i, Box-
@@ -246,7 +246,8 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
  * Errors: LJ_EINVAL (NULL sys/npairs, cap < 0, ij NULL with cap > 0, another device current),
  * LJ_ESTATE (no particles or no list), LJ_ERANGE (the list has more than
  * LJ_PAIRS_STATIC_MAX_ENTRIES entries; a line naming both sizes goes to stderr and nothing is
- * written), LJ_EDEVICE.
+ * written), LJ_EDEVICE (a CUDA error, or the device status word was raised, e.g. by a list entry
+ * that decodes out of range: ij and *npairs are then left unwritten, as by ljmd_get_pairs).
  */
 int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs);
 
@@ -283,7 +284,7 @@ int ljmd_hvp(ljmd_sys* sys, const double* w, double* hw, double* dtheta, int32_t
 
 /*
  * Differentiable trajectory: from (x0, v0) (n particles, box side `box`, 3n FP64 each, id order,
- * x0 unwrapped) run nsteps of velocity-Verlet (Sec. 4.4) with step dt and return
+ * x0 unwrapped) run nsteps of velocity-Verlet (Sec. 4.5) with step dt and return
  *   *loss = (1 / n_pe) sum_{t > nsteps - n_pe} PE(x_t) / n  +  (1 / n) sum_i |x_i(nsteps) - x_i(0)|^2
  * (unwrapped positions), and, if any of gx0, gv0, gtheta is non-NULL, its gradients with respect
  * to x0, v0 (3n FP64 each) and (eps, sigma) (gtheta[2]).  The gradients come from the reverse-time
@@ -299,6 +300,20 @@ int ljmd_hvp(ljmd_sys* sys, const double* w, double* hw, double* dtheta, int32_t
 int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, const double* v0, double dt,
                         int64_t nsteps, int64_t n_pe, int64_t ckpt_every, double* loss, double* gx0, double* gv0,
                         double* gtheta, int32_t on_device);
+
+/*
+ * The cell grid of the last list construction (Sec. 2.2, Fig. 3), read only: the particles were
+ * folded into the box, labelled c = (cx n + cy) n + cz with ck = floor(x_k n / L) (n cells per
+ * side), counting-sorted by label with ties in id order, and every particle array was reordered
+ * that way (Sec. 3.3).  grid_pointer[c] (c <= n^3, the first min(pointer_cap, n^3 + 1) values) is
+ * GridPointer, the position of cell c's first particle in that order (grid_pointer[n^3] = N);
+ * grid_list[k] (the first min(list_cap, N) values) is GridList, the id of the particle in
+ * position k.  *ncells receives n^3.  Caller-owned host arrays; synchronises the stream.
+ * Errors: LJ_EINVAL (NULL sys or ncells, negative capacity, NULL array with a positive capacity),
+ * LJ_ESTATE (no particles or no list yet), LJ_EDEVICE.
+ */
+int ljmd_get_grid(ljmd_sys* sys, int64_t* grid_pointer, int64_t pointer_cap, int64_t* grid_list, int64_t list_cap,
+                  int64_t* ncells);
 
 /* Counters and state of the handle (synchronises the stream). */
 int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out);
@@ -379,7 +394,7 @@ void ljmd_batch_destroy(ljmd_batch* b);
 int ljmd_batch_set_state(ljmd_batch* b, const double* x, const double* v, int32_t on_device);
 
 /*
- * Advance every replica nsteps velocity-Verlet steps (Sec. 4.4) with step dt.  graph_steps = K > 0:
+ * Advance every replica nsteps velocity-Verlet steps (Sec. 4.5) with step dt.  graph_steps = K > 0:
  * the K-step sequence (kick-drift with displacement check, device-decided rebuild, force; final
  * kick) is captured once as a CUDA graph (re-captured when dt or K changes) and replayed
  * floor(nsteps / K) times, the rest run as plain launches; K = 0: plain launches.  No host

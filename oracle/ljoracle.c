@@ -118,7 +118,7 @@ static double min_image_any(double d, double L) {
 }
 
 /*
- * FCC lattice (benchmark initial condition, Sec. 4.4): M^3 cubic cells of side
+ * FCC lattice (benchmark initial condition, Sec. 4.5): M^3 cubic cells of side
  * a = (4/rho)^(1/3), four sites per cell at a*(0,0,0), a*(0,1/2,1/2),
  * a*(1/2,0,1/2), a*(1/2,1/2,0).  Particle id order: ix outermost, then iy, iz,
  * then the basis site.  Returns the box length L = M a.
@@ -264,7 +264,7 @@ double or_kinetic(int64_t N, const double* v) {
 }
 
 /*
- * Velocity-Verlet ("second-order symplectic", Sec. 4.4), m = 1:
+ * Velocity-Verlet ("second-order symplectic", Sec. 4.5), m = 1:
  *   v <- v + (dt/2) F(x);  x <- x + dt v;  v <- v + (dt/2) F(x).
  * F must hold F(x) on entry and holds F(x) on exit.  Positions are not
  * wrapped (the min image handles the periodic box), so x stays unwrapped.

@@ -134,7 +134,7 @@ def pair_f(r2, p: LJParams = LJParams()):
 
 
 def fcc_lattice(M: int, rho: float):
-    """FCC start (Sec. 4.4): M^3 cells x 4 sites at density rho. Returns (x[N,3], L)."""
+    """FCC start (Sec. 4.5): M^3 cells x 4 sites at density rho. Returns (x[N,3], L)."""
     N = 4 * M ** 3
     x = np.empty((N, 3), dtype=np.float64)
     L = lib().or_fcc_lattice(int(M), float(rho), _ptr(x))

@@ -75,7 +75,7 @@ void launch_energy_finalize(const double* pe_vir_part, int nb_force, const doubl
 }
 
 // ---------------------------------------------------------------------------------------------
-// FCC lattice of the benchmark (Sec. 4.4): id p = ((ix M + iy) M + iz) 4 + b at
+// FCC lattice of the benchmark (Sec. 4.5): id p = ((ix M + iy) M + iz) 4 + b at
 // a ((ix, iy, iz) + basis_b), stored as offset + coordinate (SoA x[k * N + p]).
 __global__ void k_fcc(double* __restrict__ x, int64_t M, double a, double offset) {
   const int64_t N = 4 * M * M * M;

@@ -1032,6 +1032,26 @@ int ljmd_get_pairs(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npairs) {
   return check_status(sys);
 }
 
+int ljmd_get_grid(ljmd_sys* sys, int64_t* grid_pointer, int64_t pointer_cap, int64_t* grid_list, int64_t list_cap,
+                  int64_t* ncells) {
+  if (!sys || !ncells || pointer_cap < 0 || list_cap < 0 || (pointer_cap > 0 && !grid_pointer) ||
+      (list_cap > 0 && !grid_list))
+    return LJ_EINVAL;
+  if (sys->broken) return LJ_EDEVICE;
+  if (sys->n <= 0 || !sys->have_list) return LJ_ESTATE;
+  *ncells = sys->ncells;
+  const int64_t np = std::min<int64_t>(pointer_cap, sys->ncells + 1);
+  const int64_t nl = std::min<int64_t>(list_cap, sys->n);
+  std::vector<uint32_t> ptr((size_t)std::max<int64_t>(np, 1));
+  std::vector<int32_t> ids((size_t)std::max<int64_t>(nl, 1));
+  if (np > 0) CK(cudaMemcpyAsync(ptr.data(), sys->cell_start, sizeof(uint32_t) * np, cudaMemcpyDeviceToHost, sys->st));
+  if (nl > 0) CK(cudaMemcpyAsync(ids.data(), sys->id, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, sys->st));
+  CK(cudaStreamSynchronize(sys->st));
+  for (int64_t c = 0; c < np; ++c) grid_pointer[c] = (int64_t)ptr[(size_t)c];
+  for (int64_t k = 0; k < nl; ++k) grid_list[k] = (int64_t)ids[(size_t)k];
+  return check_status(sys);
+}
+
 int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out) {
   if (!sys || !out) return LJ_EINVAL;
   memset(out, 0, sizeof(*out));
@@ -1148,8 +1168,12 @@ int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npai
   CKL();
   sys->launches += 2 + launch_bitonic_sort(keys, P, sys->st);
   CKL();
+  // the kept-pair count and the status word together; a raised status (an entry that decoded out
+  // of range) returns before anything is written, as in ljmd_get_pairs
   CK(cudaMemcpyAsync(sys->h_u32, counter, sizeof(uint32_t), cudaMemcpyDeviceToHost, sys->st));
+  CK(cudaMemcpyAsync(sys->h_i32, sys->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, sys->st));
   CK(cudaStreamSynchronize(sys->st));
+  if (*sys->h_i32) return LJ_EDEVICE;
   const int64_t count = (int64_t)sys->h_u32[0];
   const int64_t m = std::min<int64_t>(cap, count);
   if (m > 0) {

@@ -95,6 +95,7 @@ _SIGS = {
     "ljmd_batch_autotune": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "ljmd_traj_loss_grad": (ctypes.c_int, [_P, _I64, _D, _P, _P, _D, _I64, _I64, _I64, _P, _P, _P, _P, _I32]),
     "ljmd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_stats)]),
+    "ljmd_get_grid": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _P]),
     "ljmd_set_profiling": (ctypes.c_int, [_P, _I32]),
     "ljmd_set_tuning": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),
     "ljmd_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_profile)]),
@@ -266,6 +267,17 @@ def ljmd_traj_loss_grad(h, n: int, box: float, x0, v0, dt: float, nsteps: int, n
     return loss.value, (float(gth[0]), float(gth[1]))
 
 
+def ljmd_get_grid(h, n: int):
+    """(GridPointer[n_cells + 1], GridList[n]) of the last list construction, int64 numpy arrays."""
+    nc = _I64()
+    _chk(load().ljmd_get_grid(h, None, 0, None, 0, ctypes.byref(nc)), "ljmd_get_grid")
+    ptr = np.empty(nc.value + 1, dtype=np.int64)
+    lst = np.empty(max(n, 1), dtype=np.int64)
+    _chk(load().ljmd_get_grid(h, ptr.ctypes.data_as(_P), ptr.size, lst.ctypes.data_as(_P), n, ctypes.byref(nc)),
+         "ljmd_get_grid")
+    return ptr, lst[:n]
+
+
 def ljmd_get_stats(h) -> dict:
     st = ljmd_stats()
     _chk(load().ljmd_get_stats(h, ctypes.byref(st)), "ljmd_get_stats")
@@ -394,6 +406,10 @@ class System:
 
     def stats(self):
         return ljmd_get_stats(self.h)
+
+    def grid(self):
+        """(GridPointer, GridList) of the cell grid of the last list construction."""
+        return ljmd_get_grid(self.h, self.n)
 
     def set_tuning(self, tile_cells=0, lanes=0, force_ctas_per_sm=0, force_buffers=0):
         ljmd_set_tuning(self.h, tile_cells, lanes, force_ctas_per_sm, force_buffers)

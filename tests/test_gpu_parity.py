@@ -111,16 +111,47 @@ def test_pair_list_edge_cases(list_form):
     assert np.array_equal(got, O.pairs_within(x, L, rs))
 
 
-def test_cell_grid_matches_counting_sort():
-    """The library's cell order is the oracle's GridList order by cell label (ties by id)."""
+def _oracle_grid(x, L, rs):
+    n = O.cells_per_side(L, rs)
+    count, pointer, order = O.grid_list(O.cell_labels(O.wrap(x, L), L, n), n ** 3)
+    return count, pointer, order
+
+
+@pytest.mark.parametrize("precision", [ljmd.LJ_MIXED, ljmd.LJ_FP64])
+def test_cell_grid_matches_counting_sort(precision):
+    """The library's cell grid is the oracle's counting sort (Sec. 2.2, Fig. 3) element by element:
+    GridParticleNumber (the pointer differences), GridPointer and GridList (labels ascending, ties in
+    id order), on a random state, on particles placed exactly on cell faces, and after a run whose
+    rebuilds left the particles in a cell order unrelated to their ids (the stable order must still
+    come out by id)."""
     L, rc, margin = 14.0, 2.5, 0.5
+    rs = rc + margin
+    n = O.cells_per_side(L, rs)
+    h = L / n
     x = synth.dyadic(synth.uniform_positions(1500, L, 12))
-    with _system(ljmd.LJ_MIXED, cutoff=rc, margin=margin) as s:
+    faces = synth.dyadic(np.array([[i * h, j * h, (i + j) % n * h] for i in range(n) for j in range(n)]))
+    x = np.vstack([x, faces])
+    with _system(precision, cutoff=rc, margin=margin) as s:
         s.set_state(x, None, L)
         s.build_pairlist()
-        st = s.stats()
-    n = O.cells_per_side(L, rc + margin)
-    assert st["cells_per_side"] == n
+        ptr, lst = s.grid()
+        assert s.stats()["cells_per_side"] == n
+    count, pointer, order = _oracle_grid(x, L, rs)
+    assert np.array_equal(ptr, pointer)
+    assert np.array_equal(np.diff(ptr), count)
+    assert np.array_equal(lst, order)
+    # a liquid run: rebuilds re-sort the particles, so the order entering the next sort is not by id
+    x, v, L = thermal(8, 0.6, 1.2, 9)
+    with _system(precision, cutoff=rc, margin=margin) as s:
+        s.set_state(x, v, L)
+        s.step(0.005, 40)
+        assert s.stats()["rebuilds"] >= 2
+        s.build_pairlist()                      # the grid of the current (folded) positions
+        gx, _, _, _ = s.get_state()
+        ptr, lst = s.grid()
+    count, pointer, order = _oracle_grid(gx, L, rs)
+    assert np.array_equal(ptr, pointer)
+    assert np.array_equal(lst, order)
 
 
 # ------------------------------------------------------------------------------------ forces
@@ -368,6 +399,32 @@ def test_validity_rules_never_miss_a_pair(mode):
             assert _pairs_set(_brute_pairs_numpy(gx, L, rc)) <= listed
         st = s.stats()
     assert st["validity"] == mode and st["status_word"] == 0 and st["rebuilds"] >= 2
+
+
+@pytest.mark.parametrize("precision", [ljmd.LJ_FP64, ljmd.LJ_MIXED])
+def test_margin_rule_at_its_limit(precision):
+    """Two particles, just outside r_s, approach each other by margin/2 + 1.9e-9 each in one step, so
+    that they end inside r_c.  (margin/2)^2 = 0.04 has an FP32 neighbour below it that a
+    displacement this close to the limit would round to; the measured maximum must not undershoot
+    (Sec. 2.3: a rebuild once any particle moved more than margin/2), so the pair is listed after
+    the step."""
+    rc, margin, L = 2.5, 0.4, 16.0
+    rs = rc + margin
+    delta = 128 * 2.0 ** -36                   # 1.86e-9
+    x = np.array([[4.0, 8.0, 8.0], [4.0 + rs + 2.0 ** -30, 8.0, 8.0]])
+    dt = 0.5
+    u = (0.5 * margin + delta) / dt
+    v = np.array([[u, 0.0, 0.0], [-u, 0.0, 0.0]])
+    with _system(precision, ljmd.LJ_LIST_FULL, cutoff=rc, margin=margin) as s:
+        s.set_state(x, v, L)
+        s.build_pairlist()
+        assert len(s.pairs()) == 0             # r_s + 2^-30 apart: not listed
+        s.step(dt, 1)
+        gx, _, _, _ = s.get_state()
+        r = np.linalg.norm(gx[1] - gx[0])
+        assert r < rc                          # now interacting
+        assert _pairs_set(s.pairs()) == {(0, 1)}
+        assert s.stats()["rebuilds"] == 2
 
 
 def test_ldc_extends_list_lifetime_with_same_trajectory():

@@ -208,7 +208,7 @@ def test_sorted_pair_list_like_fig6():
 # ---------------------------------------------------------------- initial state
 
 def test_fcc_lattice_matches_paper_benchmark_box():
-    """Sec. 4.4: 500,000 particles at density 0.5 fill a 100^3 box per process."""
+    """Sec. 4.5: 500,000 particles at density 0.5 fill a 100^3 box per process."""
     g = _golden("paper_benchmark_pairs.txt")
     M = round((g["particles_per_process"] / 4) ** (1 / 3))
     x, L = O.fcc_lattice(M, g["density"])
@@ -345,8 +345,8 @@ def test_trajectory_gradient_matches_finite_differences():
 
 @pytest.mark.slow
 def test_pair_count_of_paper_benchmark_final_state():
-    """Sec. 5.3 prints 11,629,010..11,656,318 search-length pairs per 500,000-particle process at
-    the end of the Sec. 4.4 run.  A 4,000-particle replica of that run, with cross-border pairs of a
+    """Sec. 5.4 prints 11,629,010..11,656,318 search-length pairs per 500,000-particle process at
+    the end of the Sec. 4.5 run.  A 4,000-particle replica of that run, with cross-border pairs of a
     100^3 process domain counted by both sides as a domain-decomposed list does, lands within 1%."""
     g = _golden("paper_benchmark_pairs.txt")
     x, L = O.fcc_lattice(10, g["density"])
@@ -359,3 +359,21 @@ def test_pair_count_of_paper_benchmark_final_state():
     per_process = (len(pairs) + np.abs(d).sum() / g["box_per_process"]) / len(x)
     paper = 0.5 * (g["pairs_max"] + g["pairs_min"]) / g["particles_per_process"]
     assert per_process == pytest.approx(paper, rel=0.01)
+
+
+# ---------------------------------------------------------------- truncation variants over a run
+
+def test_stored_truncation_drifts_order_as_the_paper_argues():
+    """Sec. 2.1: a potential that jumps at r_c (the plain cut) conserves energy far worse than the
+    forms with V(r_c) = 0, and a longer cutoff narrows the gap.  Checked on the oracle runs stored
+    in truncation_drift_c1.txt (written by make_truncation_drift.py, oracle only), which the GPU
+    drift tests compare against."""
+    d = {}
+    for line in open(os.path.join(GOLDEN, "truncation_drift_c1.txt")):
+        if line.strip() and not line.startswith("#"):
+            rc, mode, mx, rms, slope = line.split()
+            d[(float(rc), mode)] = float(rms)
+    assert len(d) == 6
+    for rc in (2.5, 3.0):
+        assert d[(rc, "cut")] > 4 * max(d[(rc, "quadratic")], d[(rc, "shift")])
+    assert d[(3.0, "cut")] < d[(2.5, "cut")]

@@ -108,3 +108,23 @@ def test_static_export_empty_and_errors():
             s.pairs_static(cap=1)
         assert e.value.code == ljmd.LJ_ERANGE
         assert len(s.pairs()) > 0  # the handle is still usable
+
+
+@pytest.mark.gpu
+def test_static_export_leaves_free_device_memory_unchanged():
+    """After the first call (which resolves the scratch address), further calls change the free
+    device memory by nothing: no allocation anywhere below the entry point, helpers included."""
+    torch = pytest.importorskip("torch")
+    x = synth.dyadic(synth.uniform_positions(1200, 14.0, 31))
+    with _system(ljmd.LJ_MIXED, ljmd.LJ_LIST_FULL) as s:
+        s.set_state(x, None, 14.0)
+        s.build_pairlist()
+        ref, _ = s.pairs_static()
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        for _ in range(5):
+            got, n = s.pairs_static()
+            assert n == len(ref) and np.array_equal(got, ref)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
