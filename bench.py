@@ -34,8 +34,13 @@ WORKLOADS = {
     "fcc4k_rho0.5": dict(M=10, rho=0.5, T=1.0, seed=1, cutoff=2.5, margin=0.5, dt=0.005),
 }
 
-# Nominal FP32 peak of the GPU from its unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Measured peaks of the non-tensor pipes of this GPU type (GB300, 152 SMs, 2070 MHz max): a kernel of
+# independent FMA chains (8 per thread, 256-thread blocks, 4 and 8 blocks per SM), best of 5 launches
+# timed with CUDA events.  FP32 FFMA 75.8 TFLOP/s (94 % of 152 x 128 lanes x 2 x 2.07 GHz); FP64 DFMA
+# 1.008 TFLOP/s.
+FP32_PEAK_TFLOPS = 75.8
+FP64_PEAK_TFLOPS = 1.008
+ALU_PEAK_SOURCE = "measured: FMA-chain kernel on GB300 (FP32 75.8, FP64 1.008 TFLOP/s)"
 
 
 def measured_peaks():
@@ -160,17 +165,43 @@ def recorded_traffic(kernel_name, N):
         return None
 
 
-def force_kernel_work(N, entries, precision, energy=True):
-    """Algorithmic bytes and flops of one force launch over the full list.  Bytes: each list
-    entry once (2 B: a 16-bit index into the key's staged tile), each particle's row (start,
-    length: 8 B), its position once (mixed: FP32 hi and lo parts, 32 B; FP64: 32 B) and its force
-    written once (mixed: float4, 16 B; FP64: 32 B).  Re-reads of neighbour cells for the halo of
-    a tile count zero.  Flops: 22 per listed pair (Alg. 6 with the r^2 < r_c^2 select), 8 more
-    with the energy and virial."""
-    fout = 16 if precision == "mixed" else 32
-    bytes_ = 2 * entries + N * (8 + 32 + fout)
-    flops = entries * (22 + (8 if energy else 0))
-    return bytes_, flops
+def force_kernel_work(N, entries, form, energy=True):
+    """Algorithmic bytes and flops of one force launch.
+
+    bytes (the scope table's count): each list entry once as a 4-byte index and each particle's own
+    position and force once, 32 B in the mixed form (16 B each) and 64 B in the FP64 form; partner
+    positions come from on-chip memory (cell-sorted tiles) and count zero.
+    stored_bytes (this library's layout): 2-byte entries (indices into the key's staged tile), an
+    8-byte row, the own position record (mixed: 16 B fixed point; FP64: 32 B) and the force (mixed:
+    16 B; FP64: 32 B).
+    flops: 22 per list entry (Alg. 6 with the r^2 < r_c^2 select: 3 difference, 5 r^2, 1
+    reciprocal, 4 r^6 and r^14, 3 coefficient, 3 force, 3 accumulation), 3 more for the partner's
+    update with the half list (FP64 form), 8 more with the energy and virial."""
+    half = form == "fp64"
+    own = 32 if form == "mixed" else 64
+    bytes_ = 4 * entries + own * N
+    stored = 2 * entries + N * (8 + own)
+    flops = entries * (22 + (3 if half else 0) + (8 if energy else 0))
+    return bytes_, stored, flops
+
+
+def roofline(kernel, ms, bytes_, flops, peaks, alu_peak, alu_name, peak_kind, traffic=None, extra=None):
+    """Roofline block of one kernel: achieved algorithmic bytes and flops per launch over its mean
+    launch time, each against its measured peak; `bound` names the larger fraction."""
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    tfs = flops / (ms * 1e-3) / 1e12
+    hbm = {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
+           "peak_source": peak_kind + " (copy bandwidth)"}
+    alu = {"achieved": round(tfs, 3), "peak": alu_peak, "unit": "TFLOP/s", "frac": round(tfs / alu_peak, 4),
+           "peak_source": ALU_PEAK_SOURCE, "pipe": alu_name}
+    main, other = (hbm, alu) if hbm["frac"] >= alu["frac"] else (alu, hbm)
+    out = {"bound": "hbm" if main is hbm else "alu", "achieved": main["achieved"], "peak": main["peak"],
+           "unit": main["unit"], "frac": main["frac"], "traffic": traffic, "peak_source": main["peak_source"],
+           ("alu" if main is hbm else "hbm"): other, "kernel": kernel, "kernel_ms": round(ms, 4),
+           "algorithmic_bytes_per_launch": int(bytes_), "algorithmic_flops_per_launch": int(flops)}
+    if extra:
+        out.update(extra)
+    return out
 
 
 def run_ours(args, wl, world, rank, local):
@@ -184,92 +215,85 @@ def run_ours(args, wl, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
     seed = replica_seed(wl["seed"], rank)  # independent replica per rank
+    peaks, peak_kind = measured_peaks()
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    s = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=ljmd.LJ_MIXED, list_form=ljmd.LJ_LIST_AUTO,
-                    energy_every=1, stream=stream)
-    s.init_lattice(wl["M"], wl["rho"], wl["T"], seed)
-    N = s.n
-    s.step(wl["dt"], args.warmup)
-    torch.cuda.synchronize()
-    st0 = s.stats()
-    s.set_profiling(True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(wl["dt"], args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    prof = s.profile()
-    st1 = s.stats()
-    pe, ke, vir = s.energies()
-    s.set_profiling(False)
-    ms = reduce_max(ms, dist)
-    value = job_value(N * args.steps, world, ms * 1e-3)
+    def timed_run(precision, list_form, with_clocks):
+        """Warm-up, then the timed steps between CUDA events on the library's stream (per-phase
+        events on while timing).  Returns the system (still open) and the measurements."""
+        sy = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=precision, list_form=list_form,
+                         energy_every=1, stream=stream)
+        sy.init_lattice(wl["M"], wl["rho"], wl["T"], seed)
+        sy.step(wl["dt"], args.warmup)
+        torch.cuda.synchronize()
+        st0 = sy.stats()
+        sy.set_profiling(True)
+        clocks = ClockSampler(local) if with_clocks else None
+        if clocks:
+            clocks.start()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sy.step(wl["dt"], args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        ms_ = reduce_max(e0.elapsed_time(e1), dist)
+        prof = sy.profile()
+        st1 = sy.stats()
+        sy.set_profiling(False)
+        return sy, dict(ms=ms_, prof=prof, st0=st0, st1=st1, clocks=clk)
 
-    # dominant kernel: the force kernel (CUDA events around each launch on the library's stream)
-    f_ms = prof["force_ms"] / max(prof["force_launches"], 1)
+    # ---- the headline: mixed form, automatic list form
+    s, m = timed_run(ljmd.LJ_MIXED, ljmd.LJ_LIST_AUTO, True)
+    N = s.n
+    ms, prof, st0, st1 = m["ms"], m["prof"], m["st0"], m["st1"]
+    value = job_value(N * args.steps, world, ms * 1e-3)
+    pe, ke, vir = s.energies()
     entries = st1["list_entries"]
-    b, fl = force_kernel_work(N, entries, "mixed")
-    peaks, peak_kind = measured_peaks()
-    ach_gbs = b / (f_ms * 1e-3) / 1e9
-    ach_tf = fl / (f_ms * 1e-3) / 1e12
-    hbm_frac = ach_gbs / peaks["hbm_gbs"]
-    alu_frac = ach_tf / FP32_PEAK_TFLOPS
     half = st1["list_form"] == ljmd.LJ_LIST_HALF  # the automatic list form of this density
     # the mixed form on tiles: the pipelined kernel with the full list, the single-buffer one with the half
     kernel_name = "k_force_tile" if half else "k_force_pipe"
-    traffic = recorded_traffic(kernel_name, N)
-    if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": round(ach_tf, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                "frac": round(alu_frac, 4), "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "hbm": {"achieved": round(ach_gbs, 1), "peak": peaks["hbm_gbs"], "frac": round(hbm_frac, 4),
-                        "peak_source": peak_kind}}
-    else:
-        roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(hbm_frac, 4), "traffic": traffic, "peak_source": peak_kind,
-                "alu": {"achieved": round(ach_tf, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "frac": round(alu_frac, 4)}}
-    roof["kernel"] = kernel_name
-    roof["kernel_ms"] = round(f_ms, 4)
-    roof["algorithmic_bytes_per_launch"] = b
-    roof["algorithmic_flops_per_launch"] = fl
-
+    f_ms = prof["force_ms"] / max(prof["force_launches"], 1)
+    b, stored, fl = force_kernel_work(N, entries, "mixed")
+    roof = roofline(kernel_name, f_ms, b, fl, peaks, FP32_PEAK_TFLOPS, "fp32", peak_kind,
+                    traffic=recorded_traffic(kernel_name, N),
+                    extra={"stored_list": {"bytes_per_launch": int(stored),
+                                           "hbm_frac": round(stored / (f_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                                           "note": "2-byte tile-local entries, 8-byte rows, 16-byte records"}})
     breakdown = {k: round(prof[k], 3) for k in ("force_ms", "integrate_ms", "rebuild_ms", "energy_ms")}
     breakdown.update({k: prof[k] for k in ("force_launches", "integrate_launches", "rebuilds", "energy_launches")})
+    x_mixed, f_mixed, box = None, None, s.box
+    if rank == 0 and not args.no_cpu_baseline and not args.skip_cpu:
+        x_mixed, _, f_mixed, _ = s.get_state()
     s.close()
 
-    # FP64 form, same workload (shorter run: it is FP64-pipe bound)
+    # ---- the FP64 form on the same workload and window (half list: its pair arithmetic is FP64)
     fp64 = None
+    x64 = f64 = None
     if not args.no_fp64:
-        k64 = max(3, args.steps // 20)
-        s64 = ljmd.System(cutoff=wl["cutoff"], margin=wl["margin"], precision=ljmd.LJ_FP64,
-                          list_form=ljmd.LJ_LIST_HALF, energy_every=1, stream=stream)
-        s64.init_lattice(wl["M"], wl["rho"], wl["T"], seed)
-        s64.step(wl["dt"], 3)
-        torch.cuda.synchronize()
-        barrier()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        s64.step(wl["dt"], k64)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms64 = a0.elapsed_time(a1)
-        fp64 = {"value": N * k64 * world / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
-                "list": "half", "speedup_mixed_over_fp64": (ms64 / k64) / (ms / args.steps)}
+        s64, m64 = timed_run(ljmd.LJ_FP64, ljmd.LJ_LIST_HALF, False)
+        p64 = m64["prof"]
+        e64 = m64["st1"]["list_entries"]
+        f64_ms = p64["force_ms"] / max(p64["force_launches"], 1)
+        b64, stored64, fl64 = force_kernel_work(N, e64, "fp64")
+        fp64 = {"value": job_value(N * args.steps, world, m64["ms"] * 1e-3), "unit": UNIT,
+                "ms_per_step": m64["ms"] / args.steps, "steps": args.steps, "warmup": args.warmup, "list": "half",
+                "rebuilds": m64["st1"]["rebuilds"] - m64["st0"]["rebuilds"],
+                "speedup_mixed_over_fp64": (m64["ms"] / args.steps) / (ms / args.steps),
+                "roofline": roofline("k_force_pipe (FP64, half list)", f64_ms, b64, fl64, peaks, FP64_PEAK_TFLOPS,
+                                     "fp64", peak_kind),
+                "phases": {k: round(p64[k], 3) for k in ("force_ms", "integrate_ms", "rebuild_ms")}}
+        if rank == 0 and not args.no_cpu_baseline and not args.skip_cpu:
+            x64, _, f64, _ = s64.get_state()
         s64.close()
 
-    # end to end through the public API with host buffers: H2D of the initial state from pinned
+    # ---- end to end through the public API with host buffers: H2D of the initial state from pinned
     # memory, K steps, D2H of the final state and energies, all inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -297,9 +321,10 @@ def run_ours(args, wl, world, rank, local):
                "note": "set_state from pinned host + K steps + get_state/energies to host, per K-step job"}
         s2.close()
 
-    batched = None if args.no_batch else run_batched(args, stream, world, rank, barrier)
+    batched = None if args.no_batch else run_batched(args, stream, world, rank, barrier, peaks, peak_kind)
     replica = None if args.no_replica else run_paper_replica(stream)
-    adjoint = None if args.no_adjoint else run_adjoint(stream)
+    adjoint = None if args.no_adjoint else run_adjoint(stream, peaks, peak_kind)
+    truncation = None if args.no_truncation else run_truncation(stream)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -313,7 +338,7 @@ def run_ours(args, wl, world, rank, local):
         "fp64": fp64,
         "e2e": e2e,
         "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
-        "clocks": clk,
+        "clocks": m["clocks"],
         "phases": breakdown,
         "list": {"entries_per_particle": entries / N, "rebuilds": st1["rebuilds"] - st0["rebuilds"],
                  "mean_lifetime_steps": args.steps / max(st1["rebuilds"] - st0["rebuilds"], 1)},
@@ -321,10 +346,15 @@ def run_ours(args, wl, world, rank, local):
         "batched": batched,
         "paper_replica": replica,
         "adjoint": adjoint,
+        "truncation": truncation,
         "pair_interactions_per_s": entries * args.steps * world / (ms * 1e-3),
     }
     if rank == 0 and not args.no_cpu_baseline and not args.skip_cpu:
-        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+        base, acc = cpu_baseline(wl, args.cpu_seconds, x_mixed, f_mixed, box, x64, f64)
+        out["cpu_baseline"] = base
+        out["accuracy_vs_oracle"] = acc
+        if not args.no_cpu_verlet:
+            out["cpu_verlet_list"] = cpu_verlet_list(wl)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -364,10 +394,12 @@ def run_paper_replica(stream):
     return out
 
 
-def run_batched(args, stream, world, rank, barrier):
+def run_batched(args, stream, world, rank, barrier, peaks, peak_kind):
     """Batched-replica workload: 256 replicas, N ~ U[500, 50000], rho ~ U[0.3, 0.9], T ~ U[0.7, 1.5]
     (FCC filled then thinned), r_c 2.5, margin 0.3, dt 0.004, mixed form; tiles autotuned, steps
-    replayed as a captured 10-step CUDA graph.  Timed with CUDA events on the library's stream."""
+    replayed as a captured 10-step CUDA graph.  Timed with the host clock around one batch call
+    (graph replays, one synchronisation at the end); the force kernel's roofline from CUDA events
+    around plain launches afterwards."""
     import torch
     from paper_1012_2677_gb300 import ljmd, synth
     n, box, x, v, _ = synth.batch_workload(256, 1000 + 100 * rank)
@@ -384,19 +416,23 @@ def run_batched(args, stream, world, rank, barrier):
         b.step(0.004, steps, graph_steps=K)  # returns after the stream is synchronised
         dt_s = time.perf_counter() - t0
         st1 = b.stats()
+        f_ms = b.time_force(trials=5)
     N = int(n.sum())
+    bb, stored, fl = force_kernel_work(N, st1["list_entries"], "mixed", energy=False)
     return {"workload": "256 replicas, N in [500, 50000] (%d particles), rho in [0.3, 0.9], T in [0.7, 1.5], "
                         "margin 0.3, dt 0.004" % N,
             "value": N * steps * world / dt_s, "unit": UNIT, "steps": steps, "ms_per_step": dt_s / steps * 1e3,
             "graph_steps": K, "autotuned": {"tile_cells": tile, "lanes": lanes, "cost_ms": round(tune_ms, 4)},
             "rebuilds": st1["rebuilds"] - st0["rebuilds"],
             "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+            "roofline": roofline("k_force_batch", f_ms, bb, fl, peaks, FP32_PEAK_TFLOPS, "fp32", peak_kind),
             "timing": "host clock around one ljmd_batch_step call (graph replays, one synchronisation at the end)"}
 
 
-def run_adjoint(stream):
-    """Differentiable-trajectory workload: 32,000 particles (FCC 20^3 x 4), rho 0.6, T 1.2,
-    50 steps, loss over the last 10, checkpoints every 10; forward + checkpointed reverse pass."""
+def run_adjoint(stream, peaks, peak_kind):
+    """Differentiable-trajectory workload: 32,000 particles (FCC 20^3 x 4 thinned), rho 0.6, T 1.2,
+    50 steps, loss over the last 10, checkpoints every 10; forward + checkpointed reverse pass.  The
+    adjoint kernel's roofline from its CUDA-event phase timer."""
     import numpy as np
     import torch
     from paper_1012_2677_gb300 import ljmd, synth
@@ -407,24 +443,74 @@ def run_adjoint(stream):
         with ljmd.System(cutoff=2.5, margin=0.5, precision=prec, energy_every=0, stream=stream) as s:
             s.traj_loss_grad(x, v, L, 0.005, 10, 2, 5)  # warm-up
             torch.cuda.synchronize()
+            s.set_profiling(True)
             t0 = time.perf_counter()
             loss, gx, gv, gth = s.traj_loss_grad(x, v, L, 0.005, 50, 10, 10)
             t = time.perf_counter() - t0
-        res[name] = {"seconds": t, "particle_steps_per_s": len(x) * 50 / t, "loss": loss,
-                     "grad_norm_x0": float(np.linalg.norm(gx)), "dloss_deps": gth[0], "dloss_dsigma": gth[1]}
+            prof = s.profile()
+            st = s.stats()
+        a_ms = prof["adjoint_ms"] / max(prof["adjoint_launches"], 1)
+        E, n = st["list_entries"], len(x)
+        # per list entry 12 flops (difference, r^2, cutoff test); per pair inside r_c (the continuum
+        # fraction (r_c / r_s)^3 of the entries) 83 more: u, u', u'', the sigma derivatives, the
+        # Hessian-vector row, force and parameter sums.  Bytes: 4 per entry, and per particle the
+        # position (16 B mixed, 32 B FP64), w, H w and F (32 B each).
+        inner = (2.5 / 3.0) ** 3
+        flops = E * (12 + 83 * inner)
+        bytes_ = 4 * E + n * ((16 if name == "mixed" else 32) + 96)
+        res[name] = {"seconds": t, "particle_steps_per_s": n * 50 / t, "loss": loss,
+                     "grad_norm_x0": float(np.linalg.norm(gx)), "dloss_deps": gth[0], "dloss_dsigma": gth[1],
+                     "roofline": roofline("k_adjoint_tile", a_ms, bytes_, flops, peaks,
+                                          FP32_PEAK_TFLOPS if name == "mixed" else FP64_PEAK_TFLOPS,
+                                          "fp32" if name == "mixed" else "fp64", peak_kind,
+                                          extra={"launches": prof["adjoint_launches"]})}
     res["note"] = "forward 50 steps + reverse pass (one Hessian-vector product per state, segments recomputed)"
     return res
 
 
-def _oracle_sample_rate(wl, target_s, sample_seed=7):
-    """Oracle (all-pairs FP64) on a sample of the workload: forces on S particles against all N.
-    Returns (particle-steps/s, cores, sample description)."""
+def drift_stats(E, n, dt):
+    """(max |E(t) - E(0)| / |E(0)|, rms of (E(t) - E(0)) / |E(0)|, least-squares slope of E / N)."""
     import numpy as np
+    e0 = abs(E[0])
+    t = np.arange(len(E)) * dt
+    return (float(np.abs(E - E[0]).max() / e0), float(np.sqrt(((E - E[0]) ** 2).mean()) / e0),
+            float(np.polyfit(t, E / n, 1)[0]))
+
+
+def run_truncation(stream):
+    """Energy conservation of each truncation of the potential (Sec. 2.1: Eq. 2, the constant shift,
+    the plain cut) at r_c = 2.5 and 3.0 on the small FP64 configuration (FCC 10^3 x 4, rho 0.5, T 1,
+    seed 1, dt 0.005, 1000 steps, FP64 form): drift and slope of the total energy per particle."""
+    import torch
+    from paper_1012_2677_gb300 import ljmd
+    steps, dt = 1000, 0.005
+    out = {}
+    for rc in (2.5, 3.0):
+        for name, mode in (("quadratic", ljmd.LJ_TRUNC_QUADRATIC), ("shift", ljmd.LJ_TRUNC_SHIFT),
+                           ("cut", ljmd.LJ_TRUNC_CUT)):
+            log = torch.zeros((steps + 8, 4), dtype=torch.float64, device="cuda")
+            with ljmd.System(cutoff=rc, margin=0.5, truncation=mode, precision=ljmd.LJ_FP64,
+                             list_form=ljmd.LJ_LIST_AUTO, energy_every=1, stream=stream) as s:
+                s.init_lattice(10, 0.5, 1.0, 1)
+                s.set_energy_log(log)
+                s.step(dt, steps)
+                n = s.n
+            rec = log.cpu().numpy()[:steps + 1]
+            mx, rms, slope = drift_stats(rec[:, 1] + rec[:, 2], n, dt)
+            out["rc%.1f_%s" % (rc, name)] = {"max_rel_drift": mx, "rms_rel_drift": rms, "slope_per_particle": slope}
+    out["workload"] = "FCC 10^3 x 4, rho 0.5, T 1, seed 1, dt 0.005, 1000 steps, FP64 form"
+    return out
+
+
+def _oracle_sample_rate(wl, target_s, x=None, L=None, sample_seed=7):
+    """Oracle (all-pairs FP64) on a sample of the workload: forces on S particles against all N, on
+    the given state (else the FCC start, displaced).  Returns (rate, cores, description, seconds, idx, F)."""
     import oracle as O
     from paper_1012_2677_gb300 import synth
-    x, L = O.fcc_lattice(wl["M"], wl["rho"])
+    if x is None:
+        x, L = O.fcc_lattice(wl["M"], wl["rho"])
+        x = O.wrap(x + synth.displacements(len(x), 0.05, sample_seed), L)
     N = len(x)
-    x = O.wrap(x + synth.displacements(N, 0.05, sample_seed), L)
     p = O.LJParams(rc_over_sigma=wl["cutoff"])
     idx = synth.subset(N, 64, sample_seed)
     t0 = time.perf_counter()
@@ -433,14 +519,56 @@ def _oracle_sample_rate(wl, target_s, sample_seed=7):
     S = int(max(64, min(N, 64 * target_s / max(t_small, 1e-6))))
     idx = synth.subset(N, S, sample_seed + 1)
     t0 = time.perf_counter()
-    O.forces_sample(x, L, idx, p)
+    F = O.forces_sample(x, L, idx, p)
     t = time.perf_counter() - t0
-    return S / t, O.num_threads(), "all-pairs FP64 forces on %d of %d particles (%.1f s)" % (S, N, t), t, S
+    return S / t, O.num_threads(), "all-pairs FP64 forces on %d of %d particles (%.1f s)" % (S, N, t), t, idx, F
 
 
-def cpu_baseline(wl, seconds):
-    rate, cores, desc, _, _ = _oracle_sample_rate(wl, seconds)
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+def _force_error(f, idx, F):
+    import numpy as np
+    rms = float(np.sqrt((F ** 2).sum(1).mean()))
+    err = float(np.sqrt(((f[idx] - F) ** 2).sum(1)).max() / rms)
+    return {"max_dF_over_rms_F": err, "rms_F": rms, "sample": int(len(idx))}
+
+
+def cpu_baseline(wl, seconds, x_mixed=None, f_mixed=None, L=None, x64=None, f64=None):
+    """The oracle timed on the host cores on a bounded sample; the same sample (forces of the
+    mixed form's final state) gives the measured error of the GPU forces against the oracle, and a
+    small second sample that of the FP64 form's final state."""
+    rate, cores, desc, _, idx, F = _oracle_sample_rate(wl, seconds, x_mixed, L)
+    base = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    acc = {}
+    if f_mixed is not None:
+        acc["mixed"] = _force_error(f_mixed, idx, F)
+        acc["mixed"]["tolerance"] = 1e-5
+    if x64 is not None:
+        import oracle as O
+        from paper_1012_2677_gb300 import synth
+        idx64 = synth.subset(len(x64), 512, 17)
+        acc["fp64"] = _force_error(f64, idx64, O.forces_sample(x64, L, idx64, O.LJParams(rc_over_sigma=wl["cutoff"])))
+        acc["fp64"]["tolerance"] = 1e-11
+    acc["state"] = "after the timed steps (liquid), forces as the GPU last computed them"
+    return base, acc
+
+
+def cpu_verlet_list(wl, target_steps=None):
+    """The paper's Verlet-list method on the host cores in FP64 (oracle/cellverlet.c: cell sort, half
+    list, branch-free force with Newton's third law, velocity-Verlet, margin/2 rebuilds) on the full
+    workload, a few steps after its first construction."""
+    import oracle as O
+    from oracle import cellverlet as CV
+    x, L = O.fcc_lattice(wl["M"], wl["rho"])
+    v = O.init_velocities(len(x), wl["T"], wl["seed"])
+    N = len(x)
+    steps = target_steps or int(min(100, max(3, 6e7 // N)))
+    t0 = time.perf_counter()
+    r = CV.run(x, v, L, wl["dt"], steps, wl["margin"], O.LJParams(rc_over_sigma=wl["cutoff"]))
+    wall = time.perf_counter() - t0
+    return {"value": N * steps / r["seconds"], "unit": UNIT, "cores": O.num_threads(),
+            "kind": "cell-list + sorted Verlet list (Alg. 1, 4-6), FP64, OpenMP",
+            "sample": "%d particles, %d steps after the first construction (%d constructions in all, %.1f s of "
+                      "%.1f s wall)" % (N, steps, r["rebuilds"], r["seconds"], wall),
+            "pairs_per_particle": r["pairs"] / N}
 
 
 def run_reference(args, wl, world, rank):
@@ -492,6 +620,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-replica", action="store_true")
+    ap.add_argument("--no-truncation", action="store_true")
+    ap.add_argument("--no-cpu-verlet", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--skip-cpu", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()

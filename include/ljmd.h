@@ -111,6 +111,8 @@ typedef struct ljmd_profile {
   int64_t rebuilds;
   double energy_ms;        /* final energy reductions */
   int64_t energy_launches;
+  double adjoint_ms;       /* adjoint kernel (Hessian-vector product, forces, parameter derivatives) */
+  int64_t adjoint_launches;
 } ljmd_profile;
 
 typedef struct ljmd_sys ljmd_sys;
@@ -320,8 +322,8 @@ int ljmd_get_stats(ljmd_sys* sys, ljmd_stats* out);
 
 /*
  * Turn per-phase timing on (enable = 1, resets the accumulators) or off (0).  While on, CUDA
- * events are recorded on the handle's stream around every force, integrate, rebuild and
- * energy launch; the kernels themselves are unchanged.
+ * events are recorded on the handle's stream around every force, integrate, rebuild, energy and
+ * adjoint launch; the kernels themselves are unchanged.
  */
 int ljmd_set_profiling(ljmd_sys* sys, int32_t enable);
 
@@ -426,6 +428,16 @@ int ljmd_batch_set_tuning(ljmd_batch* b, int32_t tile_cells, int32_t lanes);
  * shape with the least force + construction / 10.  The state is unchanged.  Outputs may be NULL.
  */
 int ljmd_batch_autotune(ljmd_batch* b, int32_t trials, int32_t* best_tile, int32_t* best_lanes, double* best_ms);
+
+/*
+ * Mean device time, in milliseconds, of one force launch over all replicas (the kernel of Alg. 4-6
+ * on every replica's list at the current positions): one warm-up launch, then `trials` launches
+ * timed with CUDA events on the batch's stream.  The forces are recomputed; positions, velocities
+ * and lists are unchanged.  A measurement call (no counterpart in the paper), for the roofline of
+ * the batched form.  Synchronises.  Errors: LJ_EINVAL (NULL b or ms_per_launch, trials <= 0),
+ * LJ_ESTATE (no state set), LJ_EDEVICE.
+ */
+int ljmd_batch_time_force(ljmd_batch* b, int32_t trials, double* ms_per_launch);
 
 /*
  * List-validity rule (Sec. 2.3, Alg. 2); the list is rebuilt when the rule says it expired.

@@ -125,6 +125,25 @@ __device__ __forceinline__ void split_hi_lo(double xs, float& hi, float& lo) {
   if (sign) lo = -lo;
 }
 
+// Fixed-point coordinate of a stored FP64 coordinate x_state (positive, normal): round(x_state 2^qk)
+// mod 2^32, from the FP64 bits with integer operations only.  x_state = m 2^(e - 52) with the
+// 53-bit significand m, so x_state 2^qk = m 2^(e + qk - 52); the kernels keep 52 - e - qk in
+// [1, 63] (qk <= 40 and stored coordinates in [2, 2^11)), so the value is m shifted right with
+// rounding half up.
+__device__ __forceinline__ uint32_t fixq(double xs, int qk) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(xs);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const unsigned long long m = (b & 0xfffffffffffffULL) | (1ULL << 52);
+  const int sh = 52 - e - qk;
+  if (sh <= 0) return (uint32_t)(m << (-sh < 63 ? -sh : 63));
+  if (sh >= 64) return 0u;
+  return (uint32_t)((m + (1ULL << (sh - 1))) >> sh);
+}
+
+// Difference of two fixed-point coordinates as an FP32 number of units u (one rounding, to 24
+// significant bits; the integer difference itself is exact modulo 2^32).
+__device__ __forceinline__ float qdiff(uint32_t a, uint32_t b) { return __int2float_rn((int)(a - b)); }
+
 // ---- asynchronous bulk copies into shared memory (cp.async.bulk + mbarrier, sm_90 and later) ----
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -134,6 +153,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)
 __device__ __forceinline__ float4 lds_f4(uint32_t a) {
   float4 v;
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint4 lds_u4(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
   return v;
 }
 __device__ __forceinline__ uint32_t lds_u16(uint32_t a) {

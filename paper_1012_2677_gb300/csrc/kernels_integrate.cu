@@ -4,8 +4,10 @@
 //   v     <- v + (kpre + kpost) F (the first half-kick of the next step folded in)
 //   x     <- x + dt v             (drift)
 //
-// then the force kernel's copy of the positions is rewritten and the displacement since the
-// last list construction is reduced (device-wide max) for the margin/2 validity rule.
+// then the force kernel's copy of the positions is rewritten (mixed form: the 32-bit fixed-point
+// records, X = round(x_state / u) mod 2^32 with u = 2^-qk and the sorted index in w; FP64 form: a
+// dvec4 copy) and the displacement since the last list construction is reduced (device-wide max)
+// for the margin/2 validity rule.
 // State x, v is FP64 (positions stored as offset + x).  Per component the FP64 pipe does two
 // FMAs; the kinetic energy of the mixed form is taken in FP32 per particle and summed in FP64.
 // In the mixed form every FP32 <-> FP64 conversion is done with integer operations (exact for
@@ -18,9 +20,10 @@ namespace ljmd {
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, double* __restrict__ v,
                                                    const void* __restrict__ fptr, void* __restrict__ pos,
-                                                   float4* __restrict__ lo, const void* __restrict__ refp,
-                                                   int64_t N, IntegrateArgs a, double* __restrict__ ke_part,
-                                                   uint32_t* __restrict__ dmax_bits, int32_t* __restrict__ status) {
+                                                   const void* __restrict__ refp, int64_t N, IntegrateArgs a,
+                                                   double* __restrict__ ke_part, uint32_t* __restrict__ dmax_bits,
+                                                   int32_t* __restrict__ status) {
+  const float qu = __int_as_float((127 - a.qk) << 23);  // u = 2^-qk
   const double kk = a.kpre + a.kpost;
   const float kpre_f = (float)a.kpre;
   double ke_acc = 0.0;
@@ -76,17 +79,12 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
       // speed of the drift (the velocity that moved the particle this step), for the DUTC rule
       v2max = fmaxf(v2max, vd2);
       if (MIXED) {
-        float4 h, l;
-        split_hi_lo(xs[0], h.x, l.x);
-        split_hi_lo(xs[1], h.y, l.y);
-        split_hi_lo(xs[2], h.z, l.z);
-        h.w = 0.0f;
-        l.w = 0.0f;
-        ((float4*)pos)[i] = h;
-        lo[i] = l;
-        // displacement since the list was built: (hi - hi_ref) is exact, plus lo
-        const float4 r = ((const float4*)refp)[i];
-        const float dx = (h.x - r.x) + l.x, dy = (h.y - r.y) + l.y, dz = (h.z - r.z) + l.z;
+        const uint4 q = make_uint4(fixq(xs[0], a.qk), fixq(xs[1], a.qk), fixq(xs[2], a.qk), (uint32_t)i);
+        ((uint4*)pos)[i] = q;
+        // displacement since the list was built, from the records: exact integer differences
+        // (within u of the FP64 ones), converted once and scaled by u
+        const uint4 r = ((const uint4*)refp)[i];
+        const float dx = qdiff(q.x, r.x) * qu, dy = qdiff(q.y, r.y) * qu, dz = qdiff(q.z, r.z) * qu;
         d2max = fmaxf(d2max, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
       } else {
         ((dvec4*)pos)[i] = make_dvec4(xs[0], xs[1], xs[2], 0.0);
@@ -145,46 +143,49 @@ static int one_wave(int64_t N) {
   return b < per_sm * sms ? b : per_sm * sms;
 }
 
-int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, float4* lo, const void* ref,
-                     int64_t N, IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status,
-                     cudaStream_t s) {
+int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, const void* ref, int64_t N,
+                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, cudaStream_t s) {
   const int blocks = precision == LJ_MIXED ? one_wave<true>(N) : one_wave<false>(N);
   if (precision == LJ_MIXED)
-    k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, lo, ref, N, a, ke_part, dmax_bits, status);
+    k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status);
   else
-    k_integrate<false><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, lo, ref, N, a, ke_part, dmax_bits, status);
+    k_integrate<false><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status);
   return blocks;
 }
 
-// Position copies for the force and list kernels from the FP64 state (no integration):
-// the hi/lo split always (the list build uses it in both forms); for FP64 also the dvec4
-// copy; and the displacement reference (hi for mixed, the dvec4 for FP64) if ref != NULL.
-__global__ void k_shadow(const double* __restrict__ x, int64_t N, int mixed, float4* __restrict__ hi,
-                         float4* __restrict__ lo, dvec4* __restrict__ pos64, void* __restrict__ ref, const int* __restrict__ pred) {
+// Position copies for the force and list kernels from the FP64 state (no integration): the FP32
+// hi parts always (the list construction filters on them in both forms); for the mixed form the
+// fixed-point records, for FP64 the dvec4 copy; and the displacement reference (the records for
+// mixed, the dvec4 for FP64) if ref != NULL.
+__global__ void k_shadow(const double* __restrict__ x, int64_t N, int mixed, int qk, float4* __restrict__ hi,
+                         uint4* __restrict__ xq, dvec4* __restrict__ pos64, void* __restrict__ ref,
+                         const int* __restrict__ pred) {
   if (pred && !*pred) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double a = x[i], b = x[N + i], c = x[2 * N + i];
-    float4 h, l;
-    split_hi_lo(a, h.x, l.x);
-    split_hi_lo(b, h.y, l.y);
-    split_hi_lo(c, h.z, l.z);
+    float4 h;
+    float unused;
+    split_hi_lo(a, h.x, unused);
+    split_hi_lo(b, h.y, unused);
+    split_hi_lo(c, h.z, unused);
     h.w = 0.0f;
-    l.w = 0.0f;
     hi[i] = h;
-    lo[i] = l;
-    if (!mixed) pos64[i] = make_dvec4(a, b, c, 0.0);
-    if (ref) {
-      if (mixed) ((float4*)ref)[i] = h;
-      else ((dvec4*)ref)[i] = make_dvec4(a, b, c, 0.0);
+    if (mixed) {
+      const uint4 q = make_uint4(fixq(a, qk), fixq(b, qk), fixq(c, qk), (uint32_t)i);
+      xq[i] = q;
+      if (ref) ((uint4*)ref)[i] = q;
+    } else {
+      pos64[i] = make_dvec4(a, b, c, 0.0);
+      if (ref) ((dvec4*)ref)[i] = make_dvec4(a, b, c, 0.0);
     }
   }
 }
 
-void launch_shadow_all(const double* x, int64_t N, int mixed, float4* hi, float4* lo, dvec4* pos64, void* ref,
+void launch_shadow_all(const double* x, int64_t N, int mixed, int qk, float4* hi, uint4* xq, dvec4* pos64, void* ref,
                        cudaStream_t s, const int* pred) {
   int64_t b = (N + 255) / 256;
   if (b < 1) b = 1;
-  k_shadow<<<(int)(b < 1048576 ? b : 1048576), 256, 0, s>>>(x, N, mixed, hi, lo, pos64, ref, pred);
+  k_shadow<<<(int)(b < 1048576 ? b : 1048576), 256, 0, s>>>(x, N, mixed, qk, hi, xq, pos64, ref, pred);
 }
 
 }  // namespace ljmd

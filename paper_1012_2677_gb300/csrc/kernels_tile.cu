@@ -9,10 +9,12 @@
 // the tile's rows and its list segment, all completing on one mbarrier that the CTA waits on
 // (bounded).  The periodic image shifts (-L, 0, +L per axis) are then added in shared memory.
 //
-// Mixed form: the copies are the hi/lo FP32 split of the stored FP64 coordinates and the shift
-// is split the same way, so hi + shift_hi is exact and a partner difference
-// d = (hi_j - hi_i) + (lo_j - lo_i) carries one rounding.  FP64 form: the FP64 coordinates,
-// with the shift code kept in w and added to the exact difference.
+// Mixed form, force and adjoint kernels: the copies are the fixed-point coordinates of the stored
+// FP64 positions (X = round(x / u) mod 2^32, u = 2^-qk, one 16-byte record per particle with the
+// sorted index in w), the image shift is the integer round(L / u), and a partner difference is
+// the exact integer X_j - X_i converted once to FP32.  List kernels: the FP32 hi parts (top 24
+// significand bits) of the stored coordinates, whose differences are exact.  FP64 form: the FP64
+// coordinates, with the shift code kept in w and added to the exact difference.
 //
 // The list holds 16-bit indices into the key particle's staged tile; rows are (start, length)
 // per particle; the rows of one tile form one contiguous segment, padded to 8 entries so that
@@ -205,9 +207,8 @@ __device__ __forceinline__ int slot_cell(const TileShared& S, int s) {
 
 // Shared-memory layout of a staged tile (byte offsets from the dynamic shared base).
 struct TileLayout {
-  size_t pos;    // MIXED: hi float4 [ms]; FP64: dvec4 [ms]
-  size_t lo;     // MIXED: lo float4 [ms] (force only)
-  size_t gid;    // int [ms]
+  size_t pos;    // MIXED: fixed-point uint4 [ms] (force, adjoint) or hi float4 [ms] (list); FP64: dvec4 [ms]
+  size_t gid;    // int [ms] (where the sorted index is not carried in the staged record)
   size_t rows;   // uint2 [max_own + 2] (force only)
   size_t ent;    // uint16 [list_cap] (force only)
   size_t cnt;    // int [max_own] (list only), then pre [max_own], then masks [max_own * max_chunks]
@@ -222,8 +223,6 @@ __host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, b
   const size_t ms = (size_t)ta.max_staged;
   L.pos = 0;
   size_t o = align16(ms * (mixed ? 16 : 32));
-  L.lo = o;
-  if (mixed && force) o += align16(ms * 16);
   L.gid = o;
   if (gid) o += align16(ms * 4);  // the full-list force kernel needs no sorted indices
   L.rows = o;
@@ -241,17 +240,17 @@ __host__ __device__ __forceinline__ TileLayout tile_layout(const TileArgs& ta, b
 }
 
 // Issue the bulk copies of one tile (warp `issuer`; lane k < 9 handles column k, lane 9 the rows
-// and list segment), all completing on `bar`.  Copies: positions (hi [+ lo] or FP64), and for the
+// and list segment), all completing on `bar`.  Copies: positions (fixed-point records, hi or FP64), and for the
 // force kernel the own rows and the list segment.  No barrier inside: the other warps go on.
 template <bool MIXED, bool FORCE>
 __device__ __forceinline__ void stage_issue(const TileInfo& ti, const TileArgs& ta, const void* __restrict__ pos,
-                                            const float4* __restrict__ lo, const uint2* __restrict__ rows,
-                                            const uint16_t* __restrict__ ent, TileShared& S, unsigned char* smem,
-                                            const TileLayout& L, uint64_t* bar, int issuer = 0) {
+                                            const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
+                                            TileShared& S, unsigned char* smem, const TileLayout& L, uint64_t* bar,
+                                            int issuer = 0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned bpp = MIXED ? 16u : 32u;
   if (warp != issuer) return;
-  unsigned bytes = (unsigned)S.total * bpp * ((MIXED && FORCE) ? 2u : 1u);
+  unsigned bytes = (unsigned)S.total * bpp;
   int r0 = 0, r1 = 0;
   const int n_own = S.own1 - S.own0;
   if (FORCE) {
@@ -283,8 +282,7 @@ __device__ __forceinline__ void stage_issue(const TileInfo& ti, const TileArgs& 
         const size_t gsrc = (size_t)S.g0[q0];
         const size_t dst = (size_t)S.offq[q0];
         if (MIXED) {
-          bulk_g2s(smem + L.pos + 16 * dst, (const float4*)pos + gsrc, 16u * n, bar);
-          if (FORCE) bulk_g2s(smem + L.lo + 16 * dst, lo + gsrc, 16u * n, bar);
+          bulk_g2s(smem + L.pos + 16 * dst, (const uint4*)pos + gsrc, 16u * n, bar);
         } else {
           bulk_g2s(smem + L.pos + 32 * dst, (const dvec4*)pos + gsrc, 32u * n, bar);
         }
@@ -298,21 +296,15 @@ __device__ __forceinline__ void stage_issue(const TileInfo& ti, const TileArgs& 
   }
 }
 
-// Image shift of one staged hi/lo coordinate by S = s L_hi (+ s L_lo into lo), exact in hi + lo:
-// hi + S can round when it leaves the binade of hi (a particle that drifted below the offset
-// since the last wrap sits on the finer grid of the binade below), so the rounding error is
-// recovered with Knuth's two-sum and moved into lo.
-__device__ __forceinline__ void shift_hi_lo(float& h, float& l, float s, const Geom& g) {
-  const float S = s * g.L_hi;  // exact: s is -1, 0 or +1
-  const float t = __fadd_rn(h, S);
-  const float bv = __fsub_rn(t, h);
-  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bv)), __fsub_rn(S, bv));
-  h = t;
-  l = __fadd_rn(l, __fadd_rn(err, s * g.L_lo));
+// Image shift of one staged fixed-point coordinate by s L (s = -1, 0, +1): the integer s round(L / u)
+// added modulo 2^32 (exact; the image carries the rounding of L / u, at most u / 2).
+__device__ __forceinline__ uint32_t shift_q(uint32_t q, int s, const Geom& g) {
+  return s > 0 ? q + g.Lq : (s < 0 ? q - g.Lq : q);
 }
 
 // Wait (all threads, bounded) for the copies of a staged tile, then fill in the image shifts
-// (mixed: added to hi/lo; FP64: code in w) and, if wanted, the sorted indices.  Returns false
+// (mixed: added to the fixed-point record or to hi; FP64: code in w) and, if wanted, the sorted
+// indices.  Returns false
 // (all threads) on timeout, after recording it; the caller drains any other copies in flight.
 template <bool MIXED, bool FORCE>
 __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs& ta, const Geom& g, TileShared& S,
@@ -345,13 +337,13 @@ __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs&
     for (int s = a + lane; s < b; s += 32) {
       if (MIXED) {
         if (shifted) {
-          float4* h = (float4*)(smem + L.pos) + s;
           if (FORCE) {
-            float4* l = (float4*)(smem + L.lo) + s;
-            shift_hi_lo(h->x, l->x, (float)sx, g);
-            shift_hi_lo(h->y, l->y, (float)sy, g);
-            shift_hi_lo(h->z, l->z, (float)sz, g);
+            uint4* q = (uint4*)(smem + L.pos) + s;
+            q->x = shift_q(q->x, sx, g);
+            q->y = shift_q(q->y, sy, g);
+            q->z = shift_q(q->z, sz, g);
           } else {  // list filter: hi only; a rounding of hi stays inside the FP32 band
+            float4* h = (float4*)(smem + L.pos) + s;
             h->x = fmaf((float)sx, g.L_hi, h->x);
             h->y = fmaf((float)sy, g.L_hi, h->y);
             h->z = fmaf((float)sz, g.L_hi, h->z);
@@ -372,28 +364,29 @@ __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs&
 // Issue, wait and fix up one tile (single-buffered use).
 template <bool MIXED, bool FORCE>
 __device__ __forceinline__ bool stage_copy_async(const TileInfo& ti, const TileArgs& ta, const Geom& g,
-                                                 const void* __restrict__ pos, const float4* __restrict__ lo,
-                                                 const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
-                                                 TileShared& S, unsigned char* smem, const TileLayout& L,
-                                                 uint64_t* bar, uint32_t& phase, bool want_gid, int32_t* status) {
-  stage_issue<MIXED, FORCE>(ti, ta, pos, lo, rows, ent, S, smem, L, bar);
+                                                 const void* __restrict__ pos, const uint2* __restrict__ rows,
+                                                 const uint16_t* __restrict__ ent, TileShared& S, unsigned char* smem,
+                                                 const TileLayout& L, uint64_t* bar, uint32_t& phase, bool want_gid,
+                                                 int32_t* status) {
+  stage_issue<MIXED, FORCE>(ti, ta, pos, rows, ent, S, smem, L, bar);
   return stage_finish<MIXED, FORCE>(ti, ta, g, S, smem, L, bar, phase, want_gid, status);
 }
 
 // Whole box as one tile (fewer than 3 cells per side): everything staged directly, no shifts.
-template <bool MIXED, bool WANT_LO>
-__device__ __forceinline__ void stage_whole(int64_t N, const void* __restrict__ pos, const float4* __restrict__ lo,
-                                            TileShared& S, unsigned char* smem, const TileLayout& L) {
+// GID: also the sorted indices (every layout but the mixed force and adjoint kernels', whose
+// fixed-point records carry them).
+template <bool MIXED, bool GID>
+__device__ __forceinline__ void stage_whole(int64_t N, const void* __restrict__ pos, TileShared& S,
+                                            unsigned char* smem, const TileLayout& L) {
   for (int e = threadIdx.x; e < N; e += blockDim.x) {
     if (MIXED) {
-      ((float4*)(smem + L.pos))[e] = ((const float4*)pos)[e];
-      if (WANT_LO) ((float4*)(smem + L.lo))[e] = lo[e];
+      ((uint4*)(smem + L.pos))[e] = ((const uint4*)pos)[e];
     } else {
       dvec4 p = ((const dvec4*)pos)[e];
       p.w = 13.0;  // no shift
       ((dvec4*)(smem + L.pos))[e] = p;
     }
-    ((int*)(smem + L.gid))[e] = e;
+    if (GID) ((int*)(smem + L.gid))[e] = e;
   }
   if (threadIdx.x == 0) {
     S.ncol = 1;
@@ -568,7 +561,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   for (int64_t t = blockIdx.x; t < ta.ntiles; t += gridDim.x) {
     TileInfo ti{0, 0, 0, 1};
     if (WHOLE) {
-      stage_whole<MIXED, false>(N, pos, nullptr, S, smem, L);
+      stage_whole<MIXED, true>(N, pos, S, smem, L);
     } else {
       ti = tile_info(t, ta);
       if (!stage_offsets(ti, ta, cs, S)) {
@@ -576,8 +569,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         __syncthreads();
         continue;
       }
-      if (!stage_copy_async<MIXED, false>(ti, ta, g, pos, nullptr, nullptr, nullptr, S, smem, L, &bar, phase, true,
-                                          status))
+      if (!stage_copy_async<MIXED, false>(ti, ta, g, pos, nullptr, nullptr, S, smem, L, &bar, phase, true, status))
         return;
     }
     __syncthreads();
@@ -908,7 +900,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   const KeyListLayout K = key_list_layout(ta_in, NT);
   TileLayout L;  // the staging helpers' view: positions and sorted indices
   L.pos = K.pos;
-  L.lo = K.pos;
   L.gid = K.gid;
   L.rows = L.ent = L.cnt = L.total = 0;
   const float4* sh_pos = (const float4*)(smem + K.pos);
@@ -965,8 +956,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
       __syncthreads();
       continue;
     }
-    if (!stage_copy_async<true, false>(ti, ta, g, pos, nullptr, nullptr, nullptr, S, smem, L, &bar, phase, true,
-                                       status))
+    if (!stage_copy_async<true, false>(ti, ta, g, pos, nullptr, nullptr, S, smem, L, &bar, phase, true, status))
       return;
     const int n_own = S.own1 - S.own0;
     if (n_own > ta.max_own) {  // sizing inconsistency: record and skip the tile
@@ -1265,7 +1255,8 @@ __device__ __forceinline__ double gsum(double v) {
 // Shared memory of the force kernel: `nbuf` tile buffers (with two, the next tile's copies are in
 // flight while the current one is computed); one for the whole-box case.
 size_t force_buffer_bytes(const TileArgs& ta, int precision, int half) {
-  return align16(tile_layout(ta, precision == LJ_MIXED, true, half || ta.whole).total);
+  const bool mixed = precision == LJ_MIXED;
+  return align16(tile_layout(ta, mixed, true, !mixed && (half || ta.whole)).total);
 }
 size_t force_smem_bytes(const TileArgs& ta, int precision, int nbuf, int half) {
   return (ta.whole ? 1 : (nbuf == 2 ? 2 : 1)) * force_buffer_bytes(ta, precision, half);
@@ -1293,36 +1284,38 @@ struct AccF {
   float fx, fy, fz, pe, vir;
 };
 
-// One listed pair in the mixed form (Alg. 6 in eps/sigma form):
+// Partner difference of two fixed-point records in units of u: the exact integer difference
+// converted once to FP32.  WHOLE: the nearest periodic image is chosen per pair (the raw
+// difference is below 2^31 u there) and round(L / u) subtracted as an integer.
+template <bool WHOLE>
+__device__ __forceinline__ float qd(uint32_t a, uint32_t b, const Geom& g) {
+  int d = (int)(a - b);
+  if (WHOLE) d -= (int)rintf(__int2float_rn(d) * g.q_inv_L) * (int)g.Lq;
+  return __int2float_rn(d);
+}
+
+// One listed pair in the mixed form (Alg. 6 in eps/sigma form) on differences in units of u:
 //   f = ri2 s3i (24 eps - 48 eps s3i) + 8 eps c2 / sigma^2, zero for r^2 >= r_c^2 (select)
 //   V = 4 eps [s3i (s3i - 1) + c2 r^2 / sigma^2 + c0],  W += -f r^2
+// with the constants scaled by powers of u (LJConst::*q), so f d and V come out in sigma units and
+// W in units of 1/u.  HALF: Newton-3 scatter to the partner's sorted index, carried in qj.w.
 template <bool HALF, bool ENERGY, bool WHOLE>
-__device__ __forceinline__ void pair_mixed(const float4& hi_i, const float4& lo_i, const float4& hj, const float4& lj,
-                                           const LJConst& c, const Geom& g, AccF& a, float4* fout, int gj) {
-  float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;  // exact
-  if (WHOLE) {
-    const float mx = rintf(dx * g.inv_L), my = rintf(dy * g.inv_L), mz = rintf(dz * g.inv_L);
-    dx = fmaf(-mx, g.L_hi, dx) + fmaf(-mx, g.L_lo, lj.x - lo_i.x);
-    dy = fmaf(-my, g.L_hi, dy) + fmaf(-my, g.L_lo, lj.y - lo_i.y);
-    dz = fmaf(-mz, g.L_hi, dz) + fmaf(-mz, g.L_lo, lj.z - lo_i.z);
-  } else {
-    dx += lj.x - lo_i.x;
-    dy += lj.y - lo_i.y;
-    dz += lj.z - lo_i.z;
-  }
+__device__ __forceinline__ void pair_q(const uint4& qi, const uint4& qj, const LJConst& c, const Geom& g, AccF& a,
+                                       float4* fout) {
+  const float dx = qd<WHOLE>(qj.x, qi.x, g), dy = qd<WHOLE>(qj.y, qi.y, g), dz = qd<WHOLE>(qj.z, qi.z, g);
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float ri2 = rcp_nr(r2);
-  const float si = c.sig2f * ri2;
+  const float si = c.sig2q * ri2;
   const float s3i = si * si * si;
-  const bool in = r2 < c.rc2f;
-  float ff = fmaf(ri2 * s3i, fmaf(-c.f48, s3i, c.f24), c.f8c2);
+  const bool in = r2 < c.rc2q;
+  float ff = fmaf(ri2 * s3i, fmaf(-c.f48q, s3i, c.f24q), c.f8c2q);
   ff = in ? ff : 0.0f;
   a.fx = fmaf(ff, dx, a.fx);
   a.fy = fmaf(ff, dy, a.fy);
   a.fz = fmaf(ff, dz, a.fz);
-  if (HALF) atomicAdd(&fout[gj], make_float4(-ff * dx, -ff * dy, -ff * dz, 0.0f));
+  if (HALF) atomicAdd(&fout[qj.w], make_float4(-ff * dx, -ff * dy, -ff * dz, 0.0f));
   if (ENERGY) {
-    const float v = c.e4 * fmaf(s3i, s3i - 1.0f, fmaf(c.c2f, r2, c.c0f));
+    const float v = c.e4 * fmaf(s3i, s3i - 1.0f, fmaf(c.c2q, r2, c.c0f));
     a.pe += in ? v : 0.0f;
     a.vir = fmaf(-ff, r2, a.vir);
   }
@@ -1337,7 +1330,6 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
                                                    int32_t* __restrict__ status, double& pe_acc, double& vir_acc,
                                                    int list_cap) {
   const void* sh_pos = buf + L.pos;
-  const float4* sh_lo = (const float4*)(buf + L.lo);
   const int* sh_gid = (const int*)(buf + L.gid);
   const uint2* s_rows = (const uint2*)(buf + L.rows);
   const uint16_t* s_ent = (const uint16_t*)(buf + L.ent);
@@ -1369,14 +1361,12 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
       // the row's pairs; one instance per memory space of the list (in_smem: staged segment)
       auto row_pairs = [&](const uint16_t* __restrict__ el, bool in_smem) {
       if (MIXED) {
-        // staged positions by 32-bit shared address: hi at a_pos + 16 j, lo at a_pos + d_lo + 16 j
-        const uint32_t a_pos = smem_addr(sh_pos), d_lo = smem_addr(sh_lo) - a_pos, a_gid = smem_addr(sh_gid);
-        const float4 hi_i = lds_f4(a_pos + 16u * l), lo_i = lds_f4(a_pos + d_lo + 16u * l);
+        // staged fixed-point records by 32-bit shared address: record j at a_pos + 16 j
+        const uint32_t a_pos = smem_addr(sh_pos);
+        const uint4 qi = lds_u4(a_pos + 16u * l);
         float4* F = (float4*)fout;
         auto pair_at = [&](uint32_t j, AccF& acc) {
-          const uint32_t b = a_pos + (j << 4);
-          pair_mixed<HALF, ENERGY, WHOLE>(hi_i, lo_i, lds_f4(b), lds_f4(b + d_lo), c, g, acc, F,
-                                          HALF ? lds_s32(a_gid + 4u * j) : 0);
+          pair_q<HALF, ENERGY, WHOLE>(qi, lds_u4(a_pos + (j << 4)), c, g, acc, F);
         };
         if (in_smem) {
           // list segment staged: entries by 32-bit shared address, two independent per iteration
@@ -1455,7 +1445,7 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
         const float pe = gsum<LANES>(a0.pe + a1.pe), vir = gsum<LANES>(a0.vir + a1.vir);
         if (lane == 0) {
           pe_acc += (double)pe;
-          vir_acc += (double)vir;
+          vir_acc += (double)(vir * g.qu);  // units of 1/u -> sigma units (exact: u = 2^-qk)
         }
       }
     } else {
@@ -1509,19 +1499,19 @@ __device__ __forceinline__ bool force_tile_prepare(const TileInfo& ti, int64_t t
 // sums -> one partial per block.
 template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLIST>
 __global__ void __launch_bounds__(kTileThreads, 4)
-    k_force_tile(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
-                 int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows,
-                 const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent, void* __restrict__ fout,
-                 double* __restrict__ part, int32_t* __restrict__ status, int nbuf) {
+    k_force_tile(const void* __restrict__ pos, const uint32_t* __restrict__ cs, int64_t N, Geom g, TileArgs ta,
+                 LJConst c, const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
+                 const uint16_t* __restrict__ ent, void* __restrict__ fout, double* __restrict__ part,
+                 int32_t* __restrict__ status, int nbuf) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared SS[2];
   __shared__ __align__(8) uint64_t bars[2];
-  const TileLayout L = tile_layout(ta, MIXED, true, HALF || WHOLE);
+  const TileLayout L = tile_layout(ta, MIXED, true, !MIXED && (HALF || WHOLE));
   const size_t buf_bytes = align16(L.total);
   double pe_acc = 0.0, vir_acc = 0.0;
   if (WHOLE) {
     if (blockIdx.x == 0) {
-      stage_whole<MIXED, true>(N, pos, lo, SS[0], smem, L);
+      stage_whole<MIXED, !MIXED>(N, pos, SS[0], smem, L);
       __syncthreads();
       force_tile_compute<MIXED, LANES, HALF, ENERGY, true, false>(SS[0], smem, L, rows, ent, c, g, fout, status, pe_acc,
                                                            vir_acc, ta.list_cap);
@@ -1540,26 +1530,26 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     bool v_cur = false, v_next = false;
     if (pipelined && t < ta.ntiles) {
       v_cur = force_tile_prepare(tile_info(t, ta), t, ta, cs, tile_list, SS[0], status);
-      if (v_cur) stage_issue<MIXED, true>(tile_info(t, ta), ta, pos, lo, rows, ent, SS[0], smem, L, &bars[0]);
+      if (v_cur) stage_issue<MIXED, true>(tile_info(t, ta), ta, pos, rows, ent, SS[0], smem, L, &bars[0]);
     }
     for (; t < ta.ntiles; t += gridDim.x) {
       if (!pipelined) {
         v_cur = force_tile_prepare(tile_info(t, ta), t, ta, cs, tile_list, SS[0], status);
-        if (v_cur) stage_issue<MIXED, true>(tile_info(t, ta), ta, pos, lo, rows, ent, SS[0], smem, L, &bars[0]);
+        if (v_cur) stage_issue<MIXED, true>(tile_info(t, ta), ta, pos, rows, ent, SS[0], smem, L, &bars[0]);
       } else {
         const int64_t tn = t + gridDim.x;
         v_next = false;
         if (tn < ta.ntiles) {
           v_next = force_tile_prepare(tile_info(tn, ta), tn, ta, cs, tile_list, SS[b ^ 1], status);
           if (v_next)
-            stage_issue<MIXED, true>(tile_info(tn, ta), ta, pos, lo, rows, ent, SS[b ^ 1],
-                                     smem + (b ^ 1) * buf_bytes, L, &bars[b ^ 1]);
+            stage_issue<MIXED, true>(tile_info(tn, ta), ta, pos, rows, ent, SS[b ^ 1], smem + (b ^ 1) * buf_bytes, L,
+                                     &bars[b ^ 1]);
         }
       }
       if (v_cur) {
         uint32_t& ph = b ? ph1 : ph0;
-        if (!stage_finish<MIXED, true>(tile_info(t, ta), ta, g, SS[b], smem + b * buf_bytes, L, &bars[b], ph, HALF,
-                                       status)) {
+        if (!stage_finish<MIXED, true>(tile_info(t, ta), ta, g, SS[b], smem + b * buf_bytes, L, &bars[b], ph,
+                                       !MIXED && HALF, status)) {
           if (v_next) mbar_wait(&bars[b ^ 1], b ? ph0 : ph1, kWaitBudget);  // drain the other buffer's copies
           return;
         }
@@ -1625,9 +1615,10 @@ __device__ __forceinline__ void stage_codes_warp(const TileInfo& ti, const TileA
 }
 
 // Image shifts of a staged tile's periodic cells by the consumer warps (warp per cell, lanes over
-// its particles).  Every writer orders its writes before later bulk copies into the same bytes;
-// the caller then waits for all consumer warps (a bounded mbarrier wait, not bar.sync, so that a
-// warp that left on a timeout cannot hold the others forever).
+// its particles): integer adds of round(L / u) to the fixed-point records.  Every writer orders its
+// writes before later bulk copies into the same bytes; the caller then waits for all consumer
+// warps (a bounded mbarrier wait, not bar.sync, so that a warp that left on a timeout cannot hold
+// the others forever).
 __device__ __forceinline__ void stage_shift_consumers(const TileInfo& ti, const TileArgs& ta, const Geom& g,
                                                       const TileShared& S, unsigned char* smem, const TileLayout& L,
                                                       int consumers) {
@@ -1637,11 +1628,10 @@ __device__ __forceinline__ void stage_shift_consumers(const TileInfo& ti, const 
     cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
     if ((sx | sy | sz) == 0) continue;
     for (int e = S.offq[q] + lane; e < S.offq[q + 1]; e += 32) {
-      float4* h = (float4*)(smem + L.pos) + e;
-      float4* l = (float4*)(smem + L.lo) + e;
-      shift_hi_lo(h->x, l->x, (float)sx, g);
-      shift_hi_lo(h->y, l->y, (float)sy, g);
-      shift_hi_lo(h->z, l->z, (float)sz, g);
+      uint4* r = (uint4*)(smem + L.pos) + e;
+      r->x = shift_q(r->x, sx, g);
+      r->y = shift_q(r->y, sy, g);
+      r->z = shift_q(r->z, sz, g);
     }
   }
   fence_proxy_async_smem();
@@ -1657,8 +1647,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // the consumers scatter the partners' forces with atomics).
 template <bool MIXED, bool HALF, int LANES, bool ENERGY, bool LONGLIST, int CW>
 __global__ void __launch_bounds__(pipe_threads(CW), 2)
-    k_force_pipe(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
-                 Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
+    k_force_pipe(const void* __restrict__ pos, const uint32_t* __restrict__ cs, Geom g, TileArgs ta, LJConst c,
+                 const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
                  const uint16_t* __restrict__ ent, void* __restrict__ fout, double* __restrict__ part,
                  int32_t* __restrict__ status) {
   static_assert(MIXED != HALF, "pipelined forms: mixed with the full list, FP64 with the half list");
@@ -1667,7 +1657,7 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
   __shared__ TileInfo s_ti[kPipeSlots];
   __shared__ int s_valid[kPipeSlots];  // 1: interior tile, 2: periodic tile (shifts), 0: skip, -1: abort
   __shared__ __align__(8) uint64_t full[2], ready[2], empty[2], shifted[2];
-  const TileLayout L = tile_layout(ta, MIXED, true, HALF);
+  const TileLayout L = tile_layout(ta, MIXED, true, !MIXED && HALF);
   const size_t buf_bytes = align16(L.total);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -1720,7 +1710,7 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
         staged = false;
       }
       if (!staged && lane == 0 && !ok_next) atomicOr(status, LJ_ST_CELL_RANGE);
-      if (staged) stage_issue<MIXED, true>(ti, ta, pos, lo, rows, ent, S, buf, L, &full[b], warp);
+      if (staged) stage_issue<MIXED, true>(ti, ta, pos, rows, ent, S, buf, L, &full[b], warp);
       // bookkeeping of this producer's next tile (its slot was released with tile k - 2), then
       // the loads for the one after it
       const int64_t tn = t + 2 * stride;
@@ -1808,8 +1798,8 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
 // e_rep[2 r + 1]).
 template <int LANES, bool ENERGY>
 __global__ void __launch_bounds__(kTileThreads, 4)
-    k_force_batch(const float4* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs_in,
-                  int64_t N, TileArgs caps, LJConst c, const uint2* __restrict__ rows,
+    k_force_batch(const uint4* __restrict__ pos, const uint32_t* __restrict__ cs_in, int64_t N, TileArgs caps,
+                  LJConst c, const uint2* __restrict__ rows,
                   const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent, float4* __restrict__ fout,
                   double* __restrict__ e_rep, int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps,
                   int R, const int32_t* __restrict__ tile_rep) {
@@ -1834,7 +1824,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     const TileInfo ti = tile_info(t - rg.tile_base, ta);
     double pe_acc = 0.0, vir_acc = 0.0;
     if (force_tile_prepare(ti, t, ta, cs, tile_list, S, status)) {
-      stage_issue<true, true>(ti, ta, pos, lo, rows, ent, S, smem, L, &bar);
+      stage_issue<true, true>(ti, ta, pos, rows, ent, S, smem, L, &bar);
       if (!stage_finish<true, true>(ti, ta, g, S, smem, L, &bar, ph, false, status)) return;
       force_tile_compute<true, LANES, false, ENERGY, false, true>(S, smem, L, rows, ent, c, g, fout, status, pe_acc,
                                                             vir_acc, ta.list_cap);
@@ -1911,7 +1901,6 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
                                                      dvec4* __restrict__ hw, dvec4* __restrict__ fo,
                                                      int32_t* __restrict__ status, double* acc, int list_cap) {
   const void* sh_pos = buf + L.pos;
-  const float4* sh_lo = (const float4*)(buf + L.lo);
   const int* sh_gid = (const int*)(buf + L.gid);
   const uint2* s_rows = (const uint2*)(buf + L.rows);
   const uint16_t* s_ent = (const uint16_t*)(buf + L.ent);
@@ -1943,28 +1932,21 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
       }
       const dvec4 wi = w[gi];
       if (MIXED) {
-        const float4 hi_i = ((const float4*)sh_pos)[l], lo_i = sh_lo[l];
+        const uint4 qi = ((const uint4*)sh_pos)[l];
         const float e4f = (float)e4, sig2f = (float)c.sig2, c2sf = (float)c2s, rc2f = (float)c.rc2,
                     c0f = (float)c.c0, isgf = (float)inv_sig;
         float ah[3] = {0.f, 0.f, 0.f}, af[3] = {0.f, 0.f, 0.f}, aq[kAdjParts] = {0.f, 0.f, 0.f, 0.f, 0.f};
         const float wx = (float)wi.x, wy = (float)wi.y, wz = (float)wi.z;
         for (unsigned e = lane; e < row.y; e += kAdjLanes) {
           const int j = el[row.x + e];
-          const float4 hj = ((const float4*)sh_pos)[j], lj = sh_lo[j];
-          float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;
-          if (WHOLE) {
-            const float mx = rintf(dx * g.inv_L), my = rintf(dy * g.inv_L), mz = rintf(dz * g.inv_L);
-            dx = fmaf(-mx, g.L_hi, dx) + fmaf(-mx, g.L_lo, lj.x - lo_i.x);
-            dy = fmaf(-my, g.L_hi, dy) + fmaf(-my, g.L_lo, lj.y - lo_i.y);
-            dz = fmaf(-mz, g.L_hi, dz) + fmaf(-mz, g.L_lo, lj.z - lo_i.z);
-          } else {
-            dx += lj.x - lo_i.x;
-            dy += lj.y - lo_i.y;
-            dz += lj.z - lo_i.z;
-          }
+          const uint4 qj = ((const uint4*)sh_pos)[j];
+          // differences in sigma units: the integer difference in units of u, converted once and
+          // scaled by u (a power of two: exact)
+          const float dx = qd<WHOLE>(qj.x, qi.x, g) * g.qu, dy = qd<WHOLE>(qj.y, qi.y, g) * g.qu,
+                      dz = qd<WHOLE>(qj.z, qi.z, g) * g.qu;
           const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (!(s2 < rc2f)) continue;
-          const dvec4 wj = w[sh_gid[j]];
+          const dvec4 wj = w[qj.w];
           const float is = 1.0f / s2;
           const float a = sig2f * is, a3 = a * a * a, a6 = a3 * a3;
           const float u = e4f * (a6 - a3 + c2sf * s2 + c0f);
@@ -2052,19 +2034,19 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
 
 template <bool MIXED, bool WHOLE>
 __global__ void __launch_bounds__(kTileThreads, 2)
-    k_adjoint_tile(const void* __restrict__ pos, const float4* __restrict__ lo, const uint32_t* __restrict__ cs,
-                   int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* __restrict__ rows,
+    k_adjoint_tile(const void* __restrict__ pos, const uint32_t* __restrict__ cs, int64_t N, Geom g, TileArgs ta,
+                   LJConst c, const uint2* __restrict__ rows,
                    const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent,
                    const dvec4* __restrict__ w, dvec4* __restrict__ hw, dvec4* __restrict__ fo,
                    double* __restrict__ part, int32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared S;
   __shared__ __align__(8) uint64_t bar;
-  const TileLayout L = tile_layout(ta, MIXED, true, true);
+  const TileLayout L = tile_layout(ta, MIXED, true, !MIXED);
   double acc[kAdjParts] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (WHOLE) {
     if (blockIdx.x == 0) {
-      stage_whole<MIXED, true>(N, pos, lo, S, smem, L);
+      stage_whole<MIXED, !MIXED>(N, pos, S, smem, L);
       __syncthreads();
       adjoint_tile_compute<MIXED, true>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc, ta.list_cap);
     }
@@ -2079,8 +2061,8 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       const bool ok = force_tile_prepare(tile_info(t, ta), t, ta, cs, tile_list, S, status);
       if (ok) {
         const TileInfo ti = tile_info(t, ta);
-        stage_issue<MIXED, true>(ti, ta, pos, lo, rows, ent, S, smem, L, &bar);
-        if (!stage_finish<MIXED, true>(ti, ta, g, S, smem, L, &bar, ph, true, status)) return;
+        stage_issue<MIXED, true>(ti, ta, pos, rows, ent, S, smem, L, &bar);
+        if (!stage_finish<MIXED, true>(ti, ta, g, S, smem, L, &bar, ph, !MIXED, status)) return;
         adjoint_tile_compute<MIXED, false>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc, ta.list_cap);
       }
       __syncthreads();
@@ -2229,15 +2211,14 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
 
 // Returns the grid launched (the number of energy partials written).
 template <bool MIXED, int LANES, bool HALF, bool ENERGY>
-static int force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
-                   const uint2* rows, const uint2* tl, const uint16_t* ent, void* f, double* part, int32_t* status,
-                   int nbuf, int grid, size_t sm, cudaStream_t s) {
+static int force_w(const void* pos, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
+                   const uint2* tl, const uint16_t* ent, void* f, double* part, int32_t* status, int nbuf, int grid,
+                   size_t sm, cudaStream_t s) {
 #define LJ_FW(W, LONG)                                                                                           \
   do {                                                                                                           \
     set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, W, LONG>, sm);                                             \
-    k_force_tile<MIXED, LANES, HALF, ENERGY, W, LONG><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c,     \
-                                                                                    rows, tl, ent, f, part, status, \
-                                                                                    nbuf);                          \
+    k_force_tile<MIXED, LANES, HALF, ENERGY, W, LONG><<<grid, kTileThreads, sm, s>>>(pos, cs, N, g, ta, c, rows,   \
+                                                                                    tl, ent, f, part, status, nbuf); \
   } while (0)
   if constexpr (MIXED != HALF) {  // the pipelined forms: mixed + full list, FP64 + half list
     if (!ta.whole && nbuf == 2) {  // producer warps + consumer warps over two buffers
@@ -2247,8 +2228,8 @@ static int force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_
     const int64_t want = (int64_t)sm_count() *                                                                   \
                          resident_per_sm(k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW>, pipe_threads(CW), sm); \
     grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, ta.ntiles), (int64_t)kMaxRedBlocks)); \
-    k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW><<<grid, pipe_threads(CW), sm, s>>>(pos, lo, cs, g, ta, c,  \
-                                                                                       rows, tl, ent, f, part, status); \
+    k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW><<<grid, pipe_threads(CW), sm, s>>>(pos, cs, g, ta, c, rows, \
+                                                                                       tl, ent, f, part, status);     \
   } while (0)
       const bool lg = ta.list_cap < ta.max_list;
       if (ta.T <= 4) {
@@ -2270,43 +2251,42 @@ static int force_w(const void* pos, const float4* lo, const uint32_t* cs, int64_
 }
 
 template <bool MIXED, int LANES>
-static int force_l(int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
-                   TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
-                   double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
+static int force_l(int half, int energy, const void* pos, const uint32_t* cs, int64_t N, Geom g, TileArgs ta,
+                   LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f, double* part,
+                   int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
   if (half) {
-    if (energy) return force_w<MIXED, LANES, true, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    return force_w<MIXED, LANES, true, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    if (energy) return force_w<MIXED, LANES, true, true>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    return force_w<MIXED, LANES, true, false>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
   }
-  if (energy) return force_w<MIXED, LANES, false, true>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-  return force_w<MIXED, LANES, false, false>(pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+  if (energy) return force_w<MIXED, LANES, false, true>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+  return force_w<MIXED, LANES, false, false>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
 }
 
 template <bool MIXED>
-static int force_p(int lanes, int half, int energy, const void* pos, const float4* lo, const uint32_t* cs, int64_t N,
-                    Geom g, TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
-                    double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
+static int force_p(int lanes, int half, int energy, const void* pos, const uint32_t* cs, int64_t N, Geom g,
+                   TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
+                   double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
   switch (lanes) {
-    case 1: return force_l<MIXED, 1>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    case 2: return force_l<MIXED, 2>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    case 4: return force_l<MIXED, 4>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    case 8: return force_l<MIXED, 8>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    case 16: return force_l<MIXED, 16>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    default: return force_l<MIXED, 32>(half, energy, pos, lo, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 1: return force_l<MIXED, 1>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 2: return force_l<MIXED, 2>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 4: return force_l<MIXED, 4>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 8: return force_l<MIXED, 8>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 16: return force_l<MIXED, 16>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    default: return force_l<MIXED, 32>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
   }
 }
 
-int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const float4* lo,
-                      const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
-                      const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
-                      int nbuf, cudaStream_t s) {
+int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const uint32_t* cs, int64_t N,
+                      Geom g, TileArgs ta, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
+                      void* f, double* part, int32_t* status, int per_sm, int nbuf, cudaStream_t s) {
   const size_t sm = force_smem_bytes(ta, precision, nbuf, half);
   if (per_sm <= 0) per_sm = per_sm_for(sm);
   const int grid = tile_grid(ta, per_sm);
   if (precision == LJ_MIXED)
-    return force_p<true>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf,
-                         grid, sm, s);
-  return force_p<false>(lanes, half, energy, pos, lo, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf,
-                        grid, sm, s);
+    return force_p<true>(lanes, half, energy, pos, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf, grid,
+                         sm, s);
+  return force_p<false>(lanes, half, energy, pos, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf, grid,
+                        sm, s);
 }
 
 void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,
@@ -2375,18 +2355,18 @@ void launch_max_count(const uint32_t* cnt, int64_t n, unsigned int* out, cudaStr
 }
 
 size_t adjoint_smem_bytes(const TileArgs& ta, int precision) {
-  return align16(tile_layout(ta, precision == LJ_MIXED, true, true).total);
+  return align16(tile_layout(ta, precision == LJ_MIXED, true, precision != LJ_MIXED).total);
 }
 
-int launch_adjoint_tile(int precision, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
-                        TileArgs ta, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
-                        const void* w, void* hw, void* fo, double* part, int32_t* status, cudaStream_t s) {
-  const size_t sm = align16(tile_layout(ta, precision == LJ_MIXED, true, true).total);
+int launch_adjoint_tile(int precision, const void* pos, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
+                        const uint2* rows, const uint2* tile_list, const uint16_t* ent, const void* w, void* hw,
+                        void* fo, double* part, int32_t* status, cudaStream_t s) {
+  const size_t sm = adjoint_smem_bytes(ta, precision);
   const int grid = tile_grid(ta, min(per_sm_for(sm), 2));
 #define LJ_ADJ_LAUNCH(M, W)                                                                                 \
   do {                                                                                                      \
     set_smem(k_adjoint_tile<M, W>, sm);                                                                     \
-    k_adjoint_tile<M, W><<<grid, kTileThreads, sm, s>>>(pos, lo, cs, N, g, ta, c, rows, tile_list, ent,     \
+    k_adjoint_tile<M, W><<<grid, kTileThreads, sm, s>>>(pos, cs, N, g, ta, c, rows, tile_list, ent,         \
                                                         (const dvec4*)w, (dvec4*)hw, (dvec4*)fo, part, status); \
   } while (0)
   if (precision == LJ_MIXED) {
@@ -2424,7 +2404,7 @@ void launch_list_batch(const float4* hi, const double* x, const uint32_t* cs, in
                                                           counter, max_list, status, reps, R, pred, tile_rep);
 }
 
-int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo, const uint32_t* cs, int64_t N,
+int launch_force_batch(int lanes, int energy, const uint4* xq, const uint32_t* cs, int64_t N,
                        TileArgs caps, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
                        float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R,
                        const int32_t* tile_rep, cudaStream_t s) {
@@ -2434,11 +2414,11 @@ int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo
   do {                                                                                                          \
     if (energy) {                                                                                               \
       set_smem(k_force_batch<LN, true>, sm);                                                                    \
-      k_force_batch<LN, true><<<grid, kTileThreads, sm, s>>>(hi, lo, cs, N, caps, c, rows, tile_list, ent, f,   \
+      k_force_batch<LN, true><<<grid, kTileThreads, sm, s>>>(xq, cs, N, caps, c, rows, tile_list, ent, f,       \
                                                              e_rep, status, reps, R, tile_rep);                          \
     } else {                                                                                                    \
       set_smem(k_force_batch<LN, false>, sm);                                                                   \
-      k_force_batch<LN, false><<<grid, kTileThreads, sm, s>>>(hi, lo, cs, N, caps, c, rows, tile_list, ent, f,  \
+      k_force_batch<LN, false><<<grid, kTileThreads, sm, s>>>(xq, cs, N, caps, c, rows, tile_list, ent, f,      \
                                                               e_rep, status, reps, R, tile_rep);                         \
     }                                                                                                           \
   } while (0)

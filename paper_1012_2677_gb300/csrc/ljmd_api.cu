@@ -46,8 +46,9 @@ struct ljmd_sys {
   // device buffers (sorted order)
   double *x = nullptr, *v = nullptr, *x_alt = nullptr, *v_alt = nullptr;
   void *f = nullptr, *f_alt = nullptr;
-  float4 *hi = nullptr, *lo = nullptr;
-  dvec4* pos64 = nullptr;
+  float4* hi = nullptr;   // FP32 hi parts of the positions (the list construction's filter)
+  uint4* xq = nullptr;    // mixed form: fixed-point records of the positions (force and adjoint)
+  dvec4* pos64 = nullptr; // FP64 form: position copies for the force and adjoint kernels
   void* ref = nullptr;
   int32_t *id = nullptr, *id_alt = nullptr, *img = nullptr, *img_alt = nullptr;
   uint32_t *cell_of = nullptr, *cell_alt = nullptr, *perm = nullptr;
@@ -77,8 +78,8 @@ struct ljmd_sys {
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;  // (phase, (start, stop))
-  double prof_ms[4] = {0, 0, 0, 0};
-  int64_t prof_n[4] = {0, 0, 0, 0};
+  double prof_ms[5] = {0, 0, 0, 0, 0};
+  int64_t prof_n[5] = {0, 0, 0, 0, 0};
   int64_t launches = 0;
   // list validity rule (Sec. 2.3 / Alg. 2)
   int valid_mode = LJ_VALID_HALF_MARGIN;
@@ -136,7 +137,7 @@ static int dalloc_t(ljmd_sys* sys, T** p, size_t count) {
 }
 
 static void free_all(ljmd_sys* s) {
-  void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->lo, s->pos64, s->ref, s->id,
+  void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->xq, s->pos64, s->ref, s->id,
                   s->id_alt, s->img, s->img_alt, s->cell_of, s->cell_alt, s->perm, s->cell_count, s->cell_start,
                   s->cell_fill, s->rows, s->tile_list, s->ent, s->scan_tmp, s->part_force, s->part_ke,
                   s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64, s->d_sizes,
@@ -153,7 +154,7 @@ static void free_all(ljmd_sys* s) {
   if (s->h_i32) cudaFreeHost(s->h_i32);
 }
 
-enum { PH_FORCE = 0, PH_INTEGRATE = 1, PH_REBUILD = 2, PH_ENERGY = 3 };
+enum { PH_FORCE = 0, PH_INTEGRATE = 1, PH_REBUILD = 2, PH_ENERGY = 3, PH_ADJOINT = 4 };
 
 static cudaEvent_t ev_get(ljmd_sys* s) {
   if (!s->ev_pool.empty()) {
@@ -228,6 +229,12 @@ static int check_params(const ljmd_params* p) {
   return LJ_OK;
 }
 
+// How far the measured largest displacement can fall short of the FP64 one.
+static double disp_slack(const ljmd_sys* s) {
+  if (s->precision != LJ_MIXED) return 1e-12;
+  return 2.0 * sqrt(3.0) * (double)s->g.qu + 1e-6 * (0.5 * s->prm.margin) + 1e-9;
+}
+
 // Box, cutoff and margin -> grid, offsets, constants.  Requires L >= 2 (r_s + margin) so that a
 // listed pair, which can close in by at most the margin, keeps a unique minimum image.
 static int setup_geometry(ljmd_sys* s, double L) {
@@ -255,6 +262,19 @@ static int setup_geometry(ljmd_sys* s, double L) {
   g.L_lo = (float)(L - Lhi);
   g.inv_L = (float)(1.0 / L);
   g.inv_L64 = 1.0 / L;
+  // Fixed-point records (mixed form): u = 2^-qk with 2^31 u above every difference the kernels
+  // take: two staged neighbour cells (2 h) or the whole box (fewer than 3 cells per side), plus
+  // the drift of both particles since the build and a unit of headroom.
+  {
+    const double W = (n < 3 ? L : 2.0 * L / (double)n) + 2.0 * p.margin + 1.0;
+    int qk = 31 - (int)ceil(log2(W));
+    if (qk > 30) qk = 30;
+    g.qk = qk;
+    const double u = ldexp(1.0, -qk);
+    g.qu = (float)u;
+    g.Lq = (uint32_t)fmod(nearbyint(ldexp(L, qk)), 4294967296.0);
+    g.q_inv_L = (float)(u / L);
+  }
 
   double c2, c0;
   truncation_terms(p.cutoff / p.sigma, p.truncation, &c2, &c0);
@@ -273,6 +293,12 @@ static int setup_geometry(ljmd_sys* s, double L) {
   c.e4 = (float)(4.0 * p.eps);
   c.c2f = (float)(c2 / c.sig2);
   c.c0f = (float)c0;
+  c.f24q = ldexpf(c.f24, g.qk);
+  c.f48q = ldexpf(c.f48, g.qk);
+  c.f8c2q = ldexpf(c.f8c2, -g.qk);
+  c.sig2q = ldexpf(c.sig2f, 2 * g.qk);
+  c.rc2q = ldexpf(c.rc2f, 2 * g.qk);
+  c.c2q = ldexpf(c.c2f, -2 * g.qk);
 
   // FP32 list filter on hi parts: each hi difference is exact and differs from the exact
   // difference by at most eps = 2^(p-22) + 2^(p-24) (two dropped lo parts, the split of L and
@@ -287,11 +313,11 @@ static int setup_geometry(ljmd_sys* s, double L) {
     s->band.lo = (float)(rs * rs - band);
     s->band.hi = (float)(rs * rs + band);
   }
-  // Displacement rule: rebuild when max |x - x_ref| > margin / 2.  The measured value can
-  // undershoot by the FP32 hi/lo reference error (mixed: dropped lo of the reference,
-  // <= 2^(p-23) per component), so the limit is lowered by twice that bound.
-  const double slack = (s->precision == LJ_MIXED) ? 2.0 * sqrt(3.0) * ldexp(1.0, pw - 23) + 1e-6 : 1e-12;
-  s->disp_limit = 0.5 * p.margin - slack;
+  // Displacement rule: rebuild when max |x - x_ref| > margin / 2.  The mixed form measures it on
+  // the fixed-point records (each component within u of the FP64 difference, then FP32 rounding),
+  // so the limit is lowered by twice that bound and a relative 2e-6 of margin/2; the FP64 form
+  // rounds the squared displacement up.
+  s->disp_limit = 0.5 * p.margin - disp_slack(s);
   return LJ_OK;
 }
 
@@ -336,7 +362,7 @@ static int ensure_particles(ljmd_sys* s, int64_t n) {
   TRY(dalloc(s, &s->f, fsz * n));
   TRY(dalloc(s, &s->f_alt, fsz * n));
   TRY(dalloc_t(s, &s->hi, n));
-  TRY(dalloc_t(s, &s->lo, n));
+  if (mixed) TRY(dalloc_t(s, &s->xq, n));
   if (!mixed) TRY(dalloc_t(s, &s->pos64, n));
   TRY(dalloc(s, &s->ref, fsz * n));
   TRY(dalloc_t(s, &s->id, n));
@@ -495,7 +521,7 @@ static int rebuild(ljmd_sys* s) {
   std::swap(s->img, s->img_alt);
   std::swap(s->cell_of, s->cell_alt);
   std::swap(s->f, s->f_alt);
-  launch_shadow_all(s->x, N, s->precision == LJ_MIXED, s->hi, s->lo, s->pos64, s->ref, st);
+  launch_shadow_all(s->x, N, s->precision == LJ_MIXED, s->g.qk, s->hi, s->xq, s->pos64, s->ref, st);
   CKL();
   const int half = s->list_half ? 1 : 0;
   uint64_t total = 0;
@@ -516,7 +542,9 @@ static int rebuild(ljmd_sys* s) {
       }
       CK(cudaMemsetAsync(s->d_total64, 0, 2 * sizeof(unsigned long long), st));
       CK(cudaMemsetAsync(s->d_sizes + 3, 0, sizeof(unsigned int), st));
-      launch_list_tile(s->precision, half, force_pos(s), s->hi, s->x, s->cell_start, N, s->g, s->ta, s->band, s->rows,
+      // the list kernels filter on the FP32 hi copies (mixed) or the FP64 copies (FP64 form, whole box)
+      const void* list_pos = s->precision == LJ_MIXED ? (const void*)s->hi : (const void*)s->pos64;
+      launch_list_tile(s->precision, half, list_pos, s->hi, s->x, s->cell_start, N, s->g, s->ta, s->band, s->rows,
                        s->tile_list, s->ent, (uint64_t)s->ent_cap, s->d_total64, s->d_sizes + 3, s->d_status, st);
       s->launches += 1;
       CKL();
@@ -577,12 +605,13 @@ static int rebuild(ljmd_sys* s) {
   return LJ_OK;
 }
 
-static void* force_pos(ljmd_sys* s) { return s->precision == LJ_MIXED ? (void*)s->hi : (void*)s->pos64; }
+static void* force_pos(ljmd_sys* s) { return s->precision == LJ_MIXED ? (void*)s->xq : (void*)s->pos64; }
 
 static int integrate(ljmd_sys* s, IntegrateArgs a) {
   PhaseTimer timer(s, PH_INTEGRATE);
   s->launches += 1;
-  return launch_integrate(s->precision, s->x, s->v, s->f, force_pos(s), s->lo, s->ref, s->n, a, s->part_ke, s->d_dmax,
+  a.qk = s->g.qk;
+  return launch_integrate(s->precision, s->x, s->v, s->f, force_pos(s), s->ref, s->n, a, s->part_ke, s->d_dmax,
                           s->d_status, s->st);
 }
 
@@ -605,8 +634,8 @@ static int run_force(ljmd_sys* s, bool energy) {
   const int per_sm = s->force_per_sm;  // 0: as many CTAs per SM as shared memory allows
   {
     PhaseTimer timer(s, PH_FORCE);
-    s->nb_force = launch_force_tile(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->lo, s->cell_start, s->n,
-                                    s->g, s->ta, s->c, s->rows, s->tile_list, s->ent, s->f, s->part_force, s->d_status,
+    s->nb_force = launch_force_tile(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->cell_start, s->n, s->g,
+                                    s->ta, s->c, s->rows, s->tile_list, s->ent, s->f, s->part_force, s->d_status,
                                     per_sm, force_buffers(s), s->st);
   }
   s->launches += 1;
@@ -636,8 +665,7 @@ static int ldc_valid(ljmd_sys* s, bool* valid) {
   ljmd_sys* sys = s;
   *valid = false;
   s->ldc_checks += 1;
-  const double slack = (s->precision == LJ_MIXED) ? 2.0 * sqrt(3.0) * ldexp(1.0, s->g.p - 23) + 1e-6 : 1e-12;
-  const double th = s->prm.margin - (s->last_dmax + slack) - 1e-9;
+  const double th = s->prm.margin - (s->last_dmax + disp_slack(s)) - 1e-9;
   if (!(th > 0.0) || !s->xref64) return LJ_OK;
   if (!s->ldc_list) TRY(dalloc_t(s, &s->ldc_list, (size_t)s->max_ld));
   if (!s->d_ldc) TRY(dalloc_t(s, &s->d_ldc, 2));
@@ -1107,7 +1135,7 @@ int ljmd_set_profiling(ljmd_sys* sys, int32_t enable) {
   if (sys->broken) return LJ_EDEVICE;
   resolve_events(sys);
   sys->profiling = enable != 0;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     sys->prof_ms[k] = 0.0;
     sys->prof_n[k] = 0;
   }
@@ -1126,6 +1154,8 @@ int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out) {
   out->rebuilds = sys->prof_n[PH_REBUILD];
   out->energy_ms = sys->prof_ms[PH_ENERGY];
   out->energy_launches = sys->prof_n[PH_ENERGY];
+  out->adjoint_ms = sys->prof_ms[PH_ADJOINT];
+  out->adjoint_launches = sys->prof_n[PH_ADJOINT];
   return LJ_OK;
 }
 
@@ -1216,9 +1246,13 @@ static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* 
   const int64_t N = s->n;
   cudaStream_t st = s->st;
   launch_to_sorted(w_id, s->id, N, s->adj_w, st);
-  const int nb = launch_adjoint_tile(s->precision, force_pos(s), s->lo, s->cell_start, N, s->g, s->ta, s->c, s->rows,
+  int nb = 0;
+  {
+    PhaseTimer timer(s, PH_ADJOINT);
+    nb = launch_adjoint_tile(s->precision, force_pos(s), s->cell_start, N, s->g, s->ta, s->c, s->rows,
                                      s->tile_list, s->ent, s->adj_w, s->adj_hw, f_id ? s->adj_f : nullptr,
                                      s->part_adj, s->d_status, st);
+  }
   launch_final_reduce(s->part_adj, nb, 5, s->d_adj, st);
   s->launches += 3;
   if (hw_id) {

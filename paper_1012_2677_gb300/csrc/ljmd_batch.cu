@@ -39,7 +39,8 @@ struct ljmd_batch {
   int lanes = 4;   // threads per key in the force kernel
   // device state (sorted by cell within each replica)
   double *x = nullptr, *v = nullptr, *x_alt = nullptr, *v_alt = nullptr;
-  float4 *f = nullptr, *hi = nullptr, *lo = nullptr, *ref = nullptr;
+  float4 *f = nullptr, *hi = nullptr;  // forces; FP32 hi parts of the positions (list filter)
+  uint4 *xq = nullptr, *ref = nullptr;  // fixed-point position records (force); the records at the build
   int32_t *id = nullptr, *id_alt = nullptr, *img = nullptr, *img_alt = nullptr, *rep_of = nullptr;
   uint32_t *cell_of = nullptr, *perm = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
   uint32_t* scan_tmp = nullptr;
@@ -103,7 +104,7 @@ static void drop_graph(ljmd_batch* b) {
 
 static void free_batch(ljmd_batch* b) {
   drop_graph(b);
-  void* ptrs[] = {b->reps, b->tile_rep, b->x, b->v, b->x_alt, b->v_alt, b->f, b->hi, b->lo, b->ref, b->id, b->id_alt, b->img,
+  void* ptrs[] = {b->reps, b->tile_rep, b->x, b->v, b->x_alt, b->v_alt, b->f, b->hi, b->xq, b->ref, b->id, b->id_alt, b->img,
                   b->img_alt, b->rep_of, b->cell_of, b->perm, b->cell_count, b->cell_start, b->cell_fill,
                   b->scan_tmp, b->rows, b->tile_list, b->ent, b->e_rep, b->ke_rep, b->status, b->dmax, b->flag,
                   b->d_rebuilds, b->counter, b->sizes};
@@ -173,6 +174,15 @@ static int setup_replicas(ljmd_batch* b) {
   while (ldexp(1.0, pw) < Lmax + p.margin + 1.0 || ldexp(1.0, pw - 1) < p.margin + 1.0) ++pw;
   b->pw = pw;
   b->offset = ldexp(1.0, pw);
+  // one fixed-point unit u = 2^-qk for the batch, with 2^31 u above two cells of the coarsest
+  // replica grid plus the drift since the build (the single-system rule, over all replicas)
+  double W = 0.0;
+  for (double L : b->box) {
+    const double nr = std::max(1.0, floor(L / rs));
+    W = std::max(W, 2.0 * L / nr + 2.0 * p.margin + 1.0);
+  }
+  int qk = 31 - (int)ceil(log2(W));
+  if (qk > 30) qk = 30;
   b->reps_h.assign(b->R, ReplicaGeo{});
   int64_t tiles = 0, cells = 0;
   for (int r = 0; r < b->R; ++r) {
@@ -195,6 +205,10 @@ static int setup_replicas(ljmd_batch* b) {
     g.L_lo = (float)(L - Lhi);
     g.inv_L = (float)(1.0 / L);
     g.inv_L64 = 1.0 / L;
+    g.qk = qk;
+    g.qu = (float)ldexp(1.0, -qk);
+    g.Lq = (uint32_t)fmod(nearbyint(ldexp(L, qk)), 4294967296.0);
+    g.q_inv_L = (float)(ldexp(1.0, -qk) / L);
     const int T = replica_tile(b->tile_T, n, b->count[r], L);
     rg.n = (int32_t)n;
     rg.T = T;
@@ -231,15 +245,21 @@ static int setup_replicas(ljmd_batch* b) {
   c.e4 = (float)(4.0 * p.eps);
   c.c2f = (float)(c2 / c.sig2);
   c.c0f = (float)c0;
+  c.f24q = ldexpf(c.f24, qk);
+  c.f48q = ldexpf(c.f48, qk);
+  c.f8c2q = ldexpf(c.f8c2, -qk);
+  c.sig2q = ldexpf(c.sig2f, 2 * qk);
+  c.rc2q = ldexpf(c.rc2f, 2 * qk);
+  c.c2q = ldexpf(c.c2f, -2 * qk);
   // band of the FP32 list filter and the displacement limit: the single-system derivation with
-  // the batch's common p
+  // the batch's common p and u
   const double eps = ldexp(1.0, pw - 22) + ldexp(1.0, pw - 24);
   const double bound = eps * (2.0 * sqrt(3.0) * rs + 3.0 * eps) + 4.0 * 1.2e-7 * rs * rs;
   const double band = 2.0 * bound + 1e-6 * rs * rs;
   b->band.rs2 = rs * rs;
   b->band.lo = (float)(rs * rs - band);
   b->band.hi = (float)(rs * rs + band);
-  b->disp_limit = 0.5 * p.margin - (2.0 * sqrt(3.0) * ldexp(1.0, pw - 23) + 1e-6);
+  b->disp_limit = 0.5 * p.margin - (2.0 * sqrt(3.0) * ldexp(1.0, -qk) + 1e-6 * (0.5 * p.margin) + 1e-9);
   BTRY(balloc(&b->reps, b->R));
   BK(cudaMemcpyAsync(b->reps, b->reps_h.data(), sizeof(ReplicaGeo) * b->R, cudaMemcpyHostToDevice, b->st));
   BTRY(upload_tile_rep(b));
@@ -272,7 +292,7 @@ static int enqueue_rebuild(ljmd_batch* b, const int* pred) {
   launch_copy_words(b->v_alt, b->v, 24 * N, pred, st);
   launch_copy_words(b->id_alt, b->id, 4 * N, pred, st);
   launch_copy_words(b->img_alt, b->img, 12 * N, pred, st);
-  launch_shadow_all(b->x, N, 1, b->hi, b->lo, nullptr, b->ref, st, pred);
+  launch_shadow_all(b->x, N, 1, b->g0.qk, b->hi, b->xq, nullptr, b->ref, st, pred);
   launch_zero_words(b->counter, 2 * sizeof(unsigned long long), pred, st);
   launch_zero_words(b->sizes, 4 * sizeof(unsigned int), pred, st);
   launch_list_batch(b->hi, b->x, b->cell_start, N, b->g0, b->caps, b->band, b->rows, b->tile_list, b->ent,
@@ -378,7 +398,7 @@ static int host_build(ljmd_batch* b) {
 
 static int enqueue_force(ljmd_batch* b, bool energy) {
   if (energy) BK(cudaMemsetAsync(b->e_rep, 0, 2 * sizeof(double) * b->R, b->st));
-  launch_force_batch(b->lanes, energy ? 1 : 0, b->hi, b->lo, b->cell_start, b->N, b->caps, b->c, b->rows,
+  launch_force_batch(b->lanes, energy ? 1 : 0, b->xq, b->cell_start, b->N, b->caps, b->c, b->rows,
                      b->tile_list, b->ent, b->f, b->e_rep, b->status, b->reps, b->R, b->tile_rep, b->st);
   b->launches += 1;
   BKL();
@@ -392,15 +412,15 @@ static int enqueue_steps(ljmd_batch* b, double dt, int64_t k) {
   const float limit2 = (float)(b->disp_limit * b->disp_limit);
   for (int64_t s = 0; s < k; ++s) {
     BK(cudaMemsetAsync(b->dmax, 0, 2 * sizeof(uint32_t), b->st));
-    IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, 0, 1};
-    launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->hi, b->lo, b->ref, b->N, a, nullptr, b->dmax, b->status, b->st);
+    IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, 0, 1, 0, b->g0.qk};
+    launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->xq, b->ref, b->N, a, nullptr, b->dmax, b->status, b->st);
     launch_rebuild_flag(b->dmax, limit2, b->flag, b->d_rebuilds, b->st);
     b->launches += 2;
     BTRY(enqueue_rebuild(b, b->flag));
     BTRY(enqueue_force(b, false));
   }
-  IntegrateArgs a{h, 0.0, 0.0, 0, 0};
-  launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->hi, b->lo, b->ref, b->N, a, nullptr, b->dmax, b->status, b->st);
+  IntegrateArgs a{h, 0.0, 0.0, 0, 0, 0, b->g0.qk};
+  launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->xq, b->ref, b->N, a, nullptr, b->dmax, b->status, b->st);
   b->launches += 1;
   BKL();
   return LJ_OK;
@@ -463,7 +483,7 @@ int ljmd_batch_create(ljmd_batch** out, const ljmd_params* p, int32_t replicas, 
   A(&b->v_alt, 3 * N);
   A(&b->f, N);
   A(&b->hi, N);
-  A(&b->lo, N);
+  A(&b->xq, N);
   A(&b->ref, N);
   A(&b->id, N);
   A(&b->id_alt, N);
@@ -760,6 +780,39 @@ int ljmd_batch_set_tuning(ljmd_batch* b, int32_t tile_cells, int32_t lanes) {
   }
   drop_graph(b);
   return LJ_OK;
+}
+
+// Mean device time of one force launch over all replicas at the current positions and lists:
+// one warm-up launch, then `trials` launches between CUDA events on the batch's stream.  Forces are
+// recomputed (the state is otherwise unchanged).
+int ljmd_batch_time_force(ljmd_batch* b, int32_t trials, double* ms_per_launch) {
+  if (!b || trials <= 0 || !ms_per_launch) return LJ_EINVAL;
+  if (b->broken) return LJ_EDEVICE;
+  BTRY(join_user(b));
+  if (!b->have_state) return LJ_ESTATE;
+  if (!b->have_list) BTRY(host_build(b));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return LJ_EDEVICE;
+  }
+  int rc = enqueue_force(b, false);
+  if (rc == LJ_OK && cudaEventRecord(e0, b->st) != cudaSuccess) rc = LJ_EDEVICE;
+  for (int k = 0; k < trials && rc == LJ_OK; ++k) rc = enqueue_force(b, false);
+  float ms = 0.f;
+  if (rc == LJ_OK && (cudaEventRecord(e1, b->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    rc = LJ_EDEVICE;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LJ_OK) {
+    b->broken = rc == LJ_EDEVICE;
+    return rc;
+  }
+  b->forces_current = true;
+  *ms_per_launch = (double)ms / trials;
+  return check_batch_status(b);
 }
 
 // Project autotuner: for each (tile_cells, lanes) candidate, construct the list at the current

@@ -35,6 +35,14 @@ struct Geom {
   float L_lo;      // L - L_hi rounded to FP32
   float inv_L;     // 1 / L in FP32 (picks the periodic image)
   double inv_L64;  // 1 / L in FP64
+  // Fixed-point positions of the mixed form's pair arithmetic: X = round(x_state / u) mod 2^32 with
+  // u = 2^-qk.  Two such coordinates differ by an exact 32-bit integer as long as the true
+  // difference is below 2^31 u, which qk guarantees for every difference the kernels take
+  // (staged neighbour cells, list partners, displacements since the build, the whole box).
+  int32_t qk;      // u = 2^-qk
+  uint32_t Lq;     // round(L / u) mod 2^32: the periodic image shift in units of u
+  float qu;        // u (a power of two: scaling by it is exact)
+  float q_inv_L;   // u / L in FP32 (picks the periodic image of a whole-box difference)
 };
 
 // Potential constants (Eq. 2) in the forms the kernels use.
@@ -42,6 +50,12 @@ struct LJConst {
   double eps, sigma, rc2, c2, c0, sig2;  // FP64 form
   float f24, f48, f8c2;                  // force: f = ri2 s3i (f24 - f48 s3i) + f8c2
   float sig2f, rc2f, e4, c2f, c0f;       // energy: 4 eps (s3i (s3i - 1) + c2 s + c0)
+  // The same constants for differences in units of u (fixed-point positions): with d_u = d / u and
+  // r2_u = r^2 / u^2, f_u d_u = f d when f24q = f24 / u, f48q = f48 / u, f8c2q = f8c2 u, and
+  // sig2q = sig2 / u^2, rc2q = rc2 / u^2, c2q = c2 u^2.  u is a power of two, so these are the
+  // FP32 constants above with their exponents shifted (no extra rounding); the virial comes out
+  // in units of 1/u and is multiplied by u (exactly) when it is summed.
+  float f24q, f48q, f8c2q, sig2q, rc2q, c2q;
 };
 
 struct ListBand {
@@ -101,11 +115,11 @@ void launch_load_state(const double* x_in, const double* v_in, double* x, double
                        int64_t N, double offset, double L, cudaStream_t s);
 
 // ---- shadow positions ---------------------------------------------------------------
-// mixed: hi/lo FP32 split of x_state; fp64: dvec4 copy.  ref (optional) receives hi
-// (mixed) or the dvec4 (fp64) as the displacement reference.
-void launch_shadow_all(const double* x, int64_t N, int mixed, float4* hi, float4* lo, dvec4* pos64, void* ref,
-                       cudaStream_t s,
-                       const int* pred = nullptr);
+// hi: the FP32 hi parts of x_state (the list kernels' filter, both forms); mixed: the fixed-point
+// records xq (X, Y, Z at u = 2^-qk, w = sorted index); fp64: the dvec4 copy.  ref (optional)
+// receives xq (mixed) or the dvec4 (fp64) as the displacement reference.
+void launch_shadow_all(const double* x, int64_t N, int mixed, int qk, float4* hi, uint4* xq, dvec4* pos64, void* ref,
+                       cudaStream_t s, const int* pred = nullptr);
 
 // ---- staged cell-column tiles: list and force ---------------------------------------------
 constexpr int kMaxTileT = 14;  // cells per tile along z, at most
@@ -139,18 +153,18 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
                       int64_t N, Geom g, TileArgs ta, ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent,
                       uint64_t cap, unsigned long long* counter, unsigned int* max_list, int32_t* status,
                       cudaStream_t s);
-// Returns the number of blocks (energy partials written to part[2 b], part[2 b + 1]).
-int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const float4* lo,
-                      const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
-                      const uint2* tile_list, const uint16_t* ent, void* f, double* part, int32_t* status, int per_sm,
-                      int nbuf, cudaStream_t s);
+// pos: the fixed-point records (mixed) or the dvec4 copies (FP64).  Returns the number of blocks
+// (energy partials written to part[2 b], part[2 b + 1]).
+int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const uint32_t* cs, int64_t N,
+                      Geom g, TileArgs ta, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
+                      void* f, double* part, int32_t* status, int per_sm, int nbuf, cudaStream_t s);
 size_t adjoint_smem_bytes(const TileArgs& ta, int precision);
 // Adjoint pass (HVP, forces, parameter derivatives) over the list; w, hw, fo are dvec4 [N] in sorted
 // order (fo may be null).  Writes 5 partials per block [w.dF/deps, w.dF/dsigma, dPE/deps,
 // dPE/dsigma, PE]; returns the number of blocks.
-int launch_adjoint_tile(int precision, const void* pos, const float4* lo, const uint32_t* cs, int64_t N, Geom g,
-                        TileArgs ta, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
-                        const void* w, void* hw, void* fo, double* part, int32_t* status, cudaStream_t s);
+int launch_adjoint_tile(int precision, const void* pos, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
+                        const uint2* rows, const uint2* tile_list, const uint16_t* ent, const void* w, void* hw,
+                        void* fo, double* part, int32_t* status, cudaStream_t s);
 void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,
                         uint64_t E, uint32_t* out, int32_t* status, cudaStream_t s);
 
@@ -162,13 +176,14 @@ struct IntegrateArgs {
   int ke;          // accumulate the kinetic energy of the full-step velocity
   int shadow;      // rewrite the force kernel's position copy after the drift
   int speed;       // also reduce the largest drift speed (DUTC rules)
+  int qk;          // mixed form: the fixed-point records are at u = 2^-qk
 };
 // Returns the number of blocks used for KE partials.  With a.shadow, dmax_bits[0] and [1] receive
 // (atomic max) the float bits of the largest squared displacement since the list build and of the
 // largest squared drift speed.
-int launch_integrate(int precision, double* x, double* v, const void* f, void* hi_or_pos, float4* lo,
-                     const void* ref, int64_t N, IntegrateArgs a, double* ke_part, uint32_t* dmax_bits,
-                     int32_t* status, cudaStream_t s);
+// pos: the fixed-point records (mixed) or the dvec4 copies (FP64), rewritten when a.shadow is set.
+int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, const void* ref, int64_t N,
+                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, cudaStream_t s);
 
 // ---- pair export through a static device scratch array (no allocation) ----------------
 // Address of this device's scratch (resolved once per device): the kept-pair counter word and
@@ -196,7 +211,7 @@ void launch_list_batch(const float4* hi, const double* x, const uint32_t* cs, in
                        ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
                        unsigned long long* counter, unsigned int* max_list, int32_t* status, const ReplicaGeo* reps,
                        int R, const int32_t* tile_rep, const int* pred, cudaStream_t s);
-int launch_force_batch(int lanes, int energy, const float4* hi, const float4* lo, const uint32_t* cs, int64_t N,
+int launch_force_batch(int lanes, int energy, const uint4* xq, const uint32_t* cs, int64_t N,
                        TileArgs caps, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
                        float4* f, double* e_rep, int32_t* status, const ReplicaGeo* reps, int R,
                        const int32_t* tile_rep, cudaStream_t s);

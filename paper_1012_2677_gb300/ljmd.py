@@ -52,7 +52,8 @@ class ljmd_profile(ctypes.Structure):
     _fields_ = [("force_ms", ctypes.c_double), ("force_launches", ctypes.c_int64),
                 ("integrate_ms", ctypes.c_double), ("integrate_launches", ctypes.c_int64),
                 ("rebuild_ms", ctypes.c_double), ("rebuilds", ctypes.c_int64),
-                ("energy_ms", ctypes.c_double), ("energy_launches", ctypes.c_int64)]
+                ("energy_ms", ctypes.c_double), ("energy_launches", ctypes.c_int64),
+                ("adjoint_ms", ctypes.c_double), ("adjoint_launches", ctypes.c_int64)]
 
 
 class ljmd_batch_stats(ctypes.Structure):
@@ -93,6 +94,7 @@ _SIGS = {
     "ljmd_batch_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_batch_stats)]),
     "ljmd_batch_set_tuning": (ctypes.c_int, [_P, _I32, _I32]),
     "ljmd_batch_autotune": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "ljmd_batch_time_force": (ctypes.c_int, [_P, _I32, _P]),
     "ljmd_traj_loss_grad": (ctypes.c_int, [_P, _I64, _D, _P, _P, _D, _I64, _I64, _I64, _P, _P, _P, _P, _I32]),
     "ljmd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ljmd_stats)]),
     "ljmd_get_grid": (ctypes.c_int, [_P, _P, _I64, _P, _I64, _P]),
@@ -503,6 +505,12 @@ class Batch:
 
     def set_tuning(self, tile_cells=0, lanes=0):
         _chk(load().ljmd_batch_set_tuning(self.h, int(tile_cells), int(lanes)), "ljmd_batch_set_tuning")
+
+    def time_force(self, trials=5):
+        """Mean device time (ms) of one force launch over all replicas."""
+        ms = _D()
+        _chk(load().ljmd_batch_time_force(self.h, int(trials), ctypes.byref(ms)), "ljmd_batch_time_force")
+        return ms.value
 
     def autotune(self, trials=5):
         t, l, ms = _I32(), _I32(), _D()
