@@ -105,13 +105,13 @@ _SIGS = {
 
 
 def load(build_if_missing: bool = True):
-    """Load libljmd.so (building it with nvcc first if it is missing)."""
+    """Load libljmd.so (building it with nvcc first if it is missing or stale)."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    if not os.path.exists(LIB_PATH) and build_if_missing:
+    if build_if_missing:
         from .build import build
-        build()
+        build()  # compiles only if the library is missing or older than a source
     if not os.path.exists(LIB_PATH):
         raise OSError("libljmd.so is not built (%s); run paper_1012_2677_gb300/build.py" % LIB_PATH)
     lib = ctypes.CDLL(LIB_PATH)
