@@ -1284,6 +1284,28 @@ struct AccF {
   float fx, fy, fz, pe, vir;
 };
 
+// Per-thread energy and virial sums over the keys a thread finishes: FP32 partials of at most
+// 16 keys, folded into FP64 totals (so the FP64 pipe, 1/64 of the FP32 rate on this part, sees one
+// add per 16 keys).  The mixed form's virial partial is in units of 1/u and is scaled by u
+// (exactly: u = 2^-qk) when folded.
+struct EAcc {
+  double pe = 0.0, vir = 0.0;
+  float pe32 = 0.0f, vir32 = 0.0f;
+  int n = 0;
+  float vscale = 1.0f;
+  __device__ __forceinline__ void flush() {
+    pe += (double)pe32;
+    vir += (double)(vir32 * vscale);
+    pe32 = vir32 = 0.0f;
+    n = 0;
+  }
+  __device__ __forceinline__ void add32(float p, float v) {
+    pe32 += p;
+    vir32 += v;
+    if (++n == 16) flush();
+  }
+};
+
 // Partner difference of two fixed-point records in units of u: the exact integer difference
 // converted once to FP32.  WHOLE: the nearest periodic image is chosen per pair (the raw
 // difference is below 2^31 u there) and round(L / u) subtracted as an integer.
@@ -1327,8 +1349,7 @@ template <bool MIXED, int LANES, bool HALF, bool ENERGY, bool WHOLE, bool LONGLI
 __device__ __forceinline__ void force_tile_compute(const TileShared& S, const unsigned char* buf, const TileLayout& L,
                                                    const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
                                                    const LJConst& c, const Geom& g, void* __restrict__ fout,
-                                                   int32_t* __restrict__ status, double& pe_acc, double& vir_acc,
-                                                   int list_cap) {
+                                                   int32_t* __restrict__ status, EAcc& eacc, int list_cap) {
   const void* sh_pos = buf + L.pos;
   const int* sh_gid = (const int*)(buf + L.gid);
   const uint2* s_rows = (const uint2*)(buf + L.rows);
@@ -1441,12 +1462,9 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
         if (HALF) atomicAdd(&((float4*)fout)[gi], make_float4(fx, fy, fz, 0.0f));
         else ((float4*)fout)[gi] = make_float4(fx, fy, fz, 0.0f);
       }
-      if (ENERGY) {  // the group's lanes reduce in FP32, one lane accumulates in FP64
+      if (ENERGY) {  // the group's lanes reduce in FP32, one lane accumulates
         const float pe = gsum<LANES>(a0.pe + a1.pe), vir = gsum<LANES>(a0.vir + a1.vir);
-        if (lane == 0) {
-          pe_acc += (double)pe;
-          vir_acc += (double)(vir * g.qu);  // units of 1/u -> sigma units (exact: u = 2^-qk)
-        }
+        if (lane == 0) eacc.add32(pe, vir);
       }
     } else {
       dfx = gsum<LANES>(dfx);
@@ -1463,8 +1481,8 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
         }
       }
       if (ENERGY) {
-        pe_acc += dpe;
-        vir_acc += dvir;
+        eacc.pe += dpe;
+        eacc.vir += dvir;
       }
     }
   }
@@ -1508,13 +1526,14 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   __shared__ __align__(8) uint64_t bars[2];
   const TileLayout L = tile_layout(ta, MIXED, true, !MIXED && (HALF || WHOLE));
   const size_t buf_bytes = align16(L.total);
-  double pe_acc = 0.0, vir_acc = 0.0;
+  EAcc eacc;
+  eacc.vscale = g.qu;
   if (WHOLE) {
     if (blockIdx.x == 0) {
       stage_whole<MIXED, !MIXED>(N, pos, SS[0], smem, L);
       __syncthreads();
-      force_tile_compute<MIXED, LANES, HALF, ENERGY, true, false>(SS[0], smem, L, rows, ent, c, g, fout, status, pe_acc,
-                                                           vir_acc, ta.list_cap);
+      force_tile_compute<MIXED, LANES, HALF, ENERGY, true, false>(SS[0], smem, L, rows, ent, c, g, fout, status, eacc,
+                                                                  ta.list_cap);
     }
   } else {
     const bool pipelined = nbuf == 2;
@@ -1553,8 +1572,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
           if (v_next) mbar_wait(&bars[b ^ 1], b ? ph0 : ph1, kWaitBudget);  // drain the other buffer's copies
           return;
         }
-        force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST>(SS[b], smem + b * buf_bytes, L, rows, ent, c, g, fout,
-                                                              status, pe_acc, vir_acc, ta.list_cap);
+        force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST>(SS[b], smem + b * buf_bytes, L, rows, ent, c, g,
+                                                                        fout, status, eacc, ta.list_cap);
       }
       __syncthreads();
       if (pipelined) {
@@ -1565,9 +1584,10 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   }
   if (ENERGY) {
     __shared__ double sh[32];
-    const double tp = block_sum(pe_acc, sh);
+    eacc.flush();
+    const double tp = block_sum(eacc.pe, sh);
     __syncthreads();
-    const double tv = block_sum(vir_acc, sh);
+    const double tv = block_sum(eacc.vir, sh);
     if (threadIdx.x == 0) {
       part[2 * (size_t)blockIdx.x] = tp;
       part[2 * (size_t)blockIdx.x + 1] = tv;
@@ -1646,7 +1666,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // and the FP64 form with the half list (the producer writes the shift codes and sorted indices;
 // the consumers scatter the partners' forces with atomics).
 template <bool MIXED, bool HALF, int LANES, bool ENERGY, bool LONGLIST, int CW>
-__global__ void __launch_bounds__(pipe_threads(CW), 2)
+__global__ void __launch_bounds__(pipe_threads(CW), (MIXED && CW <= 8) ? 3 : 2)
     k_force_pipe(const void* __restrict__ pos, const uint32_t* __restrict__ cs, Geom g, TileArgs ta, LJConst c,
                  const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
                  const uint16_t* __restrict__ ent, void* __restrict__ fout, double* __restrict__ part,
@@ -1670,7 +1690,8 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
     fence_proxy_async_smem();
   }
   __syncthreads();
-  double pe_acc = 0.0, vir_acc = 0.0;
+  EAcc eacc;
+  eacc.vscale = g.qu;
   const int64_t stride = gridDim.x;
   if (warp >= CW) {
     // ---- producer p: tiles k = p, p + 2, ... in buffer p ----
@@ -1772,8 +1793,7 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
       }
       if (v > 0)
         force_tile_compute<MIXED, LANES, HALF, ENERGY, false, LONGLIST, 32 * CW>(SS[slot], buf, L, rows, ent, c, g,
-                                                                                    fout, status, pe_acc, vir_acc,
-                                                                                    ta.list_cap);
+                                                                                    fout, status, eacc, ta.list_cap);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
     }
@@ -1781,9 +1801,10 @@ __global__ void __launch_bounds__(pipe_threads(CW), 2)
   __syncthreads();
   if (ENERGY) {
     __shared__ double sh[32];
-    const double tp = block_sum(pe_acc, sh);
+    eacc.flush();
+    const double tp = block_sum(eacc.pe, sh);
     __syncthreads();
-    const double tv = block_sum(vir_acc, sh);
+    const double tv = block_sum(eacc.vir, sh);
     if (threadIdx.x == 0) {
       part[2 * (size_t)blockIdx.x] = tp;
       part[2 * (size_t)blockIdx.x + 1] = tv;
@@ -1822,17 +1843,19 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     replica_view(rg, ta, g);
     const uint32_t* cs = cs_in + rg.cell_base;
     const TileInfo ti = tile_info(t - rg.tile_base, ta);
-    double pe_acc = 0.0, vir_acc = 0.0;
+    EAcc eacc;
+    eacc.vscale = g.qu;
     if (force_tile_prepare(ti, t, ta, cs, tile_list, S, status)) {
       stage_issue<true, true>(ti, ta, pos, rows, ent, S, smem, L, &bar);
       if (!stage_finish<true, true>(ti, ta, g, S, smem, L, &bar, ph, false, status)) return;
-      force_tile_compute<true, LANES, false, ENERGY, false, true>(S, smem, L, rows, ent, c, g, fout, status, pe_acc,
-                                                            vir_acc, ta.list_cap);
+      force_tile_compute<true, LANES, false, ENERGY, false, true>(S, smem, L, rows, ent, c, g, fout, status, eacc,
+                                                                  ta.list_cap);
     }
     if (ENERGY) {
-      const double tp = block_sum(pe_acc, sh);
+      eacc.flush();
+      const double tp = block_sum(eacc.pe, sh);
       __syncthreads();
-      const double tv = block_sum(vir_acc, sh);
+      const double tv = block_sum(eacc.vir, sh);
       if (threadIdx.x == 0) {
         atomicAdd(&e_rep[2 * r], 0.5 * tp);  // full list: each pair twice
         atomicAdd(&e_rep[2 * r + 1], 0.5 * tv);
