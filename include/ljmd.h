@@ -332,8 +332,10 @@ int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out);
 
 /*
  * Kernel shape of the list and force kernels (the autotuner's knobs); 0 keeps the default.
- * tile_cells: cells per shared-memory tile along z (1..14); lanes: threads per key particle
- * in the force kernel (1, 2, 4, 8, 16, 32); force_ctas_per_sm: resident force CTAs per SM
+ * tile_cells: cells per shared-memory tile along z (1..14; default: for the mixed form with the
+ * full list about 140 particles per tile, at most 12 cells, else 4); lanes: threads per key
+ * particle in the force kernel (1, 2, 4, 8, 16, 32; default: for the mixed form with the full list
+ * 2 for tiles of 96 or more particles, else 4); force_ctas_per_sm: resident force CTAs per SM
  * (1..4; the pipelined kernel takes as many as fit); force_buffers: tile buffers per force CTA
  * (1: tiles staged one after the other; 2: the next tile's copies overlap the current tile's
  * arithmetic; for the mixed form with the full list and the FP64 form with the half list this is

@@ -444,6 +444,31 @@ static int force_buffers(const ljmd_sys* s) {
   return ((s->precision == LJ_MIXED) != s->list_half) ? 2 : 1;
 }
 
+// Default cells per tile along z.  The mixed form with the full list (the pipelined force kernel):
+// about 140 key particles per tile, so that the staging of the 9 (T + 2) neighbour cells and the
+// per-tile bookkeeping are spread over many keys; measured on GB300 at 16.4M particles, rho 0.5
+// (13.8 particles per cell), T = 4, 8, 10, 12 give force launches of 2.41, 2.10, 1.96, 1.88 ms and
+// list constructions of 12.6, 14.7, 13.9, 15.5 ms, and T = 10 the shortest step.  The half-list
+// forms keep 4 cells: at rho 0.8 (mixed, half list) T = 3, 4, 6 give force 3.76, 3.56, 4.06 ms and
+// construction 19.0, 19.8, 33.7 ms; the FP64 form at rho 0.5 gives force 45.5 ms at T = 4 and
+// 49.4 ms at T = 10 with 2 lanes.
+static int default_tile_cells(const ljmd_sys* s) {
+  if (s->precision != LJ_MIXED || s->list_half) return 4;
+  const double ppc = (double)s->n / (double)std::max<int64_t>(s->ncells, 1);
+  const int T = (int)lround(140.0 / std::max(ppc, 1.0));
+  return std::max(1, std::min(T, 12));
+}
+
+// Default threads per key in the force kernel: for the mixed form with the full list, 2 for tiles
+// of about 100 keys or more (more keys than 4-lane groups otherwise), 4 below (measured as above:
+// T = 10 with 2 lanes 1.96 ms, 4 lanes 2.01 ms; T = 4 with 2 lanes 2.41 ms, 4 lanes 2.41 ms,
+// 8 lanes 2.67 ms); 4 for the half-list forms.
+static int default_lanes(const ljmd_sys* s) {
+  if (s->precision != LJ_MIXED || s->list_half) return 4;
+  const double ppc = (double)s->n / (double)std::max<int64_t>(s->ncells, 1);
+  return (double)s->ta.T * ppc >= 96.0 ? 2 : 4;
+}
+
 static int choose_tiles(ljmd_sys* s, int t_cap) {
   ljmd_sys* sys = s;
   TileArgs& ta = s->ta;
@@ -464,7 +489,7 @@ static int choose_tiles(ljmd_sys* s, int t_cap) {
     return ensure_tile_list(s);
   }
   ta.whole = 0;
-  int T = s->tile_T > 0 ? s->tile_T : 4;
+  int T = s->tile_T > 0 ? s->tile_T : default_tile_cells(s);
   if (T > t_cap) T = t_cap;
   if (T > n - 2) T = n - 2;
   if (T > kMaxTileT) T = kMaxTileT;
@@ -630,7 +655,7 @@ static int run_force(ljmd_sys* s, bool energy) {
   const int half = s->list_half ? 1 : 0;
   if (half) CK(cudaMemsetAsync(s->f, 0, (s->precision == LJ_MIXED ? 16 : 32) * (size_t)s->n, s->st));
   int lanes = s->prm.lanes;
-  if (lanes == 0) lanes = 4;
+  if (lanes == 0) lanes = default_lanes(s);
   const int per_sm = s->force_per_sm;  // 0: as many CTAs per SM as shared memory allows
   {
     PhaseTimer timer(s, PH_FORCE);
