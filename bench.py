@@ -325,6 +325,7 @@ def run_ours(args, wl, world, rank, local):
     replica = None if args.no_replica else run_paper_replica(stream)
     adjoint = None if args.no_adjoint else run_adjoint(stream, peaks, peak_kind)
     truncation = None if args.no_truncation else run_truncation(stream)
+    small = None if args.no_small else run_small(stream)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -347,6 +348,7 @@ def run_ours(args, wl, world, rank, local):
         "paper_replica": replica,
         "adjoint": adjoint,
         "truncation": truncation,
+        "small_system": small,
         "pair_interactions_per_s": entries * args.steps * world / (ms * 1e-3),
     }
     if rank == 0 and not args.no_cpu_baseline and not args.skip_cpu:
@@ -466,6 +468,35 @@ def run_adjoint(stream, peaks, peak_kind):
                                           extra={"launches": prof["adjoint_launches"]})}
     res["note"] = "forward 50 steps + reverse pass (one Hessian-vector product per state, segments recomputed)"
     return res
+
+
+def run_small(stream):
+    """The small FP64 configuration (FCC 10^3 x 4, rho 0.5, T 1, seed 1, dt 0.005, 100 steps, energies
+    every step) in both forms, timed with CUDA events after 20 warm-up steps: a size where launch and
+    synchronisation costs, not the kernels, set the rate."""
+    import torch
+    from paper_1012_2677_gb300 import ljmd
+    out = {}
+    for name, prec in (("fp64", ljmd.LJ_FP64), ("mixed", ljmd.LJ_MIXED)):
+        with ljmd.System(cutoff=2.5, margin=0.5, precision=prec, list_form=ljmd.LJ_LIST_AUTO, energy_every=1,
+                         stream=stream) as s:
+            s.init_lattice(10, 0.5, 1.0, 1)
+            s.step(0.005, 20)
+            torch.cuda.synchronize()
+            st0 = s.stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(0.005, 100)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st1 = s.stats()
+            n = s.n
+        out[name] = {"value": n * 100 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / 100,
+                     "rebuilds": st1["rebuilds"] - st0["rebuilds"],
+                     "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"]}
+    out["workload"] = "FCC 10^3 x 4 (4,000 particles), rho 0.5, T 1, seed 1, dt 0.005, 100 steps"
+    return out
 
 
 def drift_stats(E, n, dt):
@@ -621,6 +652,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-replica", action="store_true")
     ap.add_argument("--no-truncation", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-cpu-verlet", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--skip-cpu", action="store_true", help=argparse.SUPPRESS)

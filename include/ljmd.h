@@ -293,7 +293,8 @@ int ljmd_hvp(ljmd_sys* sys, const double* w, double* hw, double* dtheta, int32_t
  * recurrences of velocity-Verlet with h = dt / 2 (one adjoint pass, i.e. one Hessian-vector
  * product, per state), recomputing the states of each segment of ckpt_every steps from a
  * checkpoint stored in the forward run.  Arrays are host (on_device = 0) or device (1).  The
- * handle's state is replaced (it ends at x0 of the last recomputed segment).  The paper has no
+ * handle's state is replaced: it ends at the positions x0, velocities unspecified; the energy log
+ * registered with ljmd_set_energy_log receives nothing from this call.  The paper has no
  * adjoint; this differentiates its integrator and pair force.  Synchronises the stream.
  * Like ljmd_hvp it needs the full list (LJ_LIST_HALF: LJ_ESTATE; LJ_LIST_AUTO: full from now on).
  * Errors: LJ_EINVAL (n <= 0, nsteps < 1, n_pe outside [0, nsteps], ckpt_every < 1, NULL x0, v0 or
@@ -333,7 +334,7 @@ int ljmd_get_profile(ljmd_sys* sys, ljmd_profile* out);
 /*
  * Kernel shape of the list and force kernels (the autotuner's knobs); 0 keeps the default.
  * tile_cells: cells per shared-memory tile along z (1..14; default: for the mixed form with the
- * full list about 140 particles per tile, at most 12 cells, else 4); lanes: threads per key
+ * full list about 165 particles per tile, at most 12 cells, else 4); lanes: threads per key
  * particle in the force kernel (1, 2, 4, 8, 16, 32; default: for the mixed form with the full list
  * 2 for tiles of 96 or more particles, else 4); force_ctas_per_sm: resident force CTAs per SM
  * (1..4; the pipelined kernel takes as many as fit); force_buffers: tile buffers per force CTA

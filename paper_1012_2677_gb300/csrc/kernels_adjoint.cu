@@ -43,6 +43,35 @@ void launch_unwrapped(const double* x, const int32_t* img, const int32_t* id, in
   k_unwrapped<<<grid_of(N), 256, 0, s>>>(x, img, id, N, offset, L, out);
 }
 
+// The inverse of k_unwrapped for the current sorted order and image counts: x[k N + s] =
+// offset + u[3 id[s] + k] - img[k N + s] L, so that positions given unwrapped in id order are
+// stored without re-sorting the particles (the list built for this order stays usable while the
+// displacement rule holds).
+__global__ void k_load_unwrapped(const double* __restrict__ u, const int32_t* __restrict__ img,
+                                 const int32_t* __restrict__ id, int64_t N, double offset, double L,
+                                 double* __restrict__ x) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = id[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) x[k * N + s] = offset + (u[3 * p + k] - (double)img[k * N + s] * L);
+  }
+}
+void launch_load_unwrapped(const double* u, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
+                           double* x, cudaStream_t s) {
+  k_load_unwrapped<<<grid_of(N), 256, 0, s>>>(u, img, id, N, offset, L, x);
+}
+
+// Parameter-gradient accumulation on the device: gth[0] += a0 q[0] + a4 q[4], gth[1] += a1 q[1] +
+// a3 q[3], with q the five reduced sums of an adjoint pass (one thread).
+__global__ void k_accum_q(const double* __restrict__ q, double a0, double a1, double a3, double a4,
+                          double* __restrict__ gth) {
+  gth[0] += a0 * q[0] + a4 * q[4];
+  gth[1] += a1 * q[1] + a3 * q[3];
+}
+void launch_accum_q(const double* q, double a0, double a1, double a3, double a4, double* gth, cudaStream_t s) {
+  k_accum_q<<<1, 1, 0, s>>>(q, a0, a1, a3, a4, gth);
+}
+
 // y += a x (n doubles)
 __global__ void k_axpy(double* __restrict__ y, double a, const double* __restrict__ x, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

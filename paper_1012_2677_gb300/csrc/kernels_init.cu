@@ -34,7 +34,9 @@ void launch_final_reduce(const double* partials, int nblocks, int nq, double* ou
 // integrator partials.  Appends (step, pe, ke, vir) to the log if there is room.
 __global__ void k_energy_finalize(const double* __restrict__ pv, int nbf, const double* __restrict__ kp, int nbi,
                                   double pe_scale, double* __restrict__ energies, double* __restrict__ log,
-                                  int64_t cap, int64_t* __restrict__ count, double step) {
+                                  int64_t cap, int64_t* __restrict__ count, double step,
+                                  const int* __restrict__ skip) {
+  if (skip && *skip) return;  // a device-decided run stopped before this step
   __shared__ double sh[32];
   double pe = 0.0, vir = 0.0, ke = 0.0;
   for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
@@ -69,9 +71,9 @@ __global__ void k_energy_finalize(const double* __restrict__ pv, int nbf, const 
 
 void launch_energy_finalize(const double* pe_vir_part, int nb_force, const double* ke_part, int nb_int,
                             double pe_scale, double* energies, double* log, int64_t log_cap, int64_t* log_count,
-                            double step, cudaStream_t s) {
+                            double step, cudaStream_t s, const int* skip) {
   k_energy_finalize<<<1, 1024, 0, s>>>(pe_vir_part, nb_force, ke_part, nb_int, pe_scale, energies, log, log_cap,
-                                        log_count, step);
+                                        log_count, step, skip);
 }
 
 // ---------------------------------------------------------------------------------------------

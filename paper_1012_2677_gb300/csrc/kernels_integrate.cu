@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
                                                    const void* __restrict__ fptr, void* __restrict__ pos,
                                                    const void* __restrict__ refp, int64_t N, IntegrateArgs a,
                                                    double* __restrict__ ke_part, uint32_t* __restrict__ dmax_bits,
-                                                   int32_t* __restrict__ status) {
+                                                   int32_t* __restrict__ status, const int* __restrict__ skip) {
+  if (skip && *skip) return;  // a device-decided run stopped before this step
   const float qu = __int_as_float((127 - a.qk) << 23);  // u = 2^-qk
   const double kk = a.kpre + a.kpost;
   const float kpre_f = (float)a.kpre;
@@ -144,19 +145,49 @@ static int one_wave(int64_t N) {
 }
 
 int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, const void* ref, int64_t N,
-                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, cudaStream_t s) {
+                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, cudaStream_t s,
+                     const int* skip) {
   const int blocks = precision == LJ_MIXED ? one_wave<true>(N) : one_wave<false>(N);
   if (precision == LJ_MIXED)
-    k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status);
+    k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, skip);
   else
-    k_integrate<false><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status);
+    k_integrate<false><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, skip);
   return blocks;
 }
 
+// The list-validity decision of a device-decided run (the host rule of ljmd_step, taken on the
+// device so that steps follow each other without a host round trip).
+__global__ void k_step_check(uint32_t* __restrict__ dmax_bits, StepCtl* __restrict__ ctl, int s, double disp_limit,
+                             int dutc, double two_dt) {
+  if (ctl->stop) return;
+  const float d2 = __uint_as_float(dmax_bits[0]), v2 = __uint_as_float(dmax_bits[1]);
+  ctl->last[0] = d2;
+  ctl->last[1] = v2;
+  dmax_bits[0] = 0u;
+  dmax_bits[1] = 0u;
+  bool expired;
+  if (dutc) {
+    const double b = ctl->dutc - two_dt * sqrt((double)v2) * (1.0 + 1e-6);
+    ctl->dutc = b;
+    expired = !(b > 0.0);
+  } else {
+    expired = sqrt((double)d2) > disp_limit;
+  }
+  if (expired) {
+    ctl->stop = 1;
+    ctl->stop_at = s;
+  }
+}
+
+void launch_step_check(uint32_t* dmax_bits, StepCtl* ctl, int s, double disp_limit, int dutc, double two_dt,
+                       cudaStream_t st) {
+  k_step_check<<<1, 1, 0, st>>>(dmax_bits, ctl, s, disp_limit, dutc, two_dt);
+}
+
 // Position copies for the force and list kernels from the FP64 state (no integration): the FP32
-// hi parts always (the list construction filters on them in both forms); for the mixed form the
-// fixed-point records, for FP64 the dvec4 copy; and the displacement reference (the records for
-// mixed, the dvec4 for FP64) if ref != NULL.
+// hi parts always, with the sorted index in w (the list construction filters on them in both
+// forms); for the mixed form the fixed-point records, for FP64 the dvec4 copy; and the
+// displacement reference (the records for mixed, the dvec4 for FP64) if ref != NULL.
 __global__ void k_shadow(const double* __restrict__ x, int64_t N, int mixed, int qk, float4* __restrict__ hi,
                          uint4* __restrict__ xq, dvec4* __restrict__ pos64, void* __restrict__ ref,
                          const int* __restrict__ pred) {
@@ -168,7 +199,7 @@ __global__ void k_shadow(const double* __restrict__ x, int64_t N, int mixed, int
     split_hi_lo(a, h.x, unused);
     split_hi_lo(b, h.y, unused);
     split_hi_lo(c, h.z, unused);
-    h.w = 0.0f;
+    h.w = __int_as_float((int)i);  // the sorted index, for the list construction
     hi[i] = h;
     if (mixed) {
       const uint4 q = make_uint4(fixq(a, qk), fixq(b, qk), fixq(c, qk), (uint32_t)i);

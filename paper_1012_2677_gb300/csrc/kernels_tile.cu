@@ -486,8 +486,7 @@ constexpr int kListItems = 9 * kListSplit;     // work items per 32-key chunk
 constexpr size_t kListSmemTarget = 48 * 1024;  // 4 CTAs per SM for typical liquids
 constexpr int kListThreads = 256;               // threads of a list-construction CTA (128 or 256)
 struct KeyListLayout {
-  size_t pos;    // hi float4 [max_staged]
-  size_t gid;    // int [max_staged]
+  size_t pos;    // hi float4 [max_staged] (w: the sorted index, as int bits)
   size_t cnt;    // int [nch * kListItems * 32]: per (key, column part) counts, then offsets in the row
   size_t kst;    // int [nch * 32] row start within the tile segment, then int [nch * 32] row length
   size_t ibase;  // int [nch * kListItems + 1]: first mask word of each item
@@ -504,8 +503,6 @@ __host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs
   K.nch = (ta.max_own + 31) / 32;
   K.pos = 0;
   size_t o = align16(ms * 16);
-  K.gid = o;
-  o += align16(ms * 4);
   K.cnt = o;
   o += align16((size_t)K.nch * kListItems * 32 * 4);
   K.kst = o;
@@ -518,9 +515,21 @@ __host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs
   K.mask = o;
   o += (size_t)K.mask_words * 32 * 4;
   K.seg = o;
-  // 128-thread CTAs: smaller footprint, more of them per SM
+  // The segment staging area: what is left of 48 KB (4 CTAs per SM; 128-thread CTAs: 36 KB).  When
+  // the tile's other areas leave less than 8 KB of that (large tiles), the CTA takes up to 110 KB
+  // (2 per SM) so that a segment of up to ~80 entries per key still fits; a segment that does not fit
+  // is written to global memory directly.
   const size_t target = nt == 128 ? kListSmemTarget * 3 / 4 : kListSmemTarget;
-  size_t room = o + 8192 < target ? target - o : 8192;
+  size_t room;
+  if (o + 8192 <= target) {
+    room = target - o;
+  } else {
+    const size_t cap2 = (size_t)(112 * 1024 - 2048);
+    const size_t want = 160 * (size_t)ta.max_own;
+    room = o < cap2 ? cap2 - o : 0;
+    if (room > want) room = want;
+    if (room < 8192) room = 8192;
+  }
   K.seg_cap = (int)((room / 2) & ~(size_t)7);
   K.total = o + 2 * (size_t)K.seg_cap;
   return K;
@@ -685,7 +694,7 @@ __device__ __forceinline__ void key_item_range(const TileShared& S, int Tp, int 
 // MODE 0: count; 1: count and store the kept-candidate bits (word w of the item at
 // mask[(wbase + w) * 32 + lane]); 2: write the kept partners to dst[p], dst[p + 1], ...
 template <bool HALF, int MODE>
-__device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float4* sh_pos, const int* sh_gid,
+__device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float4* sh_pos,
                                         const double* __restrict__ x, int64_t N, const Geom& g,
                                         const ListBand& band, int c, int k, int h, int n_own, uint16_t* dst, int p,
                                         uint32_t* mask, int wbase) {
@@ -697,7 +706,7 @@ __device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float
   key_item_range(S, Tp, c, k, h, n_own, j0, j1);
   const int l = S.own0 + (valid ? o : o_last);
   const float4 pi = sh_pos[l];
-  const int gi = sh_gid[l];
+  const int gi = __float_as_int(sh_pos[l].w);
   int cnt = 0;
   uint32_t bits = 0;
   int j = j0;
@@ -709,14 +718,14 @@ __device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float
     bool ina = key_test(fmaf(ax, ax, fmaf(ay, ay, az * az)), band, ma_);
     bool inb = key_test(fmaf(bx, bx, fmaf(by, by, bz * bz)), band, mb_);
     if (__any_sync(0xffffffffu, ma_ || mb_)) {
-      if (ma_) ina = pair_in_exact(x, N, gi, sh_gid[j], g, band.rs2);
-      if (mb_) inb = pair_in_exact(x, N, gi, sh_gid[j + 1], g, band.rs2);
+      if (ma_) ina = pair_in_exact(x, N, gi, __float_as_int(sh_pos[j].w), g, band.rs2);
+      if (mb_) inb = pair_in_exact(x, N, gi, __float_as_int(sh_pos[j + 1].w), g, band.rs2);
     }
     ina = ina && valid && j != l;
     inb = inb && valid && j + 1 != l;
     if (HALF) {
-      ina = ina && sh_gid[j] > gi;
-      inb = inb && sh_gid[j + 1] > gi;
+      ina = ina && __float_as_int(sh_pos[j].w) > gi;
+      inb = inb && __float_as_int(sh_pos[j + 1].w) > gi;
     }
     if (MODE == 2) {
       if (ina) dst[p++] = (uint16_t)j;
@@ -738,10 +747,10 @@ __device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float
     bool ma_;
     bool ina = key_test(fmaf(ax, ax, fmaf(ay, ay, az * az)), band, ma_);
     if (__any_sync(0xffffffffu, ma_)) {
-      if (ma_) ina = pair_in_exact(x, N, gi, sh_gid[j], g, band.rs2);
+      if (ma_) ina = pair_in_exact(x, N, gi, __float_as_int(sh_pos[j].w), g, band.rs2);
     }
     ina = ina && valid && j != l;
-    if (HALF) ina = ina && sh_gid[j] > gi;
+    if (HALF) ina = ina && __float_as_int(sh_pos[j].w) > gi;
     if (MODE == 2 && ina) dst[p++] = (uint16_t)j;
     if (MODE == 1) bits |= (ina ? 1u : 0u) << ((j - j0) & 31);
     cnt += ina ? 1 : 0;
@@ -756,7 +765,7 @@ __device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float
 // FP64 test, the key itself and the slots past the range are cleared, and the word is stored.
 // Slots past the range read whatever follows in shared memory; their bits are masked off.
 template <bool HALF>
-__device__ __forceinline__ int key_item_bits(const TileShared& S, int Tp, const float4* sh_pos, const int* sh_gid,
+__device__ __forceinline__ int key_item_bits(const TileShared& S, int Tp, const float4* sh_pos,
                                              const double* __restrict__ x, int64_t N, const Geom& g,
                                              const ListBand& band, int c, int k, int h, int n_own, uint32_t* mask,
                                              int wbase) {
@@ -768,7 +777,7 @@ __device__ __forceinline__ int key_item_bits(const TileShared& S, int Tp, const 
   key_item_range(S, Tp, c, k, h, n_own, j0, j1);
   const int l = S.own0 + (valid ? o : o_last);
   const float4 pi = sh_pos[l];
-  const int gi = sh_gid[l];
+  const int gi = __float_as_int(sh_pos[l].w);
   int cnt = 0;
   for (int jb = j0, w = 0; jb < j1; jb += 32, ++w) {
     uint32_t bits = 0, mbits = 0;
@@ -791,7 +800,7 @@ __device__ __forceinline__ int key_item_bits(const TileShared& S, int Tp, const 
       while (mbits) {
         const int bit = __ffs(mbits) - 1;
         mbits &= mbits - 1;
-        if (pair_in_exact(x, N, gi, sh_gid[jb + bit], g, band.rs2)) bits |= 1u << bit;
+        if (pair_in_exact(x, N, gi, __float_as_int(sh_pos[jb + bit].w), g, band.rs2)) bits |= 1u << bit;
       }
     }
     if (l >= jb && l < jb + 32) bits &= ~(1u << (l - jb));  // the key itself
@@ -800,7 +809,7 @@ __device__ __forceinline__ int key_item_bits(const TileShared& S, int Tp, const 
       while (m) {
         const int bit = __ffs(m) - 1;
         m &= m - 1;
-        if (sh_gid[jb + bit] <= gi) bits &= ~(1u << bit);
+        if (__float_as_int(sh_pos[jb + bit].w) <= gi) bits &= ~(1u << bit);
       }
     }
     if (!valid) bits = 0u;
@@ -831,7 +840,7 @@ __device__ __forceinline__ void key_item_from_mask(const TileShared& S, int Tp, 
 // the lane's key l (sorted index gi); bit b set iff j0 + b is listed for the key.  Same tests as
 // key_item_bits.
 template <bool HALF>
-__device__ __forceinline__ uint32_t unit_bits(const float4* sh_pos, const int* sh_gid, const double* __restrict__ x,
+__device__ __forceinline__ uint32_t unit_bits(const float4* sh_pos, const double* __restrict__ x,
                                               int64_t N, const Geom& g, const ListBand& band, int j0, int len, int l,
                                               int gi, bool valid) {
   const float4 pi = sh_pos[l];
@@ -854,7 +863,7 @@ __device__ __forceinline__ uint32_t unit_bits(const float4* sh_pos, const int* s
     while (mbits) {
       const int bit = __ffs(mbits) - 1;
       mbits &= mbits - 1;
-      if (pair_in_exact(x, N, gi, sh_gid[j0 + bit], g, band.rs2)) bits |= 1u << bit;
+      if (pair_in_exact(x, N, gi, __float_as_int(sh_pos[j0 + bit].w), g, band.rs2)) bits |= 1u << bit;
     }
   }
   if (l >= j0 && l < j0 + 32) bits &= ~(1u << (l - j0));  // the key itself
@@ -863,7 +872,7 @@ __device__ __forceinline__ uint32_t unit_bits(const float4* sh_pos, const int* s
     while (m) {
       const int bit = __ffs(m) - 1;
       m &= m - 1;
-      if (sh_gid[j0 + bit] <= gi) bits &= ~(1u << bit);
+      if (__float_as_int(sh_pos[j0 + bit].w) <= gi) bits &= ~(1u << bit);
     }
   }
   return valid ? bits : 0u;
@@ -898,12 +907,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   __shared__ int s_nchunk, s_nunit;
   constexpr int kLW = NT / 32;  // warps of the CTA
   const KeyListLayout K = key_list_layout(ta_in, NT);
-  TileLayout L;  // the staging helpers' view: positions and sorted indices
+  TileLayout L;  // the staging helpers' view: positions (sorted indices in w)
   L.pos = K.pos;
-  L.gid = K.gid;
+  L.gid = K.pos;
   L.rows = L.ent = L.cnt = L.total = 0;
   const float4* sh_pos = (const float4*)(smem + K.pos);
-  const int* sh_gid = (const int*)(smem + K.gid);
   int* s_cnt = (int*)(smem + K.cnt);
   int* s_kst = (int*)(smem + K.kst);
   int* s_len = s_kst + K.nch * 32;
@@ -956,7 +964,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
       __syncthreads();
       continue;
     }
-    if (!stage_copy_async<true, false>(ti, ta, g, pos, nullptr, nullptr, S, smem, L, &bar, phase, true, status))
+    if (!stage_copy_async<true, false>(ti, ta, g, pos, nullptr, nullptr, S, smem, L, &bar, phase, false, status))
       return;
     const int n_own = S.own1 - S.own0;
     if (n_own > ta.max_own) {  // sizing inconsistency: record and skip the tile
@@ -1051,8 +1059,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
         const int o = u_ck0[c] + lane;
         const bool valid = o < u_ck0[c + 1];
         const int l = S.own0 + (valid ? o : u_ck0[c + 1] - 1);
-        s_mask[u * 32 + lane] = unit_bits<HALF>(sh_pos, sh_gid, x, N, g, band, u_info[u] & 0xffff, u_info[u] >> 16,
-                                                l, sh_gid[l], valid);
+        s_mask[u * 32 + lane] = unit_bits<HALF>(sh_pos, x, N, g, band, u_info[u] & 0xffff, u_info[u] >> 16, l,
+                                                __float_as_int(sh_pos[l].w), valid);
       }
       __syncthreads();
       // phase B: row lengths (one warp per chunk), and each unit's offset in its keys' rows
@@ -1165,9 +1173,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     for (int item = warp; item < nch * kItems; item += kLW) {
       const int c = item / kItems, r = item - kItems * c;
       s_cnt[item * 32 + lane] =
-          keep_bits ? key_item_bits<HALF>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit,
+          keep_bits ? key_item_bits<HALF>(S, ti.Tp, sh_pos, x, N, g, band, c, r / kListSplit, r % kListSplit,
                                           n_own, s_mask, s_ibase[item])
-                    : key_item<HALF, 0>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit,
+                    : key_item<HALF, 0>(S, ti.Tp, sh_pos, x, N, g, band, c, r / kListSplit, r % kListSplit,
                                         n_own, nullptr, 0, nullptr, 0);
     }
     __syncthreads();
@@ -1224,7 +1232,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
         if (keep_bits)
           key_item_from_mask(S, ti.Tp, c, r / kListSplit, r % kListSplit, n_own, dst, p, s_mask, s_ibase[item]);
         else
-          key_item<HALF, 2>(S, ti.Tp, sh_pos, sh_gid, x, N, g, band, c, r / kListSplit, r % kListSplit, n_own, dst,
+          key_item<HALF, 2>(S, ti.Tp, sh_pos, x, N, g, band, c, r / kListSplit, r % kListSplit, n_own, dst,
                             p, nullptr, 0);
       }
       if (staged) {
@@ -1520,7 +1528,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     k_force_tile(const void* __restrict__ pos, const uint32_t* __restrict__ cs, int64_t N, Geom g, TileArgs ta,
                  LJConst c, const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
                  const uint16_t* __restrict__ ent, void* __restrict__ fout, double* __restrict__ part,
-                 int32_t* __restrict__ status, int nbuf) {
+                 int32_t* __restrict__ status, int nbuf, const int* __restrict__ skip) {
+  if (skip && *skip) return;  // a device-decided run stopped before this step
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared SS[2];
   __shared__ __align__(8) uint64_t bars[2];
@@ -1670,8 +1679,9 @@ __global__ void __launch_bounds__(pipe_threads(CW), (MIXED && CW <= 8) ? 3 : 2)
     k_force_pipe(const void* __restrict__ pos, const uint32_t* __restrict__ cs, Geom g, TileArgs ta, LJConst c,
                  const uint2* __restrict__ rows, const uint2* __restrict__ tile_list,
                  const uint16_t* __restrict__ ent, void* __restrict__ fout, double* __restrict__ part,
-                 int32_t* __restrict__ status) {
+                 int32_t* __restrict__ status, const int* __restrict__ skip) {
   static_assert(MIXED != HALF, "pipelined forms: mixed with the full list, FP64 with the half list");
+  if (skip && *skip) return;  // a device-decided run stopped before this step
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared SS[kPipeSlots];
   __shared__ TileInfo s_ti[kPipeSlots];
@@ -2236,12 +2246,13 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
 template <bool MIXED, int LANES, bool HALF, bool ENERGY>
 static int force_w(const void* pos, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c, const uint2* rows,
                    const uint2* tl, const uint16_t* ent, void* f, double* part, int32_t* status, int nbuf, int grid,
-                   size_t sm, cudaStream_t s) {
+                   size_t sm, cudaStream_t s, const int* skip) {
 #define LJ_FW(W, LONG)                                                                                           \
   do {                                                                                                           \
     set_smem(k_force_tile<MIXED, LANES, HALF, ENERGY, W, LONG>, sm);                                             \
     k_force_tile<MIXED, LANES, HALF, ENERGY, W, LONG><<<grid, kTileThreads, sm, s>>>(pos, cs, N, g, ta, c, rows,   \
-                                                                                    tl, ent, f, part, status, nbuf); \
+                                                                                    tl, ent, f, part, status, nbuf,  \
+                                                                                    skip);                          \
   } while (0)
   if constexpr (MIXED != HALF) {  // the pipelined forms: mixed + full list, FP64 + half list
     if (!ta.whole && nbuf == 2) {  // producer warps + consumer warps over two buffers
@@ -2252,7 +2263,8 @@ static int force_w(const void* pos, const uint32_t* cs, int64_t N, Geom g, TileA
                          resident_per_sm(k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW>, pipe_threads(CW), sm); \
     grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, ta.ntiles), (int64_t)kMaxRedBlocks)); \
     k_force_pipe<MIXED, HALF, LANES, ENERGY, LONG, CW><<<grid, pipe_threads(CW), sm, s>>>(pos, cs, g, ta, c, rows, \
-                                                                                       tl, ent, f, part, status);     \
+                                                                                       tl, ent, f, part, status,      \
+                                                                                       skip);                         \
   } while (0)
       const bool lg = ta.list_cap < ta.max_list;
       if (ta.T <= 4) {
@@ -2276,40 +2288,40 @@ static int force_w(const void* pos, const uint32_t* cs, int64_t N, Geom g, TileA
 template <bool MIXED, int LANES>
 static int force_l(int half, int energy, const void* pos, const uint32_t* cs, int64_t N, Geom g, TileArgs ta,
                    LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f, double* part,
-                   int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
+                   int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s, const int* skip) {
   if (half) {
-    if (energy) return force_w<MIXED, LANES, true, true>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    return force_w<MIXED, LANES, true, false>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    if (energy) return force_w<MIXED, LANES, true, true>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
+    return force_w<MIXED, LANES, true, false>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
   }
-  if (energy) return force_w<MIXED, LANES, false, true>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-  return force_w<MIXED, LANES, false, false>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+  if (energy) return force_w<MIXED, LANES, false, true>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
+  return force_w<MIXED, LANES, false, false>(pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
 }
 
 template <bool MIXED>
 static int force_p(int lanes, int half, int energy, const void* pos, const uint32_t* cs, int64_t N, Geom g,
                    TileArgs ta, LJConst c, const uint2* rows, const uint2* tl, const uint16_t* ent, void* f,
-                   double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s) {
+                   double* part, int32_t* status, int nbuf, int grid, size_t sm, cudaStream_t s, const int* skip) {
   switch (lanes) {
-    case 1: return force_l<MIXED, 1>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    case 2: return force_l<MIXED, 2>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    case 4: return force_l<MIXED, 4>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    case 8: return force_l<MIXED, 8>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    case 16: return force_l<MIXED, 16>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
-    default: return force_l<MIXED, 32>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s);
+    case 1: return force_l<MIXED, 1>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
+    case 2: return force_l<MIXED, 2>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
+    case 4: return force_l<MIXED, 4>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
+    case 8: return force_l<MIXED, 8>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
+    case 16: return force_l<MIXED, 16>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
+    default: return force_l<MIXED, 32>(half, energy, pos, cs, N, g, ta, c, rows, tl, ent, f, part, status, nbuf, grid, sm, s, skip);
   }
 }
 
 int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const uint32_t* cs, int64_t N,
                       Geom g, TileArgs ta, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
-                      void* f, double* part, int32_t* status, int per_sm, int nbuf, cudaStream_t s) {
+                      void* f, double* part, int32_t* status, int per_sm, int nbuf, cudaStream_t s, const int* skip) {
   const size_t sm = force_smem_bytes(ta, precision, nbuf, half);
   if (per_sm <= 0) per_sm = per_sm_for(sm);
   const int grid = tile_grid(ta, per_sm);
   if (precision == LJ_MIXED)
     return force_p<true>(lanes, half, energy, pos, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf, grid,
-                         sm, s);
+                         sm, s, skip);
   return force_p<false>(lanes, half, energy, pos, cs, N, g, ta, c, rows, tile_list, ent, f, part, status, nbuf, grid,
-                        sm, s);
+                        sm, s, skip);
 }
 
 void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,

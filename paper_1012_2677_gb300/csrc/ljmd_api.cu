@@ -72,6 +72,10 @@ struct ljmd_sys {
   int64_t* d_log_count = nullptr;
   int32_t* d_status = nullptr;
   uint32_t* d_dmax = nullptr;
+  StepCtl* d_ctl = nullptr;     // device-decided runs: stop flag, stopping step, last maxima, DUTC buffer
+  StepCtl* h_ctl = nullptr;     // pinned mirror
+  int64_t last_build_step = 0;  // sys->steps at the last list construction
+  int64_t lifetime_est = 16;    // steps the last list lived (sizes the next device-decided run)
   unsigned long long* d_total64 = nullptr;
   unsigned int* d_sizes = nullptr;
   // profiling: event pairs per phase, resolved when the profile is read
@@ -140,7 +144,7 @@ static void free_all(ljmd_sys* s) {
   void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->xq, s->pos64, s->ref, s->id,
                   s->id_alt, s->img, s->img_alt, s->cell_of, s->cell_alt, s->perm, s->cell_count, s->cell_start,
                   s->cell_fill, s->rows, s->tile_list, s->ent, s->scan_tmp, s->part_force, s->part_ke,
-                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_total64, s->d_sizes,
+                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_ctl, s->d_total64, s->d_sizes,
                   s->adj_w, s->adj_hw, s->adj_f, s->part_adj, s->d_adj, s->xref64, s->ldc_list, s->d_ldc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -152,6 +156,7 @@ static void free_all(ljmd_sys* s) {
   if (s->h_u32) cudaFreeHost(s->h_u32);
   if (s->h_f64) cudaFreeHost(s->h_f64);
   if (s->h_i32) cudaFreeHost(s->h_i32);
+  if (s->h_ctl) cudaFreeHost(s->h_ctl);
 }
 
 enum { PH_FORCE = 0, PH_INTEGRATE = 1, PH_REBUILD = 2, PH_ENERGY = 3, PH_ADJOINT = 4 };
@@ -398,6 +403,8 @@ static int ensure_cells(ljmd_sys* s) {
 }
 
 static void reset_counters(ljmd_sys* s) {
+  s->last_build_step = 0;
+  s->lifetime_est = 16;
   s->ldc_checks = 0;
   s->ldc_kept = 0;
   s->have_list = false;
@@ -439,24 +446,44 @@ static int ensure_tile_list(ljmd_sys* s) {
 // Tile buffers per force CTA: the requested number, else two for the forms with a pipelined
 // kernel (producer warps stage the next tile while consumer warps compute): the mixed form with
 // the full list and the FP64 form with the half list; one otherwise.
+// Multiprocessors of a device (152 if the attribute cannot be read).
+static int sm_count_of(int dev) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  return sms;
+}
+
 static int force_buffers(const ljmd_sys* s) {
   if (s->force_nbuf) return s->force_nbuf;
+  // fewer tiles than two per SM: the single-buffer kernel (the pipelined one holds one CTA per SM
+  // with two producer warps; 4,000 particles, FP64 form: 40 against 44 us per force launch)
+  if (s->ta.ntiles > 0 && s->ta.ntiles < 2 * (int64_t)sm_count_of(s->device)) return 1;
   return ((s->precision == LJ_MIXED) != s->list_half) ? 2 : 1;
 }
 
 // Default cells per tile along z.  The mixed form with the full list (the pipelined force kernel):
-// about 140 key particles per tile, so that the staging of the 9 (T + 2) neighbour cells and the
+// about 165 key particles per tile, so that the staging of the 9 (T + 2) neighbour cells and the
 // per-tile bookkeeping are spread over many keys; measured on GB300 at 16.4M particles, rho 0.5
-// (13.8 particles per cell), T = 4, 8, 10, 12 give force launches of 2.41, 2.10, 1.96, 1.88 ms and
-// list constructions of 12.6, 14.7, 13.9, 15.5 ms, and T = 10 the shortest step.  The half-list
+// (13.8 particles per cell), T = 4, 8, 10, 12 give force launches of 2.41, 2.09, 1.96, 1.88 ms and
+// list constructions of 11.7, 14.0, 13.2, 13.2 ms, and T = 12 the shortest step.  The half-list
 // forms keep 4 cells: at rho 0.8 (mixed, half list) T = 3, 4, 6 give force 3.76, 3.56, 4.06 ms and
 // construction 19.0, 19.8, 33.7 ms; the FP64 form at rho 0.5 gives force 45.5 ms at T = 4 and
 // 49.4 ms at T = 10 with 2 lanes.
+// Small boxes: the tile length is lowered until there are at least two tiles per SM, so that the
+// force launch spreads over the GPU (4,000 particles, 6 cells per side, FP64 form: T = 4, 2, 1 give
+// 72, 108, 216 tiles and force launches of 69, 40, 39 us).
 static int default_tile_cells(const ljmd_sys* s) {
-  if (s->precision != LJ_MIXED || s->list_half) return 4;
-  const double ppc = (double)s->n / (double)std::max<int64_t>(s->ncells, 1);
-  const int T = (int)lround(140.0 / std::max(ppc, 1.0));
-  return std::max(1, std::min(T, 12));
+  int T = 4;
+  if (s->precision == LJ_MIXED && !s->list_half) {
+    const double ppc = (double)s->n / (double)std::max<int64_t>(s->ncells, 1);
+    T = std::max(1, std::min((int)lround(165.0 / std::max(ppc, 1.0)), 12));
+  }
+  const int64_t n = s->g.n, want = 2 * (int64_t)sm_count_of(s->device);
+  while (T > 1 && n * n * ((n + T - 1) / T) < want) --T;
+  return T;
 }
 
 // Default threads per key in the force kernel: for the mixed form with the full list, 2 for tiles
@@ -464,8 +491,8 @@ static int default_tile_cells(const ljmd_sys* s) {
 // T = 10 with 2 lanes 1.96 ms, 4 lanes 2.01 ms; T = 4 with 2 lanes 2.41 ms, 4 lanes 2.41 ms,
 // 8 lanes 2.67 ms); 4 for the half-list forms.
 static int default_lanes(const ljmd_sys* s) {
-  if (s->precision != LJ_MIXED || s->list_half) return 4;
   const double ppc = (double)s->n / (double)std::max<int64_t>(s->ncells, 1);
+  if (s->precision != LJ_MIXED || s->list_half) return (double)s->ta.T * ppc <= 32.0 ? 8 : 4;
   return (double)s->ta.T * ppc >= 96.0 ? 2 : 4;
 }
 
@@ -607,7 +634,21 @@ static int rebuild(ljmd_sys* s) {
                                        adjoint_smem_bytes(tz, s->precision));
     const int nbuf = s->ta.whole ? 1 : force_buffers(s);
     if (base_bytes <= (size_t)smem_max) {
-      const int64_t room = ((int64_t)smem_max - (int64_t)base_bytes) / (2 * nbuf) - 16;
+      int64_t room = ((int64_t)smem_max - (int64_t)base_bytes) / (2 * nbuf) - 16;
+      // The pipelined kernel of the mixed form with the full list runs 3 CTAs per SM with 8
+      // consumer warps (T <= 4) and 2 with 12: the staged segments are capped so that this many
+      // fit in an SM's shared memory (1 KB reserved and at most 6 KB of static shared memory per
+      // CTA), when that still stages at least three quarters of the largest segment.  Longer
+      // segments are read from HBM.
+      if (s->precision == LJ_MIXED && !s->list_half && !s->ta.whole && nbuf == 2) {
+        int smem_sm = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const int target = s->ta.T <= 4 ? 3 : 2;
+        const int64_t per_cta = (int64_t)smem_sm / target - 1024 - 6144;
+        const int64_t fb = (int64_t)force_smem_bytes(tz, s->precision, 2, 0);
+        const int64_t room_occ = (per_cta - fb) / (2 * nbuf) - 16;
+        if (room_occ >= (int64_t)s->ta.max_list * 3 / 4) room = std::min(room, room_occ);
+      }
       s->ta.list_cap = (int32_t)std::max<int64_t>(0, std::min<int64_t>(s->ta.max_list, room) & ~(int64_t)7);
       break;
     }
@@ -616,6 +657,8 @@ static int rebuild(ljmd_sys* s) {
   }
   s->list_entries = total;
   s->have_list = true;
+  if (s->rebuilds > 0 && s->steps > s->last_build_step) s->lifetime_est = s->steps - s->last_build_step;
+  s->last_build_step = s->steps;
   s->rebuilds += 1;
   s->dutc_buffer = s->prm.margin;
   if (s->valid_mode == LJ_VALID_DUTC_LDC || s->valid_mode == LJ_VALID_HALF_MARGIN_LDC) {
@@ -632,25 +675,27 @@ static int rebuild(ljmd_sys* s) {
 
 static void* force_pos(ljmd_sys* s) { return s->precision == LJ_MIXED ? (void*)s->xq : (void*)s->pos64; }
 
-static int integrate(ljmd_sys* s, IntegrateArgs a) {
+static int integrate(ljmd_sys* s, IntegrateArgs a, const int* skip = nullptr) {
   PhaseTimer timer(s, PH_INTEGRATE);
   s->launches += 1;
   a.qk = s->g.qk;
   return launch_integrate(s->precision, s->x, s->v, s->f, force_pos(s), s->ref, s->n, a, s->part_ke, s->d_dmax,
-                          s->d_status, s->st);
+                          s->d_status, s->st, skip);
 }
 
-static void energy_record(ljmd_sys* s, int nb_ke, bool to_log) {
+// Energy record of state `step` (default: the current one); skipped on the device if *skip is set.
+static void energy_record(ljmd_sys* s, int nb_ke, bool to_log, int64_t step = -1, const int* skip = nullptr) {
   PhaseTimer timer(s, PH_ENERGY);
   s->launches += 1;
+  if (step < 0) step = s->steps;
   const double scale = s->list_half ? 1.0 : 0.5;
   launch_energy_finalize(s->part_force, s->nb_force, s->part_ke, nb_ke, scale, s->d_energies,
-                         to_log ? s->log_ptr : nullptr, to_log ? s->log_cap : 0, s->d_log_count, (double)s->steps,
-                         s->st);
-  s->energy_step = s->steps;
+                         to_log ? s->log_ptr : nullptr, to_log ? s->log_cap : 0, s->d_log_count, (double)step, s->st,
+                         skip);
+  s->energy_step = step;
 }
 
-static int run_force(ljmd_sys* s, bool energy) {
+static int run_force(ljmd_sys* s, bool energy, const int* skip = nullptr) {
   ljmd_sys* sys = s;
   const int half = s->list_half ? 1 : 0;
   if (half) CK(cudaMemsetAsync(s->f, 0, (s->precision == LJ_MIXED ? 16 : 32) * (size_t)s->n, s->st));
@@ -661,7 +706,7 @@ static int run_force(ljmd_sys* s, bool energy) {
     PhaseTimer timer(s, PH_FORCE);
     s->nb_force = launch_force_tile(s->precision, half, lanes, energy ? 1 : 0, force_pos(s), s->cell_start, s->n, s->g,
                                     s->ta, s->c, s->rows, s->tile_list, s->ent, s->f, s->part_force, s->d_status,
-                                    per_sm, force_buffers(s), s->st);
+                                    per_sm, force_buffers(s), s->st, skip);
   }
   s->launches += 1;
   CKL();
@@ -762,6 +807,87 @@ static int finalize_energies_now(ljmd_sys* s) {
   return LJ_OK;
 }
 
+// Up to `remaining` velocity-Verlet steps with the list-validity rule decided on the device: each
+// step is the kick-drift (with the first half-kick fused into the previous step's second, except
+// for the first step of the call), the energy record when due, the validity check (k_step_check)
+// and the force; all of them are enqueued at once and the host synchronises once at the end.  When
+// the check of a step finds the list expired it sets the stop flag, which every later launch of
+// the run reads first and returns on; that step's drift has happened but not its force.  The run
+// is sized from the lifetime of the last list, so that few launches are skipped.  *advanced: the
+// steps whose drift happened; *stopped: the last of them expired the list.
+static int device_run(ljmd_sys* s, double dt, bool first_of_call, int64_t remaining, int64_t* advanced,
+                      bool* stopped) {
+  ljmd_sys* sys = s;
+  cudaStream_t st = s->st;
+  const int ee = s->prm.energy_every;
+  auto want_energy = [&](int64_t t) { return ee > 0 && (t % ee) == 0; };
+  const double h = 0.5 * dt;
+  const int dutc = s->valid_mode == LJ_VALID_DUTC;
+  const int64_t age = s->steps - s->last_build_step;
+  const int64_t K = std::max<int64_t>(1, std::min<int64_t>({remaining, std::max<int64_t>(4, s->lifetime_est - age + 2),
+                                                           256}));
+  StepCtl* hc = s->h_ctl;
+  hc->stop = 0;
+  hc->stop_at = -1;
+  hc->last[0] = hc->last[1] = 0.0f;
+  hc->dutc = s->dutc_buffer;
+  CK(cudaMemcpyAsync(s->d_ctl, hc, sizeof(StepCtl), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(s->d_dmax, 0, 8, st));
+  const int* skip = &s->d_ctl->stop;
+  const size_t ev0 = s->ev_pending.size();
+  const int64_t energy_step0 = s->energy_step;
+  std::vector<size_t> ev_force(K);     // profiling entries before each step's force launch
+  std::vector<int64_t> ln_force(K);    // launch count before each step's force launch
+  std::vector<char> recorded(K, 0);
+  for (int64_t k = 0; k < K; ++k) {
+    const int64_t t = s->steps + k;  // state index before the step
+    const bool rec = (k == 0 ? s->pe_step == s->steps : true) && want_energy(t);
+    IntegrateArgs a{(first_of_call && k == 0) ? 0.0 : h, h, dt, rec ? 1 : 0, 1, dutc};
+    const int nb = integrate(s, a, skip);
+    if (rec) {
+      energy_record(s, nb, true, t, skip);
+      recorded[k] = 1;
+    }
+    launch_step_check(s->d_dmax, s->d_ctl, (int)k, s->disp_limit, dutc, 2.0 * fabs(dt), st);
+    s->launches += 1;
+    ev_force[k] = s->ev_pending.size();
+    ln_force[k] = s->launches;
+    TRY(run_force(s, want_energy(t + 1), skip));
+  }
+  CKL();
+  CK(cudaMemcpyAsync(hc, s->d_ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *stopped = hc->stop != 0;
+  const int64_t done = *stopped ? (int64_t)hc->stop_at + 1 : K;
+  // skipped launches of the run leave the counters and the profile; the stopping step's force too
+  if (*stopped && s->profiling && ev_force[done - 1] >= ev0 && ev_force[done - 1] <= s->ev_pending.size()) {
+    for (size_t q = ev_force[done - 1]; q < s->ev_pending.size(); ++q) {
+      s->ev_pool.push_back(s->ev_pending[q].second.first);
+      s->ev_pool.push_back(s->ev_pending[q].second.second);
+    }
+    s->ev_pending.resize(ev_force[done - 1]);
+  }
+  if (*stopped) s->launches = ln_force[done - 1];  // launches that ran: up to the stopping step's check
+  s->energy_step = energy_step0;
+  for (int64_t k = 0; k < done; ++k)
+    if (recorded[k]) s->energy_step = s->steps + k;
+  s->steps += done;
+  *advanced = done;
+  s->last_dmax = sqrt((double)hc->last[0]);
+  s->last_vmax = sqrt((double)hc->last[1]);
+  s->dutc_buffer = hc->dutc;
+  if (*stopped) {
+    s->forces_current = false;
+    s->pe_step = -1;
+  } else {
+    s->forces_current = true;
+    s->pe_step = want_energy(s->steps) ? s->steps : -1;
+  }
+  return LJ_OK;
+}
+
+static int step_steps(ljmd_sys* sys, double dt, int64_t nsteps);
+
 // ----------------------------------------------------------------------------------------------
 extern "C" {
 
@@ -803,6 +929,8 @@ int ljmd_create(ljmd_sys** out, const ljmd_params* p, int32_t precision, void* c
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_log_count, 1);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_status, 1);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_dmax, 2);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_ctl, 1);
+  if (r == LJ_OK && cudaMallocHost(&sys->h_ctl, sizeof(StepCtl)) != cudaSuccess) r = LJ_ENOMEM;
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_total64, 2);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_sizes, 4);
   if (r == LJ_OK && cudaMallocHost(&sys->h_u32, 64) != cudaSuccess) r = LJ_ENOMEM;
@@ -973,12 +1101,34 @@ int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
   if (sys->broken) return LJ_EDEVICE;
   if (sys->n <= 0) return LJ_ESTATE;
   if (nsteps == 0) return LJ_OK;
+  TRY(step_steps(sys, dt, nsteps));
+  return check_status(sys);
+}
+
+}  // extern "C"
+
+// The steps of ljmd_step without its final read of the device status word.
+static int step_steps(ljmd_sys* sys, double dt, int64_t nsteps) {
   const int ee = sys->prm.energy_every;
   auto want_energy = [&](int64_t t) { return ee > 0 && (t % ee) == 0; };
   TRY(ensure_forces(sys, want_energy(sys->steps)));
   const double h = 0.5 * dt;
   cudaStream_t st = sys->st;
-  for (int64_t s = 0; s < nsteps; ++s) {
+  // The margin/2 and DUTC rules are decided on the device (device_run); the rules with the large
+  // displacement check need the host between steps.
+  const bool on_device = sys->valid_mode == LJ_VALID_HALF_MARGIN || sys->valid_mode == LJ_VALID_DUTC;
+  for (int64_t s = 0; s < nsteps;) {
+    if (on_device) {
+      int64_t advanced = 0;
+      bool stopped = false;
+      TRY(device_run(sys, dt, s == 0, nsteps - s, &advanced, &stopped));
+      s += advanced;
+      if (stopped) {  // the drift of the last step expired the list: rebuild, then its force
+        TRY(rebuild(sys));
+        TRY(run_force(sys, want_energy(sys->steps)));
+      }
+      continue;
+    }
     const bool rec = sys->pe_step == sys->steps && want_energy(sys->steps);
     const int dutc = sys->valid_mode == LJ_VALID_DUTC || sys->valid_mode == LJ_VALID_DUTC_LDC;
     IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, rec ? 1 : 0, 1, dutc};
@@ -996,6 +1146,7 @@ int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
     TRY(list_expired(sys, dt, &expired));
     if (expired) TRY(rebuild(sys));
     TRY(run_force(sys, want_energy(sys->steps)));
+    s += 1;
   }
   // final half-kick: v at the full step of the last state
   const bool rec = sys->pe_step == sys->steps && want_energy(sys->steps);
@@ -1006,8 +1157,10 @@ int ljmd_step(ljmd_sys* sys, double dt, int64_t nsteps) {
     energy_record(sys, nb, true);
     CKL();
   }
-  return check_status(sys);
+  return LJ_OK;
 }
+
+extern "C" {
 
 int ljmd_energies(ljmd_sys* sys, double* pe, double* ke, double* virial) {
   if (!sys) return LJ_EINVAL;
@@ -1263,8 +1416,9 @@ static int ensure_adjoint(ljmd_sys* s) {
 
 // One adjoint pass at the current positions with the vector w (device, id order; null = 0):
 // hw = H w and f = F (device, id order; either may be null), q = [w.F, w.dF/dsigma, PE,
-// dPE/dsigma, PE] (host; w.dF/deps = w.F / eps, dPE/deps = PE / eps).  Synchronises.
-static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* f_id, double q[5]) {
+// dPE/dsigma, PE] (w.dF/deps = w.F / eps, dPE/deps = PE / eps).  With q non-null the sums are read
+// to the host (synchronises); with q null they stay in the device scalars s->d_adj[0..4].
+static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* f_id, double* q) {
   ljmd_sys* sys = s;
   if (!s->have_list) TRY(rebuild(s));
   TRY(ensure_adjoint(s));
@@ -1289,6 +1443,7 @@ static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* 
     s->launches += 1;
   }
   CKL();
+  if (!q) return LJ_OK;
   CK(cudaMemcpyAsync(s->h_f64, s->d_adj, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   for (int k = 0; k < 5; ++k) q[k] = s->h_f64[k];
@@ -1310,6 +1465,30 @@ struct DevBuf {  // device scratch owned by one call
     return LJ_OK;
   }
 };
+
+// Store positions given unwrapped in id order (device) without re-sorting the particles: the
+// current order and image counts are kept, the force kernels' copies are rewritten, and the list
+// stays if no particle moved more than margin/2 from where it was built (else it is rebuilt).
+// Velocities are left as they are.  Synchronises once (the displacement maximum).
+static int load_keeping_list(ljmd_sys* s, const double* u) {
+  ljmd_sys* sys = s;
+  if (!s->have_list) {  // nothing to keep: the general path
+    return ljmd_set_state(s, s->n, s->L, u, nullptr, 1);
+  }
+  launch_load_unwrapped(u, s->img, s->id, s->n, s->g.offset, s->L, s->x, s->st);
+  s->launches += 1;
+  CKL();
+  CK(cudaMemsetAsync(s->d_dmax, 0, 8, s->st));
+  IntegrateArgs a{0.0, 0.0, 0.0, 0, 1};  // no kick, no drift: copies and displacement only
+  integrate(s, a);
+  CKL();
+  TRY(read_dmax(s, &s->last_dmax));
+  s->forces_current = false;
+  s->pe_step = -1;
+  s->energy_step = -1;
+  if (s->last_dmax > s->disp_limit) TRY(rebuild(s));
+  return LJ_OK;
+}
 
 extern "C" {
 
@@ -1358,7 +1537,9 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
   const size_t bytes = sizeof(double) * n3;
   const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
   cudaStream_t st = sys->st;
-  DevBuf<double> ck_x, ck_v, seg_x, x0u, xNu, lx, lv, b, f, part;
+  DevBuf<double> ck_x, ck_v, seg_x, x0u, xNu, lx, lv, b, f, part, elog;
+  DevBuf<int64_t> ecount;
+  const int64_t elog_cap = nsteps + 2 * nseg + 4;
   TRY(ck_x.alloc(n3 * (size_t)nseg));
   TRY(ck_v.alloc(n3 * (size_t)nseg));
   TRY(seg_x.alloc(n3 * (size_t)ckpt_every));
@@ -1369,6 +1550,8 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
   TRY(b.alloc(n3));
   TRY(f.alloc(n3));
   TRY(part.alloc(kMaxRedBlocks + 8));
+  TRY(elog.alloc(4 * (size_t)elog_cap));
+  TRY(ecount.alloc(1));
   // the initial state on the device
   if (on_device) {
     CK(cudaMemcpyAsync(x0u.p, x0, bytes, cudaMemcpyDeviceToDevice, st));
@@ -1386,25 +1569,68 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
     return LJ_OK;
   };
   const double h = 0.5 * dt, wpe = n_pe > 0 ? 1.0 / ((double)n_pe * (double)n) : 0.0;
+  // the caller's energy settings are replaced while this call runs: every state's PE goes to an
+  // internal log (one device-decided run per checkpoint segment, no host round trip per step)
   const int saved_ee = sys->prm.energy_every;
-  sys->prm.energy_every = 0;
-  // ---- forward: checkpoints every ckpt_every steps, PE over the last n_pe states
+  double* const saved_log = sys->log_ptr;
+  const int64_t saved_cap = sys->log_cap;
+  int64_t* const saved_count = sys->d_log_count;
+  auto restore = [&]() {
+    sys->prm.energy_every = saved_ee;
+    sys->log_ptr = saved_log;
+    sys->log_cap = saved_cap;
+    sys->d_log_count = saved_count;
+  };
+  auto run_or_restore = [&](int r) {
+    if (r != LJ_OK) restore();
+    return r;
+  };
+  // ---- forward: checkpoints every ckpt_every steps, PE of the last n_pe states from the log
   TRY(ljmd_set_state(sys, n, box, ck_x.p, ck_v.p, 1));
-  double acc_pe = 0.0;
-  for (int64_t t = 1; t <= nsteps; ++t) {
-    int r = ljmd_step(sys, dt, 1);
-    if (r != LJ_OK) {
-      sys->prm.energy_every = saved_ee;
-      return r;
-    }
-    if (t > nsteps - n_pe) {
-      double pe = 0.0;
-      TRY(ljmd_energies(sys, &pe, nullptr, nullptr));
-      acc_pe += pe;
-    }
-    if (t % ckpt_every == 0 && t < nsteps) TRY(capture(ck_x.p + n3 * (size_t)(t / ckpt_every), ck_v.p + n3 * (size_t)(t / ckpt_every)));
+  sys->prm.energy_every = n_pe > 0 ? 1 : 0;
+  sys->log_ptr = elog.p;
+  sys->log_cap = elog_cap;
+  sys->d_log_count = ecount.p;
+  if (cudaMemsetAsync(ecount.p, 0, sizeof(int64_t), st) != cudaSuccess) {
+    restore();
+    sys->broken = true;
+    return LJ_EDEVICE;
   }
-  sys->prm.energy_every = saved_ee;
+  for (int64_t seg = 0; seg < nseg; ++seg) {
+    const int64_t t0 = seg * ckpt_every, t1 = std::min<int64_t>(t0 + ckpt_every, nsteps);
+    TRY(run_or_restore(step_steps(sys, dt, t1 - t0)));
+    if (t1 < nsteps) TRY(run_or_restore(capture(ck_x.p + n3 * (size_t)(seg + 1), ck_v.p + n3 * (size_t)(seg + 1))));
+  }
+  int64_t nrec = 0;
+  std::vector<double> recs;
+  {
+    cudaError_t e = cudaMemcpyAsync(&nrec, ecount.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    nrec = std::min<int64_t>(nrec, elog_cap);
+    recs.resize(4 * (size_t)std::max<int64_t>(nrec, 1));
+    if (e == cudaSuccess && nrec > 0)
+      e = cudaMemcpyAsync(recs.data(), elog.p, sizeof(double) * 4 * nrec, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    restore();
+    if (e != cudaSuccess) {
+      sys->broken = true;
+      return LJ_EDEVICE;
+    }
+  }
+  // PE of the states nsteps - n_pe + 1 .. nsteps (a state is recorded twice at a segment boundary)
+  double acc_pe = 0.0;
+  if (n_pe > 0) {
+    std::vector<char> seen((size_t)nsteps + 1, 0);
+    for (int64_t k = 0; k < nrec; ++k) {
+      const int64_t t = (int64_t)recs[4 * k];
+      if (t > nsteps - n_pe && t <= nsteps && !seen[(size_t)t]) {
+        seen[(size_t)t] = 1;
+        acc_pe += recs[4 * k + 1];
+      }
+    }
+    for (int64_t t = nsteps - n_pe + 1; t <= nsteps; ++t)
+      if (!seen[(size_t)t]) return LJ_EDEVICE;  // a state's energy record is missing
+  }
   TRY(capture(xNu.p, nullptr));
   const int nb = launch_sqdiff(xNu.p, x0u.p, (int64_t)n3, part.p, st);
   launch_final_reduce(part.p, nb, 1, part.p + kMaxRedBlocks, st);
@@ -1415,17 +1641,19 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
   *loss = acc_pe * wpe + msd;
   if (!gx0 && !gv0 && !gtheta) return check_status(sys);
 
-  // ---- reverse: lx = dloss/dx_n, lv = 0; then state by state back to t = 0
-  double gth[2] = {0.0, 0.0};
+  // ---- reverse: lx = dloss/dx_n, lv = 0; then state by state back to t = 0.  The parameter
+  // gradient is summed on the device (one read at the end).
   const double eps = sys->prm.eps;
-  double q[5];
+  DevBuf<double> gthd;
+  TRY(gthd.alloc(2));
+  CK(cudaMemsetAsync(gthd.p, 0, 2 * sizeof(double), st));
   launch_scaled_diff(lx.p, 2.0 / (double)n, xNu.p, x0u.p, (int64_t)n3, st);
   CK(cudaMemsetAsync(lv.p, 0, bytes, st));
   if (n_pe > 0) {
-    TRY(adjoint_pass(sys, nullptr, nullptr, f.p, q));  // at x_n: F and dPE
+    TRY(adjoint_pass(sys, nullptr, nullptr, f.p, nullptr));  // at x_n: F and dPE
     launch_axpy(lx.p, -wpe, f.p, (int64_t)n3, st);
-    gth[0] += wpe * q[4] / eps;
-    gth[1] += wpe * q[3];
+    launch_accum_q(sys->d_adj, 0.0, 0.0, wpe, wpe / eps, gthd.p, st);
+    sys->launches += 2;
   }
   for (int64_t seg = nseg - 1; seg >= 0; --seg) {
     const int64_t t0 = seg * ckpt_every, t1 = std::min<int64_t>(t0 + ckpt_every, nsteps);
@@ -1434,42 +1662,36 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
     CK(cudaMemcpyAsync(seg_x.p, ck_x.p + n3 * (size_t)seg, bytes, cudaMemcpyDeviceToDevice, st));
     sys->prm.energy_every = 0;
     for (int64_t t = t0 + 1; t < t1; ++t) {
-      int r = ljmd_step(sys, dt, 1);
-      if (r != LJ_OK) {
-        sys->prm.energy_every = saved_ee;
-        return r;
-      }
-      TRY(capture(seg_x.p + n3 * (size_t)(t - t0), nullptr));
+      TRY(run_or_restore(step_steps(sys, dt, 1)));
+      TRY(run_or_restore(capture(seg_x.p + n3 * (size_t)(t - t0), nullptr)));
     }
     sys->prm.energy_every = saved_ee;
     for (int64_t t = t1 - 1; t >= t0; --t) {
       launch_axpy(lv.p, dt, lx.p, (int64_t)n3, st);  // x_{t+1} = x_t + dt v'
-      TRY(ljmd_set_state(sys, n, box, seg_x.p + n3 * (size_t)(t - t0), nullptr, 1));
-      TRY(adjoint_pass(sys, lv.p, b.p, f.p, q));
+      // state t in the particle order of the recomputation: its list is kept while it is valid
+      TRY(load_keeping_list(sys, seg_x.p + n3 * (size_t)(t - t0)));
+      TRY(adjoint_pass(sys, lv.p, b.p, f.p, nullptr));
       const double c = t == 0 ? h : dt;  // both half-kicks touching state t (one at t = 0)
+      const bool in_pe = t > nsteps - n_pe;
       launch_axpy(lx.p, -c, b.p, (int64_t)n3, st);
-      gth[0] += c * q[0] / eps;
-      gth[1] += c * q[1];
-      if (t > nsteps - n_pe) {
-        launch_axpy(lx.p, -wpe, f.p, (int64_t)n3, st);
-        gth[0] += wpe * q[4] / eps;
-        gth[1] += wpe * q[3];
-      }
+      launch_accum_q(sys->d_adj, c / eps, c, in_pe ? wpe : 0.0, in_pe ? wpe / eps : 0.0, gthd.p, st);
+      if (in_pe) launch_axpy(lx.p, -wpe, f.p, (int64_t)n3, st);
       if (t == 0) {
         // MSD term at t = 0: -2 (x_n - x_0) / N
         launch_scaled_diff(b.p, -2.0 / (double)n, xNu.p, x0u.p, (int64_t)n3, st);
         launch_axpy(lx.p, 1.0, b.p, (int64_t)n3, st);
       }
-      sys->launches += 3;
+      sys->launches += 3 + (in_pe ? 1 : 0) + (t == 0 ? 2 : 0);
       CKL();
     }
   }
   if (gx0) CK(cudaMemcpyAsync(gx0, lx.p, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   if (gv0) CK(cudaMemcpyAsync(gv0, lv.p, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(sys->h_f64, gthd.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (gtheta) {
-    gtheta[0] = gth[0];
-    gtheta[1] = gth[1];
+    gtheta[0] = sys->h_f64[0];
+    gtheta[1] = sys->h_f64[1];
   }
   return check_status(sys);
 }

@@ -65,9 +65,10 @@ struct ListBand {
 
 // ---- reductions / status -------------------------------------------------------
 void launch_final_reduce(const double* partials, int nblocks, int nq, double* out, cudaStream_t s);
+// skip (optional): a device flag; set, the launch does nothing (a device-decided run stopped).
 void launch_energy_finalize(const double* pe_vir_part, int nb_force, const double* ke_part, int nb_int,
                             double pe_scale, double* energies, double* log, int64_t log_cap, int64_t* log_count,
-                            double step, cudaStream_t s);
+                            double step, cudaStream_t s, const int* skip = nullptr);
 
 // ---- init ---------------------------------------------------------------------------
 void launch_fcc(double* x, int64_t M, double a, double offset, cudaStream_t s);
@@ -157,7 +158,8 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
 // (energy partials written to part[2 b], part[2 b + 1]).
 int launch_force_tile(int precision, int half, int lanes, int energy, const void* pos, const uint32_t* cs, int64_t N,
                       Geom g, TileArgs ta, LJConst c, const uint2* rows, const uint2* tile_list, const uint16_t* ent,
-                      void* f, double* part, int32_t* status, int per_sm, int nbuf, cudaStream_t s);
+                      void* f, double* part, int32_t* status, int per_sm, int nbuf, cudaStream_t s,
+                      const int* skip = nullptr);
 size_t adjoint_smem_bytes(const TileArgs& ta, int precision);
 // Adjoint pass (HVP, forces, parameter derivatives) over the list; w, hw, fo are dvec4 [N] in sorted
 // order (fo may be null).  Writes 5 partials per block [w.dF/deps, w.dF/dsigma, dPE/deps,
@@ -183,7 +185,22 @@ struct IntegrateArgs {
 // largest squared drift speed.
 // pos: the fixed-point records (mixed) or the dvec4 copies (FP64), rewritten when a.shadow is set.
 int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, const void* ref, int64_t N,
-                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, cudaStream_t s);
+                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, cudaStream_t s,
+                     const int* skip = nullptr);
+// Device-side list-validity decision after the drift of step s of a device-decided run (one thread):
+// unless ctl->stop is already set, reads the maxima of the step (squared displacement since the
+// build and squared drift speed, float bits in dmax_bits[0], [1]), keeps them in ctl->last, clears
+// dmax_bits for the next step and, if the list expired (margin/2 rule: the displacement above
+// disp_limit; DUTC: the buffer, reduced by 2 v_max |dt|, at or below zero), sets ctl->stop and
+// ctl->stop_at = s.  Every later kernel of the run is launched with &ctl->stop as its skip flag.
+struct StepCtl {
+  int stop;         // set: the run stopped (the list must be rebuilt before the next force)
+  int stop_at;      // the step of the run whose drift expired the list
+  float last[2];    // squared largest displacement and drift speed of the last checked step
+  double dutc;      // DUTC buffer length
+};
+void launch_step_check(uint32_t* dmax_bits, StepCtl* ctl, int s, double disp_limit, int dutc, double two_dt,
+                       cudaStream_t st);
 
 // ---- pair export through a static device scratch array (no allocation) ----------------
 // Address of this device's scratch (resolved once per device): the kept-pair counter word and
@@ -198,7 +215,12 @@ int launch_bitonic_sort(unsigned long long* keys, uint32_t P, cudaStream_t s);
 void launch_to_sorted(const double* w_id, const int32_t* id, int64_t N, dvec4* out, cudaStream_t s);
 void launch_unwrapped(const double* x, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
                       double* out, cudaStream_t s);
+// x (sorted order, SoA) = offset + u (unwrapped, id order) - img L with the current order and images
+void launch_load_unwrapped(const double* u, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
+                           double* x, cudaStream_t s);
 void launch_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s);
+// gth[0] += a0 q[0] + a4 q[4], gth[1] += a1 q[1] + a3 q[3] (device scalars)
+void launch_accum_q(const double* q, double a0, double a1, double a3, double a4, double* gth, cudaStream_t s);
 void launch_scaled_diff(double* y, double a, const double* u, const double* w, int64_t n, cudaStream_t s);
 int launch_sqdiff(const double* u, const double* w, int64_t n, double* part, cudaStream_t s);
 
