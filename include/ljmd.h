@@ -380,9 +380,11 @@ typedef struct ljmd_batch_stats {
  * Create a batch of `replicas` systems with common potential and list parameters p (cutoff,
  * margin, eps, sigma, truncation; list_form is full; p->lanes 2, 4 or 8 or 0 for the default)
  * and per-replica particle counts n[r] and box sides box[r] (host arrays).  Every box needs
- * L >= 2 (r_s + margin) and at least 3 cells per side (L >= 3 r_s).  The batch works on its own
+ * L >= 2 (r_s + margin); boxes under 3 r_s have 2 cells per side, whose tiles stage aliased
+ * neighbour cells under both periodic images (at most one of which is ever within r_s + margin of
+ * a key, so the lists stay exact).  The batch works on its own
  * stream; every call first waits for the work queued so far on cuda_stream (a cudaStream_t, NULL =
- * legacy default stream).  Errors: LJ_EINVAL, LJ_ERANGE (a box under 3 cells per side, more than
+ * legacy default stream).  Errors: LJ_EINVAL (a box under 2 (r_s + margin)), LJ_ERANGE (more than
  * 2^32 - 1 cells, more than 10^9 particles), LJ_ENOMEM, LJ_EDEVICE.
  */
 int ljmd_batch_create(ljmd_batch** out, const ljmd_params* p, int32_t replicas, const int64_t* n, const double* box,

@@ -190,7 +190,11 @@ static int setup_replicas(ljmd_batch* b) {
     if (!(L >= 2.0 * (rs + p.margin)) || !isfinite(L)) return LJ_EINVAL;
     int64_t n = (int64_t)floor(L / rs);
     if (n > 1024) n = 1024;
-    if (n < 3) return LJ_ERANGE;  // batched replicas need at least 3 cells per side
+    // Two cells per side (L / r_s below 3): the neighbour columns and cells of a tile alias, so the
+    // tile stages a cell twice with different periodic images.  L >= 2 (r_s + margin) keeps at most
+    // one image of a particle within r_s + margin of any key, so each partner is still listed once
+    // (by the image the exact distance test accepts) and the force takes that image.
+    if (n < 2) return LJ_ERANGE;
     ReplicaGeo& rg = b->reps_h[r];
     Geom& g = rg.g;
     g.L = L;

@@ -108,7 +108,45 @@ def test_batch_autotune_keeps_results():
         assert np.sqrt(((fr - F) ** 2).sum(1)).max() / rms <= 1e-5
 
 
-def test_batch_rejects_boxes_under_three_cells():
+def test_batch_rejects_boxes_under_two_search_lengths():
+    """A box under 2 (r_s + margin) could hold two images of one partner within reach of a key."""
     with pytest.raises(ljmd.LjmdError) as e:
-        ljmd.Batch([500, 800], [7.0, 9.5], cutoff=RC, margin=MARGIN)
-    assert e.value.code == ljmd.LJ_ERANGE
+        ljmd.Batch([300, 800], [6.1, 9.5], cutoff=RC, margin=MARGIN)
+    assert e.value.code == ljmd.LJ_EINVAL
+
+
+def test_batch_with_two_cell_replicas():
+    """Replicas under 3 r_s (N = 500 at rho 0.9 is L = 8.22 < 3 x 2.8: 2 cells per side) beside
+    ordinary ones: pairs bit-exact and forces against the oracle, and a 20-step run against single
+    systems (whose two-cell boxes take the whole-box path)."""
+    spec = [(500, 0.9), (480, 0.85), (600, 0.9), (2000, 0.5)]
+    xs, vs, box = [], [], []
+    for r, (N, rho) in enumerate(spec):
+        x, L = synth.fcc_thinned(N, rho, 300 + r)
+        x = np.mod(x + synth.displacements(N, 0.1, 500 + r), L)  # off the lattice: forces well away from zero
+        xs.append(synth.dyadic(x))
+        vs.append(synth.thermal_velocities(N, 1.0, 400 + r))
+        box.append(L)
+    n = np.array([N for N, _ in spec])
+    box = np.array(box)
+    assert box[0] < 3 * (RC + MARGIN) and box[1] < 3 * (RC + MARGIN)
+    x, v = np.concatenate(xs), np.concatenate(vs)
+    with ljmd.Batch(n, box, cutoff=RC, margin=MARGIN) as b:
+        b.set_state(x, v)
+        _, _, gf = b.get_state()
+        pairs = [b.pairs(r) for r in range(len(n))]
+        b.step(0.004, 20, graph_steps=5)
+        bx, _, _ = b.get_state()
+        st = b.stats()
+    assert st["status_word"] == 0
+    for r, (xr, fr, Lr) in enumerate(zip(xs, _split(gf, n), box)):
+        F, _, _ = O.forces(xr, Lr)
+        rms = np.sqrt((F ** 2).sum(1).mean())
+        assert np.sqrt(((fr - F) ** 2).sum(1)).max() / rms <= 1e-5, r
+        assert np.array_equal(pairs[r], O.pairs_within(xr, Lr, RC + MARGIN)), r
+    for r, (xr, vr, Lr) in enumerate(zip(xs, vs, box)):
+        with ljmd.System(cutoff=RC, margin=MARGIN, precision=ljmd.LJ_MIXED) as s:
+            s.set_state(xr, vr, Lr)
+            s.step(0.004, 20)
+            sx, _, _, _ = s.get_state()
+        assert np.abs(_min_image(_split(bx, n)[r] - sx, Lr)).max() < 1e-5, r
