@@ -13,35 +13,44 @@ static int grid_for(int64_t n, int threads) {
 // Fold x_state into [offset, offset + L) (one correction per component, counted in img),
 // label c = (cx n + cy) n + cz with cx = floor((x_state - offset) * n / L) clamped to [0, n-1],
 // and count particles per cell.
+// The lanes of a warp that land in one cell (neighbours in the previous cell order mostly do) add
+// their count with one atomic.
 __global__ void k_wrap_label(double* __restrict__ x, int32_t* __restrict__ img, int64_t N, Geom g,
                              uint32_t* __restrict__ cell_of, uint32_t* __restrict__ count,
                              int32_t* __restrict__ status) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    int c[3];
-    bool bad = false;
-    for (int k = 0; k < 3; ++k) {
-      double xs = x[k * N + i];
-      if (!finite_d(xs)) bad = true;
-      if (xs >= g.offset + g.L) {
-        xs -= g.L;
-        img[k * N + i] += 1;
-      } else if (xs < g.offset) {
-        xs += g.L;
-        img[k * N + i] -= 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < N; i0 += stride) {
+    const int64_t i = i0 + lane;
+    uint32_t cell = 0xffffffffu;  // the warp's tail (no particle) takes part in the match only
+    if (i < N) {
+      int c[3];
+      bool bad = false;
+      for (int k = 0; k < 3; ++k) {
+        double xs = x[k * N + i];
+        if (!finite_d(xs)) bad = true;
+        if (xs >= g.offset + g.L) {
+          xs -= g.L;
+          img[k * N + i] += 1;
+        } else if (xs < g.offset) {
+          xs += g.L;
+          img[k * N + i] -= 1;
+        }
+        x[k * N + i] = xs;
+        const double rel = xs - g.offset;  // exact: both in [offset/2, 2 offset)
+        int ck = (int)floor(rel * g.inv_h);
+        ck = ck < 0 ? 0 : (ck >= g.n ? g.n - 1 : ck);
+        c[k] = ck;
       }
-      x[k * N + i] = xs;
-      const double rel = xs - g.offset;  // exact: both in [offset/2, 2 offset)
-      int ck = (int)floor(rel * g.inv_h);
-      ck = ck < 0 ? 0 : (ck >= g.n ? g.n - 1 : ck);
-      c[k] = ck;
+      if (bad) {
+        atomicOr(status, LJ_ST_NONFINITE);
+        c[0] = c[1] = c[2] = 0;
+      }
+      cell = ((uint32_t)c[0] * (uint32_t)g.n + (uint32_t)c[1]) * (uint32_t)g.n + (uint32_t)c[2];
+      cell_of[i] = cell;
     }
-    if (bad) {
-      atomicOr(status, LJ_ST_NONFINITE);
-      c[0] = c[1] = c[2] = 0;
-    }
-    const uint32_t cell = ((uint32_t)c[0] * (uint32_t)g.n + (uint32_t)c[1]) * (uint32_t)g.n + (uint32_t)c[2];
-    cell_of[i] = cell;
-    atomicAdd(&count[cell], 1u);
+    const unsigned peers = __match_any_sync(0xffffffffu, cell);
+    if (i < N && lane == __ffs(peers) - 1) atomicAdd(&count[cell], (uint32_t)__popc(peers));
   }
 }
 
@@ -135,13 +144,21 @@ int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
 // ---------------------------------------------------------------------------------------------
 // Scatter (Fig. 3 (ii)-(iii)): place each particle at its cell's pointer and advance it.
 // The arrival order inside a cell is made deterministic afterwards by k_cell_order.
+// The lanes of a warp bound for one cell reserve their slots with one atomic.
 __global__ void k_scatter(const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ start,
                           uint32_t* __restrict__ fill, uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
   if (pred && !*pred) return;  // predicated: skipped unless the flag is set
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t c = cell_of[i];
-    const uint32_t slot = atomicAdd(&fill[c], 1u);
-    perm[start[c] + slot] = (uint32_t)i;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < N; i0 += stride) {
+    const int64_t i = i0 + lane;
+    const uint32_t c = i < N ? cell_of[i] : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader && i < N) base = atomicAdd(&fill[c], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (i < N) perm[start[c] + base + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
   }
 }
 

@@ -21,12 +21,16 @@
 // it can be bulk-copied.  If the box has fewer than 3 cells per side the whole box is one tile
 // (all particles staged directly, no shifts, image chosen per pair).
 //
-// List construction: a warp per key particle tests its 27 neighbour cells from shared memory
-// in chunks of 32 (FP32 hi differences, which are exact, so r^2 is within a bounded error of
-// the FP64 value; inside that band the FP64 no-FMA test of the oracle decides, and the pair
-// set equals brute force bit for bit).  Ballots are kept in shared memory; one atomic per tile
-// reserves the tile's segment; the entries are written with ballot compaction.
+// List construction: one lane per key particle tests the three cells around its own in each of
+// the 9 neighbour columns (the 27 cells of Alg. 1) from shared memory, FP32 on hi differences,
+// which are exact, so r^2 is within a bounded error of the FP64 value; inside that band the FP64
+// no-FMA test of the oracle decides, and the pair set equals brute force bit for bit.  The kept
+// bits are counted, one atomic per tile reserves the tile's segment, and the entries are written
+// from the bits (k_list_win).  The whole-box case (k_list_tile) takes a warp per key particle
+// with ballot compaction.
 #include "common.cuh"
+
+#include <type_traits>
 
 namespace ljmd {
 
@@ -480,66 +484,6 @@ __device__ __forceinline__ void replica_view(const ReplicaGeo& rg, TileArgs& ta,
   g = rg.g;
 }
 
-// Shared-memory layout of the thread-per-key list kernel (mixed form, staged tiles).
-constexpr int kListSplit = 2;  // candidate sub-ranges per neighbour column (work balance)
-constexpr int kListItems = 9 * kListSplit;     // work items per 32-key chunk
-constexpr size_t kListSmemTarget = 48 * 1024;  // 4 CTAs per SM for typical liquids
-constexpr int kListThreads = 256;               // threads of a list-construction CTA (128 or 256)
-struct KeyListLayout {
-  size_t pos;    // hi float4 [max_staged] (w: the sorted index, as int bits)
-  size_t cnt;    // int [nch * kListItems * 32]: per (key, column part) counts, then offsets in the row
-  size_t kst;    // int [nch * 32] row start within the tile segment, then int [nch * 32] row length
-  size_t ibase;  // int [nch * kListItems + 1]: first mask word of each item
-  size_t mask;   // uint32 [mask_words * 32]: kept-candidate bits, word-major, lane-minor
-  size_t seg;    // uint16 [seg_cap]: the tile's list segment before it is copied out
-  int nch;       // 32-key chunks per tile, at most
-  int mask_words;  // mask words per lane for one tile
-  int seg_cap;   // entries (a multiple of 8)
-  size_t total;
-};
-__host__ __device__ __forceinline__ KeyListLayout key_list_layout(const TileArgs& ta, int nt = kListThreads) {
-  KeyListLayout K;
-  const size_t ms = (size_t)ta.max_staged;
-  K.nch = (ta.max_own + 31) / 32;
-  K.pos = 0;
-  size_t o = align16(ms * 16);
-  K.cnt = o;
-  o += align16((size_t)K.nch * kListItems * 32 * 4);
-  K.kst = o;
-  o += align16((size_t)K.nch * 32 * 8);
-  K.ibase = o;
-  o += align16(((size_t)K.nch * kListItems + 1) * 4);
-  // every item needs ceil(len / 32) words; the items of a chunk cover at most all staged slots
-  int mw = K.nch * ((int)(ms / 32) + kListItems + 1);
-  K.mask_words = mw < 128 ? mw : 128;
-  K.mask = o;
-  o += (size_t)K.mask_words * 32 * 4;
-  K.seg = o;
-  // The segment staging area: what is left of 48 KB (4 CTAs per SM; 128-thread CTAs: 36 KB).  When
-  // the tile's other areas leave less than 8 KB of that (large tiles), the CTA takes up to 110 KB
-  // (2 per SM) so that a segment of up to ~80 entries per key still fits; a segment that does not fit
-  // is written to global memory directly.
-  const size_t target = nt == 128 ? kListSmemTarget * 3 / 4 : kListSmemTarget;
-  size_t room;
-  if (o + 8192 <= target) {
-    room = target - o;
-  } else {
-    const size_t cap2 = (size_t)(112 * 1024 - 2048);
-    const size_t want = 160 * (size_t)ta.max_own;
-    room = o < cap2 ? cap2 - o : 0;
-    if (room > want) room = want;
-    if (room < 8192) room = 8192;
-  }
-  K.seg_cap = (int)((room / 2) & ~(size_t)7);
-  K.total = o + 2 * (size_t)K.seg_cap;
-  return K;
-}
-
-size_t list_smem_bytes(const TileArgs& ta, int precision) {
-  if (!ta.whole) return key_list_layout(ta).total;  // both forms: the FP32 filter on the hi copies
-  return tile_layout(ta, precision == LJ_MIXED, false).total;
-}
-
 template <bool MIXED, bool HALF, bool WHOLE>
 __global__ void __launch_bounds__(kTileThreads, 4)
     k_list_tile(const void* __restrict__ pos, const double* __restrict__ x, const uint32_t* __restrict__ cs, int64_t N,
@@ -668,265 +612,167 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Candidates of one work item for the lane's key: part `h` (of kListSplit) of the range of
-// cells m_a - 1 .. m_b + 1 of neighbour column k (m_a, m_b: own cells of the first and last key
-// of the 32-key chunk c), tested in ascending staged order.  Partners beyond the key's own 3
-// cells fail the distance test (cells are at least r_s wide), so the chunk can share one
-// candidate range.  With WRITE the kept partners go to dst[p], dst[p + 1], ...  Returns the
-// number kept.
-__device__ __forceinline__ bool key_test(float r2, const ListBand& band, bool& maybe) {
-  const bool in = r2 < band.lo;
-  maybe = !in && r2 < band.hi;
-  return in;
+// Pair-list construction by cell windows (staged tiles, both forms, both list kinds).
+//
+// The keys of a tile are taken 32 at a time (a group, one key per lane, consecutive in the cell
+// order, so a group spans two or three own cells).  A work item is (group, neighbour column k):
+// every lane tests its own key against the three cells m-1, m, m+1 of column k around its own
+// cell m (the window of Alg. 1: partners farther along z fail the distance test, cells being at
+// least r_s wide).  Lanes in one cell read the same staged record, so a load serves a group with
+// one or a few distinct addresses.  The kept-candidate bits of each 32-candidate word go to a
+// per-tile pool in shared memory; a count per (key, column) gives every key its row and each
+// column its place in the row (columns in order, partners ascending: the list is deterministic);
+// one atomic reserves the tile's segment (padded to 8 entries); the entries are written from the
+// bits into shared memory and copied out with 16-byte stores.  Items whose bits do not fit in the
+// pool are tested again when written.  With the half list, a column other than the key's own has
+// all its cells before or all after the key's in the cell order (cell = (X n + Y) n + Z), so such
+// a column is kept or skipped as a whole; in the own column the sorted indices decide per pair.
+constexpr int kWinPoolPerItem = 2;  // pool words per work item on average (two words hold 64 candidates)
+constexpr int kWinThreads = 256;    // threads of a window-kernel CTA
+constexpr int kWinCtas = 3;         // window-kernel CTAs resident per SM (register budget)
+
+struct WinLayout {
+  size_t pos;    // hi float4 [max_staged + 32] (w: sorted index bits; 32 slack records for the last word);
+                 // once the bits are taken, the tile's segment (uint16 [seg_cap]) before it is copied out
+  size_t cell;   // uint8 [max_own]: own cell (1..Tp) of each key
+  size_t cnt;    // uint16 [ngrp * 9 * 32]: per (key, column) count, then its offset in the key's row
+  size_t kst;    // int [max_own]: row start in the segment; then int [max_own]: row length
+  size_t ib;     // int [ngrp * 9]: first pool word of each item (-1: tested again when written)
+  size_t mask;   // uint32 [pool_words * 32]
+  int ngrp, pool_words, seg_cap;
+  size_t total;
+};
+
+__host__ __device__ __forceinline__ WinLayout win_layout(const TileArgs& ta) {
+  WinLayout W;
+  const size_t ms = (size_t)ta.max_staged + 32;
+  W.ngrp = (ta.max_own + 31) / 32;
+  W.pos = 0;
+  size_t o = align16(ms * 16);
+  W.seg_cap = (int)((ms * 8) & ~(size_t)7);
+  W.cell = o;
+  o += align16((size_t)ta.max_own);
+  W.cnt = o;
+  o += align16((size_t)W.ngrp * 9 * 32 * 2);
+  W.kst = o;
+  o += align16((size_t)ta.max_own * 8);
+  W.ib = o;
+  o += align16((size_t)W.ngrp * 9 * 4);
+  W.pool_words = W.ngrp * 9 * kWinPoolPerItem + 8;
+  W.mask = o;
+  o += (size_t)W.pool_words * 32 * 4;
+  W.total = o;
+  return W;
 }
 
-// Candidate range [j0, j1) of item (chunk c, column k, part h).
-__device__ __forceinline__ void key_item_range(const TileShared& S, int Tp, int c, int k, int h, int n_own, int& j0,
-                                               int& j1) {
-  const int ncol = S.ncol;
-  const int o_last = min(32 * c + 31, n_own - 1);
-  const int ma = own_cell(S, S.own0 + 32 * c, Tp), mb = own_cell(S, S.own0 + o_last, Tp);
-  const int r0 = S.offq[k * ncol + ma - 1], r1 = S.offq[k * ncol + mb + 2];
-  j0 = r0 + ((r1 - r0) * h) / kListSplit;
-  j1 = r0 + ((r1 - r0) * (h + 1)) / kListSplit;
+// Own column's cells of the key particle's neighbour column k, for the half list: +1 if all
+// cells of column k come after the tile's own cells in the cell order, -1 if all come before,
+// 0 for the own column (decided per pair by the sorted indices).
+__device__ __forceinline__ int win_column_order(const TileInfo& ti, int n, int k) {
+  if (k == 4) return 0;
+  int sx, sy;
+  const int X = wrap_cell(ti.cx + k / 3 - 1, n, sx);
+  const int Y = wrap_cell(ti.cy + k % 3 - 1, n, sy);
+  return (X > ti.cx || (X == ti.cx && Y > ti.cy)) ? 1 : -1;
 }
 
-// MODE 0: count; 1: count and store the kept-candidate bits (word w of the item at
-// mask[(wbase + w) * 32 + lane]); 2: write the kept partners to dst[p], dst[p + 1], ...
-template <bool HALF, int MODE>
-__device__ __forceinline__ int key_item(const TileShared& S, int Tp, const float4* sh_pos,
-                                        const double* __restrict__ x, int64_t N, const Geom& g,
-                                        const ListBand& band, int c, int k, int h, int n_own, uint16_t* dst, int p,
-                                        uint32_t* mask, int wbase) {
-  const int lane = threadIdx.x & 31;
-  const int o = 32 * c + lane;
-  const bool valid = o < n_own;
-  const int o_last = min(32 * c + 31, n_own - 1);
-  int j0, j1;
-  key_item_range(S, Tp, c, k, h, n_own, j0, j1);
-  const int l = S.own0 + (valid ? o : o_last);
-  const float4 pi = sh_pos[l];
-  const int gi = __float_as_int(sh_pos[l].w);
-  int cnt = 0;
+// One 32-candidate word of a key: bit u set iff staged slot jb + u is listed for the key (slot l,
+// sorted index gi, hi record pi).  `rem` candidates of the key remain from jb on (the rest of the
+// word is masked); lanes without any read slots 0..31 and keep nothing.  Only the first nblk blocks of
+// 8 candidates are tested (the windows of all lanes end before the rest).  FP32 filter on the exact
+// hi differences; for a word with a kept r^2 inside the band the FP64 test of the oracle decides
+// those.  OWN: the key's own column (the key itself is dropped; HALF keeps larger sorted indices).
+template <bool HALF, bool OWN>
+__device__ __forceinline__ uint32_t win_word(const float4* sh_pos, const double* __restrict__ x, int64_t N,
+                                             const Geom& g, const ListBand& band, int jb, int rem, int nblk, int l,
+                                             int gi, float4 pi) {
   uint32_t bits = 0;
-  int j = j0;
-  for (; j + 1 < j1; j += 2) {  // two candidates per iteration (same address in every lane: broadcasts)
-    const float4 pa = sh_pos[j], pb = sh_pos[j + 1];
-    const float ax = pa.x - pi.x, ay = pa.y - pi.y, az = pa.z - pi.z;  // exact
-    const float bx = pb.x - pi.x, by = pb.y - pi.y, bz = pb.z - pi.z;
-    bool ma_, mb_;
-    bool ina = key_test(fmaf(ax, ax, fmaf(ay, ay, az * az)), band, ma_);
-    bool inb = key_test(fmaf(bx, bx, fmaf(by, by, bz * bz)), band, mb_);
-    if (__any_sync(0xffffffffu, ma_ || mb_)) {
-      if (ma_) ina = pair_in_exact(x, N, gi, __float_as_int(sh_pos[j].w), g, band.rs2);
-      if (mb_) inb = pair_in_exact(x, N, gi, __float_as_int(sh_pos[j + 1].w), g, band.rs2);
-    }
-    ina = ina && valid && j != l;
-    inb = inb && valid && j + 1 != l;
-    if (HALF) {
-      ina = ina && __float_as_int(sh_pos[j].w) > gi;
-      inb = inb && __float_as_int(sh_pos[j + 1].w) > gi;
-    }
-    if (MODE == 2) {
-      if (ina) dst[p++] = (uint16_t)j;
-      if (inb) dst[p++] = (uint16_t)(j + 1);
-    }
-    if (MODE == 1) {  // q = j - j0 is even, so a pair never straddles a word
-      const int q = j - j0;
-      bits |= ((ina ? 1u : 0u) | (inb ? 2u : 0u)) << (q & 31);
-      if ((q & 31) == 30) {
-        mask[(wbase + (q >> 5)) * 32 + lane] = bits;
-        bits = 0;
-      }
-    }
-    cnt += (ina ? 1 : 0) + (inb ? 1 : 0);
-  }
-  if (j < j1) {
-    const float4 pa = sh_pos[j];
-    const float ax = pa.x - pi.x, ay = pa.y - pi.y, az = pa.z - pi.z;
-    bool ma_;
-    bool ina = key_test(fmaf(ax, ax, fmaf(ay, ay, az * az)), band, ma_);
-    if (__any_sync(0xffffffffu, ma_)) {
-      if (ma_) ina = pair_in_exact(x, N, gi, __float_as_int(sh_pos[j].w), g, band.rs2);
-    }
-    ina = ina && valid && j != l;
-    if (HALF) ina = ina && __float_as_int(sh_pos[j].w) > gi;
-    if (MODE == 2 && ina) dst[p++] = (uint16_t)j;
-    if (MODE == 1) bits |= (ina ? 1u : 0u) << ((j - j0) & 31);
-    cnt += ina ? 1 : 0;
-    ++j;
-  }
-  if (MODE == 1 && ((j - j0) & 31) != 0) mask[(wbase + ((j - j0) >> 5)) * 32 + lane] = bits;
-  return cnt;
-}
-
-// Count pass with bits, 32 candidates per word: the FP32 filter sets `bits` (r^2 < lo) and
-// `mbits` (r^2 < hi) with compile-time bit positions, then the rare band members get the exact
-// FP64 test, the key itself and the slots past the range are cleared, and the word is stored.
-// Slots past the range read whatever follows in shared memory; their bits are masked off.
-template <bool HALF>
-__device__ __forceinline__ int key_item_bits(const TileShared& S, int Tp, const float4* sh_pos,
-                                             const double* __restrict__ x, int64_t N, const Geom& g,
-                                             const ListBand& band, int c, int k, int h, int n_own, uint32_t* mask,
-                                             int wbase) {
-  const int lane = threadIdx.x & 31;
-  const int o = 32 * c + lane;
-  const bool valid = o < n_own;
-  const int o_last = min(32 * c + 31, n_own - 1);
-  int j0, j1;
-  key_item_range(S, Tp, c, k, h, n_own, j0, j1);
-  const int l = S.own0 + (valid ? o : o_last);
-  const float4 pi = sh_pos[l];
-  const int gi = __float_as_int(sh_pos[l].w);
-  int cnt = 0;
-  for (int jb = j0, w = 0; jb < j1; jb += 32, ++w) {
-    uint32_t bits = 0, mbits = 0;
+  float mx = 0.f;
 #pragma unroll
-    for (int u = 0; u < 32; u += 8) {
-#pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const float4 pj = sh_pos[jb + u + v];  // same address in every lane: one broadcast
-        const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;  // exact
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < band.lo) bits |= 1u << (u + v);
-        if (r2 < band.hi) mbits |= 1u << (u + v);
-      }
-    }
-    const int nv = j1 - jb;
-    const uint32_t tail = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
-    bits &= tail;
-    mbits &= tail & ~bits;
-    if (__any_sync(0xffffffffu, mbits != 0u)) {
-      while (mbits) {
-        const int bit = __ffs(mbits) - 1;
-        mbits &= mbits - 1;
-        if (pair_in_exact(x, N, gi, __float_as_int(sh_pos[jb + bit].w), g, band.rs2)) bits |= 1u << bit;
-      }
-    }
-    if (l >= jb && l < jb + 32) bits &= ~(1u << (l - jb));  // the key itself
-    if (HALF) {
-      uint32_t m = bits;
-      while (m) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        if (__float_as_int(sh_pos[jb + bit].w) <= gi) bits &= ~(1u << bit);
-      }
-    }
-    if (!valid) bits = 0u;
-    mask[(wbase + w) * 32 + lane] = bits;
-    cnt += __popc(bits);
-  }
-  return cnt;
-}
-
-// Write pass from stored bits: the kept partners of the lane's key in ascending order.
-__device__ __forceinline__ void key_item_from_mask(const TileShared& S, int Tp, int c, int k, int h, int n_own,
-                                                   uint16_t* dst, int p, const uint32_t* mask, int wbase) {
-  const int lane = threadIdx.x & 31;
-  int j0, j1;
-  key_item_range(S, Tp, c, k, h, n_own, j0, j1);
-  const int nw = (j1 - j0 + 31) >> 5;
-  for (int w = 0; w < nw; ++w) {
-    uint32_t m = mask[(wbase + w) * 32 + lane];
-    while (m) {
-      const int bit = __ffs(m) - 1;
-      m &= m - 1;
-      dst[p++] = (uint16_t)(j0 + 32 * w + bit);
-    }
-  }
-}
-
-// One work unit of the list construction: 32 consecutive staged candidates [j0, j0 + len) against
-// the lane's key l (sorted index gi); bit b set iff j0 + b is listed for the key.  Same tests as
-// key_item_bits.
-template <bool HALF>
-__device__ __forceinline__ uint32_t unit_bits(const float4* sh_pos, const double* __restrict__ x,
-                                              int64_t N, const Geom& g, const ListBand& band, int j0, int len, int l,
-                                              int gi, bool valid) {
-  const float4 pi = sh_pos[l];
-  uint32_t bits = 0, mbits = 0;
-#pragma unroll
-  for (int u = 0; u < 32; u += 8) {
+  for (int b = 0; b < 4; ++b) {
+    if (b >= nblk) break;  // warp-uniform: blocks of 8 past every lane's window are not tested
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-      const float4 pj = sh_pos[j0 + u + v];  // same address in every lane: one broadcast
+      const int u = 8 * b + v;
+      const float4 pj = sh_pos[jb + u];
       const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;  // exact
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (r2 < band.lo) bits |= 1u << (u + v);
-      if (r2 < band.hi) mbits |= 1u << (u + v);
+      bool in = r2 < band.hi;
+      if (HALF && OWN) in = in && __float_as_int(pj.w) > gi;
+      if (in) {
+        bits |= 1u << u;
+        mx = fmaxf(mx, r2);
+      }
     }
   }
-  const uint32_t tail = len >= 32 ? 0xffffffffu : ((1u << len) - 1u);
-  bits &= tail;
-  mbits &= tail & ~bits;
-  if (__any_sync(0xffffffffu, mbits != 0u)) {
-    while (mbits) {
-      const int bit = __ffs(mbits) - 1;
-      mbits &= mbits - 1;
-      if (pair_in_exact(x, N, gi, __float_as_int(sh_pos[j0 + bit].w), g, band.rs2)) bits |= 1u << bit;
+  bits &= rem >= 32 ? 0xffffffffu : (rem > 0 ? (1u << rem) - 1u : 0u);
+  if (OWN) {
+    const int d = l - jb;
+    if (d >= 0 && d < 32) bits &= ~(1u << d);  // the key itself
+  }
+  const bool band_hit = bits != 0u && mx >= band.lo;
+  if (__any_sync(0xffffffffu, band_hit) && band_hit) {
+    uint32_t mb = bits;
+    while (mb) {
+      const int u = __ffs(mb) - 1;
+      mb &= mb - 1;
+      const float4 pj = sh_pos[jb + u];
+      const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (r2 >= band.lo && !pair_in_exact(x, N, gi, __float_as_int(pj.w), g, band.rs2)) bits &= ~(1u << u);
     }
   }
-  if (l >= j0 && l < j0 + 32) bits &= ~(1u << (l - j0));  // the key itself
-  if (HALF) {
-    uint32_t m = bits;
-    while (m) {
-      const int bit = __ffs(m) - 1;
-      m &= m - 1;
-      if (__float_as_int(sh_pos[j0 + bit].w) <= gi) bits &= ~(1u << bit);
-    }
-  }
-  return valid ? bits : 0u;
+  return bits;
 }
 
-constexpr int kUnitChunks = 24;   // chunks per tile in the unit path
-constexpr int kUnitMax = 160;     // work units per tile in the unit path
+template <bool HALF>
+__device__ __forceinline__ uint32_t win_word_k(bool own, const float4* sh_pos, const double* __restrict__ x,
+                                               int64_t N, const Geom& g, const ListBand& band, int jb, int rem,
+                                               int nblk, int l, int gi, float4 pi) {
+  return own ? win_word<HALF, true>(sh_pos, x, N, g, band, jb, rem, nblk, l, gi, pi)
+             : win_word<HALF, false>(sh_pos, x, N, g, band, jb, rem, nblk, l, gi, pi);
+}
 
-// Pair-list construction, mixed form, staged tiles: one thread per key particle.  Work items
-// are (32-key chunk, neighbour column); a first pass counts each key's partners per column, a
-// prefix gives every key its row and every column its place in the row (columns in order,
-// partners ascending: the list is deterministic), one atomic reserves the tile's segment
-// (padded to 8 entries), and a second pass writes the entries into shared memory, from where
-// they are copied out with 16-byte stores (directly to global memory if the segment does not
-// fit).
+size_t list_smem_bytes(const TileArgs& ta, int precision) {
+  if (!ta.whole) return win_layout(ta).total;  // both forms: the FP32 filter on the hi copies
+  return tile_layout(ta, precision == LJ_MIXED, false).total;
+}
+
 template <bool HALF, bool BATCHED, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT)
-    k_list_keys(const float4* __restrict__ pos, const double* __restrict__ x, const uint32_t* __restrict__ cs_in,
-                int64_t N, Geom g_in, TileArgs ta_in, ListBand band, uint2* __restrict__ rows,
-                uint2* __restrict__ tile_list, uint16_t* __restrict__ ent, uint64_t cap,
-                unsigned long long* __restrict__ counter, unsigned int* __restrict__ max_list,
-                int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps, int R,
-                const int* __restrict__ pred, const int32_t* __restrict__ tile_rep) {
+__global__ void __launch_bounds__(NT, kWinCtas)
+    k_list_win(const float4* __restrict__ pos, const double* __restrict__ x, const uint32_t* __restrict__ cs_in,
+               int64_t N, Geom g_in, TileArgs ta_in, ListBand band, uint2* __restrict__ rows,
+               uint2* __restrict__ tile_list, uint16_t* __restrict__ ent, uint64_t cap,
+               unsigned long long* __restrict__ counter, unsigned int* __restrict__ max_list,
+               int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps, int R,
+               const int* __restrict__ pred, const int32_t* __restrict__ tile_rep) {
   if (pred && !*pred) return;  // predicated (batched rebuild inside a graph)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared S;
   __shared__ __align__(8) uint64_t bar;
-  __shared__ unsigned int s_base, s_total, s_padded;
-  __shared__ int s_ok;
-  __shared__ int u_ck0[kUnitChunks + 1], u_ub[kUnitChunks + 1], u_info[kUnitMax];
-  __shared__ unsigned char u_chunk[kUnitMax];
-  __shared__ int s_nchunk, s_nunit;
-  constexpr int kLW = NT / 32;  // warps of the CTA
-  const KeyListLayout K = key_list_layout(ta_in, NT);
-  TileLayout L;  // the staging helpers' view: positions (sorted indices in w)
-  L.pos = K.pos;
-  L.gid = K.pos;
+  __shared__ unsigned int s_base, s_padded;
+  __shared__ int s_ok, s_staged_ok, s_pool, s_retest;
+  constexpr int kNW = NT / 32;
+  const WinLayout W = win_layout(ta_in);
+  TileLayout L;  // the staging helpers' view: hi records (sorted indices in w)
+  L.pos = W.pos;
+  L.gid = W.pos;
   L.rows = L.ent = L.cnt = L.total = 0;
-  const float4* sh_pos = (const float4*)(smem + K.pos);
-  int* s_cnt = (int*)(smem + K.cnt);
-  int* s_kst = (int*)(smem + K.kst);
-  int* s_len = s_kst + K.nch * 32;
-  int* s_ibase = (int*)(smem + K.ibase);
-  uint32_t* s_mask = (uint32_t*)(smem + K.mask);
-  uint16_t* s_seg = (uint16_t*)(smem + K.seg);
+  const float4* sh_pos = (const float4*)(smem + W.pos);
+  unsigned char* s_cell = smem + W.cell;
+  uint16_t* s_cnt = (uint16_t*)(smem + W.cnt);
+  int* s_kst = (int*)(smem + W.kst);
+  int* s_len = s_kst + ta_in.max_own;
+  int* s_ib = (int*)(smem + W.ib);
+  uint32_t* s_mask = (uint32_t*)(smem + W.mask);
+  uint16_t* s_seg = (uint16_t*)(smem + W.pos);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t phase = 0;
-  __shared__ int s_staged_ok;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_proxy_async_smem();
   }
-  // warp 0 holds the cell bounds of the CTA's next tile, loaded one tile ahead of their use
-  TilePrefetch pf;
+  TilePrefetch pf;  // warp 0: the cell bounds of the CTA's next tile, loaded a tile ahead
   auto prefetch = [&](int64_t tp) {
     TileArgs tap = ta_in;
     Geom gp = g_in;
@@ -955,252 +801,92 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     const TileInfo ti = tile_info(tl, ta);
     if (warp == 0) {
       const bool okp = tile_prepare_pf(pf, ta, S, lane);
-      if (lane == 0) s_staged_ok = okp ? 1 : 0;
+      if (lane == 0) {
+        const int n_own_p = S.own1 - S.own0;
+        s_staged_ok = (okp && n_own_p <= ta.max_own) ? 1 : 0;
+        s_pool = 0;
+        s_retest = 0;
+      }
       if (t + gridDim.x < ta_in.ntiles) prefetch(t + gridDim.x);
     }
     __syncthreads();
-    if (!s_staged_ok) {
+    if (!s_staged_ok) {  // sizing inconsistency: record and skip the tile
       if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
       __syncthreads();
       continue;
     }
-    if (!stage_copy_async<true, false>(ti, ta, g, pos, nullptr, nullptr, S, smem, L, &bar, phase, false, status))
-      return;
-    const int n_own = S.own1 - S.own0;
-    if (n_own > ta.max_own) {  // sizing inconsistency: record and skip the tile
-      if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
-      __syncthreads();
-      continue;
+    const int n_own = S.own1 - S.own0, ncol = S.ncol;
+    // own cell of every key (ordered before the staged records by the barrier that ends the wait)
+    for (int m = 1 + warp; m <= ti.Tp; m += kNW) {
+      const int a = S.offq[4 * ncol + m] - S.own0, b = S.offq[4 * ncol + m + 1] - S.own0;
+      for (int o = a + lane; o < b; o += 32) s_cell[o] = (unsigned char)m;
     }
-    // ---- unit path: chunks of whole own cells (at most 32 keys), one 32-candidate word per unit
-    if (threadIdx.x == 0) {
-      const int base4 = 4 * S.ncol;
-      int nc = 0, kpos = 0, acc = 0;
-      bool ok = true;
-      u_ck0[0] = 0;
-      for (int m = 1; m <= ti.Tp && ok; ++m) {
-        int nm = S.offq[base4 + m + 1] - S.offq[base4 + m];
-        if (acc + nm <= 32) {
-          acc += nm;
-          continue;
-        }
-        if (acc > 0) {
-          kpos += acc;
-          if (nc + 1 > kUnitChunks) ok = false;
-          else u_ck0[++nc] = kpos;
-          acc = 0;
-        }
-        while (nm > 32 && ok) {
-          kpos += 32;
-          if (nc + 1 > kUnitChunks) ok = false;
-          else u_ck0[++nc] = kpos;
-          nm -= 32;
-        }
-        acc = nm;
-      }
-      if (ok && acc > 0) {
-        kpos += acc;
-        if (nc + 1 > kUnitChunks) ok = false;
-        else u_ck0[++nc] = kpos;
-      }
-      s_nchunk = ok ? nc : -1;
-    }
-    __syncwarp();
-    if (warp == 0) {
-      // units in (chunk, column, word) order: lane p takes the pairs (c, k) = (p / 9, p % 9), ...
-      const int nc = s_nchunk;
-      const int ucap = min(kUnitMax, K.mask_words);
-      int run = 0;
-      bool ok = nc >= 0;
-      for (int base = 0; ok && base < nc * 9; base += 32) {
-        const int pk = base + lane;
-        int r0 = 0, r1 = 0;
-        if (pk < nc * 9) {
-          const int c = pk / 9, k = pk - 9 * (pk / 9);
-          const int ma = own_cell(S, S.own0 + u_ck0[c], ti.Tp), mb = own_cell(S, S.own0 + u_ck0[c + 1] - 1, ti.Tp);
-          r0 = S.offq[k * S.ncol + ma - 1];
-          r1 = S.offq[k * S.ncol + mb + 2];
-        }
-        const int nw = (r1 - r0 + 31) >> 5;
-        int inc = nw;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, inc, d);
-          if (lane >= d) inc += y;
-        }
-        const int first = run + inc - nw;
-        run += __shfl_sync(0xffffffffu, inc, 31);
-        if (run > ucap) {
-          ok = false;
-          break;
-        }
-        if (pk < nc * 9) {
-          const int c = pk / 9;
-          if (pk % 9 == 0) u_ub[c] = first;
-          for (int w = 0; w < nw; ++w) {
-            const int j0 = r0 + 32 * w;
-            u_info[first + w] = j0 | (min(32, r1 - j0) << 16);
-            u_chunk[first + w] = (unsigned char)c;
-          }
-        }
-      }
+    stage_issue<true, false>(ti, ta, pos, nullptr, nullptr, S, smem, L, &bar);
+    if (!stage_finish<true, false>(ti, ta, g, S, smem, L, &bar, phase, false, status)) return;
+    const int ngrp = (n_own + 31) >> 5, nitem = 9 * ngrp;
+    // phase A: the kept-candidate bits of every item, a count per (key, column)
+    for (int item = warp; item < nitem; item += kNW) {
+      const int gq = item / 9, k = item - 9 * gq;
+      const int o = 32 * gq + lane;
+      const bool valid = o < n_own;
+      const int oc = valid ? o : n_own - 1;
+      const int l = S.own0 + oc;
+      const float4 pi = sh_pos[l];
+      const int gi = __float_as_int(pi.w);
+      const int m = s_cell[oc];
+      const int j0 = S.offq[k * ncol + m - 1];
+      int len = valid ? S.offq[k * ncol + m + 2] - j0 : 0;
+      if (HALF && win_column_order(ti, ta.n, k) < 0) len = 0;
+      const int maxlen = __reduce_max_sync(0xffffffffu, len);
+      const int nw = (maxlen + 31) >> 5;
+      int base = 0;
       if (lane == 0) {
-        if (ok && nc >= 0) u_ub[nc] = run;
-        s_nunit = ok ? run : -1;
-        if (!ok) s_nchunk = -1;
+        base = nw > 0 ? atomicAdd(&s_pool, nw) : 0;
+        if (base + nw > W.pool_words) {
+          base = -1;
+          s_retest = 1;
+        }
+        s_ib[item] = base;
       }
+      base = __shfl_sync(0xffffffffu, base, 0);
+      int cnt = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int rem = len - 32 * w;
+        const uint32_t bits = win_word_k<HALF>(k == 4, sh_pos, x, N, g, band, rem > 0 ? j0 + 32 * w : 0, rem,
+                                               (maxlen - 32 * w + 7) >> 3, l, gi, pi);
+        if (base >= 0) s_mask[(base + w) * 32 + lane] = bits;
+        cnt += __popc(bits);
+      }
+      s_cnt[item * 32 + lane] = (uint16_t)cnt;
     }
     __syncthreads();
-    if (s_nchunk >= 0) {
-      const int nc = s_nchunk, nu = s_nunit;
-      // phase A: the bits of every unit
-      for (int u = warp; u < nu; u += kLW) {
-        const int c = u_chunk[u];
-        const int o = u_ck0[c] + lane;
-        const bool valid = o < u_ck0[c + 1];
-        const int l = S.own0 + (valid ? o : u_ck0[c + 1] - 1);
-        s_mask[u * 32 + lane] = unit_bits<HALF>(sh_pos, x, N, g, band, u_info[u] & 0xffff, u_info[u] >> 16, l,
-                                                __float_as_int(sh_pos[l].w), valid);
-      }
-      __syncthreads();
-      // phase B: row lengths (one warp per chunk), and each unit's offset in its keys' rows
-      // (kept in the count area, which the unit path does not use otherwise, when it holds them)
-      int* s_upre = s_cnt;
-      const bool keep_pre = nu <= K.nch * kListItems;
-      for (int c = warp; c < nc; c += kLW) {
-        int len = 0;
-        for (int u = u_ub[c]; u < u_ub[c + 1]; ++u) {
-          if (keep_pre) s_upre[u * 32 + lane] = len;
-          len += __popc(s_mask[u * 32 + lane]);
-        }
-        const int o = u_ck0[c] + lane;
-        if (o < u_ck0[c + 1]) s_len[o] = len;
-      }
-      __syncthreads();
-      // phase C: exclusive prefix of the rows, one atomic reserves the tile's padded segment
-      if (warp == 0) {
-        unsigned run = 0;
-        for (int base = 0; base < n_own; base += 32) {
-          const int o = base + lane;
-          const unsigned v = o < n_own ? (unsigned)s_len[o] : 0u;
-          unsigned inc = v;
-#pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc += y;
-          }
-          if (o < n_own) s_kst[o] = (int)(run + inc - v);
-          run += __shfl_sync(0xffffffffu, inc, 31);
-        }
-        if (lane == 0) {
-          const unsigned padded = (run + 7u) & ~7u;
-          const unsigned long long b = atomicAdd(counter, (unsigned long long)padded);
-          atomicAdd(counter + 1, (unsigned long long)run);
-          const bool fits = b + padded <= cap;
-          s_base = (unsigned)b;
-          s_total = run;
-          s_padded = padded;
-          s_ok = fits;
-          tile_list[t] = fits ? make_uint2((unsigned)b, padded) : make_uint2(0u, 0u);
-          atomicMax(max_list, padded);
-          if (BATCHED && !fits) atomicOr(status, LJ_ST_LIST_OVERFLOW);
-        }
-      }
-      __syncthreads();
-      const bool ok = s_ok != 0;
-      for (int o = threadIdx.x; o < n_own; o += blockDim.x)
-        rows[S.gown0 + o] = ok ? make_uint2(s_base + (unsigned)s_kst[o], (unsigned)s_len[o]) : make_uint2(0u, 0u);
-      if (ok) {
-        const bool staged = s_padded <= (unsigned)K.seg_cap;
-        uint16_t* dst = staged ? s_seg : ent + s_base;
-        // phase D: entries in row order (units of a chunk in column order), one warp per unit;
-        // a unit's entries start after the key's entries in the chunk's earlier units
-        for (int u = warp; u < nu; u += kLW) {
-          const int c = u_chunk[u];
-          const int o = u_ck0[c] + lane;
-          if (o < u_ck0[c + 1]) {
-            int p = s_kst[o];
-            if (keep_pre) p += s_upre[u * 32 + lane];
-            else
-              for (int v = u_ub[c]; v < u; ++v) p += __popc(s_mask[v * 32 + lane]);
-            uint32_t m = s_mask[u * 32 + lane];
-            const int j0 = u_info[u] & 0xffff;
-            while (m) {
-              const int bit = __ffs(m) - 1;
-              m &= m - 1;
-              dst[p++] = (uint16_t)(j0 + bit);
-            }
-          }
-        }
-        if (staged) {
-          __syncthreads();
-          const uint4* src = (const uint4*)s_seg;
-          uint4* out = (uint4*)(ent + s_base);
-          for (unsigned w = threadIdx.x; w < s_padded / 8u; w += blockDim.x) out[w] = src[w];
-        }
-      }
-      __syncthreads();
-      continue;
-    }
-    // ---- item path (tiles whose chunk or unit tables do not fit)
-    const int nch = (n_own + 31) / 32;
-    constexpr int kItems = kListItems;
-    // first mask word of every item (warp 0); the bits are kept only if the tile's words fit
-    if (warp == 0) {
+    // phase B: each key's column offsets within its row and its row length (a warp per group)
+    for (int gq = warp; gq < ngrp; gq += kNW) {
       int run = 0;
-      for (int base = 0; base < nch * kItems; base += 32) {
-        const int item = base + lane;
-        int nw = 0;
-        if (item < nch * kItems) {
-          int j0, j1;
-          key_item_range(S, ti.Tp, item / kItems, (item % kItems) / kListSplit, item % kListSplit, n_own, j0, j1);
-          nw = (j1 - j0 + 31) >> 5;
-        }
-        int inc = nw;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, inc, d);
-          if (lane >= d) inc += y;
-        }
-        if (item < nch * kItems) s_ibase[item] = run + inc - nw;
-        run += __shfl_sync(0xffffffffu, inc, 31);
+      for (int k = 0; k < 9; ++k) {
+        uint16_t* c = s_cnt + (9 * gq + k) * 32 + lane;
+        const int v = *c;
+        *c = (uint16_t)run;
+        run += v;
       }
-      if (lane == 0) s_ibase[nch * kItems] = run;
+      const int o = 32 * gq + lane;
+      if (o < n_own) s_len[o] = run;
     }
     __syncthreads();
-    const bool keep_bits = s_ibase[nch * kItems] <= K.mask_words;
-    // pass 1: counts per (key, column part), kept-candidate bits
-    for (int item = warp; item < nch * kItems; item += kLW) {
-      const int c = item / kItems, r = item - kItems * c;
-      s_cnt[item * 32 + lane] =
-          keep_bits ? key_item_bits<HALF>(S, ti.Tp, sh_pos, x, N, g, band, c, r / kListSplit, r % kListSplit,
-                                          n_own, s_mask, s_ibase[item])
-                    : key_item<HALF, 0>(S, ti.Tp, sh_pos, x, N, g, band, c, r / kListSplit, r % kListSplit,
-                                        n_own, nullptr, 0, nullptr, 0);
-    }
-    __syncthreads();
+    // phase C: exclusive prefix of the rows; one atomic reserves the tile's padded segment
     if (warp == 0) {
-      // column offsets within each row, row lengths, exclusive prefix of the rows; one atomic
-      // reserves the tile's segment, padded to a multiple of 8 entries (16 bytes)
       unsigned run = 0;
-      for (int c = 0; c < nch; ++c) {
-        const int o = 32 * c + lane;
-        int tot = 0;
-#pragma unroll
-        for (int r = 0; r < kItems; ++r) {
-          const int v = s_cnt[(c * kItems + r) * 32 + lane];
-          s_cnt[(c * kItems + r) * 32 + lane] = tot;
-          tot += v;
-        }
-        if (o >= n_own) tot = 0;
-        unsigned inc = (unsigned)tot;
+      for (int b0 = 0; b0 < n_own; b0 += 32) {
+        const int o = b0 + lane;
+        const unsigned v = o < n_own ? (unsigned)s_len[o] : 0u;
+        unsigned inc = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
           const unsigned y = __shfl_up_sync(0xffffffffu, inc, d);
           if (lane >= d) inc += y;
         }
-        s_kst[o] = (int)(run + inc - (unsigned)tot);
-        s_len[o] = tot;
+        if (o < n_own) s_kst[o] = (int)(run + inc - v);
         run += __shfl_sync(0xffffffffu, inc, 31);
       }
       if (lane == 0) {
@@ -1209,7 +895,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
         atomicAdd(counter + 1, (unsigned long long)run);
         const bool fits = b + padded <= cap;
         s_base = (unsigned)b;
-        s_total = run;
         s_padded = padded;
         s_ok = fits;
         tile_list[t] = fits ? make_uint2((unsigned)b, padded) : make_uint2(0u, 0u);
@@ -1219,29 +904,67 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     }
     __syncthreads();
     const bool ok = s_ok != 0;
-    for (int o = threadIdx.x; o < n_own; o += blockDim.x)
+    for (int o = threadIdx.x; o < n_own; o += NT)
       rows[S.gown0 + o] = ok ? make_uint2(s_base + (unsigned)s_kst[o], (unsigned)s_len[o]) : make_uint2(0u, 0u);
     if (ok) {
-      const bool staged = s_padded <= (unsigned)K.seg_cap;
-      uint16_t* dst = staged ? s_seg : ent + s_base;
-      // pass 2: the same tests, entries written
-      for (int item = warp; item < nch * kItems; item += kLW) {
-        const int c = item / kItems, r = item - kItems * c;
-        const int o = 32 * c + lane;
-        const int p = o < n_own ? s_kst[o] + s_cnt[item * 32 + lane] : 0;
-        if (keep_bits)
-          key_item_from_mask(S, ti.Tp, c, r / kListSplit, r % kListSplit, n_own, dst, p, s_mask, s_ibase[item]);
-        else
-          key_item<HALF, 2>(S, ti.Tp, sh_pos, x, N, g, band, c, r / kListSplit, r % kListSplit, n_own, dst,
-                            p, nullptr, 0);
-      }
+      // phase D: the entries of every item from its bits (or tested again), in row order; staged
+      // over the positions (no longer needed unless an item is tested again) and copied out, or
+      // written to global memory directly
+      const bool staged = s_padded <= (unsigned)W.seg_cap && !s_retest;
+      auto write_items = [&](auto in_shared) {
+        uint16_t* dst = decltype(in_shared)::value ? s_seg : ent + s_base;
+        for (int item = warp; item < nitem; item += kNW) {
+          const int gq = item / 9, k = item - 9 * gq;
+          const int o = 32 * gq + lane;
+          const bool valid = o < n_own;
+          const int oc = valid ? o : n_own - 1;
+          const int m = s_cell[oc];
+          const int j0 = S.offq[k * ncol + m - 1];
+          int len = valid ? S.offq[k * ncol + m + 2] - j0 : 0;
+          if (HALF && win_column_order(ti, ta.n, k) < 0) len = 0;
+          int p = valid ? s_kst[o] + s_cnt[item * 32 + lane] : 0;
+          const int base = s_ib[item];
+          if (base >= 0) {
+            for (int w = 0; 32 * w < len; ++w) {
+              uint32_t bits = s_mask[(base + w) * 32 + lane];
+              while (bits) {
+                const int u = __ffs(bits) - 1;
+                bits &= bits - 1;
+                dst[p++] = (uint16_t)(j0 + 32 * w + u);
+              }
+            }
+          } else if (!decltype(in_shared)::value) {
+            const int l = S.own0 + oc;
+            const float4 pi = sh_pos[l];
+            const int gi = __float_as_int(pi.w);
+            const int maxlen = __reduce_max_sync(0xffffffffu, len);
+            const int nw = (maxlen + 31) >> 5;
+            for (int w = 0; w < nw; ++w) {
+              const int rem = len - 32 * w;
+              uint32_t bits = win_word_k<HALF>(k == 4, sh_pos, x, N, g, band, rem > 0 ? j0 + 32 * w : 0, rem,
+                                               (maxlen - 32 * w + 7) >> 3, l, gi, pi);
+              while (bits) {
+                const int u = __ffs(bits) - 1;
+                bits &= bits - 1;
+                dst[p++] = (uint16_t)(j0 + 32 * w + u);
+              }
+            }
+          }
+        }
+      };
       if (staged) {
+        write_items(std::true_type());
         __syncthreads();
         const uint4* src = (const uint4*)s_seg;
         uint4* out = (uint4*)(ent + s_base);
-        for (unsigned w = threadIdx.x; w < s_padded / 8u; w += blockDim.x) out[w] = src[w];
+        for (unsigned w = threadIdx.x; w < s_padded / 8u; w += NT) out[w] = src[w];
+      } else {
+        write_items(std::false_type());
       }
     }
+    // the positions' bytes were read and written by the generic proxy; the next tile's bulk copies
+    // (async proxy) write them
+    fence_proxy_async_smem();
     __syncthreads();
   }
 }
@@ -2211,9 +1934,9 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
                       cudaStream_t s) {
   const size_t sm = list_smem_bytes(ta, precision);
   int grid = tile_grid(ta, per_sm_for(sm));
-  if (!ta.whole) {  // the key kernel: as many CTAs as are resident
-    set_smem(k_list_keys<false, false, kListThreads>, sm);
-    grid = tile_grid(ta, resident_per_sm(k_list_keys<false, false, kListThreads>, kListThreads, sm));
+  if (!ta.whole) {  // the window kernel: as many CTAs as are resident
+    set_smem(k_list_win<false, false, kWinThreads>, sm);
+    grid = tile_grid(ta, resident_per_sm(k_list_win<false, false, kWinThreads>, kWinThreads, sm));
   }
 #define LJ_LIST_LAUNCH(M, H, W)                                                                                 \
   do {                                                                                                          \
@@ -2231,13 +1954,15 @@ void launch_list_tile(int precision, int half, const void* pos, const float4* hi
       else LJ_LIST_LAUNCH(false, false, true);
     }
   } else if (half) {  // tiles, either form: one thread per key on the hi copies (the list is the same)
-    set_smem(k_list_keys<true, false, kListThreads>, sm);
-    k_list_keys<true, false, kListThreads><<<grid, kListThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
-                                                            counter, max_list, status, nullptr, 0, nullptr, nullptr);
+    set_smem(k_list_win<true, false, kWinThreads>, sm);
+    k_list_win<true, false, kWinThreads><<<grid, kWinThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent,
+                                                                       cap, counter, max_list, status, nullptr, 0,
+                                                                       nullptr, nullptr);
   } else {
-    set_smem(k_list_keys<false, false, kListThreads>, sm);
-    k_list_keys<false, false, kListThreads><<<grid, kListThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent, cap,
-                                                             counter, max_list, status, nullptr, 0, nullptr, nullptr);
+    set_smem(k_list_win<false, false, kWinThreads>, sm);
+    k_list_win<false, false, kWinThreads><<<grid, kWinThreads, sm, s>>>(hi, x, cs, N, g, ta, band, rows, tile_list, ent,
+                                                                        cap, counter, max_list, status, nullptr, 0,
+                                                                        nullptr, nullptr);
   }
 #undef LJ_LIST_LAUNCH
 }
@@ -2417,7 +2142,7 @@ int launch_adjoint_tile(int precision, const void* pos, const uint32_t* cs, int6
 
 
 // ---- batched replicas -----------------------------------------------------------------------
-size_t batch_list_smem_bytes(const TileArgs& caps) { return key_list_layout(caps).total; }
+size_t batch_list_smem_bytes(const TileArgs& caps) { return win_layout(caps).total; }
 size_t batch_force_smem_bytes(const TileArgs& caps) { return align16(tile_layout(caps, true, true, false).total); }
 
 void launch_tile_sizes_batch(const uint32_t* cs, TileArgs caps, const ReplicaGeo* reps, int R,
@@ -2432,11 +2157,12 @@ void launch_list_batch(const float4* hi, const double* x, const uint32_t* cs, in
                        ListBand band, uint2* rows, uint2* tile_list, uint16_t* ent, uint64_t cap,
                        unsigned long long* counter, unsigned int* max_list, int32_t* status, const ReplicaGeo* reps,
                        int R, const int32_t* tile_rep, const int* pred, cudaStream_t s) {
-  const size_t sm = key_list_layout(caps).total;
-  set_smem(k_list_keys<false, true, kListThreads>, sm);
-  const int grid = tile_grid(caps, resident_per_sm(k_list_keys<false, true, kListThreads>, kListThreads, sm));
-  k_list_keys<false, true, kListThreads><<<grid, kListThreads, sm, s>>>(hi, x, cs, N, g, caps, band, rows, tile_list, ent, cap,
-                                                          counter, max_list, status, reps, R, pred, tile_rep);
+  const size_t sm = win_layout(caps).total;
+  set_smem(k_list_win<false, true, kWinThreads>, sm);
+  const int grid = tile_grid(caps, resident_per_sm(k_list_win<false, true, kWinThreads>, kWinThreads, sm));
+  k_list_win<false, true, kWinThreads><<<grid, kWinThreads, sm, s>>>(hi, x, cs, N, g, caps, band, rows, tile_list, ent,
+                                                                     cap, counter, max_list, status, reps, R, pred,
+                                                                     tile_rep);
 }
 
 int launch_force_batch(int lanes, int energy, const uint4* xq, const uint32_t* cs, int64_t N,
