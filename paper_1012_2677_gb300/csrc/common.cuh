@@ -191,6 +191,31 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// Cell labelling without the FP64 pipe beyond the subtraction and the product.  cmp_ge_d: a >= b
+// for a finite FP64 value b > 0 (the two's-complement order of the bit patterns matches the FP64
+// order there; a NaN compares as at least b).  floor_to_int: floor(t) for 0 <= t < 2^31 from the bit
+// pattern (mantissa shifted by the exponent), -1 for any t < 0 (also -0) and INT_MAX for t >= 2^31,
+// infinities and NaN: the callers clamp to [0, n - 1], where these agree with floor.
+__device__ __forceinline__ bool cmp_ge_d(double a, double b) {
+  return __double_as_longlong(a) >= __double_as_longlong(b);
+}
+__device__ __forceinline__ int floor_to_int(double t) {
+  const long long b = __double_as_longlong(t);
+  if (b < 0) return -1;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < 0) return 0;
+  if (e > 30) return 0x7fffffff;
+  const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffULL) | 0x10000000000000ULL;
+  return (int)(m >> (52 - e));
+}
+
+// 4-byte asynchronous copy global -> shared (cp.async, no register staging); the issuing thread's
+// copies have landed after cp_async_wait_all.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // try_wait with a suspend-time hint: the thread may sleep up to `hint_ns` nanoseconds inside the
 // instruction until the phase completes, instead of spinning on issue slots.
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity, uint32_t hint_ns = 1000000u) {

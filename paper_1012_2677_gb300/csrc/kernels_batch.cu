@@ -29,15 +29,16 @@ __global__ void k_wrap_label_batch(double* __restrict__ x, int32_t* __restrict__
     for (int k = 0; k < 3; ++k) {
       double xs = x[k * N + i];
       if (!finite_d(xs)) bad = true;
-      if (xs >= offset + g.L) {
+      if (cmp_ge_d(xs, offset + g.L)) {
         xs -= g.L;
         img[k * N + i] += 1;
-      } else if (xs < offset) {
+        x[k * N + i] = xs;
+      } else if (!cmp_ge_d(xs, offset)) {
         xs += g.L;
         img[k * N + i] -= 1;
+        x[k * N + i] = xs;
       }
-      x[k * N + i] = xs;
-      int ck = (int)floor((xs - offset) * g.inv_h);
+      int ck = floor_to_int((xs - offset) * g.inv_h);
       ck = ck < 0 ? 0 : (ck >= g.n ? g.n - 1 : ck);
       c[k] = ck;
     }

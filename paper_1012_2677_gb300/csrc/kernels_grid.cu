@@ -20,6 +20,7 @@ __global__ void k_wrap_label(double* __restrict__ x, int32_t* __restrict__ img, 
                              int32_t* __restrict__ status) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const double top = g.offset + g.L;
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < N; i0 += stride) {
     const int64_t i = i0 + lane;
     uint32_t cell = 0xffffffffu;  // the warp's tail (no particle) takes part in the match only
@@ -29,16 +30,17 @@ __global__ void k_wrap_label(double* __restrict__ x, int32_t* __restrict__ img, 
       for (int k = 0; k < 3; ++k) {
         double xs = x[k * N + i];
         if (!finite_d(xs)) bad = true;
-        if (xs >= g.offset + g.L) {
+        if (cmp_ge_d(xs, top)) {
           xs -= g.L;
           img[k * N + i] += 1;
-        } else if (xs < g.offset) {
+          x[k * N + i] = xs;
+        } else if (!cmp_ge_d(xs, g.offset)) {
           xs += g.L;
           img[k * N + i] -= 1;
+          x[k * N + i] = xs;
         }
-        x[k * N + i] = xs;
         const double rel = xs - g.offset;  // exact: both in [offset/2, 2 offset)
-        int ck = (int)floor(rel * g.inv_h);
+        int ck = floor_to_int(rel * g.inv_h);
         ck = ck < 0 ? 0 : (ck >= g.n ? g.n - 1 : ck);
         c[k] = ck;
       }
@@ -195,77 +197,44 @@ void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* per
 
 // ---------------------------------------------------------------------------------------------
 // Gathers: out[k] = in[perm[k]].
-__global__ void k_gather_f64x3(const double* __restrict__ in, double* __restrict__ out,
-                               const uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
+
+// The particle state in one pass (perm read once): positions and velocities (FP64 x 3), ids,
+// image counts (3) and, FB = 16 or 32, the last forces (float4 or double4 records).
+template <int FB>
+__global__ void k_gather_state(const uint32_t* __restrict__ perm, int64_t N, const double* __restrict__ x,
+                               double* __restrict__ x2, const double* __restrict__ v, double* __restrict__ v2,
+                               const int32_t* __restrict__ id, int32_t* __restrict__ id2,
+                               const int32_t* __restrict__ img, int32_t* __restrict__ img2,
+                               const uint4* __restrict__ f, uint4* __restrict__ f2, const int* __restrict__ pred) {
   if (pred && !*pred) return;  // predicated: skipped unless the flag is set
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t p = perm[k];
-    out[k] = in[p];
-    out[N + k] = in[N + p];
-    out[2 * N + k] = in[2 * N + p];
+    const size_t p = perm[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x2[c * N + k] = x[c * N + p];
+      v2[c * N + k] = v[c * N + p];
+      img2[c * N + k] = img[c * N + p];
+    }
+    id2[k] = id[p];
+    if (FB == 16) f2[k] = f[p];
+    if (FB == 32) {
+      f2[2 * k] = f[2 * p];
+      f2[2 * k + 1] = f[2 * p + 1];
+    }
   }
 }
-void launch_gather_f64x3(const double* in, double* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
-  k_gather_f64x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N, pred);
+void launch_gather_state(const uint32_t* perm, int64_t N, const double* x, double* x2, const double* v, double* v2,
+                         const int32_t* id, int32_t* id2, const int32_t* img, int32_t* img2, const void* f, void* f2,
+                         int fbytes, cudaStream_t s, const int* pred) {
+  const uint4* fi = (const uint4*)f;
+  uint4* fo = (uint4*)f2;
+  if (fbytes == 16)
+    k_gather_state<16><<<grid_for(N, 256), 256, 0, s>>>(perm, N, x, x2, v, v2, id, id2, img, img2, fi, fo, pred);
+  else if (fbytes == 32)
+    k_gather_state<32><<<grid_for(N, 256), 256, 0, s>>>(perm, N, x, x2, v, v2, id, id2, img, img2, fi, fo, pred);
+  else
+    k_gather_state<0><<<grid_for(N, 256), 256, 0, s>>>(perm, N, x, x2, v, v2, id, id2, img, img2, fi, fo, pred);
 }
-
-__global__ void k_gather_i32x3(const int32_t* __restrict__ in, int32_t* __restrict__ out,
-                               const uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
-  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t p = perm[k];
-    out[k] = in[p];
-    out[N + k] = in[N + p];
-    out[2 * N + k] = in[2 * N + p];
-  }
-}
-void launch_gather_i32x3(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
-  k_gather_i32x3<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N, pred);
-}
-
-__global__ void k_gather_i32(const int32_t* __restrict__ in, int32_t* __restrict__ out,
-                             const uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
-  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = in[perm[k]];
-}
-void launch_gather_i32(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
-  k_gather_i32<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N, pred);
-}
-
-__global__ void k_gather_u32(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                             const uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {
-  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = in[perm[k]];
-}
-void launch_gather_u32(const uint32_t* in, uint32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
-  k_gather_u32<<<grid_for(N, 256), 256, 0, s>>>(in, out, perm, N, pred);
-}
-
-__global__ void k_gather_16B(const uint4* __restrict__ in, uint4* __restrict__ out, const uint32_t* __restrict__ perm,
-                             int64_t N, const int* __restrict__ pred) {
-  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = in[perm[k]];
-}
-void launch_gather_16B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
-  k_gather_16B<<<grid_for(N, 256), 256, 0, s>>>((const uint4*)in, (uint4*)out, perm, N, pred);
-}
-
-__global__ void k_gather_32B(const uint4* __restrict__ in, uint4* __restrict__ out, const uint32_t* __restrict__ perm,
-                             int64_t N, const int* __restrict__ pred) {
-  if (pred && !*pred) return;  // predicated: skipped unless the flag is set
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t p = perm[k];
-    out[2 * k] = in[2 * (size_t)p];
-    out[2 * k + 1] = in[2 * (size_t)p + 1];
-  }
-}
-void launch_gather_32B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s, const int* pred) {
-  k_gather_32B<<<grid_for(N, 256), 256, 0, s>>>((const uint4*)in, (uint4*)out, perm, N, pred);
-}
-
 // ---------------------------------------------------------------------------------------------
 // Copies between the sorted SoA state and caller-order AoS (x[3 id + k]).
 __global__ void k_scatter_back_f64x3(const double* __restrict__ in, double* __restrict__ out,

@@ -198,6 +198,65 @@ __device__ __forceinline__ bool tile_prepare_pf(const TilePrefetch& pf, const Ti
   return run <= ta.max_staged;
 }
 
+// Cell bounds of a tile's staged cells copied asynchronously into shared memory (one warp; lane m
+// takes cell m of every column).  Nothing waits for the loads until tile_prepare_async.
+__device__ __forceinline__ void tile_prefetch_async(const TileInfo& ti, const TileArgs& ta,
+                                                    const uint32_t* __restrict__ cs, uint32_t* pa, uint32_t* pb,
+                                                    int lane) {
+  const int ncol = ti.Tp + 2;
+  if (lane >= ncol) return;
+  int sz;
+  const uint32_t Z = (uint32_t)wrap_cell(ti.z0 - 1 + lane, ta.n, sz);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    int sx, sy;
+    const uint32_t X = (uint32_t)wrap_cell(ti.cx + k / 3 - 1, ta.n, sx);
+    const uint32_t Y = (uint32_t)wrap_cell(ti.cy + k % 3 - 1, ta.n, sy);
+    const uint32_t c = (X * (uint32_t)ta.n + Y) * (uint32_t)ta.n + Z;
+    cp_async4(pa + k * ncol + lane, cs + c);
+    cp_async4(pb + k * ncol + lane, cs + c + 1);
+  }
+}
+
+// The bookkeeping of stage_offsets done by one warp from the bounds of tile_prefetch_async.
+__device__ __forceinline__ bool tile_prepare_async(const TileInfo& ti, const uint32_t* pa, const uint32_t* pb,
+                                                   const TileArgs& ta, TileShared& S, int lane) {
+  cp_async_wait_all();
+  __syncwarp();
+  const int ncol = ti.Tp + 2, ncell = 9 * ncol;
+  int run = 0;
+  for (int base = 0; base < ncell; base += 32) {
+    const int q = base + lane;
+    int inc = 0;
+    if (q < ncell) {
+      const uint32_t a = pa[q];
+      inc = (int)(pb[q] - a);
+      S.g0[q] = (int)a;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (q < ncell) S.offq[q + 1] = run + inc;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();  // the bounds are read before the next prefetch overwrites them
+  if (lane == 0) {
+    S.offq[0] = 0;
+    S.ncol = ncol;
+    S.ncell = ncell;
+    S.total = run;
+    S.own0 = S.offq[4 * ncol + 1];
+    S.own1 = S.offq[4 * ncol + ti.Tp + 1];
+    S.gown0 = S.g0[4 * ncol + 1];
+    S.list_base = 0;
+    S.list_len = 0;
+  }
+  __syncwarp();
+  return run <= ta.max_staged;
+}
+
 // Staged cell of staged slot s: the largest q with offq[q] <= s.
 __device__ __forceinline__ int slot_cell(const TileShared& S, int s) {
   int lo = 0, hi = S.ncell - 1;
@@ -638,6 +697,7 @@ struct WinLayout {
   size_t cnt;    // uint16 [ngrp * 9 * 32]: per (key, column) count, then its offset in the key's row
   size_t kst;    // int [max_own]: row start in the segment; then int [max_own]: row length
   size_t ib;     // int [ngrp * 9]: first pool word of each item (-1: tested again when written)
+  size_t gtot;   // int [ngrp]: entries of each group of 32 keys
   size_t mask;   // uint32 [pool_words * 32]
   int ngrp, pool_words, seg_cap;
   size_t total;
@@ -658,6 +718,8 @@ __host__ __device__ __forceinline__ WinLayout win_layout(const TileArgs& ta) {
   o += align16((size_t)ta.max_own * 8);
   W.ib = o;
   o += align16((size_t)W.ngrp * 9 * 4);
+  W.gtot = o;
+  o += align16((size_t)W.ngrp * 4);
   W.pool_words = W.ngrp * 9 * kWinPoolPerItem + 8;
   W.mask = o;
   o += (size_t)W.pool_words * 32 * 4;
@@ -746,12 +808,14 @@ __global__ void __launch_bounds__(NT, kWinCtas)
                unsigned long long* __restrict__ counter, unsigned int* __restrict__ max_list,
                int32_t* __restrict__ status, const ReplicaGeo* __restrict__ reps, int R,
                const int* __restrict__ pred, const int32_t* __restrict__ tile_rep) {
+  static_assert(NT >= 64, "warp 0 prepares the next tile while the others count");
   if (pred && !*pred) return;  // predicated (batched rebuild inside a graph)
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ TileShared S;
+  __shared__ TileShared Sb[2];  // bookkeeping of the current tile and of the next one
   __shared__ __align__(8) uint64_t bar;
-  __shared__ unsigned int s_base, s_padded;
-  __shared__ int s_ok, s_staged_ok, s_pool, s_retest;
+  __shared__ unsigned int s_base;
+  __shared__ int s_fits, s_pool, s_retest;
+  __shared__ int s_ready[2];  // the buffer's tile fits the capacities
   constexpr int kNW = NT / 32;
   const WinLayout W = win_layout(ta_in);
   TileLayout L;  // the staging helpers' view: hi records (sorted indices in w)
@@ -764,6 +828,7 @@ __global__ void __launch_bounds__(NT, kWinCtas)
   int* s_kst = (int*)(smem + W.kst);
   int* s_len = s_kst + ta_in.max_own;
   int* s_ib = (int*)(smem + W.ib);
+  int* s_gtot = (int*)(smem + W.gtot);
   uint32_t* s_mask = (uint32_t*)(smem + W.mask);
   uint16_t* s_seg = (uint16_t*)(smem + W.pos);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -772,8 +837,9 @@ __global__ void __launch_bounds__(NT, kWinCtas)
     mbar_init(&bar, 1);
     fence_proxy_async_smem();
   }
-  TilePrefetch pf;  // warp 0: the cell bounds of the CTA's next tile, loaded a tile ahead
-  auto prefetch = [&](int64_t tp) {
+  __shared__ uint32_t s_pfa[kMaxCells], s_pfb[kMaxCells];  // cell bounds of the tile being prefetched
+  TileInfo pf_ti;  // warp 0: that tile
+  auto prefetch = [&](int64_t tp) {  // warp 0: a tile's cell bounds, copied a tile ahead of their use
     TileArgs tap = ta_in;
     Geom gp = g_in;
     const uint32_t* csp = cs_in;
@@ -784,12 +850,23 @@ __global__ void __launch_bounds__(NT, kWinCtas)
       csp = cs_in + rg.cell_base;
       tlp = tp - rg.tile_base;
     }
-    tile_prefetch(tlp, tap, csp, nullptr, pf, lane);
+    pf_ti = tile_info(tlp, tap);
+    tile_prefetch_async(pf_ti, tap, csp, s_pfa, s_pfb, lane);
   };
-  if (warp == 0 && blockIdx.x < ta_in.ntiles) prefetch(blockIdx.x);
+  auto prepare = [&](int b) {  // warp 0: buffer b from the prefetched bounds
+    const bool okp = tile_prepare_async(pf_ti, s_pfa, s_pfb, ta_in, Sb[b], lane);
+    if (lane == 0) s_ready[b] = (okp && Sb[b].own1 - Sb[b].own0 <= ta_in.max_own) ? 1 : 0;
+  };
+  if (warp == 0 && blockIdx.x < ta_in.ntiles) {
+    prefetch(blockIdx.x);
+    prepare(0);
+    if (blockIdx.x + gridDim.x < ta_in.ntiles) prefetch(blockIdx.x + gridDim.x);
+  }
   __syncthreads();
 
-  for (int64_t t = blockIdx.x; t < ta_in.ntiles; t += gridDim.x) {
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < ta_in.ntiles; t += gridDim.x, buf ^= 1) {
+    TileShared& S = Sb[buf];
     TileArgs ta = ta_in;
     Geom g = g_in;
     int64_t tl = t;
@@ -799,21 +876,21 @@ __global__ void __launch_bounds__(NT, kWinCtas)
       tl = t - rg.tile_base;
     }
     const TileInfo ti = tile_info(tl, ta);
-    if (warp == 0) {
-      const bool okp = tile_prepare_pf(pf, ta, S, lane);
-      if (lane == 0) {
-        const int n_own_p = S.own1 - S.own0;
-        s_staged_ok = (okp && n_own_p <= ta.max_own) ? 1 : 0;
-        s_pool = 0;
-        s_retest = 0;
+    auto prepare_next = [&]() {  // warp 0
+      if (t + gridDim.x < ta_in.ntiles) {
+        prepare(buf ^ 1);
+        if (t + 2 * (int64_t)gridDim.x < ta_in.ntiles) prefetch(t + 2 * (int64_t)gridDim.x);
       }
-      if (t + gridDim.x < ta_in.ntiles) prefetch(t + gridDim.x);
-    }
-    __syncthreads();
-    if (!s_staged_ok) {  // sizing inconsistency: record and skip the tile
+    };
+    if (!s_ready[buf]) {  // sizing inconsistency: record and skip the tile
       if (threadIdx.x == 0) atomicOr(status, LJ_ST_CELL_RANGE);
+      if (warp == 0) prepare_next();
       __syncthreads();
       continue;
+    }
+    if (threadIdx.x == 0) {
+      s_pool = 0;
+      s_retest = 0;
     }
     const int n_own = S.own1 - S.own0, ncol = S.ncol;
     // own cell of every key (ordered before the staged records by the barrier that ends the wait)
@@ -860,8 +937,11 @@ __global__ void __launch_bounds__(NT, kWinCtas)
       s_cnt[item * 32 + lane] = (uint16_t)cnt;
     }
     __syncthreads();
-    // phase B: each key's column offsets within its row and its row length (a warp per group)
-    for (int gq = warp; gq < ngrp; gq += kNW) {
+    // phase B (warps 1..): each key's column offsets within its row, its row length and its row's
+    // place within its group of 32 keys; the group's entries.  Warp 0 meanwhile takes the next
+    // tile's bookkeeping.
+    if (warp == 0) prepare_next();
+    for (int gq = warp - 1; gq >= 0 && gq < ngrp; gq += kNW - 1) {
       int run = 0;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
@@ -871,96 +951,98 @@ __global__ void __launch_bounds__(NT, kWinCtas)
         run += v;
       }
       const int o = 32 * gq + lane;
-      if (o < n_own) s_len[o] = run;
-    }
-    __syncthreads();
-    // phase C: exclusive prefix of the rows; one atomic reserves the tile's padded segment
-    if (warp == 0) {
-      unsigned run = 0;
-      for (int b0 = 0; b0 < n_own; b0 += 32) {
-        const int o = b0 + lane;
-        const unsigned v = o < n_own ? (unsigned)s_len[o] : 0u;
-        unsigned inc = v;
+      const int v = o < n_own ? run : 0;
+      int inc = v;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const unsigned y = __shfl_up_sync(0xffffffffu, inc, d);
-          if (lane >= d) inc += y;
-        }
-        if (o < n_own) s_kst[o] = (int)(run + inc - v);
-        run += __shfl_sync(0xffffffffu, inc, 31);
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
       }
-      if (lane == 0) {
-        const unsigned padded = (run + 7u) & ~7u;
-        const unsigned long long b = atomicAdd(counter, (unsigned long long)padded);
-        atomicAdd(counter + 1, (unsigned long long)run);
-        const bool fits = b + padded <= cap;
-        s_base = (unsigned)b;
-        s_padded = padded;
-        s_ok = fits;
-        tile_list[t] = fits ? make_uint2((unsigned)b, padded) : make_uint2(0u, 0u);
-        atomicMax(max_list, padded);
-        if (BATCHED && !fits) atomicOr(status, LJ_ST_LIST_OVERFLOW);  // no host retry inside a graph
+      if (o < n_own) {
+        s_len[o] = run;
+        s_kst[o] = inc - v;
       }
+      if (lane == 31) s_gtot[gq] = inc;
     }
     __syncthreads();
-    const bool ok = s_ok != 0;
-    for (int o = threadIdx.x; o < n_own; o += NT)
-      rows[S.gown0 + o] = ok ? make_uint2(s_base + (unsigned)s_kst[o], (unsigned)s_len[o]) : make_uint2(0u, 0u);
-    if (ok) {
-      // phase D: the entries of every item from its bits (or tested again), in row order; staged
-      // over the positions (no longer needed unless an item is tested again) and copied out, or
-      // written to global memory directly
-      const bool staged = s_padded <= (unsigned)W.seg_cap && !s_retest;
-      auto write_items = [&](auto in_shared) {
-        uint16_t* dst = decltype(in_shared)::value ? s_seg : ent + s_base;
-        for (int item = warp; item < nitem; item += kNW) {
-          const int gq = item / 9, k = item - 9 * gq;
-          const int o = 32 * gq + lane;
-          const bool valid = o < n_own;
-          const int oc = valid ? o : n_own - 1;
-          const int m = s_cell[oc];
-          const int j0 = S.offq[k * ncol + m - 1];
-          int len = valid ? S.offq[k * ncol + m + 2] - j0 : 0;
-          if (HALF && win_column_order(ti, ta.n, k) < 0) len = 0;
-          int p = valid ? s_kst[o] + s_cnt[item * 32 + lane] : 0;
-          const int base = s_ib[item];
-          if (base >= 0) {
-            for (int w = 0; 32 * w < len; ++w) {
-              uint32_t bits = s_mask[(base + w) * 32 + lane];
-              while (bits) {
-                const int u = __ffs(bits) - 1;
-                bits &= bits - 1;
-                dst[p++] = (uint16_t)(j0 + 32 * w + u);
-              }
+    // the tile's entries (every thread); one atomic reserves its segment, padded to 8 entries
+    int total = 0;
+    for (int gq = 0; gq < ngrp; ++gq) total += s_gtot[gq];
+    const unsigned padded = ((unsigned)total + 7u) & ~7u;
+    const bool staged = padded <= (unsigned)W.seg_cap && !s_retest;
+    if (threadIdx.x == 0) {
+      const unsigned long long b = atomicAdd(counter, (unsigned long long)padded);
+      atomicAdd(counter + 1, (unsigned long long)total);
+      const bool fits = b + padded <= cap;
+      s_base = (unsigned)b;
+      s_fits = fits;
+      tile_list[t] = fits ? make_uint2((unsigned)b, padded) : make_uint2(0u, 0u);
+      atomicMax(max_list, padded);
+      if (BATCHED && !fits) atomicOr(status, LJ_ST_LIST_OVERFLOW);  // no host retry inside a graph
+    }
+    // phase D: the entries of every item from its bits (or tested again), in row order; staged
+    // over the positions (no longer needed unless an item is tested again) and copied out, or
+    // written to global memory directly once the segment's place is known
+    auto write_items = [&](auto in_shared) {
+      uint16_t* dst = decltype(in_shared)::value ? s_seg : ent + s_base;
+      for (int item = warp; item < nitem; item += kNW) {
+        const int gq = item / 9, k = item - 9 * gq;
+        const int o = 32 * gq + lane;
+        const bool valid = o < n_own;
+        const int oc = valid ? o : n_own - 1;
+        const int m = s_cell[oc];
+        const int j0 = S.offq[k * ncol + m - 1];
+        int len = valid ? S.offq[k * ncol + m + 2] - j0 : 0;
+        if (HALF && win_column_order(ti, ta.n, k) < 0) len = 0;
+        int gbase = 0;
+        for (int q = 0; q < gq; ++q) gbase += s_gtot[q];
+        int p = valid ? gbase + s_kst[o] + s_cnt[item * 32 + lane] : 0;
+        const int base = s_ib[item];
+        if (base >= 0) {
+          for (int w = 0; 32 * w < len; ++w) {
+            uint32_t bits = s_mask[(base + w) * 32 + lane];
+            while (bits) {
+              const int u = __ffs(bits) - 1;
+              bits &= bits - 1;
+              dst[p++] = (uint16_t)(j0 + 32 * w + u);
             }
-          } else if (!decltype(in_shared)::value) {
-            const int l = S.own0 + oc;
-            const float4 pi = sh_pos[l];
-            const int gi = __float_as_int(pi.w);
-            const int maxlen = __reduce_max_sync(0xffffffffu, len);
-            const int nw = (maxlen + 31) >> 5;
-            for (int w = 0; w < nw; ++w) {
-              const int rem = len - 32 * w;
-              uint32_t bits = win_word_k<HALF>(k == 4, sh_pos, x, N, g, band, rem > 0 ? j0 + 32 * w : 0, rem,
-                                               (maxlen - 32 * w + 7) >> 3, l, gi, pi);
-              while (bits) {
-                const int u = __ffs(bits) - 1;
-                bits &= bits - 1;
-                dst[p++] = (uint16_t)(j0 + 32 * w + u);
-              }
+          }
+        } else if (!decltype(in_shared)::value) {
+          const int l = S.own0 + oc;
+          const float4 pi = sh_pos[l];
+          const int gi = __float_as_int(pi.w);
+          const int maxlen = __reduce_max_sync(0xffffffffu, len);
+          const int nw = (maxlen + 31) >> 5;
+          for (int w = 0; w < nw; ++w) {
+            const int rem = len - 32 * w;
+            uint32_t bits = win_word_k<HALF>(k == 4, sh_pos, x, N, g, band, rem > 0 ? j0 + 32 * w : 0, rem,
+                                             (maxlen - 32 * w + 7) >> 3, l, gi, pi);
+            while (bits) {
+              const int u = __ffs(bits) - 1;
+              bits &= bits - 1;
+              dst[p++] = (uint16_t)(j0 + 32 * w + u);
             }
           }
         }
-      };
-      if (staged) {
-        write_items(std::true_type());
-        __syncthreads();
-        const uint4* src = (const uint4*)s_seg;
-        uint4* out = (uint4*)(ent + s_base);
-        for (unsigned w = threadIdx.x; w < s_padded / 8u; w += NT) out[w] = src[w];
-      } else {
-        write_items(std::false_type());
       }
+    };
+    if (staged) {
+      write_items(std::true_type());
+      __syncthreads();
+    } else {
+      __syncthreads();
+      if (s_fits) write_items(std::false_type());
+    }
+    const bool fits = s_fits != 0;
+    for (int o = threadIdx.x; o < n_own; o += NT) {
+      int gbase = 0;
+      for (int q = 0; q < (o >> 5); ++q) gbase += s_gtot[q];
+      rows[S.gown0 + o] = fits ? make_uint2(s_base + (unsigned)(gbase + s_kst[o]), (unsigned)s_len[o]) : make_uint2(0u, 0u);
+    }
+    if (staged && fits) {
+      const uint4* src = (const uint4*)s_seg;
+      uint4* out = (uint4*)(ent + s_base);
+      for (unsigned w = threadIdx.x; w < padded / 8u; w += NT) out[w] = src[w];
     }
     // the positions' bytes were read and written by the generic proxy; the next tile's bulk copies
     // (async proxy) write them

@@ -51,7 +51,7 @@ struct ljmd_sys {
   dvec4* pos64 = nullptr; // FP64 form: position copies for the force and adjoint kernels
   void* ref = nullptr;
   int32_t *id = nullptr, *id_alt = nullptr, *img = nullptr, *img_alt = nullptr;
-  uint32_t *cell_of = nullptr, *cell_alt = nullptr, *perm = nullptr;
+  uint32_t *cell_of = nullptr, *perm = nullptr;
   uint32_t *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
   uint2* rows = nullptr;        // per particle: (start, length) of its row in ent
   uint2* tile_list = nullptr;   // per tile: (start, length) of its segment of ent
@@ -142,7 +142,7 @@ static int dalloc_t(ljmd_sys* sys, T** p, size_t count) {
 
 static void free_all(ljmd_sys* s) {
   void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->xq, s->pos64, s->ref, s->id,
-                  s->id_alt, s->img, s->img_alt, s->cell_of, s->cell_alt, s->perm, s->cell_count, s->cell_start,
+                  s->id_alt, s->img, s->img_alt, s->cell_of, s->perm, s->cell_count, s->cell_start,
                   s->cell_fill, s->rows, s->tile_list, s->ent, s->scan_tmp, s->part_force, s->part_ke,
                   s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_ctl, s->d_total64, s->d_sizes,
                   s->adj_w, s->adj_hw, s->adj_f, s->part_adj, s->d_adj, s->xref64, s->ldc_list, s->d_ldc};
@@ -375,7 +375,6 @@ static int ensure_particles(ljmd_sys* s, int64_t n) {
   TRY(dalloc_t(s, &s->img, 3 * n));
   TRY(dalloc_t(s, &s->img_alt, 3 * n));
   TRY(dalloc_t(s, &s->cell_of, n));
-  TRY(dalloc_t(s, &s->cell_alt, n));
   TRY(dalloc_t(s, &s->perm, n));
   TRY(dalloc_t(s, &s->rows, n + 2));  // +2: aligned bulk copies of a tile's rows may read past the end
   s->cap_n = n;
@@ -549,8 +548,8 @@ static int rebuild(ljmd_sys* s) {
   cudaStream_t st = s->st;
   TRY(ensure_cells(s));
   PhaseTimer timer(s, PH_REBUILD);
-  // wrap_label, scatter, cell_order, 6 gathers, shadow (+ the scan, tile sizing and list below)
-  s->launches += 10;
+  // wrap_label, scatter, cell_order, gather, shadow (+ the scan, tile sizing and list below)
+  s->launches += 5;
   CK(cudaMemsetAsync(s->cell_count, 0, sizeof(uint32_t) * s->ncells, st));
   launch_wrap_label(s->x, s->img, N, s->g, s->cell_of, s->cell_count, s->d_status, st);
   CKL();
@@ -559,19 +558,13 @@ static int rebuild(ljmd_sys* s) {
   CK(cudaMemsetAsync(s->cell_fill, 0, sizeof(uint32_t) * s->ncells, st));
   launch_scatter(s->cell_of, s->cell_start, s->cell_fill, s->perm, N, st);
   launch_cell_order(s->cell_start, s->ncells, s->perm, s->id, st);
-  launch_gather_f64x3(s->x, s->x_alt, s->perm, N, st);
-  launch_gather_f64x3(s->v, s->v_alt, s->perm, N, st);
-  launch_gather_i32(s->id, s->id_alt, s->perm, N, st);
-  launch_gather_i32x3(s->img, s->img_alt, s->perm, N, st);
-  launch_gather_u32(s->cell_of, s->cell_alt, s->perm, N, st);
-  if (s->precision == LJ_MIXED) launch_gather_16B(s->f, s->f_alt, s->perm, N, st);
-  else launch_gather_32B(s->f, s->f_alt, s->perm, N, st);
+  launch_gather_state(s->perm, N, s->x, s->x_alt, s->v, s->v_alt, s->id, s->id_alt, s->img, s->img_alt, s->f,
+                      s->f_alt, s->precision == LJ_MIXED ? 16 : 32, st, nullptr);
   CKL();
   std::swap(s->x, s->x_alt);
   std::swap(s->v, s->v_alt);
   std::swap(s->id, s->id_alt);
   std::swap(s->img, s->img_alt);
-  std::swap(s->cell_of, s->cell_alt);
   std::swap(s->f, s->f_alt);
   launch_shadow_all(s->x, N, s->precision == LJ_MIXED, s->g.qk, s->hi, s->xq, s->pos64, s->ref, st);
   CKL();

@@ -288,10 +288,8 @@ static int enqueue_rebuild(ljmd_batch* b, const int* pred) {
   launch_zero_words(b->cell_fill, sizeof(uint32_t) * b->ncells, pred, st);
   launch_scatter(b->cell_of, b->cell_start, b->cell_fill, b->perm, N, st, pred);
   launch_cell_order(b->cell_start, b->ncells, b->perm, b->id, st, pred);
-  launch_gather_f64x3(b->x, b->x_alt, b->perm, N, st, pred);
-  launch_gather_f64x3(b->v, b->v_alt, b->perm, N, st, pred);
-  launch_gather_i32(b->id, b->id_alt, b->perm, N, st, pred);
-  launch_gather_i32x3(b->img, b->img_alt, b->perm, N, st, pred);
+  launch_gather_state(b->perm, N, b->x, b->x_alt, b->v, b->v_alt, b->id, b->id_alt, b->img, b->img_alt, nullptr,
+                      nullptr, 0, st, pred);
   launch_copy_words(b->x_alt, b->x, 24 * N, pred, st);
   launch_copy_words(b->v_alt, b->v, 24 * N, pred, st);
   launch_copy_words(b->id_alt, b->id, 4 * N, pred, st);
@@ -301,7 +299,7 @@ static int enqueue_rebuild(ljmd_batch* b, const int* pred) {
   launch_zero_words(b->sizes, 4 * sizeof(unsigned int), pred, st);
   launch_list_batch(b->hi, b->x, b->cell_start, N, b->g0, b->caps, b->band, b->rows, b->tile_list, b->ent,
                     (uint64_t)b->ent_cap, b->counter, b->sizes + 3, b->status, b->reps, b->R, b->tile_rep, pred, st);
-  b->launches += 17;
+  b->launches += 14;
   BKL();
   return LJ_OK;
 }

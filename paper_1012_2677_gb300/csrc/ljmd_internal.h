@@ -92,18 +92,9 @@ void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_
 void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* perm, const int32_t* id,
                        cudaStream_t s,
     const int* pred = nullptr);
-void launch_gather_f64x3(const double* in, double* out, const uint32_t* perm, int64_t N, cudaStream_t s,
-    const int* pred = nullptr);
-void launch_gather_i32x3(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s,
-    const int* pred = nullptr);
-void launch_gather_i32(const int32_t* in, int32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s,
-    const int* pred = nullptr);
-void launch_gather_u32(const uint32_t* in, uint32_t* out, const uint32_t* perm, int64_t N, cudaStream_t s,
-    const int* pred = nullptr);
-void launch_gather_16B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s,
-    const int* pred = nullptr);
-void launch_gather_32B(const void* in, void* out, const uint32_t* perm, int64_t N, cudaStream_t s,
-    const int* pred = nullptr);
+void launch_gather_state(const uint32_t* perm, int64_t N, const double* x, double* x2, const double* v, double* v2,
+                         const int32_t* id, int32_t* id2, const int32_t* img, int32_t* img2, const void* f, void* f2,
+                         int fbytes, cudaStream_t s, const int* pred);
 void launch_scatter_back_f64x3(const double* in, double* out_idorder, const int32_t* id, int64_t N,
                                double sub, cudaStream_t s);
 void launch_scatter_back_f32x4_to_f64x3(const float4* in, double* out, const int32_t* id, int64_t N,
