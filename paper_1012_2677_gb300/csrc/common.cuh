@@ -65,6 +65,46 @@ __device__ __forceinline__ float block_max(float v, float* sh) {
   return t;
 }
 
+// The energy record of one state, by one block (blockDim.x a multiple of 32): pe and virial from the
+// force kernel's per-block partials pv (scaled by pe_scale: 1/2 for a full list, where every pair
+// is visited twice), ke from the integrator's partials kp, each summed in a fixed order; thread 0
+// writes energies[0..3] = (pe, ke, virial, step) and appends (step, pe, ke, vir) to the log if there
+// is room.  The partials are read past L1 (they may have been written by other blocks of the same
+// launch).
+__device__ __forceinline__ void energy_record_block(const double* pv, int nbf, const double* kp, int nbi,
+                                                    double pe_scale, double* energies, double* log, int64_t cap,
+                                                    int64_t* count, double step, double* sh) {
+  double pe = 0.0, vir = 0.0, ke = 0.0;
+  for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+    pe += __ldcg(pv + 2 * (size_t)b);
+    vir += __ldcg(pv + 2 * (size_t)b + 1);
+  }
+  for (int b = threadIdx.x; b < nbi; b += blockDim.x) ke += __ldcg(kp + b);
+  pe = block_sum(pe, sh);
+  __syncthreads();
+  vir = block_sum(vir, sh);
+  __syncthreads();
+  ke = block_sum(ke, sh);
+  if (threadIdx.x == 0) {
+    pe *= pe_scale;
+    vir *= pe_scale;
+    energies[0] = pe;
+    energies[1] = ke;
+    energies[2] = vir;
+    energies[3] = step;
+    if (log != nullptr) {
+      const int64_t k = *count;
+      if (k < cap) {
+        log[4 * k + 0] = step;
+        log[4 * k + 1] = pe;
+        log[4 * k + 2] = ke;
+        log[4 * k + 3] = vir;
+      }
+      *count = k + 1;
+    }
+  }
+}
+
 __device__ __forceinline__ bool finite_d(double v) {
   return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
 }

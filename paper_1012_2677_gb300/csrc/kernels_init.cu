@@ -38,35 +38,7 @@ __global__ void k_energy_finalize(const double* __restrict__ pv, int nbf, const 
                                   const int* __restrict__ skip) {
   if (skip && *skip) return;  // a device-decided run stopped before this step
   __shared__ double sh[32];
-  double pe = 0.0, vir = 0.0, ke = 0.0;
-  for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-    pe += pv[2 * (size_t)b];
-    vir += pv[2 * (size_t)b + 1];
-  }
-  for (int b = threadIdx.x; b < nbi; b += blockDim.x) ke += kp[b];
-  pe = block_sum(pe, sh);
-  __syncthreads();
-  vir = block_sum(vir, sh);
-  __syncthreads();
-  ke = block_sum(ke, sh);
-  if (threadIdx.x == 0) {
-    pe *= pe_scale;
-    vir *= pe_scale;
-    energies[0] = pe;
-    energies[1] = ke;
-    energies[2] = vir;
-    energies[3] = step;
-    if (log != nullptr) {
-      int64_t k = *count;
-      if (k < cap) {
-        log[4 * k + 0] = step;
-        log[4 * k + 1] = pe;
-        log[4 * k + 2] = ke;
-        log[4 * k + 3] = vir;
-      }
-      *count = k + 1;
-    }
-  }
+  energy_record_block(pv, nbf, kp, nbi, pe_scale, energies, log, cap, count, step, sh);
 }
 
 void launch_energy_finalize(const double* pe_vir_part, int nb_force, const double* ke_part, int nb_int,

@@ -17,12 +17,39 @@
 
 namespace ljmd {
 
+// The list-validity decision of a device-decided run (the host rule of ljmd_step, taken on the
+// device so that steps follow each other without a host round trip): the largest squared
+// displacement and drift speed of the step are taken (and reset for the next one); with the
+// margin/2 rule the list expired when the displacement exceeds the limit, with DUTC when the
+// remaining buffer, less the closing 2 v_max dt of the step, is used up.  An expired list stops
+// the run at step s.  One thread.
+__device__ __forceinline__ void step_check_one(uint32_t* dmax_bits, StepCtl* ctl, int s, double disp_limit, int dutc,
+                                               double two_dt) {
+  if (ctl->stop) return;
+  const float d2 = __uint_as_float(atomicExch(dmax_bits, 0u)), v2 = __uint_as_float(atomicExch(dmax_bits + 1, 0u));
+  ctl->last[0] = d2;
+  ctl->last[1] = v2;
+  bool expired;
+  if (dutc) {
+    const double b = ctl->dutc - two_dt * sqrt((double)v2) * (1.0 + 1e-6);
+    ctl->dutc = b;
+    expired = !(b > 0.0);
+  } else {
+    expired = sqrt((double)d2) > disp_limit;
+  }
+  if (expired) {
+    ctl->stop = 1;
+    ctl->stop_at = s;
+  }
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, double* __restrict__ v,
                                                    const void* __restrict__ fptr, void* __restrict__ pos,
                                                    const void* __restrict__ refp, int64_t N, IntegrateArgs a,
                                                    double* __restrict__ ke_part, uint32_t* __restrict__ dmax_bits,
-                                                   int32_t* __restrict__ status, const int* __restrict__ skip) {
+                                                   int32_t* __restrict__ status, StepFinish fin,
+                                                   const int* __restrict__ skip) {
   if (skip && *skip) return;  // a device-decided run stopped before this step
   const float qu = __int_as_float((127 - a.qk) << 23);  // u = 2^-qk
   const double kk = a.kpre + a.kpost;
@@ -125,6 +152,23 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
       }
     }
   }
+  if (fin.ticket) {  // the last CTA to finish takes the energy record and the validity check
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(fin.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (fin.rec)
+        energy_record_block(fin.pv, fin.nbf, ke_part, gridDim.x, fin.pe_scale, fin.energies, fin.log, fin.cap,
+                            fin.count, fin.step, sh);
+      if (threadIdx.x == 0) {
+        if (fin.check) step_check_one(dmax_bits, fin.ctl, fin.s, fin.disp_limit, fin.dutc, fin.two_dt);
+        *fin.ticket = 0u;
+      }
+    }
+  }
 }
 
 // Blocks of one resident wave (at most red_blocks(N)): the grid-stride loop then ends in step on
@@ -145,43 +189,14 @@ static int one_wave(int64_t N) {
 }
 
 int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, const void* ref, int64_t N,
-                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, cudaStream_t s,
-                     const int* skip) {
+                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, StepFinish fin,
+                     cudaStream_t s, const int* skip) {
   const int blocks = precision == LJ_MIXED ? one_wave<true>(N) : one_wave<false>(N);
   if (precision == LJ_MIXED)
-    k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, skip);
+    k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, fin, skip);
   else
-    k_integrate<false><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, skip);
+    k_integrate<false><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, fin, skip);
   return blocks;
-}
-
-// The list-validity decision of a device-decided run (the host rule of ljmd_step, taken on the
-// device so that steps follow each other without a host round trip).
-__global__ void k_step_check(uint32_t* __restrict__ dmax_bits, StepCtl* __restrict__ ctl, int s, double disp_limit,
-                             int dutc, double two_dt) {
-  if (ctl->stop) return;
-  const float d2 = __uint_as_float(dmax_bits[0]), v2 = __uint_as_float(dmax_bits[1]);
-  ctl->last[0] = d2;
-  ctl->last[1] = v2;
-  dmax_bits[0] = 0u;
-  dmax_bits[1] = 0u;
-  bool expired;
-  if (dutc) {
-    const double b = ctl->dutc - two_dt * sqrt((double)v2) * (1.0 + 1e-6);
-    ctl->dutc = b;
-    expired = !(b > 0.0);
-  } else {
-    expired = sqrt((double)d2) > disp_limit;
-  }
-  if (expired) {
-    ctl->stop = 1;
-    ctl->stop_at = s;
-  }
-}
-
-void launch_step_check(uint32_t* dmax_bits, StepCtl* ctl, int s, double disp_limit, int dutc, double two_dt,
-                       cudaStream_t st) {
-  k_step_check<<<1, 1, 0, st>>>(dmax_bits, ctl, s, disp_limit, dutc, two_dt);
 }
 
 // Position copies for the force and list kernels from the FP64 state (no integration): the FP32

@@ -73,6 +73,7 @@ struct ljmd_sys {
   int32_t* d_status = nullptr;
   uint32_t* d_dmax = nullptr;
   StepCtl* d_ctl = nullptr;     // device-decided runs: stop flag, stopping step, last maxima, DUTC buffer
+  unsigned int* d_ticket = nullptr;  // CTAs of an integrator launch that finished (the last one finishes the step)
   StepCtl* h_ctl = nullptr;     // pinned mirror
   int64_t last_build_step = 0;  // sys->steps at the last list construction
   int64_t lifetime_est = 16;    // steps the last list lived (sizes the next device-decided run)
@@ -144,7 +145,7 @@ static void free_all(ljmd_sys* s) {
   void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->xq, s->pos64, s->ref, s->id,
                   s->id_alt, s->img, s->img_alt, s->cell_of, s->perm, s->cell_count, s->cell_start,
                   s->cell_fill, s->rows, s->tile_list, s->ent, s->scan_tmp, s->part_force, s->part_ke,
-                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_ctl, s->d_total64, s->d_sizes,
+                  s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_ctl, s->d_ticket, s->d_total64, s->d_sizes,
                   s->adj_w, s->adj_hw, s->adj_f, s->part_adj, s->d_adj, s->xref64, s->ldc_list, s->d_ldc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -668,12 +669,12 @@ static int rebuild(ljmd_sys* s) {
 
 static void* force_pos(ljmd_sys* s) { return s->precision == LJ_MIXED ? (void*)s->xq : (void*)s->pos64; }
 
-static int integrate(ljmd_sys* s, IntegrateArgs a, const int* skip = nullptr) {
+static int integrate(ljmd_sys* s, IntegrateArgs a, const int* skip = nullptr, const StepFinish* fin = nullptr) {
   PhaseTimer timer(s, PH_INTEGRATE);
   s->launches += 1;
   a.qk = s->g.qk;
   return launch_integrate(s->precision, s->x, s->v, s->f, force_pos(s), s->ref, s->n, a, s->part_ke, s->d_dmax,
-                          s->d_status, s->st, skip);
+                          s->d_status, fin ? *fin : StepFinish{}, s->st, skip);
 }
 
 // Energy record of state `step` (default: the current one); skipped on the device if *skip is set.
@@ -836,13 +837,26 @@ static int device_run(ljmd_sys* s, double dt, bool first_of_call, int64_t remain
     const int64_t t = s->steps + k;  // state index before the step
     const bool rec = (k == 0 ? s->pe_step == s->steps : true) && want_energy(t);
     IntegrateArgs a{(first_of_call && k == 0) ? 0.0 : h, h, dt, rec ? 1 : 0, 1, dutc};
-    const int nb = integrate(s, a, skip);
-    if (rec) {
-      energy_record(s, nb, true, t, skip);
-      recorded[k] = 1;
-    }
-    launch_step_check(s->d_dmax, s->d_ctl, (int)k, s->disp_limit, dutc, 2.0 * fabs(dt), st);
-    s->launches += 1;
+    // the integrator's last CTA records the energies of state t and takes the validity check
+    StepFinish fin{};
+    fin.ticket = s->d_ticket;
+    fin.rec = rec ? 1 : 0;
+    fin.pv = s->part_force;
+    fin.nbf = s->nb_force;
+    fin.pe_scale = s->list_half ? 1.0 : 0.5;
+    fin.energies = s->d_energies;
+    fin.log = s->log_ptr;
+    fin.cap = s->log_cap;
+    fin.count = s->d_log_count;
+    fin.step = (double)t;
+    fin.check = 1;
+    fin.ctl = s->d_ctl;
+    fin.s = (int)k;
+    fin.disp_limit = s->disp_limit;
+    fin.dutc = dutc;
+    fin.two_dt = 2.0 * fabs(dt);
+    integrate(s, a, skip, &fin);
+    if (rec) recorded[k] = 1;
     ev_force[k] = s->ev_pending.size();
     ln_force[k] = s->launches;
     TRY(run_force(s, want_energy(t + 1), skip));
@@ -923,6 +937,8 @@ int ljmd_create(ljmd_sys** out, const ljmd_params* p, int32_t precision, void* c
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_status, 1);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_dmax, 2);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_ctl, 1);
+  if (r == LJ_OK) r = dalloc_t(sys, &sys->d_ticket, 1);
+  if (r == LJ_OK && cudaMemsetAsync(sys->d_ticket, 0, sizeof(unsigned int), sys->st) != cudaSuccess) r = LJ_EDEVICE;
   if (r == LJ_OK && cudaMallocHost(&sys->h_ctl, sizeof(StepCtl)) != cudaSuccess) r = LJ_ENOMEM;
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_total64, 2);
   if (r == LJ_OK) r = dalloc_t(sys, &sys->d_sizes, 4);

@@ -415,14 +415,14 @@ static int enqueue_steps(ljmd_batch* b, double dt, int64_t k) {
   for (int64_t s = 0; s < k; ++s) {
     BK(cudaMemsetAsync(b->dmax, 0, 2 * sizeof(uint32_t), b->st));
     IntegrateArgs a{s == 0 ? 0.0 : h, h, dt, 0, 1, 0, b->g0.qk};
-    launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->xq, b->ref, b->N, a, nullptr, b->dmax, b->status, b->st);
+    launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->xq, b->ref, b->N, a, nullptr, b->dmax, b->status, StepFinish{}, b->st);
     launch_rebuild_flag(b->dmax, limit2, b->flag, b->d_rebuilds, b->st);
     b->launches += 2;
     BTRY(enqueue_rebuild(b, b->flag));
     BTRY(enqueue_force(b, false));
   }
   IntegrateArgs a{h, 0.0, 0.0, 0, 0, 0, b->g0.qk};
-  launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->xq, b->ref, b->N, a, nullptr, b->dmax, b->status, b->st);
+  launch_integrate(LJ_MIXED, b->x, b->v, b->f, b->xq, b->ref, b->N, a, nullptr, b->dmax, b->status, StepFinish{}, b->st);
   b->launches += 1;
   BKL();
   return LJ_OK;

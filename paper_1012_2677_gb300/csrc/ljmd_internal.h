@@ -171,28 +171,48 @@ struct IntegrateArgs {
   int speed;       // also reduce the largest drift speed (DUTC rules)
   int qk;          // mixed form: the fixed-point records are at u = 2^-qk
 };
+// Work done by the integrator's last CTA (an atomic ticket counts the CTAs that finished), in place
+// of separate launches: the energy record of the step (force partials pv of the state before the
+// drift, the KE partials of this launch) and the list-validity check of a device-decided run.
+struct StepCtl;
+struct StepFinish {
+  unsigned int* ticket;  // zero between launches; nullptr: nothing to finish
+  int rec;               // the energy record (as launch_energy_finalize)
+  const double* pv;
+  int nbf;
+  double pe_scale;
+  double* energies;
+  double* log;
+  int64_t cap;
+  int64_t* count;
+  double step;
+  int check;  // the validity check: the run stops at step s if the list expired
+  StepCtl* ctl;
+  int s;
+  double disp_limit;
+  int dutc;
+  double two_dt;
+};
 // Returns the number of blocks used for KE partials.  With a.shadow, dmax_bits[0] and [1] receive
 // (atomic max) the float bits of the largest squared displacement since the list build and of the
 // largest squared drift speed.
 // pos: the fixed-point records (mixed) or the dvec4 copies (FP64), rewritten when a.shadow is set.
 int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, const void* ref, int64_t N,
-                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, cudaStream_t s,
+                     IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, StepFinish fin, cudaStream_t s,
                      const int* skip = nullptr);
-// Device-side list-validity decision after the drift of step s of a device-decided run (one thread):
-// unless ctl->stop is already set, reads the maxima of the step (squared displacement since the
-// build and squared drift speed, float bits in dmax_bits[0], [1]), keeps them in ctl->last, clears
-// dmax_bits for the next step and, if the list expired (margin/2 rule: the displacement above
-// disp_limit; DUTC: the buffer, reduced by 2 v_max |dt|, at or below zero), sets ctl->stop and
-// ctl->stop_at = s.  Every later kernel of the run is launched with &ctl->stop as its skip flag.
+// Device-side list-validity decision after the drift of step s of a device-decided run (taken by the
+// integrator's last CTA, StepFinish.check): unless ctl->stop is already set, reads the maxima of the
+// step (squared displacement since the build and squared drift speed, float bits in dmax_bits[0],
+// [1]), keeps them in ctl->last, clears dmax_bits for the next step and, if the list expired
+// (margin/2 rule: the displacement above disp_limit; DUTC: the buffer, reduced by 2 v_max |dt|, at
+// or below zero), sets ctl->stop and ctl->stop_at = s.  Every later kernel of the run is launched
+// with &ctl->stop as its skip flag.
 struct StepCtl {
   int stop;         // set: the run stopped (the list must be rebuilt before the next force)
   int stop_at;      // the step of the run whose drift expired the list
   float last[2];    // squared largest displacement and drift speed of the last checked step
   double dutc;      // DUTC buffer length
 };
-void launch_step_check(uint32_t* dmax_bits, StepCtl* ctl, int s, double disp_limit, int dutc, double two_dt,
-                       cudaStream_t st);
-
 // ---- pair export through a static device scratch array (no allocation) ----------------
 // Address of this device's scratch (resolved once per device): the kept-pair counter word and
 // LJ_PAIRS_STATIC_MAX_ENTRIES 64-bit key slots.
