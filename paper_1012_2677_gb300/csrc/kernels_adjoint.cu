@@ -12,26 +12,31 @@ static int grid_of(int64_t n) {
   return (int)(b < 65535 ? b : 65535);
 }
 
-// w_sorted[s] = (w[3 id[s]], w[3 id[s] + 1], w[3 id[s] + 2]) (or zero when w is null)
+// w_sorted[s] = (w[3 id[s]], w[3 id[s] + 1], w[3 id[s] + 2]) (or zero when w is null), and its FP32
+// copy (rounded to nearest) for the mixed form's pair loop.
 __global__ void k_to_sorted(const double* __restrict__ w, const int32_t* __restrict__ id, int64_t N,
-                            dvec4* __restrict__ out) {
+                            dvec4* __restrict__ out, float4* __restrict__ out32) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    dvec4 v = make_dvec4(0.0, 0.0, 0.0, 0.0);
     if (w) {
       const int64_t p = id[s];
-      out[s] = make_dvec4(w[3 * p], w[3 * p + 1], w[3 * p + 2], 0.0);
-    } else {
-      out[s] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+      v = make_dvec4(w[3 * p], w[3 * p + 1], w[3 * p + 2], 0.0);
     }
+    out[s] = v;
+    out32[s] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.0f);
   }
 }
-void launch_to_sorted(const double* w_id, const int32_t* id, int64_t N, dvec4* out, cudaStream_t s) {
-  k_to_sorted<<<grid_of(N), 256, 0, s>>>(w_id, id, N, out);
+void launch_to_sorted(const double* w_id, const int32_t* id, int64_t N, dvec4* out, float4* out32, cudaStream_t s) {
+  k_to_sorted<<<grid_of(N), 256, 0, s>>>(w_id, id, N, out, out32);
 }
 
-// Unwrapped positions in id order: out[3 id[s] + k] = x[k N + s] - offset + img[k N + s] L.
+// Unwrapped positions in id order: out[3 id[s] + k] = x[k N + s] - offset + img[k N + s] L.  Inside a
+// device-decided run (ctl non-null, after the drift of its step k) nothing is written if the run
+// stopped at an earlier step (the drift of step k did not happen).
 __global__ void k_unwrapped(const double* __restrict__ x, const int32_t* __restrict__ img,
                             const int32_t* __restrict__ id, int64_t N, double offset, double L,
-                            double* __restrict__ out) {
+                            double* __restrict__ out, const StepCtl* __restrict__ ctl, int k_step) {
+  if (ctl && ctl->stop && ctl->stop_at < k_step) return;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = id[s];
 #pragma unroll
@@ -39,8 +44,8 @@ __global__ void k_unwrapped(const double* __restrict__ x, const int32_t* __restr
   }
 }
 void launch_unwrapped(const double* x, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
-                      double* out, cudaStream_t s) {
-  k_unwrapped<<<grid_of(N), 256, 0, s>>>(x, img, id, N, offset, L, out);
+                      double* out, cudaStream_t s, const StepCtl* ctl, int k_step) {
+  k_unwrapped<<<grid_of(N), 256, 0, s>>>(x, img, id, N, offset, L, out, ctl, k_step);
 }
 
 // The inverse of k_unwrapped for the current sorted order and image counts: x[k N + s] =

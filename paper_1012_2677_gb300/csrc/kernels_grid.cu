@@ -169,30 +169,44 @@ void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_
   k_scatter<<<grid_for(N, 256), 256, 0, s>>>(cell_of, cell_start, cell_fill, perm, N, pred);
 }
 
-// Inside each cell order the particles by id (insertion sort of the cell's slice of perm):
-// the sorted order then depends only on the positions, not on atomic arrival order.
-__global__ void k_cell_order(const uint32_t* __restrict__ start, int64_t ncells, uint32_t* __restrict__ perm,
-                             const int32_t* __restrict__ id, const int* __restrict__ pred) {
+// Inside each cell order the particles by id (the order of Fig. 3's counting sort, independent of the
+// arrival order of the scatter's atomics): a warp per cell ranks each of the cell's entries of
+// perm_in by the number of its entries with a smaller id and writes it at that rank of perm_out.
+__global__ void k_cell_rank(const uint32_t* __restrict__ start, int64_t ncells, const uint32_t* __restrict__ perm_in,
+                            const int32_t* __restrict__ id, uint32_t* __restrict__ perm_out,
+                            const int* __restrict__ pred) {
   if (pred && !*pred) return;  // predicated: skipped unless the flag is set
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t b = start[c], e = start[c + 1];
-    for (uint32_t a = b + 1; a < e; ++a) {
-      const uint32_t p = perm[a];
-      const int32_t key = id[p];
-      uint32_t q = a;
-      while (q > b && id[perm[q - 1]] > key) {
-        perm[q] = perm[q - 1];
-        --q;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncells; c += warps) {
+    const uint32_t b = start[c];
+    const int m = (int)(start[c + 1] - b);
+    for (int i0 = 0; i0 < m; i0 += 32) {
+      const int i = i0 + lane;
+      uint32_t p = 0;
+      int key = 0x7fffffff;
+      if (i < m) {
+        p = perm_in[b + i];
+        key = id[p];
       }
-      perm[q] = p;
+      int rank = 0;
+      for (int j0 = 0; j0 < m; j0 += 32) {
+        const int j = j0 + lane;
+        const int other = j < m ? id[perm_in[b + j]] : 0x7fffffff;
+        const int cnt = m - j0 < 32 ? m - j0 : 32;
+        for (int t = 0; t < cnt; ++t) rank += __shfl_sync(0xffffffffu, other, t) < key ? 1 : 0;
+      }
+      if (i < m) perm_out[b + rank] = p;
     }
   }
 }
 
-void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* perm, const int32_t* id,
-                       cudaStream_t s, const int* pred) {
-  k_cell_order<<<grid_for(ncells, 128), 128, 0, s>>>(cell_start, ncells, perm, id, pred);
+void launch_cell_rank(const uint32_t* cell_start, int64_t ncells, const uint32_t* perm_in, const int32_t* id,
+                      uint32_t* perm_out, cudaStream_t s, const int* pred) {
+  int64_t b = (ncells + 7) / 8;
+  if (b < 1) b = 1;
+  if (b > 1048576) b = 1048576;
+  k_cell_rank<<<(int)b, 256, 0, s>>>(cell_start, ncells, perm_in, id, perm_out, pred);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -173,8 +173,12 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
 
 // Blocks of one resident wave (at most red_blocks(N)): the grid-stride loop then ends in step on
 // every SM instead of leaving a partial second wave.
+// Block shape: 256-thread blocks of one resident wave (at most red_blocks(N)), so that the grid-stride
+// loop ends in step on every SM; for a system too small to give every SM a block, narrower blocks
+// (down to one warp) spread the particles over the SMs, each of whose FP64 pipes takes 1/64 of the
+// FP32 rate.
 template <bool MIXED>
-static int one_wave(int64_t N) {
+static void integrate_shape(int64_t N, int& blocks, int& threads) {
   static int per_sm = 0, sms = 0;
   if (per_sm == 0) {
     int dev = 0;
@@ -184,18 +188,28 @@ static int one_wave(int64_t N) {
         per_sm < 1)
       per_sm = 1;
   }
-  const int b = red_blocks(N);
-  return b < per_sm * sms ? b : per_sm * sms;
+  threads = kRedThreads;
+  while (threads > 32 && (N + threads - 1) / threads < sms) threads >>= 1;
+  if (threads == kRedThreads) {
+    const int b = red_blocks(N);
+    blocks = b < per_sm * sms ? b : per_sm * sms;
+  } else {
+    const int64_t b = (N + threads - 1) / threads;  // below 2 sms: within the partial arrays
+    blocks = (int)(b < 1 ? 1 : b);
+  }
 }
 
 int launch_integrate(int precision, double* x, double* v, const void* f, void* pos, const void* ref, int64_t N,
                      IntegrateArgs a, double* ke_part, uint32_t* dmax_bits, int32_t* status, StepFinish fin,
                      cudaStream_t s, const int* skip) {
-  const int blocks = precision == LJ_MIXED ? one_wave<true>(N) : one_wave<false>(N);
-  if (precision == LJ_MIXED)
-    k_integrate<true><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, fin, skip);
-  else
-    k_integrate<false><<<blocks, kRedThreads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, fin, skip);
+  int blocks = 1, threads = kRedThreads;
+  if (precision == LJ_MIXED) {
+    integrate_shape<true>(N, blocks, threads);
+    k_integrate<true><<<blocks, threads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, fin, skip);
+  } else {
+    integrate_shape<false>(N, blocks, threads);
+    k_integrate<false><<<blocks, threads, 0, s>>>(x, v, f, pos, ref, N, a, ke_part, dmax_bits, status, fin, skip);
+  }
   return blocks;
 }
 

@@ -1736,8 +1736,9 @@ template <bool MIXED, bool WHOLE>
 __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const unsigned char* buf, const TileLayout& L,
                                                      const uint2* __restrict__ rows, const uint16_t* __restrict__ ent,
                                                      const LJConst& c, const Geom& g, const dvec4* __restrict__ w,
-                                                     dvec4* __restrict__ hw, dvec4* __restrict__ fo,
-                                                     int32_t* __restrict__ status, double* acc, int list_cap) {
+                                                     const float4* __restrict__ wf, dvec4* __restrict__ hw,
+                                                     dvec4* __restrict__ fo, int32_t* __restrict__ status, double* acc,
+                                                     int list_cap) {
   const void* sh_pos = buf + L.pos;
   const int* sh_gid = (const int*)(buf + L.gid);
   const uint2* s_rows = (const uint2*)(buf + L.rows);
@@ -1745,11 +1746,12 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
   const int lane = threadIdx.x & (kAdjLanes - 1);
   const int grp = threadIdx.x / kAdjLanes;
   constexpr int kGroups = kTileThreads / kAdjLanes;
-  const double e4 = 4.0 * c.eps, inv_sig = 1.0 / c.sigma, c2s = c.c2 / c.sig2;
+  const double e4 = 4.0 * c.eps, inv_sig = c.inv_sigma, c2s = c.c2s;
   const int n_own = S.own1 - S.own0;
   for (int o = grp; __any_sync(0xffffffffu, o < n_own); o += kGroups) {
     const bool valid = o < n_own;
     double h[3] = {0.0, 0.0, 0.0}, f[3] = {0.0, 0.0, 0.0}, q[kAdjParts] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    float ah[3] = {0.f, 0.f, 0.f}, af[3] = {0.f, 0.f, 0.f}, aq[kAdjParts] = {0.f, 0.f, 0.f, 0.f, 0.f};
     int gi = 0;
     if (valid) {
       const int l = S.own0 + o;
@@ -1768,13 +1770,11 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
           row.y = 0;
         }
       }
-      const dvec4 wi = w[gi];
       if (MIXED) {
         const uint4 qi = ((const uint4*)sh_pos)[l];
-        const float e4f = (float)e4, sig2f = (float)c.sig2, c2sf = (float)c2s, rc2f = (float)c.rc2,
-                    c0f = (float)c.c0, isgf = (float)inv_sig;
-        float ah[3] = {0.f, 0.f, 0.f}, af[3] = {0.f, 0.f, 0.f}, aq[kAdjParts] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        const float wx = (float)wi.x, wy = (float)wi.y, wz = (float)wi.z;
+        const float e4f = c.e4, sig2f = c.sig2f, c2sf = c.c2sf, rc2f = c.rc2f, c0f = c.c0f, isgf = c.inv_sigmaf;
+        const float4 wif = wf[gi];  // the FP32 copy of w (no conversions per pair)
+        const float wx = wif.x, wy = wif.y, wz = wif.z;
         for (unsigned e = lane; e < row.y; e += kAdjLanes) {
           const int j = el[row.x + e];
           const uint4 qj = ((const uint4*)sh_pos)[j];
@@ -1784,15 +1784,15 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
                       dz = qd<WHOLE>(qj.z, qi.z, g) * g.qu;
           const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (!(s2 < rc2f)) continue;
-          const dvec4 wj = w[qj.w];
-          const float is = 1.0f / s2;
+          const float4 wj = wf[qj.w];
+          const float is = rcp_nr(s2);
           const float a = sig2f * is, a3 = a * a * a, a6 = a3 * a3;
           const float u = e4f * (a6 - a3 + c2sf * s2 + c0f);
           const float u1 = e4f * (is * (3.0f * a3 - 6.0f * a6) + c2sf);
           const float u2 = e4f * is * is * (42.0f * a6 - 12.0f * a3);
           const float dus = e4f * isgf * (12.0f * a6 - 6.0f * a3 - 2.0f * c2sf * s2);
           const float du1s = e4f * isgf * (is * (18.0f * a3 - 72.0f * a6) - 2.0f * c2sf);
-          const float dwx = wx - (float)wj.x, dwy = wy - (float)wj.y, dwz = wz - (float)wj.z;
+          const float dwx = wx - wj.x, dwy = wy - wj.y, dwz = wz - wj.z;
           const float ddw = dx * dwx + dy * dwy + dz * dwz;
           const float t1 = 2.0f * u1, t2 = 4.0f * u2 * ddw;
           ah[0] += t1 * dwx + t2 * dx;
@@ -1808,12 +1808,8 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
           aq[3] += 0.5f * dus;
           aq[4] += 0.5f * u;
         }
-        for (int k = 0; k < 3; ++k) {
-          h[k] = ah[k];
-          f[k] = af[k];
-        }
-        for (int k = 0; k < kAdjParts; ++k) q[k] = aq[k];
       } else {
+        const dvec4 wi = w[gi];
         const dvec4 qi = ((const dvec4*)sh_pos)[l];
         for (unsigned e = lane; e < row.y; e += kAdjLanes) {
           const int j = el[row.x + e];
@@ -1833,7 +1829,7 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
           const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
           if (!(s2 < c.rc2)) continue;
           const dvec4 wj = w[sh_gid[j]];
-          const double is = 1.0 / s2;
+          const double is = rcp_nr64(s2);
           const double a = c.sig2 * is, a3 = a * a * a, a6 = a3 * a3;
           const double u = e4 * (a6 - a3 + c2s * s2 + c.c0);
           const double u1 = e4 * (is * (3.0 * a3 - 6.0 * a6) + c2s);
@@ -1858,15 +1854,28 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
         }
       }
     }
-    for (int k = 0; k < 3; ++k) {
-      h[k] = gsum<kAdjLanes>(h[k]);
-      f[k] = gsum<kAdjLanes>(f[k]);
+    if (MIXED) {  // the group's lanes reduce in FP32; one lane converts and accumulates in FP64
+      for (int k = 0; k < 3; ++k) {
+        ah[k] = gsum<kAdjLanes>(ah[k]);
+        af[k] = gsum<kAdjLanes>(af[k]);
+      }
+      for (int k = 0; k < kAdjParts; ++k) aq[k] = gsum<kAdjLanes>(aq[k]);
+      if (valid && lane == 0) {
+        hw[gi] = make_dvec4(ah[0], ah[1], ah[2], 0.0);
+        if (fo) fo[gi] = make_dvec4(af[0], af[1], af[2], 0.0);
+        for (int k = 0; k < kAdjParts; ++k) acc[k] += (double)aq[k];
+      }
+    } else {
+      for (int k = 0; k < 3; ++k) {
+        h[k] = gsum<kAdjLanes>(h[k]);
+        f[k] = gsum<kAdjLanes>(f[k]);
+      }
+      if (valid && lane == 0) {
+        hw[gi] = make_dvec4(h[0], h[1], h[2], 0.0);
+        if (fo) fo[gi] = make_dvec4(f[0], f[1], f[2], 0.0);
+      }
+      for (int k = 0; k < kAdjParts; ++k) acc[k] += q[k];
     }
-    if (valid && lane == 0) {
-      hw[gi] = make_dvec4(h[0], h[1], h[2], 0.0);
-      if (fo) fo[gi] = make_dvec4(f[0], f[1], f[2], 0.0);
-    }
-    for (int k = 0; k < kAdjParts; ++k) acc[k] += q[k];
   }
 }
 
@@ -1875,8 +1884,9 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     k_adjoint_tile(const void* __restrict__ pos, const uint32_t* __restrict__ cs, int64_t N, Geom g, TileArgs ta,
                    LJConst c, const uint2* __restrict__ rows,
                    const uint2* __restrict__ tile_list, const uint16_t* __restrict__ ent,
-                   const dvec4* __restrict__ w, dvec4* __restrict__ hw, dvec4* __restrict__ fo,
-                   double* __restrict__ part, int32_t* __restrict__ status) {
+                   const dvec4* __restrict__ w, const float4* __restrict__ wf, dvec4* __restrict__ hw,
+                   dvec4* __restrict__ fo, double* __restrict__ part, unsigned int* __restrict__ ticket,
+                   double* __restrict__ sums, int32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared S;
   __shared__ __align__(8) uint64_t bar;
@@ -1886,7 +1896,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     if (blockIdx.x == 0) {
       stage_whole<MIXED, !MIXED>(N, pos, S, smem, L);
       __syncthreads();
-      adjoint_tile_compute<MIXED, true>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc, ta.list_cap);
+      adjoint_tile_compute<MIXED, true>(S, smem, L, rows, ent, c, g, w, wf, hw, fo, status, acc, ta.list_cap);
     }
   } else {
     if (threadIdx.x == 0) {
@@ -1901,7 +1911,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const TileInfo ti = tile_info(t, ta);
         stage_issue<MIXED, true>(ti, ta, pos, rows, ent, S, smem, L, &bar);
         if (!stage_finish<MIXED, true>(ti, ta, g, S, smem, L, &bar, ph, !MIXED, status)) return;
-        adjoint_tile_compute<MIXED, false>(S, smem, L, rows, ent, c, g, w, hw, fo, status, acc, ta.list_cap);
+        adjoint_tile_compute<MIXED, false>(S, smem, L, rows, ent, c, g, w, wf, hw, fo, status, acc, ta.list_cap);
       }
       __syncthreads();
     }
@@ -1911,6 +1921,22 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     const double t = block_sum(acc[k], sh);
     if (threadIdx.x == 0) part[kAdjParts * (size_t)blockIdx.x + k] = t;
     __syncthreads();
+  }
+  // the last CTA to finish sums the partials of all CTAs in block order
+  __shared__ int s_last;
+  __threadfence();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int k = 0; k < kAdjParts; ++k) {
+      double v = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(part + kAdjParts * (size_t)b + k);
+      v = block_sum(v, sh);
+      if (threadIdx.x == 0) sums[k] = v;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
   }
 }
 
@@ -2201,15 +2227,17 @@ size_t adjoint_smem_bytes(const TileArgs& ta, int precision) {
 }
 
 int launch_adjoint_tile(int precision, const void* pos, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
-                        const uint2* rows, const uint2* tile_list, const uint16_t* ent, const void* w, void* hw,
-                        void* fo, double* part, int32_t* status, cudaStream_t s) {
+                        const uint2* rows, const uint2* tile_list, const uint16_t* ent, const void* w,
+                        const float4* wf, void* hw, void* fo, double* part, unsigned int* ticket, double* sums,
+                        int32_t* status, cudaStream_t s) {
   const size_t sm = adjoint_smem_bytes(ta, precision);
   const int grid = tile_grid(ta, min(per_sm_for(sm), 2));
 #define LJ_ADJ_LAUNCH(M, W)                                                                                 \
   do {                                                                                                      \
     set_smem(k_adjoint_tile<M, W>, sm);                                                                     \
     k_adjoint_tile<M, W><<<grid, kTileThreads, sm, s>>>(pos, cs, N, g, ta, c, rows, tile_list, ent,         \
-                                                        (const dvec4*)w, (dvec4*)hw, (dvec4*)fo, part, status); \
+                                                        (const dvec4*)w, wf, (dvec4*)hw, (dvec4*)fo, part,      \
+                                                        ticket, sums, status);                                  \
   } while (0)
   if (precision == LJ_MIXED) {
     if (ta.whole) LJ_ADJ_LAUNCH(true, true);

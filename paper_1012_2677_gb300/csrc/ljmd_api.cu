@@ -51,7 +51,7 @@ struct ljmd_sys {
   dvec4* pos64 = nullptr; // FP64 form: position copies for the force and adjoint kernels
   void* ref = nullptr;
   int32_t *id = nullptr, *id_alt = nullptr, *img = nullptr, *img_alt = nullptr;
-  uint32_t *cell_of = nullptr, *perm = nullptr;
+  uint32_t *cell_of = nullptr, *perm = nullptr, *perm_id = nullptr;  // perm_id: perm ordered by id in each cell
   uint32_t *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
   uint2* rows = nullptr;        // per particle: (start, length) of its row in ent
   uint2* tile_list = nullptr;   // per tile: (start, length) of its segment of ent
@@ -74,6 +74,10 @@ struct ljmd_sys {
   uint32_t* d_dmax = nullptr;
   StepCtl* d_ctl = nullptr;     // device-decided runs: stop flag, stopping step, last maxima, DUTC buffer
   unsigned int* d_ticket = nullptr;  // CTAs of an integrator launch that finished (the last one finishes the step)
+  // Capture hook of the trajectory gradient: if set, the unwrapped positions (id order) of every
+  // state t reached by a step go to cap_x + 3 n (t - cap_step0).
+  double* cap_x = nullptr;
+  int64_t cap_step0 = 0;
   StepCtl* h_ctl = nullptr;     // pinned mirror
   int64_t last_build_step = 0;  // sys->steps at the last list construction
   int64_t lifetime_est = 16;    // steps the last list lived (sizes the next device-decided run)
@@ -98,6 +102,8 @@ struct ljmd_sys {
   int64_t ldc_checks = 0, ldc_kept = 0;
   // adjoint pass (allocated on first use)
   dvec4 *adj_w = nullptr, *adj_hw = nullptr, *adj_f = nullptr;
+  float4* adj_wf = nullptr;           // FP32 copy of adj_w
+  unsigned int* adj_ticket = nullptr;  // CTAs of an adjoint launch that finished
   double* part_adj = nullptr;
   double* d_adj = nullptr;
   int64_t adj_cap = 0;
@@ -143,10 +149,10 @@ static int dalloc_t(ljmd_sys* sys, T** p, size_t count) {
 
 static void free_all(ljmd_sys* s) {
   void* ptrs[] = {s->x, s->v, s->x_alt, s->v_alt, s->f, s->f_alt, s->hi, s->xq, s->pos64, s->ref, s->id,
-                  s->id_alt, s->img, s->img_alt, s->cell_of, s->perm, s->cell_count, s->cell_start,
+                  s->id_alt, s->img, s->img_alt, s->cell_of, s->perm, s->perm_id, s->cell_count, s->cell_start,
                   s->cell_fill, s->rows, s->tile_list, s->ent, s->scan_tmp, s->part_force, s->part_ke,
                   s->part_misc, s->d_scalars, s->d_energies, s->d_log_count, s->d_status, s->d_dmax, s->d_ctl, s->d_ticket, s->d_total64, s->d_sizes,
-                  s->adj_w, s->adj_hw, s->adj_f, s->part_adj, s->d_adj, s->xref64, s->ldc_list, s->d_ldc};
+                  s->adj_w, s->adj_hw, s->adj_f, s->adj_wf, s->adj_ticket, s->part_adj, s->d_adj, s->xref64, s->ldc_list, s->d_ldc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& p : s->ev_pending) {
@@ -291,6 +297,10 @@ static int setup_geometry(ljmd_sys* s, double L) {
   c.rc2 = p.cutoff * p.cutoff;
   c.c2 = c2;
   c.c0 = c0;
+  c.inv_sigma = 1.0 / c.sigma;
+  c.c2s = c.c2 / c.sig2;
+  c.inv_sigmaf = (float)c.inv_sigma;
+  c.c2sf = (float)c.c2s;
   c.f24 = (float)(24.0 * p.eps);
   c.f48 = (float)(48.0 * p.eps);
   c.f8c2 = (float)(8.0 * p.eps * c2 / c.sig2);
@@ -377,6 +387,7 @@ static int ensure_particles(ljmd_sys* s, int64_t n) {
   TRY(dalloc_t(s, &s->img_alt, 3 * n));
   TRY(dalloc_t(s, &s->cell_of, n));
   TRY(dalloc_t(s, &s->perm, n));
+  TRY(dalloc_t(s, &s->perm_id, n));
   TRY(dalloc_t(s, &s->rows, n + 2));  // +2: aligned bulk copies of a tile's rows may read past the end
   s->cap_n = n;
   return LJ_OK;
@@ -558,8 +569,8 @@ static int rebuild(ljmd_sys* s) {
   CKL();
   CK(cudaMemsetAsync(s->cell_fill, 0, sizeof(uint32_t) * s->ncells, st));
   launch_scatter(s->cell_of, s->cell_start, s->cell_fill, s->perm, N, st);
-  launch_cell_order(s->cell_start, s->ncells, s->perm, s->id, st);
-  launch_gather_state(s->perm, N, s->x, s->x_alt, s->v, s->v_alt, s->id, s->id_alt, s->img, s->img_alt, s->f,
+  launch_cell_rank(s->cell_start, s->ncells, s->perm, s->id, s->perm_id, st);
+  launch_gather_state(s->perm_id, N, s->x, s->x_alt, s->v, s->v_alt, s->id, s->id_alt, s->img, s->img_alt, s->f,
                       s->f_alt, s->precision == LJ_MIXED ? 16 : 32, st, nullptr);
   CKL();
   std::swap(s->x, s->x_alt);
@@ -857,6 +868,11 @@ static int device_run(ljmd_sys* s, double dt, bool first_of_call, int64_t remain
     fin.two_dt = 2.0 * fabs(dt);
     integrate(s, a, skip, &fin);
     if (rec) recorded[k] = 1;
+    if (s->cap_x) {  // the state after this step's drift (skipped if the run stopped earlier)
+      launch_unwrapped(s->x, s->img, s->id, s->n, s->g.offset, s->L, s->cap_x + 3 * s->n * (t + 1 - s->cap_step0),
+                       st, s->d_ctl, (int)k);
+      s->launches += 1;
+    }
     ev_force[k] = s->ev_pending.size();
     ln_force[k] = s->launches;
     TRY(run_force(s, want_energy(t + 1), skip));
@@ -1150,6 +1166,11 @@ static int step_steps(ljmd_sys* sys, double dt, int64_t nsteps) {
     }
     sys->steps += 1;
     sys->forces_current = false;
+    if (sys->cap_x) {
+      launch_unwrapped(sys->x, sys->img, sys->id, sys->n, sys->g.offset, sys->L,
+                       sys->cap_x + 3 * sys->n * (sys->steps - sys->cap_step0), st);
+      sys->launches += 1;
+    }
     TRY(read_dmax(sys, &sys->last_dmax));
     bool expired = false;
     TRY(list_expired(sys, dt, &expired));
@@ -1414,9 +1435,14 @@ int ljmd_get_pairs_static(ljmd_sys* sys, int64_t* ij, int64_t cap, int64_t* npai
 static int ensure_adjoint(ljmd_sys* s) {
   if (s->adj_cap < s->n) {
     TRY(dalloc_t(s, &s->adj_w, s->n));
+    TRY(dalloc_t(s, &s->adj_wf, s->n));
     TRY(dalloc_t(s, &s->adj_hw, s->n));
     TRY(dalloc_t(s, &s->adj_f, s->n));
     s->adj_cap = s->n;
+  }
+  if (!s->adj_ticket) {
+    TRY(dalloc_t(s, &s->adj_ticket, 1));
+    if (cudaMemsetAsync(s->adj_ticket, 0, sizeof(unsigned int), s->st) != cudaSuccess) return LJ_EDEVICE;
   }
   if (!s->part_adj) TRY(dalloc_t(s, &s->part_adj, 5 * (size_t)kMaxRedBlocks));
   if (!s->d_adj) TRY(dalloc_t(s, &s->d_adj, 8));
@@ -1433,16 +1459,14 @@ static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* 
   TRY(ensure_adjoint(s));
   const int64_t N = s->n;
   cudaStream_t st = s->st;
-  launch_to_sorted(w_id, s->id, N, s->adj_w, st);
-  int nb = 0;
+  launch_to_sorted(w_id, s->id, N, s->adj_w, s->adj_wf, st);
   {
     PhaseTimer timer(s, PH_ADJOINT);
-    nb = launch_adjoint_tile(s->precision, force_pos(s), s->cell_start, N, s->g, s->ta, s->c, s->rows,
-                                     s->tile_list, s->ent, s->adj_w, s->adj_hw, f_id ? s->adj_f : nullptr,
-                                     s->part_adj, s->d_status, st);
+    launch_adjoint_tile(s->precision, force_pos(s), s->cell_start, N, s->g, s->ta, s->c, s->rows, s->tile_list,
+                        s->ent, s->adj_w, s->adj_wf, s->adj_hw, f_id ? s->adj_f : nullptr, s->part_adj,
+                        s->adj_ticket, s->d_adj, s->d_status, st);
   }
-  launch_final_reduce(s->part_adj, nb, 5, s->d_adj, st);
-  s->launches += 3;
+  s->launches += 2;
   if (hw_id) {
     launch_scatter_back_f64x4_to_f64x3(s->adj_hw, hw_id, s->id, N, st);
     s->launches += 1;
@@ -1479,7 +1503,9 @@ struct DevBuf {  // device scratch owned by one call
 // current order and image counts are kept, the force kernels' copies are rewritten, and the list
 // stays if no particle moved more than margin/2 from where it was built (else it is rebuilt).
 // Velocities are left as they are.  Synchronises once (the displacement maximum).
-static int load_keeping_list(ljmd_sys* s, const double* u) {
+// known_valid: the state was reached by a step that the validity rule accepted for the current list
+// (no rebuild since), so its displacement need not be read back.
+static int load_keeping_list(ljmd_sys* s, const double* u, bool known_valid = false) {
   ljmd_sys* sys = s;
   if (!s->have_list) {  // nothing to keep: the general path
     return ljmd_set_state(s, s->n, s->L, u, nullptr, 1);
@@ -1491,10 +1517,11 @@ static int load_keeping_list(ljmd_sys* s, const double* u) {
   IntegrateArgs a{0.0, 0.0, 0.0, 0, 1};  // no kick, no drift: copies and displacement only
   integrate(s, a);
   CKL();
-  TRY(read_dmax(s, &s->last_dmax));
   s->forces_current = false;
   s->pe_step = -1;
   s->energy_step = -1;
+  if (known_valid) return LJ_OK;
+  TRY(read_dmax(s, &s->last_dmax));
   if (s->last_dmax > s->disp_limit) TRY(rebuild(s));
   return LJ_OK;
 }
@@ -1669,16 +1696,24 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
     // recompute the segment's states t0 .. t1 - 1 from its checkpoint
     TRY(ljmd_set_state(sys, n, box, ck_x.p + n3 * (size_t)seg, ck_v.p + n3 * (size_t)seg, 1));
     CK(cudaMemcpyAsync(seg_x.p, ck_x.p + n3 * (size_t)seg, bytes, cudaMemcpyDeviceToDevice, st));
+    // one run over the segment (the forward pass's call structure, so the same states), the
+    // state after every step captured on the device
     sys->prm.energy_every = 0;
-    for (int64_t t = t0 + 1; t < t1; ++t) {
-      TRY(run_or_restore(step_steps(sys, dt, 1)));
-      TRY(run_or_restore(capture(seg_x.p + n3 * (size_t)(t - t0), nullptr)));
+    if (t1 - t0 > 1) {
+      sys->cap_x = seg_x.p;
+      sys->cap_step0 = 0;  // the state counter restarts at the checkpoint
+      const int r = step_steps(sys, dt, t1 - t0 - 1);
+      sys->cap_x = nullptr;
+      TRY(run_or_restore(r));
     }
     sys->prm.energy_every = saved_ee;
+    // states from the last construction on were accepted by the validity rule for the current list
+    const int64_t valid_from = sys->last_build_step;
+    const int64_t builds = sys->rebuilds;
     for (int64_t t = t1 - 1; t >= t0; --t) {
       launch_axpy(lv.p, dt, lx.p, (int64_t)n3, st);  // x_{t+1} = x_t + dt v'
       // state t in the particle order of the recomputation: its list is kept while it is valid
-      TRY(load_keeping_list(sys, seg_x.p + n3 * (size_t)(t - t0)));
+      TRY(load_keeping_list(sys, seg_x.p + n3 * (size_t)(t - t0), t - t0 >= valid_from && sys->rebuilds == builds));
       TRY(adjoint_pass(sys, lv.p, b.p, f.p, nullptr));
       const double c = t == 0 ? h : dt;  // both half-kicks touching state t (one at t = 0)
       const bool in_pe = t > nsteps - n_pe;

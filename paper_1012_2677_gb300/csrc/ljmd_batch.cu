@@ -42,7 +42,7 @@ struct ljmd_batch {
   float4 *f = nullptr, *hi = nullptr;  // forces; FP32 hi parts of the positions (list filter)
   uint4 *xq = nullptr, *ref = nullptr;  // fixed-point position records (force); the records at the build
   int32_t *id = nullptr, *id_alt = nullptr, *img = nullptr, *img_alt = nullptr, *rep_of = nullptr;
-  uint32_t *cell_of = nullptr, *perm = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
+  uint32_t *cell_of = nullptr, *perm = nullptr, *perm_id = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
   uint32_t* scan_tmp = nullptr;
   uint2 *rows = nullptr, *tile_list = nullptr;
   uint16_t* ent = nullptr;
@@ -105,7 +105,7 @@ static void drop_graph(ljmd_batch* b) {
 static void free_batch(ljmd_batch* b) {
   drop_graph(b);
   void* ptrs[] = {b->reps, b->tile_rep, b->x, b->v, b->x_alt, b->v_alt, b->f, b->hi, b->xq, b->ref, b->id, b->id_alt, b->img,
-                  b->img_alt, b->rep_of, b->cell_of, b->perm, b->cell_count, b->cell_start, b->cell_fill,
+                  b->img_alt, b->rep_of, b->cell_of, b->perm, b->perm_id, b->cell_count, b->cell_start, b->cell_fill,
                   b->scan_tmp, b->rows, b->tile_list, b->ent, b->e_rep, b->ke_rep, b->status, b->dmax, b->flag,
                   b->d_rebuilds, b->counter, b->sizes};
   for (void* p : ptrs)
@@ -241,6 +241,10 @@ static int setup_replicas(ljmd_batch* b) {
   c.rc2 = p.cutoff * p.cutoff;
   c.c2 = c2;
   c.c0 = c0;
+  c.inv_sigma = 1.0 / c.sigma;
+  c.c2s = c.c2 / c.sig2;
+  c.inv_sigmaf = (float)c.inv_sigma;
+  c.c2sf = (float)c.c2s;
   c.f24 = (float)(24.0 * p.eps);
   c.f48 = (float)(48.0 * p.eps);
   c.f8c2 = (float)(8.0 * p.eps * c2 / c.sig2);
@@ -287,8 +291,8 @@ static int enqueue_rebuild(ljmd_batch* b, const int* pred) {
   b->launches += 1 + launch_scan_u32(b->cell_count, b->cell_start, b->ncells, b->scan_tmp, st, pred);
   launch_zero_words(b->cell_fill, sizeof(uint32_t) * b->ncells, pred, st);
   launch_scatter(b->cell_of, b->cell_start, b->cell_fill, b->perm, N, st, pred);
-  launch_cell_order(b->cell_start, b->ncells, b->perm, b->id, st, pred);
-  launch_gather_state(b->perm, N, b->x, b->x_alt, b->v, b->v_alt, b->id, b->id_alt, b->img, b->img_alt, nullptr,
+  launch_cell_rank(b->cell_start, b->ncells, b->perm, b->id, b->perm_id, st, pred);
+  launch_gather_state(b->perm_id, N, b->x, b->x_alt, b->v, b->v_alt, b->id, b->id_alt, b->img, b->img_alt, nullptr,
                       nullptr, 0, st, pred);
   launch_copy_words(b->x_alt, b->x, 24 * N, pred, st);
   launch_copy_words(b->v_alt, b->v, 24 * N, pred, st);
@@ -494,6 +498,7 @@ int ljmd_batch_create(ljmd_batch** out, const ljmd_params* p, int32_t replicas, 
   A(&b->rep_of, N);
   A(&b->cell_of, N);
   A(&b->perm, N);
+  A(&b->perm_id, N);
   A(&b->rows, N);
   A(&b->e_rep, 2 * (size_t)replicas);
   A(&b->ke_rep, (size_t)replicas);

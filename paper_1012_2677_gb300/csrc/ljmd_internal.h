@@ -56,6 +56,9 @@ struct LJConst {
   // FP32 constants above with their exponents shifted (no extra rounding); the virial comes out
   // in units of 1/u and is multiplied by u (exactly) when it is summed.
   float f24q, f48q, f8c2q, sig2q, rc2q, c2q;
+  // the adjoint kernel's constants: 1 / sigma and c2 / sigma^2, FP64 and FP32
+  double inv_sigma, c2s;
+  float inv_sigmaf, c2sf;
 };
 
 struct ListBand {
@@ -89,9 +92,9 @@ int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
 void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_t* cell_fill, uint32_t* perm,
                     int64_t N, cudaStream_t s,
     const int* pred = nullptr);
-void launch_cell_order(const uint32_t* cell_start, int64_t ncells, uint32_t* perm, const int32_t* id,
-                       cudaStream_t s,
-    const int* pred = nullptr);
+// Cell by cell, the entries of perm_in ordered by id, written to perm_out.
+void launch_cell_rank(const uint32_t* cell_start, int64_t ncells, const uint32_t* perm_in, const int32_t* id,
+                      uint32_t* perm_out, cudaStream_t s, const int* pred = nullptr);
 void launch_gather_state(const uint32_t* perm, int64_t N, const double* x, double* x2, const double* v, double* v2,
                          const int32_t* id, int32_t* id2, const int32_t* img, int32_t* img2, const void* f, void* f2,
                          int fbytes, cudaStream_t s, const int* pred);
@@ -153,11 +156,13 @@ int launch_force_tile(int precision, int half, int lanes, int energy, const void
                       const int* skip = nullptr);
 size_t adjoint_smem_bytes(const TileArgs& ta, int precision);
 // Adjoint pass (HVP, forces, parameter derivatives) over the list; w, hw, fo are dvec4 [N] in sorted
-// order (fo may be null).  Writes 5 partials per block [w.dF/deps, w.dF/dsigma, dPE/deps,
-// dPE/dsigma, PE]; returns the number of blocks.
+// order (fo may be null), wf the FP32 copy of w (read by the mixed form).  Writes 5 partials per
+// block [w.dF/deps, w.dF/dsigma, dPE/deps, dPE/dsigma, PE]; the last block to finish (ticket: zero
+// between launches) writes their sums, in block order, to sums[0..4].  Returns the number of blocks.
 int launch_adjoint_tile(int precision, const void* pos, const uint32_t* cs, int64_t N, Geom g, TileArgs ta, LJConst c,
-                        const uint2* rows, const uint2* tile_list, const uint16_t* ent, const void* w, void* hw,
-                        void* fo, double* part, int32_t* status, cudaStream_t s);
+                        const uint2* rows, const uint2* tile_list, const uint16_t* ent, const void* w,
+                        const float4* wf, void* hw, void* fo, double* part, unsigned int* ticket, double* sums,
+                        int32_t* status, cudaStream_t s);
 void launch_list_decode(const uint32_t* cs, int64_t N, TileArgs ta, const uint2* rows, const uint16_t* ent,
                         uint64_t E, uint32_t* out, int32_t* status, cudaStream_t s);
 
@@ -223,9 +228,9 @@ void launch_entries_to_keys(unsigned long long* keys, uint64_t E, const int32_t*
 int launch_bitonic_sort(unsigned long long* keys, uint32_t P, cudaStream_t s);
 
 // ---- adjoint pass helpers (kernels_adjoint.cu) ----------------------------------------
-void launch_to_sorted(const double* w_id, const int32_t* id, int64_t N, dvec4* out, cudaStream_t s);
+void launch_to_sorted(const double* w_id, const int32_t* id, int64_t N, dvec4* out, float4* out32, cudaStream_t s);
 void launch_unwrapped(const double* x, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
-                      double* out, cudaStream_t s);
+                      double* out, cudaStream_t s, const StepCtl* ctl = nullptr, int k_step = 0);
 // x (sorted order, SoA) = offset + u (unwrapped, id order) - img L with the current order and images
 void launch_load_unwrapped(const double* u, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
                            double* x, cudaStream_t s);
