@@ -170,18 +170,25 @@ void launch_scatter(const uint32_t* cell_of, const uint32_t* cell_start, uint32_
 }
 
 // Inside each cell order the particles by id (the order of Fig. 3's counting sort, independent of the
-// arrival order of the scatter's atomics): a warp per cell ranks each of the cell's entries of
-// perm_in by the number of its entries with a smaller id and writes it at that rank of perm_out.
+// arrival order of the scatter's atomics): a group of 16 lanes per cell ranks each of the cell's
+// entries of perm_in by the number of its entries with a smaller id and writes it at that rank of
+// perm_out.
 __global__ void k_cell_rank(const uint32_t* __restrict__ start, int64_t ncells, const uint32_t* __restrict__ perm_in,
                             const int32_t* __restrict__ id, uint32_t* __restrict__ perm_out,
                             const int* __restrict__ pred) {
   if (pred && !*pred) return;  // predicated: skipped unless the flag is set
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncells; c += warps) {
-    const uint32_t b = start[c];
-    const int m = (int)(start[c + 1] - b);
-    for (int i0 = 0; i0 < m; i0 += 32) {
+  constexpr int G = 16;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  // every lane of a warp runs the same number of iterations (its two groups' loops share the
+  // shuffles), so the cell index steps by warps: c0 is the warp's first group
+  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  for (int64_t c = g0; c - (g0 & 1) < ncells; c += groups) {
+    const bool have = c < ncells;
+    const uint32_t b = have ? start[c] : 0u;
+    const int m = have ? (int)(start[c + 1] - b) : 0;
+    const int mw = max(m, __shfl_xor_sync(0xffffffffu, m, G));  // the warp's larger cell
+    for (int i0 = 0; i0 < mw; i0 += G) {
       const int i = i0 + lane;
       uint32_t p = 0;
       int key = 0x7fffffff;
@@ -190,11 +197,10 @@ __global__ void k_cell_rank(const uint32_t* __restrict__ start, int64_t ncells, 
         key = id[p];
       }
       int rank = 0;
-      for (int j0 = 0; j0 < m; j0 += 32) {
+      for (int j0 = 0; j0 < mw; j0 += G) {
         const int j = j0 + lane;
         const int other = j < m ? id[perm_in[b + j]] : 0x7fffffff;
-        const int cnt = m - j0 < 32 ? m - j0 : 32;
-        for (int t = 0; t < cnt; ++t) rank += __shfl_sync(0xffffffffu, other, t) < key ? 1 : 0;
+        for (int t = 0; t < G; ++t) rank += __shfl_sync(0xffffffffu, other, t, G) < key ? 1 : 0;
       }
       if (i < m) perm_out[b + rank] = p;
     }
@@ -203,7 +209,7 @@ __global__ void k_cell_rank(const uint32_t* __restrict__ start, int64_t ncells, 
 
 void launch_cell_rank(const uint32_t* cell_start, int64_t ncells, const uint32_t* perm_in, const int32_t* id,
                       uint32_t* perm_out, cudaStream_t s, const int* pred) {
-  int64_t b = (ncells + 7) / 8;
+  int64_t b = (ncells + 15) / 16;  // 16 cells per 256-thread block
   if (b < 1) b = 1;
   if (b > 1048576) b = 1048576;
   k_cell_rank<<<(int)b, 256, 0, s>>>(cell_start, ncells, perm_in, id, perm_out, pred);
