@@ -78,6 +78,31 @@ void launch_accum_q(const double* q, double a0, double a1, double a3, double a4,
 }
 
 // y += a x (n doubles)
+// The reverse step's update of the position adjoint from one adjoint pass (sorted order):
+// lx[3 id[s] + k] -= c hw[s].k + a f[s].k (f may be null when a = 0).
+__global__ void k_adjoint_update(const dvec4* __restrict__ hw, const dvec4* __restrict__ f,
+                                 const int32_t* __restrict__ id, int64_t N, double c, double a,
+                                 double* __restrict__ lx) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = id[s];
+    const dvec4 h = hw[s];
+    double dx = c * h.x, dy = c * h.y, dz = c * h.z;
+    if (f) {
+      const dvec4 g = f[s];
+      dx = fma(a, g.x, dx);
+      dy = fma(a, g.y, dy);
+      dz = fma(a, g.z, dz);
+    }
+    lx[3 * p] -= dx;
+    lx[3 * p + 1] -= dy;
+    lx[3 * p + 2] -= dz;
+  }
+}
+void launch_adjoint_update(const dvec4* hw, const dvec4* f, const int32_t* id, int64_t N, double c, double a,
+                           double* lx, cudaStream_t s) {
+  k_adjoint_update<<<grid_of(N), 256, 0, s>>>(hw, f, id, N, c, a, lx);
+}
+
 __global__ void k_axpy(double* __restrict__ y, double a, const double* __restrict__ x, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = fma(a, x[i], y[i]);

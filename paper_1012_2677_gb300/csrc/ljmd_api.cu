@@ -1453,7 +1453,8 @@ static int ensure_adjoint(ljmd_sys* s) {
 // hw = H w and f = F (device, id order; either may be null), q = [w.F, w.dF/dsigma, PE,
 // dPE/dsigma, PE] (w.dF/deps = w.F / eps, dPE/deps = PE / eps).  With q non-null the sums are read
 // to the host (synchronises); with q null they stay in the device scalars s->d_adj[0..4].
-static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* f_id, double* q) {
+static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* f_id, double* q,
+                        bool f_sorted = false) {
   ljmd_sys* sys = s;
   if (!s->have_list) TRY(rebuild(s));
   TRY(ensure_adjoint(s));
@@ -1463,7 +1464,7 @@ static int adjoint_pass(ljmd_sys* s, const double* w_id, double* hw_id, double* 
   {
     PhaseTimer timer(s, PH_ADJOINT);
     launch_adjoint_tile(s->precision, force_pos(s), s->cell_start, N, s->g, s->ta, s->c, s->rows, s->tile_list,
-                        s->ent, s->adj_w, s->adj_wf, s->adj_hw, f_id ? s->adj_f : nullptr, s->part_adj,
+                        s->ent, s->adj_w, s->adj_wf, s->adj_hw, (f_id || f_sorted) ? s->adj_f : nullptr, s->part_adj,
                         s->adj_ticket, s->d_adj, s->d_status, st);
   }
   s->launches += 2;
@@ -1513,7 +1514,7 @@ static int load_keeping_list(ljmd_sys* s, const double* u, bool known_valid = fa
   launch_load_unwrapped(u, s->img, s->id, s->n, s->g.offset, s->L, s->x, s->st);
   s->launches += 1;
   CKL();
-  CK(cudaMemsetAsync(s->d_dmax, 0, 8, s->st));
+  if (!known_valid) CK(cudaMemsetAsync(s->d_dmax, 0, 8, s->st));  // (a run clears it before its use)
   IntegrateArgs a{0.0, 0.0, 0.0, 0, 1};  // no kick, no drift: copies and displacement only
   integrate(s, a);
   CKL();
@@ -1714,18 +1715,19 @@ int ljmd_traj_loss_grad(ljmd_sys* sys, int64_t n, double box, const double* x0, 
       launch_axpy(lv.p, dt, lx.p, (int64_t)n3, st);  // x_{t+1} = x_t + dt v'
       // state t in the particle order of the recomputation: its list is kept while it is valid
       TRY(load_keeping_list(sys, seg_x.p + n3 * (size_t)(t - t0), t - t0 >= valid_from && sys->rebuilds == builds));
-      TRY(adjoint_pass(sys, lv.p, b.p, f.p, nullptr));
       const double c = t == 0 ? h : dt;  // both half-kicks touching state t (one at t = 0)
       const bool in_pe = t > nsteps - n_pe;
-      launch_axpy(lx.p, -c, b.p, (int64_t)n3, st);
+      // H lv (and F where the PE term needs it) in the sorted order, then lx -= c H lv + wpe F
+      TRY(adjoint_pass(sys, lv.p, nullptr, nullptr, nullptr, in_pe));
+      launch_adjoint_update(sys->adj_hw, in_pe ? sys->adj_f : nullptr, sys->id, sys->n, c, in_pe ? wpe : 0.0, lx.p,
+                            st);
       launch_accum_q(sys->d_adj, c / eps, c, in_pe ? wpe : 0.0, in_pe ? wpe / eps : 0.0, gthd.p, st);
-      if (in_pe) launch_axpy(lx.p, -wpe, f.p, (int64_t)n3, st);
       if (t == 0) {
         // MSD term at t = 0: -2 (x_n - x_0) / N
         launch_scaled_diff(b.p, -2.0 / (double)n, xNu.p, x0u.p, (int64_t)n3, st);
         launch_axpy(lx.p, 1.0, b.p, (int64_t)n3, st);
       }
-      sys->launches += 3 + (in_pe ? 1 : 0) + (t == 0 ? 2 : 0);
+      sys->launches += 3 + (t == 0 ? 2 : 0);
       CKL();
     }
   }

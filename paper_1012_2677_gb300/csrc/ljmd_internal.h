@@ -235,6 +235,9 @@ void launch_unwrapped(const double* x, const int32_t* img, const int32_t* id, in
 void launch_load_unwrapped(const double* u, const int32_t* img, const int32_t* id, int64_t N, double offset, double L,
                            double* x, cudaStream_t s);
 void launch_axpy(double* y, double a, const double* x, int64_t n, cudaStream_t s);
+// lx[3 id[s] + k] -= c hw[s].k + a f[s].k over the sorted order (f null: a ignored).
+void launch_adjoint_update(const dvec4* hw, const dvec4* f, const int32_t* id, int64_t N, double c, double a,
+                           double* lx, cudaStream_t s);
 // gth[0] += a0 q[0] + a4 q[4], gth[1] += a1 q[1] + a3 q[3] (device scalars)
 void launch_accum_q(const double* q, double a0, double a1, double a3, double a4, double* gth, cudaStream_t s);
 void launch_scaled_diff(double* y, double a, const double* u, const double* w, int64_t n, cudaStream_t s);
