@@ -111,6 +111,47 @@ def test_pair_list_edge_cases(list_form):
     assert np.array_equal(got, O.pairs_within(x, L, rs))
 
 
+def _clustered_state(seed=21):
+    """A dense FCC cluster (rho 2.0, nearest neighbours 0.89 apart) inside a sparse jittered cubic
+    background (spacing 2): the cluster's cells hold about 54 particles, so a key's three-cell
+    windows run to about 160 candidates and its row to about 220 entries.  The list kernel's
+    bit pool and segment staging then overflow, and it takes its slower paths (tested again,
+    written to global memory directly); the force kernels read such long segments from HBM."""
+    a = (4.0 / 2.0) ** (1.0 / 3.0)
+    g = np.arange(6)
+    basis = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 1, 3)
+    cluster = 3.0 + ((cells + basis[None]) * a).reshape(-1, 3)
+    lo, hi = 3.0 - 1.0, 3.0 + 6 * a + 1.0
+    s = np.arange(12) * 2.0 + 1.0
+    bg = np.stack(np.meshgrid(s, s, s, indexing="ij"), -1).reshape(-1, 3)
+    bg = bg[~np.all((bg > lo) & (bg < hi), axis=1)]
+    bg = bg + synth.displacements(len(bg), 0.3, seed)
+    cluster = cluster + synth.displacements(len(cluster), 0.05, seed + 1)
+    return synth.dyadic(O.wrap(np.vstack([cluster, bg]), 24.0)), 24.0
+
+
+@pytest.mark.parametrize("precision,list_form", FORMS)
+def test_dense_cluster_list_and_forces(precision, list_form):
+    """Pair list bit-exact and forces within tolerance where the list kernel's shared-memory areas
+    overflow (see _clustered_state)."""
+    x, L = _clustered_state()
+    with _system(precision, list_form) as s:
+        s.set_state(x, None, L)
+        s.build_pairlist()
+        got = s.pairs()
+        s.compute_forces()
+        _, _, gf, _ = s.get_state()
+        st = s.stats()
+    assert st["status_word"] == 0
+    ref = O.pairs_within(x, L, 3.0)
+    assert np.array_equal(got, ref)
+    assert np.bincount(ref.ravel(), minlength=len(x)).max() > 150  # rows long enough to overflow
+    F, _, _ = O.forces(x, L)
+    rms = np.sqrt((F ** 2).sum(1).mean())
+    assert np.sqrt(((gf - F) ** 2).sum(1)).max() / rms <= FORCE_TOL[precision]
+
+
 def _oracle_grid(x, L, rs):
     n = O.cells_per_side(L, rs)
     count, pointer, order = O.grid_list(O.cell_labels(O.wrap(x, L), L, n), n ** 3)
