@@ -73,18 +73,41 @@ __device__ __forceinline__ float block_max(float v, float* sh) {
 // launch).
 __device__ __forceinline__ void energy_record_block(const double* pv, int nbf, const double* kp, int nbi,
                                                     double pe_scale, double* energies, double* log, int64_t cap,
-                                                    int64_t* count, double step, double* sh) {
+                                                    int64_t* count, double step) {
   double pe = 0.0, vir = 0.0, ke = 0.0;
   for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
     pe += __ldcg(pv + 2 * (size_t)b);
     vir += __ldcg(pv + 2 * (size_t)b + 1);
   }
   for (int b = threadIdx.x; b < nbi; b += blockDim.x) ke += __ldcg(kp + b);
-  pe = block_sum(pe, sh);
+  // the three sums side by side (each in block_sum's order: warp butterflies, then warp 0)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pe += __shfl_xor_sync(0xffffffffu, pe, o);
+    vir += __shfl_xor_sync(0xffffffffu, vir, o);
+    ke += __shfl_xor_sync(0xffffffffu, ke, o);
+  }
+  __shared__ double sh3[3][32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
-  vir = block_sum(vir, sh);
+  if (l == 0) {
+    sh3[0][w] = pe;
+    sh3[1][w] = vir;
+    sh3[2][w] = ke;
+  }
   __syncthreads();
-  ke = block_sum(ke, sh);
+  if (w == 0) {
+    const bool in = l < (int)(blockDim.x >> 5);
+    pe = in ? sh3[0][l] : 0.0;
+    vir = in ? sh3[1][l] : 0.0;
+    ke = in ? sh3[2][l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      pe += __shfl_xor_sync(0xffffffffu, pe, o);
+      vir += __shfl_xor_sync(0xffffffffu, vir, o);
+      ke += __shfl_xor_sync(0xffffffffu, ke, o);
+    }
+  }
   if (threadIdx.x == 0) {
     pe *= pe_scale;
     vir *= pe_scale;

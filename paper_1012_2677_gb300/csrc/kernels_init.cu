@@ -37,8 +37,7 @@ __global__ void k_energy_finalize(const double* __restrict__ pv, int nbf, const 
                                   int64_t cap, int64_t* __restrict__ count, double step,
                                   const int* __restrict__ skip) {
   if (skip && *skip) return;  // a device-decided run stopped before this step
-  __shared__ double sh[32];
-  energy_record_block(pv, nbf, kp, nbi, pe_scale, energies, log, cap, count, step, sh);
+  energy_record_block(pv, nbf, kp, nbi, pe_scale, energies, log, cap, count, step);
 }
 
 void launch_energy_finalize(const double* pe_vir_part, int nb_force, const double* ke_part, int nb_int,

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
       __threadfence();
       if (fin.rec)
         energy_record_block(fin.pv, fin.nbf, ke_part, gridDim.x, fin.pe_scale, fin.energies, fin.log, fin.cap,
-                            fin.count, fin.step, sh);
+                            fin.count, fin.step);
       if (threadIdx.x == 0) {
         if (fin.check) step_check_one(dmax_bits, fin.ctl, fin.s, fin.disp_limit, fin.dutc, fin.two_dt);
         *fin.ticket = 0u;

@@ -607,7 +607,8 @@ static int rebuild(ljmd_sys* s) {
       CKL();
       CK(cudaMemcpyAsync(s->h_u32 + 4, s->d_total64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(s->h_u32 + 12, s->d_sizes + 3, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      CK(cudaMemcpyAsync(s->h_u32 + 13, s->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));  // one round trip: list size, longest segment and status
       unsigned long long total64, actual64;
       memcpy(&total64, s->h_u32 + 4, sizeof(total64));
       memcpy(&actual64, s->h_u32 + 6, sizeof(actual64));
@@ -616,7 +617,7 @@ static int rebuild(ljmd_sys* s) {
       total = total64;
       if (total <= s->ent_cap) {
         int32_t w = 0;
-        TRY(device_status(s, &w));
+        memcpy(&w, s->h_u32 + 13, sizeof(w));
         if (w) {
           fprintf(stderr, "ljmd: list construction raised status %d (n=%d T=%d tiles=%lld staged<=%d own<=%d)\n", w,
                   s->ta.n, s->ta.T, (long long)s->ta.ntiles, s->ta.max_staged, s->ta.max_own);
