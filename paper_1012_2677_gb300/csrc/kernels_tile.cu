@@ -14,7 +14,7 @@
 // sorted index in w), the image shift is the integer round(L / u), and a partner difference is
 // the exact integer X_j - X_i converted once to FP32.  List kernels: the FP32 hi parts (top 24
 // significand bits) of the stored coordinates, whose differences are exact.  FP64 form: the FP64
-// coordinates, with the shift code kept in w and added to the exact difference.
+// coordinates, the periodic images put in place when staged (one rounding per staged coordinate).
 //
 // The list holds 16-bit indices into the key particle's staged tile; rows are (start, length)
 // per particle; the rows of one tile form one contiguous segment, padded to 8 entries so that
@@ -366,8 +366,8 @@ __device__ __forceinline__ uint32_t shift_q(uint32_t q, int s, const Geom& g) {
 }
 
 // Wait (all threads, bounded) for the copies of a staged tile, then fill in the image shifts
-// (mixed: added to the fixed-point record or to hi; FP64: code in w) and, if wanted, the sorted
-// indices.  Returns false
+// (mixed: added to the fixed-point record or to hi; FP64: s L added to the coordinates) and, if
+// wanted, the sorted indices.  Returns false
 // (all threads) on timeout, after recording it; the caller drains any other copies in flight.
 template <bool MIXED, bool FORCE>
 __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs& ta, const Geom& g, TileShared& S,
@@ -390,12 +390,12 @@ __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs&
   // interior tiles (no periodic image among the staged cells) need no shifts
   const bool interior = ti.cx >= 1 && ti.cx <= ta.n - 2 && ti.cy >= 1 && ti.cy <= ta.n - 2 && ti.z0 >= 1 &&
                         ti.z0 + ti.Tp <= ta.n - 1;
-  if (MIXED && interior && !want_gid) return true;
+  if (interior && !want_gid) return true;
   for (int q = warp; q < S.ncell; q += (int)(blockDim.x >> 5)) {
     int sx = 0, sy = 0, sz = 0;
     if (!interior) cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
     const bool shifted = (sx | sy | sz) != 0;
-    if (MIXED && !shifted && !want_gid) continue;  // FP64: every slot gets its shift code
+    if (!shifted && !want_gid) continue;
     const int a = S.offq[q], b = S.offq[q + 1], gq = S.g0[q];
     for (int s = a + lane; s < b; s += 32) {
       if (MIXED) {
@@ -412,8 +412,11 @@ __device__ __forceinline__ bool stage_finish(const TileInfo& ti, const TileArgs&
             h->z = fmaf((float)sz, g.L_hi, h->z);
           }
         }
-      } else {
-        ((dvec4*)(smem + L.pos))[s].w = (double)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
+      } else if (shifted) {  // the image itself: one rounding per staged coordinate, none per pair
+        dvec4* p = (dvec4*)(smem + L.pos) + s;
+        p->x += (double)sx * g.L;
+        p->y += (double)sy * g.L;
+        p->z += (double)sz * g.L;
       }
       if (want_gid) ((int*)(smem + L.gid))[s] = gq + (s - a);
     }
@@ -463,14 +466,6 @@ __device__ __forceinline__ void stage_whole(int64_t N, const void* __restrict__ 
   }
 }
 
-// Image shift of an FP64 staged copy (decoded from w), times L.
-__device__ __forceinline__ void shift_of(double w, const Geom& g, double& sx, double& sy, double& sz) {
-  const int code = (int)w;
-  sx = (double)(code % 3 - 1) * g.L;
-  sy = (double)((code / 3) % 3 - 1) * g.L;
-  sz = (double)(code / 9 - 1) * g.L;
-}
-
 // Exact list test of the oracle (FP64, fixed min-image formula, no FMA) on stored coordinates.
 __device__ __forceinline__ bool pair_in_exact(const double* __restrict__ x, int64_t N, int i, int j, const Geom& g,
                                               double rs2) {
@@ -504,14 +499,8 @@ __device__ __forceinline__ bool candidate_in(const unsigned char* smem, const Ti
     r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   } else {
     const dvec4 a = ((const dvec4*)(smem + L.pos))[li], b = ((const dvec4*)(smem + L.pos))[lj];
-    double dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;  // exact
-    if (!WHOLE) {
-      double sx, sy, sz;
-      shift_of(b.w, g, sx, sy, sz);
-      dx += sx;
-      dy += sy;
-      dz += sz;
-    } else {
+    double dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;  // staged tiles: images already in place
+    if (WHOLE) {
       dx = fma(-rint(dx * g.inv_L64), g.L, dx);
       dy = fma(-rint(dy * g.inv_L64), g.L, dy);
       dz = fma(-rint(dz * g.inv_L64), g.L, dz);
@@ -1225,15 +1214,9 @@ __device__ __forceinline__ void force_tile_compute(const TileShared& S, const un
         const dvec4 qi = ((const dvec4*)sh_pos)[l];
         for (unsigned e = lane; e < row.y; e += LANES) {
           const int j = el[row.x + e];
-          const dvec4 qj = ((const dvec4*)sh_pos)[j];
-          double dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;  // exact
-          if (!WHOLE) {
-            double sx, sy, sz;
-            shift_of(qj.w, g, sx, sy, sz);
-            dx += sx;
-            dy += sy;
-            dz += sz;
-          } else {
+          const dvec4 qj = ((const dvec4*)sh_pos)[j];  // its image already in place (tiles)
+          double dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;
+          if (WHOLE) {
             dx = fma(-rint(dx * g.inv_L64), g.L, dx);
             dy = fma(-rint(dy * g.inv_L64), g.L, dy);
             dz = fma(-rint(dz * g.inv_L64), g.L, dz);
@@ -1429,22 +1412,13 @@ __device__ __forceinline__ bool tile_interior(const TileInfo& ti, const TileArgs
   return ti.cx >= 1 && ti.cx <= ta.n - 2 && ti.cy >= 1 && ti.cy <= ta.n - 2 && ti.z0 >= 1 && ti.z0 + ti.Tp <= ta.n - 1;
 }
 
-// Shift codes (FP64 form: every slot's w holds (sx + 1) + 3 (sy + 1) + 9 (sz + 1)) and, for the
-// half list, the sorted indices of a staged tile, written by one producer warp after the copies
-// land (the pipelined kernel's version of stage_finish for the FP64 form).
-__device__ __forceinline__ void stage_codes_warp(const TileInfo& ti, const TileArgs& ta, const TileShared& S,
-                                                 unsigned char* smem, const TileLayout& L, bool want_gid,
-                                                 int lane) {
-  const bool interior = tile_interior(ti, ta);
+// FP64 half list, by the producer warp: the sorted indices of a staged tile (the consumers put the
+// periodic images in place, as for the mixed form).
+__device__ __forceinline__ void stage_gid_warp(const TileShared& S, unsigned char* smem, const TileLayout& L,
+                                               int lane) {
   for (int q = 0; q < S.ncell; ++q) {
-    int sx = 0, sy = 0, sz = 0;
-    if (!interior) cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
-    const double code = (double)((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
     const int a = S.offq[q], b = S.offq[q + 1], gq = S.g0[q];
-    for (int e = a + lane; e < b; e += 32) {
-      ((dvec4*)(smem + L.pos))[e].w = code;
-      if (want_gid) ((int*)(smem + L.gid))[e] = gq + (e - a);
-    }
+    for (int e = a + lane; e < b; e += 32) ((int*)(smem + L.gid))[e] = gq + (e - a);
   }
 }
 
@@ -1453,6 +1427,7 @@ __device__ __forceinline__ void stage_codes_warp(const TileInfo& ti, const TileA
 // writes before later bulk copies into the same bytes; the caller then waits for all consumer
 // warps (a bounded mbarrier wait, not bar.sync, so that a warp that left on a timeout cannot hold
 // the others forever).
+template <bool MIXED>
 __device__ __forceinline__ void stage_shift_consumers(const TileInfo& ti, const TileArgs& ta, const Geom& g,
                                                       const TileShared& S, unsigned char* smem, const TileLayout& L,
                                                       int consumers) {
@@ -1462,10 +1437,17 @@ __device__ __forceinline__ void stage_shift_consumers(const TileInfo& ti, const 
     cell_of_q(ti, ta.n, S.ncol, q, sx, sy, sz);
     if ((sx | sy | sz) == 0) continue;
     for (int e = S.offq[q] + lane; e < S.offq[q + 1]; e += 32) {
-      uint4* r = (uint4*)(smem + L.pos) + e;
-      r->x = shift_q(r->x, sx, g);
-      r->y = shift_q(r->y, sy, g);
-      r->z = shift_q(r->z, sz, g);
+      if (MIXED) {
+        uint4* r = (uint4*)(smem + L.pos) + e;
+        r->x = shift_q(r->x, sx, g);
+        r->y = shift_q(r->y, sy, g);
+        r->z = shift_q(r->z, sz, g);
+      } else {  // FP64: s L added, one rounding per staged coordinate instead of a shift per pair
+        dvec4* p = (dvec4*)(smem + L.pos) + e;
+        p->x += (double)sx * g.L;
+        p->y += (double)sy * g.L;
+        p->z += (double)sz * g.L;
+      }
     }
   }
   fence_proxy_async_smem();
@@ -1476,9 +1458,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // CW consumer warps: 8 for tiles of up to 4 cells, 12 for larger tiles (more keys per tile).
-// Forms: the mixed form with the full list (consumers apply the image shifts of periodic tiles)
-// and the FP64 form with the half list (the producer writes the shift codes and sorted indices;
-// the consumers scatter the partners' forces with atomics).
+// Forms: the mixed form with the full list and the FP64 form with the half list (the producer writes
+// the sorted indices; the consumers scatter the partners' forces with atomics).  The consumers put
+// the periodic images of a boundary tile in place before computing it.
 template <bool MIXED, bool HALF, int LANES, bool ENERGY, bool LONGLIST, int CW>
 __global__ void __launch_bounds__(pipe_threads(CW), (MIXED && CW <= 8) ? 3 : 2)
     k_force_pipe(const void* __restrict__ pos, const uint32_t* __restrict__ cs, Geom g, TileArgs ta, LJConst c,
@@ -1568,15 +1550,15 @@ __global__ void __launch_bounds__(pipe_threads(CW), (MIXED && CW <= 8) ? 3 : 2)
           }
           break;
         }
-        if (!MIXED) {  // shift codes and sorted indices by this warp; they precede later bulk copies
-          stage_codes_warp(ti, ta, S, buf, L, HALF, lane);
+        if (!MIXED) {  // sorted indices by this warp; they precede later bulk copies
+          stage_gid_warp(S, buf, L, lane);
           fence_proxy_async_smem();
           __syncwarp();
         }
       }
       if (lane == 0) {
         s_ti[slot] = ti;
-        s_valid[slot] = staged ? ((!MIXED || tile_interior(ti, ta)) ? 1 : 2) : 0;
+        s_valid[slot] = staged ? (tile_interior(ti, ta) ? 1 : 2) : 0;
         mbar_arrive(&ready[b]);  // release: bookkeeping and copies visible to the consumers
       }
     }
@@ -1596,7 +1578,7 @@ __global__ void __launch_bounds__(pipe_threads(CW), (MIXED && CW <= 8) ? 3 : 2)
       if (v < 0) break;
       unsigned char* buf = smem + b * buf_bytes;
       if (v == 2) {  // periodic tile: shifts by all consumer warps, then wait for all of them
-        stage_shift_consumers(s_ti[slot], ta, g, SS[slot], buf, L, CW);
+        stage_shift_consumers<MIXED>(s_ti[slot], ta, g, SS[slot], buf, L, CW);
         __syncwarp();
         if (lane == 0) mbar_arrive(&shifted[b]);
         ok = __all_sync(0xffffffffu, mbar_wait(&shifted[b], (shpar >> b) & 1u, wait_budget())) != 0;
@@ -1813,15 +1795,9 @@ __device__ __forceinline__ void adjoint_tile_compute(const TileShared& S, const 
         const dvec4 qi = ((const dvec4*)sh_pos)[l];
         for (unsigned e = lane; e < row.y; e += kAdjLanes) {
           const int j = el[row.x + e];
-          const dvec4 qj = ((const dvec4*)sh_pos)[j];
+          const dvec4 qj = ((const dvec4*)sh_pos)[j];  // its image already in place (tiles)
           double dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;
-          if (!WHOLE) {
-            double sx, sy, sz;
-            shift_of(qj.w, g, sx, sy, sz);
-            dx += sx;
-            dy += sy;
-            dz += sz;
-          } else {
+          if (WHOLE) {
             dx = fma(-rint(dx * g.inv_L64), g.L, dx);
             dy = fma(-rint(dy * g.inv_L64), g.L, dy);
             dz = fma(-rint(dz * g.inv_L64), g.L, dz);
