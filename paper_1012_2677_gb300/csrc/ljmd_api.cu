@@ -644,8 +644,9 @@ static int rebuild(ljmd_sys* s) {
       // The pipelined kernel of the mixed form with the full list runs 3 CTAs per SM with 8
       // consumer warps (T <= 4) and 2 with 12: the staged segments are capped so that this many
       // fit in an SM's shared memory (1 KB reserved and at most 6 KB of static shared memory per
-      // CTA), when that still stages at least three quarters of the largest segment.  Longer
-      // segments are read from HBM.
+      // CTA), when that still stages at least half of the largest segment.  Longer segments are
+      // read from HBM (on the FCC start, whose longest segment is 1.5 times the liquid's, this
+      // still beat one CTA per SM: 16.4M, 20 steps, 3.41 -> 3.35 ms per step).
       if (s->precision == LJ_MIXED && !s->list_half && !s->ta.whole && nbuf == 2) {
         int smem_sm = 0;
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -653,7 +654,7 @@ static int rebuild(ljmd_sys* s) {
         const int64_t per_cta = (int64_t)smem_sm / target - 1024 - 6144;
         const int64_t fb = (int64_t)force_smem_bytes(tz, s->precision, 2, 0);
         const int64_t room_occ = (per_cta - fb) / (2 * nbuf) - 16;
-        if (room_occ >= (int64_t)s->ta.max_list * 3 / 4) room = std::min(room, room_occ);
+        if (room_occ >= (int64_t)s->ta.max_list / 2) room = std::min(room, room_occ);
       }
       s->ta.list_cap = (int32_t)std::max<int64_t>(0, std::min<int64_t>(s->ta.max_list, room) & ~(int64_t)7);
       break;
