@@ -153,10 +153,14 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
     }
   }
   if (fin.ticket) {  // the last CTA to finish takes the energy record and the validity check
+    // thread 0 wrote the CTA's partial (the maxima went by device-wide atomics): it alone orders
+    // that write before its ticket
     __shared__ int s_last;
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(fin.ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(fin.ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (s_last) {
       __threadfence();

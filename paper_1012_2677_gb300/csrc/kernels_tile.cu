@@ -1898,10 +1898,13 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     if (threadIdx.x == 0) part[kAdjParts * (size_t)blockIdx.x + k] = t;
     __syncthreads();
   }
-  // the last CTA to finish sums the partials of all CTAs in block order
+  // the last CTA to finish sums the partials of all CTAs in block order (thread 0 wrote this CTA's
+  // partials and orders them before its ticket)
   __shared__ int s_last;
-  __threadfence();
-  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
   __syncthreads();
   if (s_last) {
     __threadfence();
