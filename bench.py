@@ -305,20 +305,26 @@ def run_ours(args, wl, world, rank, local):
         ljmd.ljmd_get_state(s2.h, x0, v0, None, None, 0)
         xo = torch.empty((N, 3), dtype=torch.float64).pin_memory()
         vo = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+
+        def job():
+            ljmd.ljmd_set_state(s2.h, N, s2.box, x0, v0)
+            s2.step(wl["dt"], args.steps)
+            ljmd.ljmd_get_state(s2.h, xo, vo, None, None, 0)
+            s2.energies()
+
+        job()  # untimed: the system's one-time allocations (list, tiles) happen in the first job
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        ljmd.ljmd_set_state(s2.h, N, s2.box, x0, v0)
-        s2.step(wl["dt"], args.steps)
-        ljmd.ljmd_get_state(s2.h, xo, vo, None, None, 0)
-        s2.energies()
+        job()
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         barrier()
         t_e2e = reduce_max(t_e2e, dist)
         e2e = {"value": job_value(N * args.steps, world, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": 2 * 24 * N / args.steps, "d2h_bytes_per_step": (2 * 24 * N + 24) / args.steps,
-               "note": "set_state from pinned host + K steps + get_state/energies to host, per K-step job"}
+               "note": "set_state from pinned host + K steps + get_state/energies to host, per K-step job "
+                       "(the second such job on the system; the first, untimed, makes its allocations)"}
         s2.close()
 
     batched = None if args.no_batch else run_batched(args, stream, world, rank, barrier, peaks, peak_kind)
