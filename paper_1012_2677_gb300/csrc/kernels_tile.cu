@@ -670,11 +670,14 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 // one or a few distinct addresses.  The kept-candidate bits of each 32-candidate word go to a
 // per-tile pool in shared memory; a count per (key, column) gives every key its row and each
 // column its place in the row (columns in order, partners ascending: the list is deterministic);
-// one atomic reserves the tile's segment (padded to 8 entries); the entries are written from the
-// bits into shared memory and copied out with 16-byte stores.  Items whose bits do not fit in the
-// pool are tested again when written.  With the half list, a column other than the key's own has
-// all its cells before or all after the key's in the cell order (cell = (X n + Y) n + Z), so such
-// a column is kept or skipped as a whole; in the own column the sorted indices decide per pair.
+// one atomic reserves the tile's segment (padded to 8 entries) while the entries are written from
+// the bits into shared memory over the staged positions (no longer needed) and then copied out
+// with 16-byte stores.  Items whose bits do not fit in the pool are tested again when written (and
+// that tile's entries go to global memory directly).  Warp 0 takes the next tile's bookkeeping while
+// the others count, its cell bounds copied a tile ahead with cp.async.  With the half list, a
+// column other than the key's own has all its cells before or all after the key's in the cell
+// order (cell = (X n + Y) n + Z), so such a column is kept or skipped as a whole; in the own column
+// the sorted indices decide per pair.
 constexpr int kWinPoolPerItem = 2;  // pool words per work item on average (two words hold 64 candidates)
 constexpr int kWinThreads = 256;    // threads of a window-kernel CTA
 constexpr int kWinCtas = 3;         // window-kernel CTAs resident per SM (register budget)
@@ -716,9 +719,9 @@ __host__ __device__ __forceinline__ WinLayout win_layout(const TileArgs& ta) {
   return W;
 }
 
-// Own column's cells of the key particle's neighbour column k, for the half list: +1 if all
-// cells of column k come after the tile's own cells in the cell order, -1 if all come before,
-// 0 for the own column (decided per pair by the sorted indices).
+// Order of neighbour column k against the tile's own column, for the half list: +1 if all cells of
+// column k come after the tile's own cells in the cell order, -1 if all come before, 0 for the own
+// column (decided per pair by the sorted indices).
 __device__ __forceinline__ int win_column_order(const TileInfo& ti, int n, int k) {
   if (k == 4) return 0;
   int sx, sy;
