@@ -43,6 +43,65 @@ __device__ __forceinline__ void step_check_one(uint32_t* dmax_bits, StepCtl* ctl
   }
 }
 
+// One particle's inputs to the integrator: force, velocity, position and (when the position copy is
+// rewritten) the displacement reference.
+template <bool MIXED>
+struct IntegrateIn;
+template <>
+struct IntegrateIn<true> {
+  float4 f;
+  uint4 r;
+  double v[3], x[3];
+};
+template <>
+struct IntegrateIn<false> {
+  dvec4 f, r;
+  double v[3], x[3];
+};
+
+template <bool MIXED>
+__device__ __forceinline__ void integrate_load(IntegrateIn<MIXED>& in, const double* __restrict__ x,
+                                               const double* __restrict__ v, const void* __restrict__ fptr,
+                                               const void* __restrict__ refp, int64_t N, int64_t i, int shadow) {
+  if constexpr (MIXED) {
+    in.f = ((const float4*)fptr)[i];
+    if (shadow) in.r = ((const uint4*)refp)[i];
+  } else {
+    in.f = ((const dvec4*)fptr)[i];
+    if (shadow) in.r = ((const dvec4*)refp)[i];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    in.v[k] = v[k * N + i];
+    in.x[k] = x[k * N + i];
+  }
+}
+
+// Hint that the lines holding particle j's inputs be brought into L2 (one prefetch per stream; no
+// registers are held for the data).
+template <bool MIXED>
+__device__ __forceinline__ void integrate_prefetch_l2(const double* x, const double* v, const void* fptr,
+                                                      const void* refp, int64_t N, int64_t j, int shadow) {
+  const void* f = MIXED ? (const void*)((const float4*)fptr + j) : (const void*)((const dvec4*)fptr + j);
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(f));
+  if (shadow) {
+    const void* r = MIXED ? (const void*)((const uint4*)refp + j) : (const void*)((const dvec4*)refp + j);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(r));
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(v + k * N + j));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(x + k * N + j));
+  }
+}
+
+// The grid-stride loop is software-pipelined: the next particle's loads are issued before the
+// FP64 kick and drift of the current one, so that the FP64 pipe (7 operations per particle at
+// 1/64 of the FP32 rate) works while those loads are in flight instead of after them, and the lines
+// of the particle kPrefetchAhead strides on are requested into L2, which keeps more of HBM's
+// requests in flight than the registers of two particles per thread can.
+constexpr int kPrefetchAhead = 2;
+
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, double* __restrict__ v,
                                                    const void* __restrict__ fptr, void* __restrict__ pos,
@@ -57,11 +116,19 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
   double ke_acc = 0.0;
   float d2max = 0.0f, v2max = 0.0f;
   bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  IntegrateIn<MIXED> cur = {};
+  if (i < N) integrate_load<MIXED>(cur, x, v, fptr, refp, N, i, a.shadow);
+  for (; i < N; i += stride) {
+    IntegrateIn<MIXED> nxt = {};
+    if (i + stride < N) integrate_load<MIXED>(nxt, x, v, fptr, refp, N, i + stride, a.shadow);
+    if (i + kPrefetchAhead * stride < N)
+      integrate_prefetch_l2<MIXED>(x, v, fptr, refp, N, i + kPrefetchAhead * stride, a.shadow);
     double F[3];
     float Ff[3] = {0.0f, 0.0f, 0.0f};
-    if (MIXED) {
-      const float4 f = ((const float4*)fptr)[i];
+    if constexpr (MIXED) {
+      const float4 f = cur.f;
       Ff[0] = f.x;
       Ff[1] = f.y;
       Ff[2] = f.z;
@@ -69,7 +136,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
       F[1] = f32_to_f64(f.y);
       F[2] = f32_to_f64(f.z);
     } else {
-      const dvec4 f = ((const dvec4*)fptr)[i];
+      const dvec4 f = cur.f;
       F[0] = f.x;
       F[1] = f.y;
       F[2] = f.z;
@@ -79,7 +146,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
     double ke_d = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      double vk = v[k * N + i];
+      double vk = cur.v[k];
       if (a.ke) {
         if (MIXED) {
           const float vf = fmaf(kpre_f, Ff[k], f64_to_f32(vk));
@@ -94,7 +161,7 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
         const float vs = MIXED ? f64_to_f32(vk) : (float)vk;
         vd2 = fmaf(vs, vs, vd2);
       }
-      double xk = x[k * N + i];
+      double xk = cur.x[k];
       if (a.dt != 0.0) xk = fma(a.dt, vk, xk);
       v[k * N + i] = vk;
       x[k * N + i] = xk;
@@ -106,23 +173,24 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
     if (a.shadow) {
       // speed of the drift (the velocity that moved the particle this step), for the DUTC rule
       v2max = fmaxf(v2max, vd2);
-      if (MIXED) {
+      if constexpr (MIXED) {
         const uint4 q = make_uint4(fixq(xs[0], a.qk), fixq(xs[1], a.qk), fixq(xs[2], a.qk), (uint32_t)i);
         ((uint4*)pos)[i] = q;
         // displacement since the list was built, from the records: exact integer differences
         // (within u of the FP64 ones), converted once and scaled by u
-        const uint4 r = ((const uint4*)refp)[i];
+        const uint4 r = cur.r;
         const float dx = qdiff(q.x, r.x) * qu, dy = qdiff(q.y, r.y) * qu, dz = qdiff(q.z, r.z) * qu;
         d2max = fmaxf(d2max, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
       } else {
         ((dvec4*)pos)[i] = make_dvec4(xs[0], xs[1], xs[2], 0.0);
-        const dvec4 r = ((const dvec4*)refp)[i];
+        const dvec4 r = cur.r;
         const double dx = xs[0] - r.x, dy = xs[1] - r.y, dz = xs[2] - r.z;
         // rounded up to FP32, so the measured maximum never falls short of the FP64 value and the
         // margin/2 rule keeps its guarantee at the FP64 form's tight limit
         d2max = fmaxf(d2max, __double2float_ru(fma(dx, dx, fma(dy, dy, dz * dz))));
       }
     }
+    cur = nxt;
   }
   if (bad) atomicOr(status, LJ_ST_NONFINITE);
   __shared__ double sh[32];
@@ -175,8 +243,6 @@ __global__ void __launch_bounds__(256) k_integrate(double* __restrict__ x, doubl
   }
 }
 
-// Blocks of one resident wave (at most red_blocks(N)): the grid-stride loop then ends in step on
-// every SM instead of leaving a partial second wave.
 // Block shape: 256-thread blocks of one resident wave (at most red_blocks(N)), so that the grid-stride
 // loop ends in step on every SM; for a system too small to give every SM a block, narrower blocks
 // (down to one warp) spread the particles over the SMs, each of whose FP64 pipes takes 1/64 of the
