@@ -70,9 +70,6 @@ void launch_rebuild_flag(const uint32_t* dmax_bits, float limit2, int* flag, lon
   k_rebuild_flag<<<1, 1, 0, s>>>(dmax_bits, limit2, flag, rebuilds);
 }
 
-__global__ void k_set_flag(int* flag, int value) { *flag = value; }
-void launch_set_flag(int* flag, int value, cudaStream_t s) { k_set_flag<<<1, 1, 0, s>>>(flag, value); }
-
 // Predicated copy of `bytes` (a multiple of 4) from in to out: 16-byte words while both
 // addresses are 16-byte aligned (the device allocations are), then the 4-byte tail.
 __global__ void k_copy_words(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,

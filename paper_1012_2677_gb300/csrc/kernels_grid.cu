@@ -145,7 +145,7 @@ int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
 
 // ---------------------------------------------------------------------------------------------
 // Scatter (Fig. 3 (ii)-(iii)): place each particle at its cell's pointer and advance it.
-// The arrival order inside a cell is made deterministic afterwards by k_cell_order.
+// The arrival order inside a cell is made deterministic afterwards by k_cell_rank (ids ascending).
 // The lanes of a warp bound for one cell reserve their slots with one atomic.
 __global__ void k_scatter(const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ start,
                           uint32_t* __restrict__ fill, uint32_t* __restrict__ perm, int64_t N, const int* __restrict__ pred) {

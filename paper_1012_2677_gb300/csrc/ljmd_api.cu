@@ -816,8 +816,8 @@ static int finalize_energies_now(ljmd_sys* s) {
 
 // Up to `remaining` velocity-Verlet steps with the list-validity rule decided on the device: each
 // step is the kick-drift (with the first half-kick fused into the previous step's second, except
-// for the first step of the call), the energy record when due, the validity check (k_step_check)
-// and the force; all of them are enqueued at once and the host synchronises once at the end.  When
+// for the first step of the call), whose last CTA takes the energy record when due and the validity
+// check, and the force; all of them are enqueued at once and the host synchronises once at the end.  When
 // the check of a step finds the list expired it sets the stop flag, which every later launch of
 // the run reads first and returns on; that step's drift has happened but not its force.  The run
 // is sized from the lifetime of the last list, so that few launches are skipped.  *advanced: the

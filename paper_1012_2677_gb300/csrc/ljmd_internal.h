@@ -263,7 +263,6 @@ void launch_rebuild_flag(const uint32_t* dmax_bits, float limit2, int* flag, lon
 void launch_copy_words(const void* in, void* out, int64_t bytes, const int* pred, cudaStream_t s);
 void launch_zero_words(void* out, int64_t bytes, const int* pred, cudaStream_t s);
 void launch_replica_ke(const double* v, int64_t N, const ReplicaGeo* reps, int R, double* ke_rep, cudaStream_t s);
-void launch_set_flag(int* flag, int value, cudaStream_t s);
 void launch_load_batch(const double* xin, const double* vin, double* x, double* v, int32_t* id, int32_t* img,
                        int64_t N, const int32_t* rep_of, const ReplicaGeo* reps, double offset, cudaStream_t s);
 
